@@ -1,0 +1,363 @@
+"""Pins for the CPU oracle: each check compares it against something other
+than itself (LAPACK through numpy/scipy, closed forms, brute force,
+Proposition 2.1, and the robustness claims the paper prints for Fig. 1)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+from paper_2507_07788_gb300 import synth
+
+U = 2.0 ** -53
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_claims.json")))
+
+
+def rng(seed):
+    return np.random.default_rng(seed)
+
+
+# ---------------------------------------------------------------- primitives
+
+def test_gram_matches_lapack(orc):
+    A = rng(1).standard_normal((257, 13))
+    X = orc.gram(A)
+    ref = A.T @ A
+    assert np.allclose(X, X.T, rtol=0, atol=0)
+    assert np.max(np.abs(X - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+def test_gemm_tn_matches_lapack(orc):
+    A = rng(2).standard_normal((100, 7))
+    B = rng(3).standard_normal((100, 5))
+    assert np.allclose(orc.gemm_tn(A, B), A.T @ B, rtol=1e-13, atol=1e-13)
+
+
+def test_chol_matches_lapack_upper(orc):
+    G = rng(4).standard_normal((40, 9))
+    X = G.T @ G
+    R, rc = orc.chol(X)
+    assert rc == 0
+    L = np.linalg.cholesky(X)
+    assert np.allclose(R, L.T, rtol=1e-12, atol=1e-12)
+    assert np.all(np.tril(R, -1) == 0)
+    # shifted: chol(X + s I)
+    R2, rc2 = orc.chol(X, 0.5)
+    assert rc2 == 0
+    assert np.allclose(R2, np.linalg.cholesky(X + 0.5 * np.eye(9)).T, rtol=1e-12, atol=1e-12)
+
+
+def test_chol_breakdown_index(orc):
+    # third pivot is exactly zero: X = [[1,1,0],[1,1,0],[0,0,1]] -> d_2 = 1 - 1 = 0
+    X = np.array([[1.0, 1.0, 0.0], [1.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
+    _, rc = orc.chol(X)
+    assert rc == 2
+    # negative pivot in position 3
+    X = np.diag([2.0, 1.0, -1e-3])
+    _, rc = orc.chol(X)
+    assert rc == 3
+    # non-finite pivot
+    X = np.diag([1.0, np.nan])
+    _, rc = orc.chol(X)
+    assert rc == 2
+    # a shift repairs it
+    _, rc = orc.chol(np.diag([2.0, 1.0, -1e-3]), 2e-3)
+    assert rc == 0
+
+
+def test_trsm_matches_solve_triangular(orc):
+    A = rng(5).standard_normal((300, 11))
+    G = rng(6).standard_normal((20, 11))
+    R = np.linalg.cholesky(G.T @ G).T
+    Q = orc.trsm(A, R)
+    ref = sla.solve_triangular(R, A.T, trans="T", lower=False).T
+    assert np.max(np.abs(Q - ref)) <= 1e-12 * np.max(np.abs(ref))
+    # transposed-operand mistake would fail this: Q R must give back A
+    assert np.max(np.abs(Q @ R - A)) <= 1e-12 * np.max(np.abs(A))
+
+
+def test_trmm_upper(orc):
+    T = np.triu(rng(7).standard_normal((8, 8)))
+    R = np.triu(rng(8).standard_normal((8, 8)))
+    assert np.allclose(orc.trmm_upper(T, R), T @ R, rtol=1e-13, atol=1e-13)
+
+
+def test_jacobi_eigvals_and_norm(orc):
+    G = rng(9).standard_normal((12, 12))
+    S = G + G.T
+    w = orc.sym_eigvals(S)
+    ref = np.linalg.eigvalsh(S)
+    assert np.allclose(w, ref, rtol=0, atol=1e-12 * np.max(np.abs(ref)))
+    assert orc.sym_norm2(S) == pytest.approx(np.max(np.abs(ref)), rel=1e-13)
+    # spectral norm differs from Frobenius norm and from max |diagonal|
+    X = np.array([[1.0, 1.0, 0.0], [1.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
+    assert orc.sym_norm2(X) == pytest.approx(2.0, rel=1e-14)
+
+
+def test_frob_minus_identity(orc):
+    X = np.eye(4)
+    X[0, 1] = X[1, 0] = 3e-7
+    X[2, 2] = 1.0 + 4e-7
+    assert orc.frob_minus_identity(X) == pytest.approx(math.sqrt(2 * 9e-14 + 16e-14), rel=1e-12)
+
+
+# ---------------------------------------------------------------- shift formulas
+
+@pytest.mark.parametrize("m,n,normX", [(300, 10, 1.0), (20000, 20, 3.5), (10**6, 64, 1e-3)])
+def test_shift_closed_form(orc, m, n, normX):
+    c = GOLD["shift_constant"]["value"]
+    expect = max(c * (m * n + n * (n + 1)) * U * normX, GOLD["shift_floor_units_of_u"]["value"] * U)
+    assert orc.shift(m, n, normX) == pytest.approx(expect, rel=1e-15)
+
+
+def test_shift_floor(orc):
+    assert orc.shift(10, 2, 1e-30) == 2 * U
+    assert orc.shift(10, 2, 0.0) == 2 * U
+
+
+def test_update_shift_uses_basis_width(orc):
+    # Alg. 2 line 9 uses q, the width of the existing basis
+    assert orc.update_shift(1000, 5, 8, 2.0) == pytest.approx(11 * (1000 * 5 + 5 * 6) * U * 2.0, rel=1e-15)
+    # q = 0: falls back to Alg. 1 with the block width
+    assert orc.update_shift(1000, 0, 8, 2.0) == pytest.approx(orc.shift(1000, 8, 2.0), rel=0)
+
+
+def test_alg1_shift_on_breakdown_uses_spectral_norm(orc):
+    # columns a, a, b with a, b orthonormal: X = [[1,1,0],[1,1,0],[0,0,1]],
+    # ||X||_2 = 2, ||X||_F = sqrt(5), max diag = 1.  The unshifted Cholesky
+    # breaks down at pivot 2, so Alg. 1 lines 5-7 apply.
+    m = 64
+    A = np.zeros((m, 3))
+    A[0, 0] = A[0, 1] = 1.0
+    A[1, 2] = 1.0
+    Q, R, st, info = orc.cholqr(A, shift_policy=orc.SHIFT_ON_BREAKDOWN, max_iter=1, tol=0.0)
+    expect = 11 * (m * 3 + 3 * 4) * U * 2.0
+    assert info.shifts == 1 and info.escalations == 0
+    assert info.sigma_first == pytest.approx(expect, rel=1e-14)
+    assert info.chol_attempts == 2
+
+
+def test_update_shift_escalation_count(orc):
+    # Q_in = (1 + 2^-20) e_1 (slightly longer than a unit vector), A_in = [e_2, e_1]:
+    # B~ = [0, 1 + 2^-20], X = diag(1, 1 - (1 + 2^-20)^2) = diag(1, -(2^-19 + 2^-40)),
+    # exactly.  Alg. 2: sigma=0 fails, first shift 11 (m q + q (q+1)) u ||X|| with
+    # q = 1 and ||X|| = 1, then x10 until sigma > 2^-19 + 2^-40.
+    m = 100
+    Qin = np.zeros((m, 1))
+    Qin[0, 0] = 1.0 + 2.0 ** -20
+    A = np.zeros((m, 2))
+    A[1, 0] = 1.0
+    A[0, 1] = 1.0
+    _, _, _, st, info = orc.cholqr_update(Qin, A, max_iter=1, tol=0.0)
+    s1 = 11 * (m * 1 + 1 * 2) * U * 1.0
+    delta = 2.0 ** -19 + 2.0 ** -40
+    k = 0
+    while s1 * 10.0 ** k <= delta:
+        k += 1
+    assert info.shifts == 1
+    assert info.sigma_first == pytest.approx(s1, rel=1e-14)
+    assert info.escalations == k
+    assert info.chol_attempts == 1 + 1 + k
+    assert info.sigma_last == pytest.approx(s1 * 10.0 ** k, rel=1e-12)
+
+
+# ---------------------------------------------------------------- Householder checker
+
+def test_householder_matches_lapack(orc):
+    A = rng(10).standard_normal((50, 6))
+    Q, R = orc.householder_qr(A)
+    Qr, Rr = np.linalg.qr(A)
+    s = np.sign(np.diag(Rr))
+    Qr, Rr = Qr * s, (Rr.T * s).T
+    assert np.allclose(R, Rr, atol=1e-13)
+    assert np.allclose(Q, Qr, atol=1e-13)
+    assert np.all(np.diag(R) > 0)
+
+
+# ---------------------------------------------------------------- Alg. 1 family
+
+@pytest.mark.parametrize("policy", [0, 1])
+@pytest.mark.parametrize("m,n,kappa", [(12, 4, 10.0), (9, 3, 1e3), (40, 7, 1e5)])
+def test_cholqr_matches_householder_tiny(orc, policy, m, n, kappa):
+    A = synth.test_matrix(m, n, kappa, rep=1)
+    Q, R, st, info = orc.cholqr(A, shift_policy=policy)
+    assert st == orc.OK
+    Qh, Rh = orc.householder_qr(A)
+    tolR = 50 * kappa * U * np.max(np.abs(Rh))
+    assert np.max(np.abs(R - Rh)) <= tolR
+    assert np.max(np.abs(Q - Qh)) <= 50 * kappa * U
+    assert np.all(np.diag(R) > 0) and np.all(np.tril(R, -1) == 0)
+
+
+def test_cholqr_n1_closed_form(orc):
+    a = rng(11).standard_normal((37, 1))
+    Q, R, st, info = orc.cholqr(a, shift_policy=orc.SHIFT_ON_BREAKDOWN)
+    nrm = np.sqrt(np.sum(a * a))
+    assert R[0, 0] == pytest.approx(nrm, rel=4 * U)
+    assert np.allclose(Q, a / nrm, rtol=4 * U, atol=0)
+
+
+@pytest.mark.parametrize("policy", [0, 1])
+def test_orthonormal_input_is_untouched(orc, policy):
+    # X = I exactly: the loop of Alg. 1 is not entered, Q = A, R = I.
+    A = np.zeros((16, 4))
+    A[[0, 3, 5, 9], [0, 1, 2, 3]] = 1.0
+    Q, R, st, info = orc.cholqr(A, shift_policy=policy)
+    assert st == orc.OK and info.iters == 0
+    assert np.array_equal(Q, A) and np.array_equal(R, np.eye(4))
+
+
+def test_scaled_orthonormal_gives_diagonal_R(orc):
+    # A = U D: X = D^2 exactly diagonal, one unshifted pass gives R = D, Q = U.
+    Uo = synth.orthonormal(200, 5, seed=3)
+    d = np.array([3.0, 0.5, 2.0, 1.0, 0.25])
+    Q, R, st, info = orc.cholqr(Uo * d, shift_policy=orc.SHIFT_ON_BREAKDOWN)
+    assert st == orc.OK
+    assert np.allclose(R, np.diag(d), atol=1e-14)
+    assert np.allclose(Q, Uo, atol=1e-14)
+
+
+def test_scholqr3_shifts_first_pass_and_takes_three(orc):
+    A = synth.test_matrix(2000, 20, 1e12)
+    Q, R, st, info = orc.cholqr(A)
+    assert st == orc.OK
+    assert info.iters == 3
+    assert info.shifts == 1
+    X = orc.gram(A)
+    assert info.sigma_first == pytest.approx(orc.shift(2000, 20, orc.sym_norm2(X)), rel=1e-14)
+    assert orc.loo_frob(Q) <= 1e-13
+    assert orc.rrr(A, Q, R) <= 1e-13
+    assert np.all(np.diag(R) > 0) and np.all(np.tril(R, -1) == 0)
+
+
+def test_stop_rule_u_sqrt_n(orc):
+    A = synth.test_matrix(500, 6, 1e3)
+    _, _, st, info = orc.cholqr(A, stop_rule=orc.STOP_U_SQRT_N, max_iter=4)
+    # ||X - I||_F >= u sqrt(n) is rarely reached; the loop uses its budget
+    assert info.iters == 4 or info.orth_frob < U * math.sqrt(6)
+
+
+def _fig1_cases():
+    kappas = [10.0 ** e for e in range(0, 21)]
+    return [(k, rep) for k in kappas for rep in range(3)]
+
+
+def test_fig1_robustness_claims(orc):
+    """Sec. 4.2 / Fig. 1 at 300 x 10: CholQR2 breaks down above ~1e8, sCholQR3
+    holds to 1e15, rsCholQR stays below the red line up to 1e20."""
+    m, n = GOLD["fig1_shape"]["m"], GOLD["fig1_shape"]["n"]
+    red = GOLD["loo_red_line"]["value"]
+    tol = GOLD["stop_tol_frob"]["value"]
+    c2_fail_high = c2_high = s3_fail_high = s3_high = 0
+    for kappa, rep in _fig1_cases():
+        A = synth.test_matrix(m, n, kappa, rep=rep, salt=1)
+        # CholQR2: two unshifted passes
+        Q2, _, st2, _ = orc.cholqr(A, shift_policy=orc.SHIFT_NONE, max_iter=2, min_iter=2, tol=tol)
+        if kappa <= 1e6:
+            assert st2 >= 0 and orc.loo(Q2) < red
+        if kappa > GOLD["cholqr2_breaks_above_kappa"]["value"]:
+            c2_high += 1
+            # "usually fails to compute the Cholesky decomposition"
+            c2_fail_high += st2 == orc.ERR_BREAKDOWN
+            assert st2 == orc.ERR_BREAKDOWN or orc.loo(Q2) >= tol
+        # sCholQR3 (Fukaya): shifted pass + two unshifted passes, no re-shift
+        Q3, R3, st3, _ = orc.cholqr(A, shift_policy=orc.SHIFT_SCHOLQR3_STRICT, max_iter=3,
+                                    min_iter=3, tol=tol)
+        if kappa < GOLD["scholqr3_robust_to_kappa"]["value"]:
+            assert st3 >= 0 and orc.loo(Q3) < red, (kappa, rep)
+        if kappa >= 1e16:
+            s3_high += 1
+            s3_fail_high += st3 == orc.ERR_BREAKDOWN or orc.loo(Q3) >= red
+        # rsCholQR (Alg. 1) and the default sCholQR3-with-recomputation
+        for pol in (orc.SHIFT_ON_BREAKDOWN, orc.SHIFT_SCHOLQR3):
+            Q, R, st, info = orc.cholqr(A, shift_policy=pol, tol=tol,
+                                        max_iter=GOLD["max_iter"]["value"])
+            assert st == orc.OK, (kappa, rep, pol, info)
+            assert orc.loo(Q) < red, (kappa, rep, pol)
+            assert orc.rrr(A, Q, R) < 1e-13
+    assert c2_fail_high >= 0.9 * c2_high
+    assert s3_fail_high >= 0.9 * s3_high
+
+
+# ---------------------------------------------------------------- Alg. 2 / Proposition 2.1
+
+def test_update_matches_householder_of_concatenation(orc):
+    m, q, p = 400, 6, 4
+    A_prev = synth.test_matrix(m, q, 1e2, rep=2)
+    A_in = rng(12).standard_normal((m, p))
+    Qh, Rh = orc.householder_qr(np.hstack([A_prev, A_in]))
+    Qin, Rin = Qh[:, :q], Rh[:q, :q]
+    Q, B, R, st, info = orc.cholqr_update(Qin, A_in, min_iter=2)
+    assert st == orc.OK and info.iters >= 2
+    # R_out = [[R_in, B], [0, R]] is the unique R of [A_prev A_in]
+    assert np.allclose(B, Rh[:q, q:], atol=1e-12)
+    assert np.allclose(R, Rh[q:, q:], atol=1e-12)
+    assert np.allclose(Q, Qh[:, q:], atol=1e-12)
+    Qo = np.hstack([Qin, Q])
+    assert orc.loo(Qo) < 1e-13
+    Ro = np.block([[Rin, B], [np.zeros((p, q)), R]])
+    assert orc.rrr(np.hstack([A_prev, A_in]), Qo, Ro) < 1e-13
+
+
+def test_update_lucky_breakdown_column_in_span(orc):
+    # a column exactly in span(Q_in) makes X_ii = 0 (Sec. 2.2): breakdown, shift path
+    m, q, p = 300, 5, 3
+    Qin = synth.orthonormal(m, q, seed=5)
+    A_in = rng(13).standard_normal((m, p))
+    A_in[:, 1] = Qin @ np.array([1.0, -2.0, 0.5, 0.0, 3.0])
+    Q, B, R, st, info = orc.cholqr_update(Qin, A_in, min_iter=2)
+    assert info.shifts >= 1
+    assert st >= 0
+    Qo = np.hstack([Qin, Q])
+    assert orc.loo(Qo) < 1e-12
+    Ro = np.block([[np.eye(q), B], [np.zeros((p, q)), R]])
+    assert np.max(np.abs(Qo @ Ro - np.hstack([Qin, A_in]))) < 1e-12 * np.max(np.abs(A_in))
+
+
+def test_update_orthogonal_block_is_kept(orc):
+    # columns orthonormal and orthogonal to Q_in: X = I, no iteration needed,
+    # Q = A_in, B = 0, R = I (X_jj = c_j^T c_j = 1).
+    m = 64
+    Qin = np.zeros((m, 2))
+    Qin[0, 0] = Qin[1, 1] = 1.0
+    A = np.zeros((m, 3))
+    A[2, 0] = A[5, 1] = A[9, 2] = 1.0
+    Q, B, R, st, info = orc.cholqr_update(Qin, A)
+    assert st == orc.OK and info.iters == 0
+    assert np.array_equal(Q, A) and np.array_equal(B, np.zeros((2, 3))) and np.array_equal(R, np.eye(3))
+
+
+def test_update_first_panel_equals_factor(orc):
+    A = synth.test_matrix(500, 8, 1e4)
+    Q, B, R, st, info = orc.cholqr_update(None, A)
+    Qh, Rh = orc.householder_qr(A)
+    assert st == orc.OK
+    assert np.allclose(R, Rh, atol=1e-10 * np.max(np.abs(Rh)))
+
+
+# ---------------------------------------------------------------- Alg. 3
+
+@pytest.mark.parametrize("r", [1, 2, 3, 5])
+def test_pncholqr_matches_householder(orc, r):
+    A = synth.test_matrix(600, 15, 1e5, rep=r)
+    Q, R, st, info = orc.pncholqr(A, r)
+    assert st >= 0
+    Qh, Rh = orc.householder_qr(A)
+    assert np.max(np.abs(R - Rh)) <= 1e-9 * np.max(np.abs(Rh))
+    assert orc.loo(Q) < 1e-12
+    assert orc.rrr(A, Q, R) < 1e-13
+
+
+# ---------------------------------------------------------------- metrics
+
+def test_metrics_match_numpy(orc):
+    A = rng(14).standard_normal((80, 6))
+    Q, R = np.linalg.qr(A)
+    Q = Q + 1e-9 * rng(15).standard_normal(Q.shape)
+    R = R + 1e-9 * np.triu(rng(16).standard_normal(R.shape))
+    assert orc.loo(Q) == pytest.approx(np.linalg.norm(np.eye(6) - Q.T @ Q, 2), rel=1e-6)
+    assert orc.loo_frob(Q) == pytest.approx(np.linalg.norm(np.eye(6) - Q.T @ Q, "fro"), rel=1e-6)
+    assert orc.rrr(A, Q, R) == pytest.approx(np.linalg.norm(A - Q @ R, 2) / np.linalg.norm(A, 2), rel=1e-6)
+    assert orc.rcr(A, R) == pytest.approx(np.linalg.norm(A.T @ A - R.T @ R, 2) / np.linalg.norm(A, 2) ** 2, rel=1e-5)
