@@ -264,9 +264,12 @@ int orc_cholqr(const orc_opts *o, int64_t m, int64_t n, const double *A,
   /* line 3: X <- Q^T Q */
   orc_gram(m, n, Q, ldq, X, n);
   double orth = orc_frob_minus_identity(n, X, n);
+  /* A non-finite Gramian (NaN or Inf in A) leaves the loop test of line 4
+   * undefined; it cannot be factored, so it is reported as a breakdown. */
+  if (!isfinite(orth)) status = ORC_ERR_BREAKDOWN;
 
   int it = 0;
-  while ((orth >= tol || it < o->min_iter) && it < o->max_iter) {
+  while (status == ORC_OK && (orth >= tol || it < o->min_iter) && it < o->max_iter) {
     int first = (it == 0);
     double sigma = 0.0;
     int shifted_first = first && (o->shift_policy == ORC_SHIFT_SCHOLQR3 ||
@@ -328,6 +331,7 @@ int orc_cholqr(const orc_opts *o, int64_t m, int64_t n, const double *A,
     orc_gram(m, n, Q, ldq, X, n);
     orth = orc_frob_minus_identity(n, X, n);
     ++it;
+    if (!isfinite(orth)) status = ORC_ERR_BREAKDOWN;
   }
   inf.iters = it;
   inf.orth_frob = orth;
@@ -405,9 +409,10 @@ int orc_cholqr_update(const orc_opts *o, int64_t m, int64_t q,
   /* line 5: X <- Q^T Q - Bt^T Bt */
   update_gram(m, q, p, Q, ldq, Bt, X);
   double orth = orc_frob_minus_identity(p, X, p);
+  if (!isfinite(orth)) status = ORC_ERR_BREAKDOWN; /* as in orc_cholqr */
 
   int it = 0;
-  while ((orth >= tol || it < o->min_iter) && it < o->max_iter) {
+  while (status == ORC_OK && (orth >= tol || it < o->min_iter) && it < o->max_iter) {
     /* lines 7-11: shift loop */
     double sigma = 0.0;
     double normX = -1.0;
@@ -463,6 +468,7 @@ int orc_cholqr_update(const orc_opts *o, int64_t m, int64_t q,
     update_gram(m, q, p, Q, ldq, Bt, X);
     orth = orc_frob_minus_identity(p, X, p);
     ++it;
+    if (!isfinite(orth)) status = ORC_ERR_BREAKDOWN;
   }
   inf.iters = it;
   inf.orth_frob = orth;

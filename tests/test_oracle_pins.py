@@ -361,3 +361,19 @@ def test_metrics_match_numpy(orc):
     assert orc.loo_frob(Q) == pytest.approx(np.linalg.norm(np.eye(6) - Q.T @ Q, "fro"), rel=1e-6)
     assert orc.rrr(A, Q, R) == pytest.approx(np.linalg.norm(A - Q @ R, 2) / np.linalg.norm(A, 2), rel=1e-6)
     assert orc.rcr(A, R) == pytest.approx(np.linalg.norm(A.T @ A - R.T @ R, 2) / np.linalg.norm(A, 2) ** 2, rel=1e-5)
+
+
+def test_nonfinite_input_is_a_breakdown(orc):
+    A = synth.test_matrix(200, 5, 10.0)
+    A[17, 2] = np.nan
+    _, _, st, info = orc.cholqr(A)
+    assert st == orc.ERR_BREAKDOWN
+    A = synth.test_matrix(200, 5, 10.0)
+    A[3, 1] = np.inf
+    _, _, st, _ = orc.cholqr(A)
+    assert st == orc.ERR_BREAKDOWN
+    Qin = synth.orthonormal(200, 3, seed=1)
+    B = synth.gaussian(200, 2, seed=2)
+    B[4, 0] = np.nan
+    _, _, _, st, _ = orc.cholqr_update(Qin, B)
+    assert st == orc.ERR_BREAKDOWN
