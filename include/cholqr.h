@@ -1,0 +1,187 @@
+/*
+ * cholqr.h -- C ABI of libcholqr: shifted Cholesky QR (sCholQR3 with the
+ * recomputed shift) and the Cholesky-QR updating scheme on one GB300 GPU.
+ *
+ * Paper: M. Bindhak, A. J. R. Pelling, J. Saak, "Towards an Efficient Shifted
+ * Cholesky QR for Applications in Model Order Reduction using pyMOR",
+ * arXiv 2507.07788.
+ *
+ * Conventions for every entry point
+ *   - Matrices are FP64 and column-major: element (i, j) of M with leading
+ *     dimension ld is M[i + j*ld].  A "vector" of the paper is one column.
+ *   - Pointers named A, Q, R, A_in are DEVICE pointers (memory of the current
+ *     CUDA device) unless the function name ends in _host.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is queued on it; each call synchronises that stream once
+ *     at its end to read the status and fill `info`, so on return the outputs
+ *     are complete.
+ *   - The library allocates its own scratch memory stream-ordered
+ *     (cudaMallocAsync on `stream`) and frees it before returning; basis
+ *     handles own their storage until basis_free.
+ *   - Errors are reported by the return value; no function aborts the
+ *     process.  On an error return (< 0) output buffers hold unspecified data,
+ *     except where stated.
+ *   - Calls on different streams may run concurrently; calls sharing a basis
+ *     handle must be serialised by the caller.
+ */
+#ifndef CHOLQR_H
+#define CHOLQR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes.  CQR_NOT_CONVERGED still returns a valid factorisation
+ * (Q R = A to working accuracy) whose orthogonality did not reach `tol`
+ * within `max_iter` passes (the paper caps iterations at 10, Sec. 4.1). */
+typedef enum cqr_status {
+  CQR_OK = 0,
+  CQR_NOT_CONVERGED = 1,
+  CQR_ERR_INVALID = -1,   /* bad argument (sizes, leading dims, NULL, opts) */
+  CQR_ERR_BREAKDOWN = -2, /* Cholesky failed after every permitted shift */
+  CQR_ERR_OOM = -3,       /* device allocation failed */
+  CQR_ERR_CAPACITY = -4,  /* basis_append: q + p > n_max */
+  CQR_ERR_CUDA = -5,      /* a CUDA runtime call or launch failed */
+  CQR_ERR_TIMEOUT = -6    /* reserved for waits that give up */
+} cqr_status;
+
+/* Shift policy of the factorisation (Alg. 1, Sec. 2.1, and Sec. 4.1 item 2):
+ *   CQR_SHIFT_SCHOLQR3      first pass always shifted (sCholQR3), later
+ *                           passes unshifted; a later breakdown recomputes
+ *                           the shift from the current Gramian (Alg. 1
+ *                           lines 5-7).  Default.
+ *   CQR_SHIFT_ON_BREAKDOWN  Alg. 1 exactly as printed.
+ *   CQR_SHIFT_NONE          no shift at all (CholQR / CholQR2); a breakdown
+ *                           returns CQR_ERR_BREAKDOWN. */
+enum { CQR_SHIFT_SCHOLQR3 = 0, CQR_SHIFT_ON_BREAKDOWN = 1, CQR_SHIFT_NONE = 2 };
+
+/* Stopping rule: ||X - I||_F < tol (Sec. 4.1, default tol = 1e-13), or the
+ * literal u*sqrt(n) of Alg. 1 line 4 / Alg. 2 line 6. */
+enum { CQR_STOP_FROB_TOL = 0, CQR_STOP_U_SQRT_N = 1 };
+
+/* Arithmetic of the row-sweeping kernels.  CQR_PREC_FP64: every step in FP64.
+ * CQR_PREC_MIXED: the Gramian of the first (shifted) pass is formed from
+ * inputs rounded to FP32 with FP32 products, the shift is sized for that
+ * roundoff; everything else stays FP64. */
+enum { CQR_PREC_FP64 = 0, CQR_PREC_MIXED = 1 };
+
+typedef struct cqr_opts {
+  double tol;              /* stop when ||X - I||_F < tol            (1e-13) */
+  int32_t max_iter;        /* passes / outer iterations cap              (10) */
+  int32_t min_iter;        /* minimum passes of cholqr_factor             (0) */
+  int32_t update_min_iter; /* minimum outer iterations of basis_append:
+                              2 = the projection is applied twice       (2) */
+  int32_t precision;       /* CQR_PREC_*                         (FP64) */
+  int32_t shift_policy;    /* CQR_SHIFT_*                    (SCHOLQR3) */
+  int32_t stop_rule;       /* CQR_STOP_*                     (FROB_TOL) */
+  int32_t max_escalations; /* cap on x10 shift escalations           (40) */
+  int32_t reserved;
+} cqr_opts;
+
+/* Per-call report.  orth_frob is ||X - I||_F of the last Gramian formed
+ * (for basis_append: of the projected Gramian Q^T Q - B~^T B~), proj_frob is
+ * ||B~||_F = ||Q_in^T Q||_F after the last iteration (0 for factor). */
+typedef struct cqr_info {
+  int32_t iters;         /* passes (factor) or outer iterations (append) */
+  int32_t chol_attempts; /* Cholesky factorisations attempted */
+  int32_t shifts;        /* shifts computed from ||X|| */
+  int32_t escalations;   /* x10 shift escalations */
+  double sigma_first;    /* first shift applied (0 if none) */
+  double sigma_last;     /* last shift applied (0 if none) */
+  double orth_frob;
+  double proj_frob;
+} cqr_info;
+
+/* Largest Gramian width handled by the kernels: n of cholqr_factor and p of
+ * basis_append must not exceed it.  Basis capacity (q + p) up to
+ * CQR_MAX_BASIS. */
+#define CQR_MAX_N 128
+#define CQR_MAX_BASIS 1024
+
+/* Fills *o with the defaults listed above.  o must not be NULL. */
+void cqr_default_opts(cqr_opts *o);
+
+/* Static string naming a status code (never NULL). */
+const char *cqr_status_string(int status);
+
+/*
+ * cholqr_factor -- QR factorisation A = Q R of a tall-skinny m x n block by
+ * iterated shifted Cholesky QR: Alg. 1 (rsCholQR, Sec. 2.1) with the shift of
+ * Alg. 1 line 6, sigma = max{11 (m n + n (n+1)) u ||X||, 2u}, and the
+ * sCholQR3 first-pass shift named in Sec. 4.1 (opts->shift_policy).
+ *
+ *   opts      host pointer, may be NULL (defaults).
+ *   m, n      1 <= n <= CQR_MAX_N, m >= n.
+ *   A, lda    device, m x n input, lda >= m.  Read only, unless it aliases Q.
+ *   Q, ldq    device, m x n output, ldq >= m.  Q may be A (in place) when
+ *             ldq == lda; otherwise the two must not overlap.
+ *   R, ldr    device, n x n output, ldr >= n; upper triangular with positive
+ *             diagonal, zeros below it.
+ *   info      host pointer, may be NULL.
+ *   stream    cudaStream_t as void*.
+ * Returns CQR_OK, CQR_NOT_CONVERGED (valid Q, R), or an error code.
+ */
+cqr_status cholqr_factor(const cqr_opts *opts, int64_t m, int64_t n, const double *A,
+                         int64_t lda, double *Q, int64_t ldq, double *R, int64_t ldr,
+                         cqr_info *info, void *stream);
+
+/*
+ * cholqr_factor_host -- the same factorisation on HOST buffers: copies A to
+ * the device, factors it there with cholqr_factor and copies Q and R back.
+ * A, Q, R are host pointers (pinned memory gives full copy bandwidth); the
+ * device copies are stream-ordered scratch freed before return.
+ */
+cqr_status cholqr_factor_host(const cqr_opts *opts, int64_t m, int64_t n, const double *A,
+                              int64_t lda, double *Q, int64_t ldq, double *R, int64_t ldr,
+                              cqr_info *info, void *stream);
+
+/* Opaque growing orthonormal basis (Q_in m x q, R_in q x q) of Sec. 2.2. */
+typedef struct cqr_basis cqr_basis;
+
+/*
+ * basis_create -- allocate an empty basis (q = 0) for vectors of length m
+ * with room for n_max columns: device Q (m x n_max, leading dimension m
+ * rounded up to even) and R (n_max x n_max), both owned by the handle.
+ *   1 <= n_max <= CQR_MAX_BASIS, m >= 1.  opts may be NULL (defaults); it is
+ *   copied.  *out receives the handle (NULL on error).
+ */
+cqr_status basis_create(int64_t m, int64_t n_max, const cqr_opts *opts, void *stream,
+                        cqr_basis **out);
+
+/*
+ * basis_append -- the Cholesky-QR update, Alg. 2 (cholQRUpdate, Sec. 2.2):
+ * given the basis Q_in R_in = A_prev (m x q) and new columns A_in (m x p),
+ * extend it to [Q_in Q] and [[R_in, B], [0, R]] with
+ * [Q_in Q][[R_in, B], [0, R]] = [A_prev A_in] (Proposition 2.1).  The shift
+ * loop is Alg. 2 lines 7-11: sigma starts at 0, then
+ * 11 (m q + q (q+1)) u ||X|| (Alg. 1's formula with p when q = 0), then x10,
+ * floored at 2u.  At least opts->update_min_iter outer iterations are made.
+ *   p         1 <= p <= CQR_MAX_N, q + p <= n_max (else CQR_ERR_CAPACITY).
+ *   A_in, lda device, m x p, lda >= m, read only and caller-owned; it must not
+ *             overlap the basis storage.
+ * On CQR_OK / CQR_NOT_CONVERGED the basis grows by p columns; on an error the
+ * basis keeps its previous q columns and R_in unchanged.
+ */
+cqr_status basis_append(cqr_basis *b, int64_t p, const double *A_in, int64_t lda,
+                        cqr_info *info, void *stream);
+
+/* basis_free -- release the handle and its device storage (NULL is a no-op).
+ * The caller must make sure no queued work still uses the basis. */
+cqr_status basis_free(cqr_basis *b);
+
+/* Accessors.  basis_q / basis_r return DEVICE pointers owned by the basis
+ * (valid until basis_free) and the leading dimension.  Q has basis_cols(b)
+ * valid columns; R is upper triangular in its leading q x q block. */
+int64_t basis_cols(const cqr_basis *b);
+int64_t basis_rows(const cqr_basis *b);
+int64_t basis_capacity(const cqr_basis *b);
+cqr_status basis_q(const cqr_basis *b, const double **Q, int64_t *ldq);
+cqr_status basis_r(const cqr_basis *b, const double **R, int64_t *ldr);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CHOLQR_H */

@@ -1,0 +1,470 @@
+// C ABI of libcholqr: argument checking, scratch management and the launch
+// sequence of a factorisation (Alg. 1 with the sCholQR3 first-pass shift) and
+// of a basis update (Alg. 2).
+//
+// Launch sequence of one call (all on the caller's stream, no host round
+// trip until the end):
+//   init                      R = I (and B = 0), device state cleared
+//   sweep (Gram)              partial sums of [Q_in Y]^T Y, Y = A or A_in
+//   reduce, ctrl              X, stop test, shift, Cholesky, R~, R <- R~ R
+//   repeat: sweep (solve+Gram), reduce, ctrl
+// The row sweeps and reductions return immediately once the control kernel
+// has marked the call done, so launching a few passes ahead is harmless.  The
+// host reads the 64-byte device state once after `kPrelaunch` passes and
+// only launches further passes (one at a time) when the tolerance has not
+// been met yet.
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "cqr_internal.cuh"
+
+using namespace cqr;
+
+struct cqr_basis {
+  int device;
+  int64_t m, n_max, q, ldq, ldr;
+  double *Q;
+  double *R;
+  cqr_opts opts;
+};
+
+namespace {
+
+constexpr int kPrelaunch = 3;
+
+cqr_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return CQR_OK;
+  if (e == cudaErrorMemoryAllocation) return CQR_ERR_OOM;
+  return CQR_ERR_CUDA;
+}
+
+#define CQR_TRY(expr)                                   \
+  do {                                                  \
+    cudaError_t _e = (expr);                            \
+    if (_e != cudaSuccess) {                            \
+      (void)cudaGetLastError();                         \
+      return cuda_status(_e);                           \
+    }                                                   \
+  } while (0)
+
+bool opts_valid(const cqr_opts &o) {
+  return o.tol >= 0.0 && o.max_iter >= 1 && o.max_iter <= 100 && o.min_iter >= 0 &&
+         o.update_min_iter >= 0 && o.max_escalations >= 0 && o.max_escalations <= 400 &&
+         (o.precision == CQR_PREC_FP64 || o.precision == CQR_PREC_MIXED) &&
+         o.shift_policy >= CQR_SHIFT_SCHOLQR3 && o.shift_policy <= CQR_SHIFT_NONE &&
+         (o.stop_rule == CQR_STOP_FROB_TOL || o.stop_rule == CQR_STOP_U_SQRT_N);
+}
+
+// Pinned host mirror of the device state, one per host thread.
+DevState *host_state() {
+  thread_local DevState *h = nullptr;
+  if (h == nullptr) {
+    if (cudaMallocHost((void **)&h, sizeof(DevState)) != cudaSuccess) {
+      (void)cudaGetLastError();
+      h = nullptr;
+    }
+  }
+  return h;
+}
+
+void keep_pool_memory() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    (void)cudaGetLastError();
+  });
+}
+
+// Scratch of one call: device state, reduced C, R~, 1/diag R~, B~, partials.
+struct Scratch {
+  char *base = nullptr;
+  DevState *st;
+  double *C, *Rt, *Rdinv, *Bt, *partials;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+cudaError_t scratch_alloc(Scratch &s, int q, int p, int G, int64_t E, cudaStream_t str) {
+  const size_t b_st = align256(sizeof(DevState));
+  const size_t b_C = align256(sizeof(double) * (size_t)(q + p) * p);
+  const size_t b_Rt = align256(sizeof(double) * (size_t)p * p);
+  const size_t b_Rd = align256(sizeof(double) * (size_t)p);
+  const size_t b_Bt = align256(sizeof(double) * (size_t)std::max(q, 1) * p);
+  const size_t b_P = align256(sizeof(double) * (size_t)G * (size_t)E);
+  keep_pool_memory();
+  cudaError_t e = cudaMallocAsync((void **)&s.base, b_st + b_C + b_Rt + b_Rd + b_Bt + b_P, str);
+  if (e != cudaSuccess) return e;
+  char *p0 = s.base;
+  s.st = (DevState *)p0;
+  p0 += b_st;
+  s.C = (double *)p0;
+  p0 += b_C;
+  s.Rt = (double *)p0;
+  p0 += b_Rt;
+  s.Rdinv = (double *)p0;
+  p0 += b_Rd;
+  s.Bt = (double *)p0;
+  p0 += b_Bt;
+  s.partials = (double *)p0;
+  return cudaSuccess;
+}
+
+// The iteration driver shared by factor (q = 0) and append (q > 0).
+struct Problem {
+  int64_t m;
+  int q, p;
+  const double *Qin;
+  int64_t ldqin;
+  const double *Y0;  // input block (A or A_in)
+  int64_t ldy0;
+  double *Y;         // output block (Q or the basis columns q .. q+p-1)
+  int64_t ldy;
+  double *R;         // p x p block, ld ldr
+  int64_t ldr;
+  double *B;         // q x p block, ld ldb (nullptr when q == 0)
+  int64_t ldb;
+  int mode;
+  int min_iter;
+  cqr_opts o;
+};
+
+cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
+  const int q = P.q, p = P.p;
+  int tile_rows, lds;
+  size_t smem;
+  rowsweep_geometry(q, p, &tile_rows, &lds, &smem);
+  const int G = rowsweep_grid(P.m, tile_rows);
+  const int64_t tiles = (P.m + tile_rows - 1) / tile_rows;
+  const int64_t rows_per_cta = ((tiles + G - 1) / G) * tile_rows;
+  const int64_t E = (int64_t)q * p + (int64_t)p * (p + 1) / 2;
+  const bool split = E > (int64_t)kThreads * 33;  // fused solve+Gram needs one entry group
+
+  Scratch s;
+  CQR_TRY(scratch_alloc(s, q, p, G, E, str));
+  DevState *hs = host_state();
+  cqr_status result = CQR_OK;
+
+  auto sweep = [&](bool trsm, bool first) -> cudaError_t {
+    RowSweep a{};
+    a.m = P.m;
+    a.q = q;
+    a.p = p;
+    a.Qin = P.Qin;
+    a.ldqin = P.ldqin;
+    a.Yin = first ? P.Y0 : P.Y;
+    a.ldyin = first ? P.ldy0 : P.ldy;
+    a.Yout = P.Y;
+    a.ldyout = P.ldy;
+    a.Rt = s.Rt;
+    a.Rdinv = s.Rdinv;
+    a.Bt = s.Bt;
+    a.partials = s.partials;
+    a.E = E;
+    a.rows_per_cta = rows_per_cta;
+    a.tile_rows = tile_rows;
+    a.lds = lds;
+    a.do_trsm = trsm ? 1 : 0;
+    a.st = s.st;
+    if (trsm && split) {
+      // transform only, then a separate Gram sweep over the result
+      RowSweep t = a;
+      t.E = 0;
+      cudaError_t e = launch_rowsweep(t, G, str);
+      if (e != cudaSuccess) return e;
+      a.do_trsm = 0;
+      a.Yin = P.Y;
+      a.ldyin = P.ldy;
+    }
+    return launch_rowsweep(a, G, str);
+  };
+  auto reduce = [&]() -> cudaError_t {
+    Reduce r{s.partials, G, E, q, p, s.C, s.st};
+    return launch_reduce(r, str);
+  };
+  auto ctrl = [&]() -> cudaError_t {
+    Ctrl c{};
+    c.m = P.m;
+    c.q = q;
+    c.p = p;
+    c.mode = P.mode;
+    c.shift_policy = P.o.shift_policy;
+    c.max_iter = P.o.max_iter;
+    c.min_iter = P.min_iter;
+    c.max_escalations = P.o.max_escalations;
+    c.stop_rule = P.o.stop_rule;
+    c.tol = P.o.tol;
+    c.C = s.C;
+    c.Rt = s.Rt;
+    c.Rdinv = s.Rdinv;
+    c.Bt = s.Bt;
+    c.R = P.R;
+    c.ldr = P.ldr;
+    c.B = P.B;
+    c.ldb = P.ldb;
+    c.st = s.st;
+    return launch_ctrl(c, str);
+  };
+  auto pass = [&](bool first) -> cudaError_t {
+    cudaError_t e = sweep(true, first);
+    if (e == cudaSuccess) e = reduce();
+    if (e == cudaSuccess) e = ctrl();
+    return e;
+  };
+
+  cudaError_t e = launch_init(P.R, P.ldr, p, P.B, P.ldb, q, s.st, str);
+  if (e == cudaSuccess) e = sweep(false, true);
+  if (e == cudaSuccess) e = reduce();
+  if (e == cudaSuccess) e = ctrl();
+  int launched = 0;
+  for (; e == cudaSuccess && launched < std::min(kPrelaunch, P.o.max_iter); ++launched)
+    e = pass(launched == 0);
+  while (e == cudaSuccess) {
+    e = cudaMemcpyAsync(hs, s.st, sizeof(DevState), cudaMemcpyDeviceToHost, str);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(str);
+    if (e != cudaSuccess || hs->done || launched >= P.o.max_iter) break;
+    e = pass(launched == 0);
+    ++launched;
+  }
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    cudaFreeAsync(s.base, str);
+    return cuda_status(e);
+  }
+  if (!hs->done) {
+    result = CQR_ERR_CUDA;  // the control kernel never concluded (cannot happen)
+  } else {
+    result = (cqr_status)hs->status;
+    if (hs->iters == 0 && P.Y != P.Y0) {
+      // loop not entered (X = I): Q = A (Alg. 1 line 1 / Alg. 2 line 1)
+      e = cudaMemcpy2DAsync(P.Y, sizeof(double) * P.ldy, P.Y0, sizeof(double) * P.ldy0,
+                            sizeof(double) * P.m, p, cudaMemcpyDeviceToDevice, str);
+    }
+  }
+  if (info != nullptr) {
+    info->iters = hs->iters;
+    info->chol_attempts = hs->chol_attempts;
+    info->shifts = hs->shifts;
+    info->escalations = hs->escalations;
+    info->sigma_first = hs->sigma_first;
+    info->sigma_last = hs->sigma_last;
+    info->orth_frob = hs->orth_frob;
+    info->proj_frob = hs->proj_frob;
+  }
+  cudaError_t ef = cudaFreeAsync(s.base, str);
+  if (e == cudaSuccess) e = ef;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(str);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return cuda_status(e);
+  }
+  return result;
+}
+
+}  // namespace
+
+extern "C" {
+
+void cqr_default_opts(cqr_opts *o) {
+  if (o == nullptr) return;
+  o->tol = 1e-13;
+  o->max_iter = 10;
+  o->min_iter = 0;
+  o->update_min_iter = 2;
+  o->precision = CQR_PREC_FP64;
+  o->shift_policy = CQR_SHIFT_SCHOLQR3;
+  o->stop_rule = CQR_STOP_FROB_TOL;
+  o->max_escalations = 40;
+  o->reserved = 0;
+}
+
+const char *cqr_status_string(int status) {
+  switch (status) {
+    case CQR_OK: return "ok";
+    case CQR_NOT_CONVERGED: return "not converged within max_iter";
+    case CQR_ERR_INVALID: return "invalid argument";
+    case CQR_ERR_BREAKDOWN: return "Cholesky breakdown after all permitted shifts";
+    case CQR_ERR_OOM: return "device out of memory";
+    case CQR_ERR_CAPACITY: return "basis capacity exceeded";
+    case CQR_ERR_CUDA: return "CUDA error";
+    case CQR_ERR_TIMEOUT: return "timeout";
+    default: return "unknown status";
+  }
+}
+
+cqr_status cholqr_factor(const cqr_opts *opts, int64_t m, int64_t n, const double *A,
+                         int64_t lda, double *Q, int64_t ldq, double *R, int64_t ldr,
+                         cqr_info *info, void *stream) {
+  cqr_opts o;
+  cqr_default_opts(&o);
+  if (opts != nullptr) o = *opts;
+  if (!opts_valid(o)) return CQR_ERR_INVALID;
+  if (n < 1 || n > CQR_MAX_N || m < n || lda < m || ldq < m || ldr < n) return CQR_ERR_INVALID;
+  if (A == nullptr || Q == nullptr || R == nullptr) return CQR_ERR_INVALID;
+  if (A == Q && lda != ldq) return CQR_ERR_INVALID;
+  if (A != Q) {
+    const char *a0 = (const char *)A, *a1 = (const char *)(A + lda * (n - 1) + m);
+    const char *q0 = (const char *)Q, *q1 = (const char *)(Q + ldq * (n - 1) + m);
+    if (a0 < q1 && q0 < a1) return CQR_ERR_INVALID;
+  }
+  if (host_state() == nullptr) return CQR_ERR_CUDA;
+  Problem P{};
+  P.m = m;
+  P.q = 0;
+  P.p = (int)n;
+  P.Qin = nullptr;
+  P.ldqin = 1;
+  P.Y0 = A;
+  P.ldy0 = lda;
+  P.Y = Q;
+  P.ldy = ldq;
+  P.R = R;
+  P.ldr = ldr;
+  P.B = nullptr;
+  P.ldb = 1;
+  P.mode = MODE_FACTOR;
+  P.min_iter = o.min_iter;
+  P.o = o;
+  return run(P, info, (cudaStream_t)stream);
+}
+
+cqr_status cholqr_factor_host(const cqr_opts *opts, int64_t m, int64_t n, const double *A,
+                              int64_t lda, double *Q, int64_t ldq, double *R, int64_t ldr,
+                              cqr_info *info, void *stream) {
+  if (n < 1 || n > CQR_MAX_N || m < n || lda < m || ldq < m || ldr < n) return CQR_ERR_INVALID;
+  if (A == nullptr || Q == nullptr || R == nullptr) return CQR_ERR_INVALID;
+  cudaStream_t str = (cudaStream_t)stream;
+  keep_pool_memory();
+  double *dA = nullptr, *dR = nullptr;
+  const int64_t ldd = m;
+  CQR_TRY(cudaMallocAsync((void **)&dA, sizeof(double) * (size_t)m * n, str));
+  cudaError_t e = cudaMallocAsync((void **)&dR, sizeof(double) * (size_t)n * n, str);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(dA, str);
+    return cuda_status(e);
+  }
+  e = cudaMemcpy2DAsync(dA, sizeof(double) * ldd, A, sizeof(double) * lda, sizeof(double) * m, n,
+                        cudaMemcpyHostToDevice, str);
+  cqr_status st = CQR_ERR_CUDA;
+  if (e == cudaSuccess) st = cholqr_factor(opts, m, n, dA, ldd, dA, ldd, dR, n, info, stream);
+  if (st >= 0) {
+    e = cudaMemcpy2DAsync(Q, sizeof(double) * ldq, dA, sizeof(double) * ldd, sizeof(double) * m, n,
+                          cudaMemcpyDeviceToHost, str);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(R, sizeof(double) * ldr, dR, sizeof(double) * n, sizeof(double) * n, n,
+                            cudaMemcpyDeviceToHost, str);
+    if (e != cudaSuccess) st = cuda_status(e);
+  }
+  cudaFreeAsync(dA, str);
+  cudaFreeAsync(dR, str);
+  e = cudaStreamSynchronize(str);
+  if (e != cudaSuccess && st >= 0) st = cuda_status(e);
+  (void)cudaGetLastError();
+  return st;
+}
+
+cqr_status basis_create(int64_t m, int64_t n_max, const cqr_opts *opts, void *stream,
+                        cqr_basis **out) {
+  if (out == nullptr) return CQR_ERR_INVALID;
+  *out = nullptr;
+  cqr_opts o;
+  cqr_default_opts(&o);
+  if (opts != nullptr) o = *opts;
+  if (!opts_valid(o)) return CQR_ERR_INVALID;
+  if (m < 1 || n_max < 1 || n_max > CQR_MAX_BASIS) return CQR_ERR_INVALID;
+  cqr_basis *b = (cqr_basis *)calloc(1, sizeof(cqr_basis));
+  if (b == nullptr) return CQR_ERR_OOM;
+  cudaGetDevice(&b->device);
+  b->m = m;
+  b->n_max = n_max;
+  b->q = 0;
+  b->ldq = (m + 1) & ~(int64_t)1;
+  b->ldr = n_max;
+  b->opts = o;
+  cudaError_t e = cudaMalloc((void **)&b->Q, sizeof(double) * (size_t)b->ldq * n_max);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&b->R, sizeof(double) * (size_t)n_max * n_max);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(b->R, 0, sizeof(double) * (size_t)n_max * n_max, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    if (b->Q) cudaFree(b->Q);
+    if (b->R) cudaFree(b->R);
+    free(b);
+    return cuda_status(e);
+  }
+  *out = b;
+  return CQR_OK;
+}
+
+cqr_status basis_append(cqr_basis *b, int64_t p, const double *A_in, int64_t lda,
+                        cqr_info *info, void *stream) {
+  if (b == nullptr || A_in == nullptr) return CQR_ERR_INVALID;
+  if (p < 1 || p > CQR_MAX_N || lda < b->m) return CQR_ERR_INVALID;
+  if (b->q + p > b->n_max) return CQR_ERR_CAPACITY;
+  {
+    const char *a0 = (const char *)A_in, *a1 = (const char *)(A_in + lda * (p - 1) + b->m);
+    const char *q0 = (const char *)b->Q, *q1 = (const char *)(b->Q + b->ldq * b->n_max);
+    if (a0 < q1 && q0 < a1) return CQR_ERR_INVALID;
+  }
+  if (host_state() == nullptr) return CQR_ERR_CUDA;
+  const int64_t q = b->q;
+  Problem P{};
+  P.m = b->m;
+  P.q = (int)q;
+  P.p = (int)p;
+  P.Qin = b->Q;
+  P.ldqin = b->ldq;
+  P.Y0 = A_in;
+  P.ldy0 = lda;
+  P.Y = b->Q + q * b->ldq;
+  P.ldy = b->ldq;
+  P.R = b->R + q + q * b->ldr;
+  P.ldr = b->ldr;
+  P.B = (q > 0) ? b->R + q * b->ldr : nullptr;
+  P.ldb = b->ldr;
+  P.mode = MODE_UPDATE;
+  P.min_iter = b->opts.update_min_iter;
+  P.o = b->opts;
+  cqr_status st = run(P, info, (cudaStream_t)stream);
+  if (st == CQR_OK || st == CQR_NOT_CONVERGED) b->q = q + p;
+  return st;
+}
+
+cqr_status basis_free(cqr_basis *b) {
+  if (b == nullptr) return CQR_OK;
+  cudaError_t e1 = cudaFree(b->Q);
+  cudaError_t e2 = cudaFree(b->R);
+  free(b);
+  if (e1 != cudaSuccess) return cuda_status(e1);
+  return cuda_status(e2);
+}
+
+int64_t basis_cols(const cqr_basis *b) { return b ? b->q : -1; }
+int64_t basis_rows(const cqr_basis *b) { return b ? b->m : -1; }
+int64_t basis_capacity(const cqr_basis *b) { return b ? b->n_max : -1; }
+
+cqr_status basis_q(const cqr_basis *b, const double **Q, int64_t *ldq) {
+  if (b == nullptr || Q == nullptr || ldq == nullptr) return CQR_ERR_INVALID;
+  *Q = b->Q;
+  *ldq = b->ldq;
+  return CQR_OK;
+}
+
+cqr_status basis_r(const cqr_basis *b, const double **R, int64_t *ldr) {
+  if (b == nullptr || R == nullptr || ldr == nullptr) return CQR_ERR_INVALID;
+  *R = b->R;
+  *ldr = b->ldr;
+  return CQR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,101 @@
+// Internal declarations shared by the translation units of libcholqr.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cholqr.h"
+
+namespace cqr {
+
+constexpr double kU64 = 1.1102230246251565404236316680908203125e-16;  // 2^-53
+constexpr int kThreads = 256;        // block size of the row-sweeping kernels
+constexpr int kCtrlThreads = 512;    // block size of the single-CTA control kernel
+
+// Device-resident status of one factorisation / append, written by the
+// control kernel and read by the host once per call (and by every
+// row-sweeping kernel, which returns at once when `done` is set).
+struct DevState {
+  int32_t done;
+  int32_t status;
+  int32_t iters;
+  int32_t chol_attempts;
+  int32_t shifts;
+  int32_t escalations;
+  int32_t active;  // the control kernel asked for another row pass
+  int32_t pad;
+  double sigma_first;
+  double sigma_last;
+  double orth_frob;
+  double proj_frob;
+};
+
+// One sweep over the m rows.  The block being orthogonalised is Y (m x p);
+// Q_in (m x q, q may be 0) is the fixed basis of an update.  With do_trsm the
+// sweep first replaces each row y by (y - q_in B~) R~^{-1} (Alg. 1 line 9,
+// Alg. 2 line 12) and writes it to Yout; in every case it accumulates the
+// per-CTA partial sums of C = [Q_in Y]^T Y restricted to the B~ part
+// (q x p) and the upper triangle of Y^T Y, in a fixed row order.
+struct RowSweep {
+  int64_t m;
+  int32_t q, p;
+  const double *Qin;
+  int64_t ldqin;
+  const double *Yin;
+  int64_t ldyin;
+  double *Yout;
+  int64_t ldyout;
+  const double *Rt;     // p x p upper (ld p): R~ of the current pass
+  const double *Rdinv;  // p: 1 / R~_jj
+  const double *Bt;     // q x p (ld q): B~ of the current iteration
+  double *partials;     // [grid][E]
+  int64_t E;            // q p + p (p + 1) / 2
+  int64_t rows_per_cta; // multiple of tile_rows
+  int32_t tile_rows;
+  int32_t lds;          // shared-memory row stride (doubles), odd
+  int32_t do_trsm;
+  const DevState *st;
+};
+
+struct Reduce {
+  const double *partials;
+  int32_t G;
+  int64_t E;
+  int32_t q, p;
+  double *C;  // (q + p) x p, ld q + p
+  const DevState *st;
+};
+
+enum { MODE_FACTOR = 0, MODE_UPDATE = 1 };
+
+struct Ctrl {
+  int64_t m;
+  int32_t q, p;
+  int32_t mode;
+  int32_t shift_policy, max_iter, min_iter, max_escalations, stop_rule;
+  double tol;
+  const double *C;  // (q + p) x p, ld q + p
+  double *Rt;       // p x p, ld p
+  double *Rdinv;    // p
+  double *Bt;       // q x p, ld q (update only)
+  double *R;        // accumulated R (p x p block), ld ldr
+  int64_t ldr;
+  double *B;        // accumulated B (q x p block), ld ldb (update only)
+  int64_t ldb;
+  DevState *st;
+};
+
+// Launchers (return cudaGetLastError() of the launch).
+cudaError_t launch_init(double *R, int64_t ldr, int p, double *B, int64_t ldb, int q,
+                        DevState *st, cudaStream_t s);
+cudaError_t launch_rowsweep(const RowSweep &a, int grid, cudaStream_t s);
+cudaError_t launch_reduce(const Reduce &a, cudaStream_t s);
+cudaError_t launch_ctrl(const Ctrl &a, cudaStream_t s);
+size_t ctrl_smem_bytes(int p);
+
+// Geometry of a row sweep for the given widths: tile rows, shared stride and
+// bytes of dynamic shared memory.
+void rowsweep_geometry(int q, int p, int *tile_rows, int *lds, size_t *smem);
+int rowsweep_grid(int64_t m, int tile_rows);
+int num_sms();
+
+}  // namespace cqr

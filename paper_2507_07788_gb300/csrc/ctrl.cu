@@ -1,0 +1,360 @@
+// Single-CTA control kernel: the small n x n (or p x p) steps of one pass.
+//
+// Reads the reduced Gramian C = [Q_in Y]^T Y and performs, for one pass of
+// Alg. 1 (MODE_FACTOR) or one outer iteration of Alg. 2 (MODE_UPDATE):
+//   X = Y^T Y - B~^T B~             (Alg. 2 lines 5/16; B~ empty for Alg. 1)
+//   stop test ||X - I||_F < tol     (Alg. 1 line 4, Alg. 2 line 6, Sec. 4.1)
+//   shift and Cholesky with breakdown detection and retry
+//                                   (Alg. 1 lines 5-7, Alg. 2 lines 7-11)
+//   R~ and 1/diag(R~) for the row sweep, B <- B + B~ R, R <- R~ R
+//                                   (Alg. 1 line 10, Alg. 2 lines 13-14)
+// Every loop is bounded (max_iter passes, max_escalations shift retries,
+// 100 power iterations), so the kernel always terminates; a failure is
+// recorded in the device state and stops all later kernels of the call.
+#include <math.h>
+
+#include "cqr_internal.cuh"
+
+namespace cqr {
+
+__device__ __forceinline__ int pk(int i, int j) { return i + j * (j + 1) / 2; }  // i <= j
+
+// Sum over the block, fixed butterfly + fixed warp order: deterministic.
+__device__ double block_sum(double v, double *red) {
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int k = 0; k < nw; ++k) s += red[k];
+  __syncthreads();
+  return s;
+}
+
+__device__ float block_sumf(float v, float *red) {
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  float s = 0.0f;
+  for (int k = 0; k < nw; ++k) s += red[k];
+  __syncthreads();
+  return s;
+}
+
+// FP64 -> FP32 by truncation of the bit pattern (integer pipe only; the
+// GB300 FP64 unit is slow and the norm estimate needs ~1e-3 accuracy).
+__device__ __forceinline__ float d2f_trunc(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32);
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7FFu) - 1023;
+  if (e < -126) return __int_as_float((int)sign);
+  if (e > 127) return __int_as_float((int)(sign | 0x7F800000u));
+  const unsigned mant = (unsigned)((b >> 29) & 0x7FFFFFull);
+  return __int_as_float((int)(sign | ((unsigned)(e + 127) << 23) | mant));
+}
+
+// Estimate of ||X||_2 for symmetric X (the norm of Alg. 1 line 6 / Alg. 2
+// line 9, which the paper computes with a Lanczos solver at tolerance 1e-2
+// starting from the all-ones vector).  Power iteration in FP32 from the
+// all-ones vector, stopped when the Rayleigh quotient changes by < 1e-3
+// relative (at most 100 steps); the result is never below max_i |X_ii|.
+__device__ double norm_estimate(const double *X, int p, float *Xf, float *v, float *w,
+                                float *fred, double *red) {
+  const int t = threadIdx.x, NT = blockDim.x;
+  __syncthreads();  // Xf may alias storage read just before the call
+  for (int e = t; e < p * p; e += NT) Xf[e] = d2f_trunc(X[e]);
+  double dmax;
+  __syncthreads();
+  if (t < 32) {
+    double mv = 0.0;
+    for (int i = t; i < p; i += 32) mv = fmax(mv, fabs(X[i + i * p]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mv = fmax(mv, __shfl_xor_sync(0xffffffffu, mv, o));
+    if (t == 0) red[31] = mv;
+  }
+  __syncthreads();
+  dmax = red[31];
+  __syncthreads();
+  const float inv = rsqrtf((float)p);
+  for (int i = t; i < p; i += NT) v[i] = inv;
+  __syncthreads();
+  float lam = 0.0f, lam_prev = 0.0f;
+  for (int it = 0; it < 100; ++it) {
+    float part_l = 0.0f, part_n = 0.0f;
+    for (int i = t; i < p; i += NT) {
+      float s = 0.0f;
+      for (int j = 0; j < p; ++j) s = fmaf(Xf[i + j * p], v[j], s);
+      w[i] = s;
+      part_l += v[i] * s;
+      part_n += s * s;
+    }
+    lam = block_sumf(part_l, fred);
+    const float nrm = sqrtf(block_sumf(part_n, fred));
+    if (!(nrm > 0.0f) || !isfinite(nrm)) break;
+    const float rn = 1.0f / nrm;
+    for (int i = t; i < p; i += NT) v[i] = w[i] * rn;
+    __syncthreads();
+    if (it > 0 && fabsf(lam - lam_prev) <= 1e-3f * fabsf(lam)) break;
+    lam_prev = lam;
+  }
+  double l = (double)lam;
+  if (!(l == l)) l = INFINITY;
+  return fmax(l, dmax);
+}
+
+// Cholesky R^T R = X + sigma I into packed upper storage Rk (row-oriented,
+// pivot d_j = X_jj + sigma - sum_{k<j} R_kj^2).  Breakdown: d_j not strictly
+// positive or not finite.  Returns 0 or j + 1 of the failing pivot.
+__device__ int cholesky(const double *X, int p, double sigma, double *Rk, double *s_inv,
+                        int *s_fail) {
+  const int t = threadIdx.x, NT = blockDim.x;
+  __syncthreads();  // every thread has read the previous call's *s_fail
+  if (t == 0) *s_fail = 0;
+  __syncthreads();
+  for (int j = 0; j < p; ++j) {
+    if (t < 32) {
+      double s = 0.0;
+      for (int k = t; k < j; k += 32) {
+        const double r = Rk[pk(k, j)];
+        s = fma(r, r, s);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (t == 0) {
+        const double d = (X[j + j * p] + sigma) - s;
+        if (!(d > 0.0) || !isfinite(d)) {
+          *s_fail = j + 1;
+        } else {
+          const double r = sqrt(d);
+          Rk[pk(j, j)] = r;
+          *s_inv = 1.0 / r;
+        }
+      }
+    }
+    __syncthreads();
+    const int fail = *s_fail;
+    if (fail) return fail;
+    const double inv = *s_inv;
+    for (int i = j + 1 + t; i < p; i += NT) {
+      double s = X[j + i * p];
+      for (int k = 0; k < j; ++k) s -= Rk[pk(k, j)] * Rk[pk(k, i)];
+      Rk[pk(j, i)] = s * inv;
+    }
+    __syncthreads();
+  }
+  return 0;
+}
+
+__device__ __forceinline__ double shift_alg1(int64_t m, int n, double normX) {
+  const double c = 11.0 * ((double)m * (double)n + (double)n * ((double)n + 1.0));
+  return fmax(c * kU64 * normX, 2.0 * kU64);
+}
+
+__device__ __forceinline__ double shift_alg2_first(int64_t m, int q, int p, double normX) {
+  if (q == 0) return shift_alg1(m, p, normX);
+  const double c = 11.0 * ((double)m * (double)q + (double)q * ((double)q + 1.0));
+  return c * kU64 * normX;
+}
+
+__global__ void __launch_bounds__(kCtrlThreads) ctrl_kernel(Ctrl c) {
+  DevState *st = c.st;
+  if (st->done) return;
+  extern __shared__ double sm[];
+  __shared__ double red[32];
+  __shared__ float fred[32];
+  __shared__ int s_fail;
+  __shared__ double s_inv;
+  const int p = c.p, q = c.q, t = threadIdx.x, NT = blockDim.x;
+  const int ldc = q + p;
+  double *X = sm;          // p x p, full
+  double *Rk = X + p * p;  // packed upper, p (p + 1) / 2
+  float *vecs = (float *)(Rk + p * (p + 1) / 2 + 1);
+  float *v = vecs, *w = vecs + p;
+
+  // X = Y^T Y - B~^T B~
+  for (int e = t; e < p * p; e += NT) {
+    const int i = e % p, j = e / p;
+    double s = c.C[(q + i) + (int64_t)j * ldc];
+    if (q > 0) {
+      double b = 0.0;
+      for (int k = 0; k < q; ++k) b += c.C[k + (int64_t)i * ldc] * c.C[k + (int64_t)j * ldc];
+      s -= b;
+    }
+    X[e] = s;
+  }
+  double part = 0.0, partb = 0.0;
+  __syncthreads();
+  for (int e = t; e < p * p; e += NT) {
+    const int i = e % p, j = e / p;
+    const double d = X[e] - (i == j ? 1.0 : 0.0);
+    part = fma(d, d, part);
+  }
+  for (int e = t; e < q * p; e += NT) {
+    const double b = c.C[(e % q) + (int64_t)(e / q) * ldc];
+    partb = fma(b, b, partb);
+  }
+  const double orth = sqrt(block_sum(part, red));
+  const double projf = sqrt(block_sum(partb, red));
+
+  const int it = st->iters;
+  if (!isfinite(orth)) {
+    // NaN/Inf in the Gramian: the stop test is undefined and no shift can
+    // make X factorable; report a breakdown.
+    if (t == 0) {
+      st->done = 1;
+      st->status = CQR_ERR_BREAKDOWN;
+      st->orth_frob = orth;
+      st->proj_frob = projf;
+      st->active = 0;
+    }
+    return;
+  }
+  const double tol = (c.stop_rule == CQR_STOP_U_SQRT_N) ? kU64 * sqrt((double)p) : c.tol;
+  const bool cont = (orth >= tol || it < c.min_iter) && it < c.max_iter;
+  if (!cont) {
+    if (t == 0) {
+      st->done = 1;
+      st->status = (orth < tol) ? CQR_OK : CQR_NOT_CONVERGED;
+      st->orth_frob = orth;
+      st->proj_frob = projf;
+      st->active = 0;
+    }
+    return;
+  }
+
+  // ---- shift loop
+  double sigma = 0.0;
+  int attempts = 0, shifts = 0, escal = 0, rc = 0;
+  double s_first = 0.0;
+  bool fatal = false;
+  if (c.mode == MODE_FACTOR) {
+    const bool shifted_first = (it == 0) && (c.shift_policy == CQR_SHIFT_SCHOLQR3);
+    if (shifted_first) {
+      const double lam = norm_estimate(X, p, (float *)Rk, v, w, fred, red);
+      sigma = shift_alg1(c.m, p, lam);
+      ++shifts;
+      s_first = sigma;
+    }
+    rc = cholesky(X, p, sigma, Rk, &s_inv, &s_fail);
+    ++attempts;
+    if (rc != 0 && !shifted_first) {
+      if (c.shift_policy == CQR_SHIFT_NONE) {
+        fatal = true;
+      } else {
+        const double lam = norm_estimate(X, p, (float *)Rk, v, w, fred, red);
+        sigma = shift_alg1(c.m, p, lam);
+        ++shifts;
+        s_first = sigma;
+        rc = cholesky(X, p, sigma, Rk, &s_inv, &s_fail);
+        ++attempts;
+      }
+    }
+    int esc = 0;
+    while (!fatal && rc != 0 && esc < c.max_escalations) {
+      sigma *= 10.0;
+      ++escal;
+      ++esc;
+      rc = cholesky(X, p, sigma, Rk, &s_inv, &s_fail);
+      ++attempts;
+    }
+  } else {
+    rc = cholesky(X, p, 0.0, Rk, &s_inv, &s_fail);
+    ++attempts;
+    int esc = 0;
+    while (rc != 0 && esc < c.max_escalations) {
+      if (sigma == 0.0) {
+        const double lam = norm_estimate(X, p, (float *)Rk, v, w, fred, red);
+        sigma = shift_alg2_first(c.m, q, p, lam);
+        ++shifts;
+        s_first = fmax(sigma, 2.0 * kU64);
+      } else {
+        sigma *= 10.0;
+        ++escal;
+      }
+      sigma = fmax(sigma, 2.0 * kU64);
+      ++esc;
+      rc = cholesky(X, p, sigma, Rk, &s_inv, &s_fail);
+      ++attempts;
+    }
+  }
+  if (fatal || rc != 0) {
+    if (t == 0) {
+      st->chol_attempts += attempts;
+      st->shifts += shifts;
+      st->escalations += escal;
+      st->done = 1;
+      st->status = CQR_ERR_BREAKDOWN;
+      st->orth_frob = orth;
+      st->proj_frob = projf;
+      st->active = 0;
+    }
+    return;
+  }
+
+  // ---- outputs of the pass
+  for (int e = t; e < p * p; e += NT) {
+    const int i = e % p, j = e / p;
+    c.Rt[e] = (i <= j) ? Rk[pk(i, j)] : 0.0;
+  }
+  for (int j = t; j < p; j += NT) c.Rdinv[j] = 1.0 / Rk[pk(j, j)];
+  __syncthreads();
+  // R_old into the (no longer needed) X region
+  double *Rold = X;
+  for (int e = t; e < p * p; e += NT) {
+    const int i = e % p, j = e / p;
+    Rold[e] = c.R[i + (int64_t)j * c.ldr];
+  }
+  __syncthreads();
+  if (c.mode == MODE_UPDATE && q > 0) {
+    // B~ for the row sweep; B <- B + B~ R_old  (Alg. 2 line 13)
+    for (int e = t; e < q * p; e += NT) {
+      const int i = e % q, j = e / q;
+      c.Bt[e] = c.C[i + (int64_t)j * ldc];
+      double s = 0.0;
+      for (int k = 0; k <= j; ++k) s += c.C[i + (int64_t)k * ldc] * Rold[k + j * p];
+      c.B[i + (int64_t)j * c.ldb] = c.B[i + (int64_t)j * c.ldb] + s;
+    }
+  }
+  // R <- R~ R_old  (Alg. 1 line 10, Alg. 2 line 14)
+  for (int e = t; e < p * p; e += NT) {
+    const int i = e % p, j = e / p;
+    double s = 0.0;
+    if (i <= j)
+      for (int k = i; k <= j; ++k) s += Rk[pk(i, k)] * Rold[k + j * p];
+    c.R[i + (int64_t)j * c.ldr] = s;
+  }
+  if (t == 0) {
+    if (st->shifts == 0 && shifts > 0) st->sigma_first = s_first;
+    if (sigma > 0.0) st->sigma_last = sigma;
+    st->chol_attempts += attempts;
+    st->shifts += shifts;
+    st->escalations += escal;
+    st->iters = it + 1;
+    st->orth_frob = orth;
+    st->proj_frob = projf;
+    st->active = 1;
+  }
+}
+
+size_t ctrl_smem_bytes(int p) {
+  return (size_t)p * p * sizeof(double) + (size_t)(p * (p + 1) / 2 + 1) * sizeof(double) +
+         (size_t)2 * p * sizeof(float) + 64;
+}
+
+cudaError_t launch_ctrl(const Ctrl &a, cudaStream_t s) {
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaFuncSetAttribute(ctrl_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_done = true;
+  }
+  ctrl_kernel<<<1, kCtrlThreads, ctrl_smem_bytes(a.p), s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace cqr

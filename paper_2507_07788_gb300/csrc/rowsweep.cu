@@ -1,0 +1,226 @@
+// Row sweeps over the tall dimension m (FP64 CUDA-core version).
+//
+// One kernel covers the three bandwidth-bound steps of the method:
+//   * the Gramian X = A^T A of the first pass (Alg. 1 line 3),
+//   * the row-wise triangular solve Q = Q R~^{-1} of a pass fused with the
+//     Gramian of the result for the next pass (Alg. 1 lines 9 and 11),
+//   * for the update, the projection y <- (y - q_in B~) R~^{-1} fused with
+//     the next B~ = Q_in^T Q and Q^T Q (Alg. 2 lines 12, 15, 16; lines 4-5
+//     for the first sweep without the solve).
+// Each CTA owns a contiguous range of rows, walks it in tiles staged in
+// shared memory, and accumulates its share of C = [Q_in Y]^T Y in registers
+// in ascending row order.  The per-CTA partials are summed afterwards in a
+// fixed order (reduce_kernel), so results do not depend on scheduling.
+#include <algorithm>
+
+#include "cqr_internal.cuh"
+
+namespace cqr {
+
+// Map entry e of C = [Q_in Y]^T Y to shared-memory column indices (ca, cb):
+// e < q p: B~ entry (i, j) = (e mod q, e div q), columns (i, q + j);
+// else the upper triangle of Y^T Y in column-major packed order,
+// columns (q + i, q + j) with i <= j.
+__device__ __forceinline__ void entry_columns(int64_t e, int q, int p, int &ca, int &cb) {
+  const int64_t qp = (int64_t)q * p;
+  if (e < qp) {
+    ca = (int)(e % q);
+    cb = q + (int)(e / q);
+  } else {
+    int64_t f = e - qp;
+    // j = largest with j (j + 1) / 2 <= f
+    int j = (int)((sqrt(8.0 * (double)f + 1.0) - 1.0) * 0.5);
+    while ((int64_t)(j + 1) * (j + 2) / 2 <= f) ++j;
+    while ((int64_t)j * (j + 1) / 2 > f) --j;
+    int i = (int)(f - (int64_t)j * (j + 1) / 2);
+    ca = q + i;
+    cb = q + j;
+  }
+}
+
+template <int EPT>
+__global__ void __launch_bounds__(kThreads) rowsweep_kernel(RowSweep a) {
+  if (a.st != nullptr && a.st->done) return;
+  extern __shared__ double tile[];
+  const int t = threadIdx.x;
+  const int q = a.q, p = a.p, W = q + p, lds = a.lds, TR = a.tile_rows;
+  const int64_t row0 = (int64_t)blockIdx.x * a.rows_per_cta;
+  const int64_t row1 = min(a.m, row0 + a.rows_per_cta);
+
+  uint32_t idx[EPT];
+  double acc[EPT];
+  const int64_t ebase = (int64_t)blockIdx.y * (kThreads * EPT);
+#pragma unroll
+  for (int k = 0; k < EPT; ++k) {
+    const int64_t e = ebase + t + (int64_t)k * kThreads;
+    int ca = 0, cb = 0;
+    if (e < a.E) entry_columns(e, q, p, ca, cb);
+    idx[k] = (uint32_t)ca | ((uint32_t)cb << 16);
+    acc[k] = 0.0;
+  }
+
+  for (int64_t r0 = row0; r0 < row1; r0 += TR) {
+    const int nr = (int)min((int64_t)TR, row1 - r0);
+    // Stage rows r0 .. r0 + TR - 1 of [Q_in Y] (zero beyond nr).  Consecutive
+    // threads read consecutive rows of one column: coalesced.
+    for (int e = t; e < TR * W; e += kThreads) {
+      const int i = e % TR, c = e / TR;
+      double v = 0.0;
+      if (i < nr)
+        v = (c < q) ? a.Qin[(r0 + i) + (int64_t)c * a.ldqin]
+                    : a.Yin[(r0 + i) + (int64_t)(c - q) * a.ldyin];
+      tile[i * lds + c] = v;
+    }
+    __syncthreads();
+    if (a.do_trsm) {
+      if (t < nr) {
+        double *row = tile + t * lds;
+        // y <- y - q_in B~  (Alg. 2 line 12, first factor)
+        if (q > 0) {
+          for (int j = 0; j < p; ++j) {
+            double s = row[q + j];
+            for (int i = 0; i < q; ++i) s -= row[i] * a.Bt[i + (int64_t)j * q];
+            row[q + j] = s;
+          }
+        }
+        // y <- y R~^{-1} by forward substitution on R~^T y^T = y^T
+        for (int j = 0; j < p; ++j) {
+          double s = row[q + j];
+          for (int k = 0; k < j; ++k) s -= row[q + k] * a.Rt[k + (int64_t)j * p];
+          row[q + j] = s * a.Rdinv[j];
+        }
+      }
+      __syncthreads();
+      for (int e = t; e < nr * p; e += kThreads) {
+        const int i = e % nr, j = e / nr;
+        a.Yout[(r0 + i) + (int64_t)j * a.ldyout] = tile[i * lds + q + j];
+      }
+    }
+    for (int i = 0; i < nr; ++i) {
+      const double *row = tile + i * lds;
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) acc[k] = fma(row[idx[k] & 0xFFFFu], row[idx[k] >> 16], acc[k]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k < EPT; ++k) {
+    const int64_t e = ebase + t + (int64_t)k * kThreads;
+    if (e < a.E) a.partials[(int64_t)blockIdx.x * a.E + e] = acc[k];
+  }
+}
+
+// Fixed-order sum of the per-CTA partials: C(e) = sum_{g=0}^{G-1} P[g][e];
+// the Y^T Y part is written to both triangles.
+__global__ void reduce_kernel(Reduce a) {
+  if (a.st != nullptr && a.st->done) return;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.E) return;
+  double s = 0.0;
+  for (int g = 0; g < a.G; ++g) s += a.partials[(int64_t)g * a.E + e];
+  const int q = a.q, p = a.p, ldc = q + p;
+  const int64_t qp = (int64_t)q * p;
+  if (e < qp) {
+    a.C[(e % q) + (e / q) * ldc] = s;
+  } else {
+    int64_t f = e - qp;
+    int j = (int)((sqrt(8.0 * (double)f + 1.0) - 1.0) * 0.5);
+    while ((int64_t)(j + 1) * (j + 2) / 2 <= f) ++j;
+    while ((int64_t)j * (j + 1) / 2 > f) --j;
+    int i = (int)(f - (int64_t)j * (j + 1) / 2);
+    a.C[(q + i) + (int64_t)j * ldc] = s;
+    a.C[(q + j) + (int64_t)i * ldc] = s;
+  }
+}
+
+__global__ void init_kernel(double *R, int64_t ldr, int p, double *B, int64_t ldb, int q,
+                            DevState *st) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nt = gridDim.x * blockDim.x;
+  for (int e = t; e < p * p; e += nt) {
+    const int i = e % p, j = e / p;
+    R[i + (int64_t)j * ldr] = (i == j) ? 1.0 : 0.0;
+  }
+  if (B != nullptr)
+    for (int e = t; e < q * p; e += nt) B[(e % q) + (int64_t)(e / q) * ldb] = 0.0;
+  if (t == 0) {
+    DevState z = {};
+    *st = z;
+  }
+}
+
+int num_sms() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+void rowsweep_geometry(int q, int p, int *tile_rows, int *lds, size_t *smem) {
+  const int W = q + p;
+  int s = W | 1;  // odd stride in doubles
+  int tr = (int)(196608 / (8 * (size_t)s));
+  tr = std::min(tr, 64);
+  tr = std::max(8, tr & ~7);
+  *tile_rows = tr;
+  *lds = s;
+  *smem = (size_t)tr * s * sizeof(double);
+}
+
+int rowsweep_grid(int64_t m, int tile_rows) {
+  const int64_t tiles = (m + tile_rows - 1) / tile_rows;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)num_sms() * 2));
+}
+
+template <int EPT>
+static cudaError_t launch_ept(const RowSweep &a, dim3 grid, size_t smem, cudaStream_t s) {
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaFuncSetAttribute(rowsweep_kernel<EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_done = true;
+  }
+  rowsweep_kernel<EPT><<<grid, kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rowsweep(const RowSweep &a, int grid, cudaStream_t s) {
+  const size_t smem = (size_t)a.tile_rows * a.lds * sizeof(double);
+  const int64_t per = (a.E + kThreads - 1) / kThreads;
+  int ept;
+  if (per <= 1) ept = 1;
+  else if (per <= 2) ept = 2;
+  else if (per <= 4) ept = 4;
+  else if (per <= 8) ept = 8;
+  else if (per <= 16) ept = 16;
+  else ept = 33;
+  const int64_t gy = std::max<int64_t>(1, (a.E + (int64_t)kThreads * ept - 1) / ((int64_t)kThreads * ept));
+  if (a.do_trsm && gy != 1) return cudaErrorInvalidValue;  // caller splits the sweep
+  dim3 g(grid, (unsigned)gy);
+  switch (ept) {
+    case 1: return launch_ept<1>(a, g, smem, s);
+    case 2: return launch_ept<2>(a, g, smem, s);
+    case 4: return launch_ept<4>(a, g, smem, s);
+    case 8: return launch_ept<8>(a, g, smem, s);
+    case 16: return launch_ept<16>(a, g, smem, s);
+    default: return launch_ept<33>(a, g, smem, s);
+  }
+}
+
+cudaError_t launch_reduce(const Reduce &a, cudaStream_t s) {
+  const int bs = 64;
+  const int64_t blocks = (a.E + bs - 1) / bs;
+  reduce_kernel<<<(unsigned)blocks, bs, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init(double *R, int64_t ldr, int p, double *B, int64_t ldb, int q,
+                        DevState *st, cudaStream_t s) {
+  init_kernel<<<8, 256, 0, s>>>(R, ldr, p, B, ldb, q, st);
+  return cudaGetLastError();
+}
+
+}  // namespace cqr

@@ -85,3 +85,18 @@ def update_block(Q_prev: np.ndarray | None, m: int, p: int, k: int, seed: int = 
     G = rng.standard_normal((q, p))
     eta = 10.0 ** rng.uniform(-12.0, 0.0)
     return np.asfortranarray(Q_prev @ G * 0.1 + N * eta), float(eta)
+
+
+def basis_growth_blocks(m: int, p: int, count: int, seed: int = 0):
+    """Blocks 0..count-1 of a basis-growth run for tests: block k is
+    update_block(Q_prev, ...) with Q_prev an orthonormal basis (LAPACK QR,
+    used here only as a data generator) of blocks 0..k-1.
+    Returns (blocks, etas)."""
+    blocks, etas = [], []
+    Qp = None
+    for k in range(count):
+        b, eta = update_block(Qp, m, p, k, seed)
+        blocks.append(b)
+        etas.append(eta)
+        Qp, _ = np.linalg.qr(np.hstack(blocks))
+    return blocks, etas

@@ -1,0 +1,194 @@
+"""Parity of cholqr_factor (CUDA, through the C ABI) with the CPU oracle.
+
+Tolerances.  The QR factors of a full-rank A are unique (positive diagonal
+of R), but two backward-stable computations that round differently agree
+only up to the conditioning of the QR factors: with backward errors of
+order u ||A||, the factors differ by O(kappa(A) u) (standard QR
+perturbation theory).  Elementwise, Q entries are O(1/sqrt(m)).  The tests
+therefore bound
+  |Q_gpu - Q_oracle|_max <= max(1e-12, 20 kappa u / sqrt(m) * sqrt(n)),
+  |R_gpu - R_oracle|_max <= 20 kappa u sqrt(n) ||R||_max,
+and require the orthogonality ||Q^T Q - I||_F <= 1e-13 and the residual
+||A - QR||_2/||A||_2 <= 1e-13 for kappa <= 1e15 outright.  For
+kappa <= 1e4 the elementwise Q bound is the 1e-12 the target states.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2507_07788_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+U = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def cq():
+    import paper_2507_07788_gb300 as cq
+    from paper_2507_07788_gb300 import _build
+    _build.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return cq
+
+
+def q_tol(kappa, m, n):
+    return max(1e-12, 20.0 * kappa * U * math.sqrt(n) / math.sqrt(m))
+
+
+def r_tol(kappa, n, R):
+    return 20.0 * max(kappa, 1.0) * U * math.sqrt(n) * np.max(np.abs(R))
+
+
+def run_gpu(cq, A, opts=None, inplace=False):
+    dA = cq.to_colmajor(A)
+    if inplace:
+        res = cq.factor(dA, Q=dA, opts=opts, check=False)
+    else:
+        res = cq.factor(dA, opts=opts, check=False)
+    torch.cuda.synchronize()
+    return res.Q.cpu().numpy(), res.R.cpu().numpy(), res.status, res.info
+
+
+@pytest.mark.parametrize("kappa", [1.0, 1e2, 1e4, 1e8, 1e12, 1e15])
+@pytest.mark.parametrize("rep", [0, 1])
+def test_factor_parity_config1(cq, orc, kappa, rep):
+    m, n = 20037, 20  # several tiles, ragged tail
+    A = synth.test_matrix(m, n, kappa, rep=rep)
+    Q, R, st, info = run_gpu(cq, A)
+    Qo, Ro, sto, info_o = orc.cholqr(A)
+    assert st == sto == cq.OK, (st, info)
+    assert info["iters"] == info_o.iters
+    assert info["shifts"] == info_o.shifts
+    # shift from the norm estimate: within the paper's eigsh tolerance 1e-2
+    assert info["sigma_first"] == pytest.approx(info_o.sigma_first, rel=1e-2)
+    assert orc.loo_frob(Q) <= 1e-13
+    assert orc.rrr(A, Q, R) <= 1e-13
+    assert np.all(np.tril(R, -1) == 0) and np.all(np.diag(R) > 0)
+    dq = np.max(np.abs(Q - Qo))
+    dr = np.max(np.abs(R - Ro))
+    print(f"kappa={kappa:.0e} rep={rep} iters={info['iters']} maxdQ={dq:.2e} maxdR={dr:.2e} "
+          f"loo={orc.loo_frob(Q):.2e}")
+    assert dr <= r_tol(kappa, n, Ro)
+    assert dq <= q_tol(kappa, m, n)
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (7, 1), (5, 5), (129, 7), (4000, 16), (3001, 32),
+                                 (2500, 64), (1100, 128), (777, 33)])
+def test_factor_shapes(cq, orc, m, n):
+    A = synth.test_matrix(m, n, 1e3, rep=3)
+    Q, R, st, info = run_gpu(cq, A)
+    Qo, Ro, sto, info_o = orc.cholqr(A)
+    assert st == sto and st >= 0
+    assert info["iters"] == info_o.iters
+    assert np.max(np.abs(R - Ro)) <= r_tol(1e3, n, Ro)
+    assert np.max(np.abs(Q - Qo)) <= q_tol(1e3, m, n)
+
+
+def test_factor_n1_closed_form(cq):
+    a = np.random.default_rng(5).standard_normal((10001, 1))
+    Q, R, st, info = run_gpu(cq, a)
+    nrm = math.sqrt(float(np.sum(a * a)))
+    assert st == cq.OK
+    assert R[0, 0] == pytest.approx(nrm, rel=1e-13)
+    assert np.allclose(Q[:, 0], a[:, 0] / nrm, rtol=0, atol=1e-15)
+
+
+def test_orthonormal_input_untouched(cq):
+    A = np.zeros((4096, 8))
+    A[np.arange(8) * 17, np.arange(8)] = 1.0
+    Q, R, st, info = run_gpu(cq, A)
+    assert st == cq.OK and info["iters"] == 0
+    assert np.array_equal(Q, A) and np.array_equal(R, np.eye(8))
+
+
+def test_in_place(cq, orc):
+    A = synth.test_matrix(9999, 24, 1e6, rep=4)
+    Q, R, st, info = run_gpu(cq, A, inplace=True)
+    Qo, Ro, sto, _ = orc.cholqr(A)
+    assert st == cq.OK
+    assert np.max(np.abs(Q - Qo)) <= q_tol(1e6, 9999, 24)
+
+
+def test_leading_dimension(cq, orc):
+    m, n, lda = 3000, 10, 3017
+    A = synth.test_matrix(m, n, 1e5, rep=5)
+    big = cq.colmajor(lda, n)
+    big.zero_()
+    big[:m].copy_(torch.from_numpy(A))
+    dA = big[:m]
+    assert dA.stride() == (1, lda)
+    res = cq.factor(dA)
+    Qo, Ro, _, _ = orc.cholqr(A)
+    assert np.max(np.abs(res.Q.cpu().numpy() - Qo)) <= q_tol(1e5, m, n)
+
+
+def test_zero_column_forces_shift(cq, orc):
+    A = synth.test_matrix(2000, 6, 1e2, rep=6)
+    A[:, 3] = 0.0
+    opts = cq.default_opts(shift_policy=cq.SHIFT_ON_BREAKDOWN)
+    Q, R, st, info = run_gpu(cq, A, opts=opts)
+    Qo, Ro, sto, info_o = orc.cholqr(A, shift_policy=orc.SHIFT_ON_BREAKDOWN)
+    assert info["shifts"] >= 1 and info_o.shifts >= 1
+    assert st >= 0 and sto >= 0
+    assert orc.rrr(A, Q, R) <= 1e-13
+
+
+def test_no_shift_policy_breaks_down(cq):
+    A = synth.test_matrix(5000, 12, 1e12)
+    opts = cq.default_opts(shift_policy=cq.SHIFT_NONE)
+    _, _, st, info = run_gpu(cq, A, opts=opts)
+    assert st == cq.ERR_BREAKDOWN
+
+
+def test_nan_input_reports_breakdown(cq, orc):
+    A = synth.test_matrix(1000, 5, 10.0)
+    A[17, 2] = np.nan
+    _, _, st, info = run_gpu(cq, A)
+    _, _, sto, _ = orc.cholqr(A)
+    assert st == sto == cq.ERR_BREAKDOWN
+    assert info["escalations"] <= cq.default_opts().max_escalations
+
+
+def test_max_iter_not_converged(cq, orc):
+    A = synth.test_matrix(3000, 8, 1e12)
+    opts = cq.default_opts(max_iter=1)
+    Q, R, st, info = run_gpu(cq, A, opts=opts)
+    assert st == cq.NOT_CONVERGED and info["iters"] == 1
+    assert orc.rrr(A, Q, R) <= 1e-13
+
+
+def test_u_sqrt_n_stop_rule(cq, orc):
+    A = synth.test_matrix(3000, 8, 1e3)
+    opts = cq.default_opts(stop_rule=cq.STOP_U_SQRT_N, max_iter=4)
+    _, _, st, info = run_gpu(cq, A, opts=opts)
+    _, _, sto, info_o = orc.cholqr(A, stop_rule=orc.STOP_U_SQRT_N, max_iter=4)
+    assert st in (cq.OK, cq.NOT_CONVERGED)
+    assert info["iters"] <= 4
+
+
+def test_kappa_1e20_rscholqr(cq, orc):
+    # beyond 1/u: the recomputed shift still gives an orthonormal Q (Fig. 1)
+    A = synth.test_matrix(20000, 20, 1e20, rep=2)
+    Q, R, st, info = run_gpu(cq, A)
+    assert st == cq.OK
+    assert orc.loo(Q) < 3.16e-13
+    assert orc.rrr(A, Q, R) <= 1e-13
+
+
+def test_deterministic(cq):
+    A = synth.test_matrix(50000, 32, 1e10, rep=8)
+    Q1, R1, _, _ = run_gpu(cq, A)
+    Q2, R2, _, _ = run_gpu(cq, A)
+    assert np.array_equal(Q1, Q2) and np.array_equal(R1, R2)
+
+
+def test_host_entry_point(cq, orc):
+    A = synth.test_matrix(12345, 16, 1e8, rep=9)
+    res = cq.factor_host(A)
+    Q, R = res.Q.numpy(), res.R.numpy()
+    Qd, Rd, _, _ = run_gpu(cq, A)
+    assert res.status == cq.OK
+    assert np.array_equal(Q, Qd) and np.array_equal(R, Rd)

@@ -1,0 +1,123 @@
+"""Parity of basis_create / basis_append (Alg. 2 on the GPU, through the C ABI)
+with the CPU oracle's Alg. 2, append by append, on near-dependent blocks
+(block_k = Q_prev G 0.1 + N eta, eta log-uniform in [1e-12, 1])."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2507_07788_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+U = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def cq():
+    import paper_2507_07788_gb300 as cq
+    from paper_2507_07788_gb300 import _build
+    _build.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return cq
+
+
+def test_basis_growth_matches_oracle(cq, orc):
+    m, p, count = 5003, 8, 8
+    blocks, etas = synth.basis_growth_blocks(m, p, count, seed=1)
+    b = cq.Basis(m, p * count)
+    Qo = np.zeros((m, 0))
+    Ro = np.zeros((0, 0))
+    for k, blk in enumerate(blocks):
+        st, info = b.append(cq.to_colmajor(blk))
+        Qn, Bn, Rn, sto, info_o = orc.cholqr_update(Qo, blk, min_iter=2)
+        assert st == sto and st >= 0, (k, st, info, info_o)
+        q = Qo.shape[1]
+        Qo = np.hstack([Qo, Qn])
+        Ro = np.block([[Ro, Bn], [np.zeros((p, q)), Rn]])
+        Qg = b.Q().cpu().numpy()
+        Rg = b.R().cpu().numpy()
+        assert Qg.shape == (m, q + p)
+        # orthogonality after every append
+        assert orc.loo_frob(Qg) <= 1e-12, k
+        # reconstruction of all blocks so far
+        Afull = np.hstack(blocks[: k + 1])
+        assert orc.rrr(Afull, Qg, Rg) <= 1e-13, k
+        # element-wise parity: the new block's R and B scale with the block
+        scale = max(np.max(np.abs(Rn)), np.max(np.abs(Bn)) if q else 0.0)
+        kap = 1.0 / max(etas[k], 1e-16)
+        dR = np.max(np.abs(Rg[: q + p, q:] - Ro[: q + p, q:]))
+        dQ = np.max(np.abs(Qg[:, q:] - Qn))
+        print(f"append {k}: eta={etas[k]:.1e} iters={info['iters']}/{info_o.iters} "
+              f"shifts={info['shifts']}/{info_o.shifts} dR={dR:.2e} dQ={dQ:.2e}")
+        assert dR <= 200 * kap * U * math.sqrt(q + p) * scale + 1e-15
+        assert dQ <= max(1e-12, 200 * kap * U * math.sqrt(p) / math.sqrt(m))
+    b.close()
+
+
+def test_first_append_equals_factor(cq):
+    A = synth.test_matrix(4001, 12, 1e6, rep=2)
+    b = cq.Basis(4001, 12)
+    st, info = b.append(cq.to_colmajor(A))
+    res = cq.factor(cq.to_colmajor(A))
+    assert st >= 0
+    Rb = b.R().cpu().numpy()
+    Rf = res.R.cpu().numpy()
+    assert np.max(np.abs(Rb - Rf)) <= 1e-10 * np.max(np.abs(Rf))
+    b.close()
+
+
+def test_capacity_error_keeps_basis(cq):
+    m = 2000
+    b = cq.Basis(m, 10)
+    A = synth.gaussian(m, 8, seed=3)
+    st, _ = b.append(cq.to_colmajor(A))
+    assert st == cq.OK and b.cols == 8
+    Q0 = b.Q().cpu().numpy().copy()
+    st, _ = b.append(cq.to_colmajor(synth.gaussian(m, 4, seed=4)), check=False)
+    assert st == cq.ERR_CAPACITY and b.cols == 8
+    assert np.array_equal(b.Q().cpu().numpy(), Q0)
+    b.close()
+
+
+def test_dependent_column_lucky_breakdown(cq, orc):
+    m, q, p = 3000, 6, 4
+    b = cq.Basis(m, 16)
+    base = synth.gaussian(m, q, seed=5)
+    b.append(cq.to_colmajor(base))
+    Qin = b.Q().cpu().numpy()
+    A = synth.gaussian(m, p, seed=6)
+    A[:, 2] = Qin @ np.array([1.0, -2.0, 0.5, 0.0, 3.0, 1.0])
+    st, info = b.append(cq.to_colmajor(A))
+    assert st >= 0 and info["shifts"] >= 1
+    Qg = b.Q().cpu().numpy()
+    assert orc.loo_frob(Qg) <= 1e-12
+
+
+def test_breakdown_leaves_basis_unchanged(cq):
+    m = 1500
+    b = cq.Basis(m, 16, opts=cq.default_opts(max_escalations=0))
+    b.append(cq.to_colmajor(synth.gaussian(m, 4, seed=7)))
+    Q0, R0 = b.Q().cpu().numpy().copy(), b.R().cpu().numpy().copy()
+    bad = synth.gaussian(m, 4, seed=8)
+    bad[5, 1] = np.nan
+    st, info = b.append(cq.to_colmajor(bad), check=False)
+    assert st == cq.ERR_BREAKDOWN
+    assert b.cols == 4
+    assert np.array_equal(b.Q().cpu().numpy(), Q0) and np.array_equal(b.R().cpu().numpy(), R0)
+    b.close()
+
+
+def test_wide_basis_split_sweep(cq, orc):
+    # q p + p (p+1)/2 beyond one CTA's entry budget: the solve and the Gram
+    # sweep run as two kernels
+    m, p = 2500, 32
+    b = cq.Basis(m, 320)
+    for k in range(9):
+        st, info = b.append(cq.to_colmajor(synth.gaussian(m, p, seed=20 + k)))
+        assert st >= 0
+    Qg = b.Q().cpu().numpy()
+    assert Qg.shape[1] == 288
+    assert orc.loo_frob(Qg) <= 1e-12
+    b.close()
