@@ -1,0 +1,332 @@
+#!/usr/bin/env python
+"""Throughput of FP64 sCholQR3 (cholqr_factor) on GB300.
+
+One step = one cholqr_factor call on a resident m x n FP64 matrix
+A = U diag(s) V^T (the paper's test-matrix recipe, Sec. 4.1), default
+m = 1,000,000, n = 64, kappa = 1e12.  Metric: rows*cols/s = m n / t_step,
+summed over ranks (each rank factors its own matrix: replicas, weak scaling).
+
+Prints ONE JSON line (rank 0) with the contract keys plus:
+  roofline      dominant kernel (the fused solve + Gramian row sweep), its
+                achieved rate from CUDA events on its launch stream, against
+                the measured peak;
+  cpu_baseline  the CPU oracle on a bounded sample of the same matrix;
+  e2e           the same metric through cholqr_factor_host (host buffers,
+                copies inside the timed region);
+  clocks        nvidia-smi samples taken during the timed region;
+  sweep         a short n x kappa sweep at the same m.
+``--impl reference`` times the CPU oracle instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("sCholQR3 rows·cols/s & %HBM roofline at ‖QᵀQ−I‖≤1e-13; "
+          "serve p50/p99 latency")
+FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9   # SMs x DFMA/clk/SM x 2 FLOP x max SM clock
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--m", type=int, default=1_000_000)
+    ap.add_argument("--n", type=int, default=64)
+    ap.add_argument("--kappa", type=float, default=1e12)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-rows", type=int, default=600_000)
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2507_07788_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch(m: int):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary (profiles/rowsweep_traffic.txt), scaled to m rows, or None when the
+    kernel sources changed since the counters were taken."""
+    d = {}
+    try:
+        for line in open(os.path.join(ROOT, "profiles", "rowsweep_traffic.txt")):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                d[k.strip()] = v.strip()
+    except Exception:
+        return None, None
+    if d.get("source_hash") != kernel_source_hash():
+        return None, d
+    try:
+        return float(d["capture_bytes_per_launch"]) * m / float(d["capture_m"]), d
+    except Exception:
+        return None, d
+
+
+def cpu_baseline(A, rows, n):
+    import oracle
+    oracle.build()
+    S = A[:rows]
+    t0 = time.perf_counter()
+    Q, R, st, info = oracle.cholqr(S)
+    dt = time.perf_counter() - t0
+    return {"value": rows * n / dt, "unit": "rows*cols/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {rows} of {A.shape[0]} rows of the benchmark matrix, one factorisation "
+                      f"({dt:.1f} s, {info.iters} passes, single-threaded plain C)",
+            "seconds": dt}
+
+
+def run_reference(args):
+    ws, rank, _ = dist()
+    if rank != 0:
+        return 0
+    from paper_2507_07788_gb300 import synth
+    import oracle
+    oracle.build()
+    rows = min(args.m, 250_000)
+    A = synth.test_matrix(args.m if args.m <= 250_000 else rows, args.n, args.kappa, rep=0)
+    times = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        Q, R, st, info = oracle.cholqr(A)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+    t = statistics.mean(times)
+    val = rows * args.n / t
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "rows*cols/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"sCholQR3 FP64 n={args.n} kappa={args.kappa:g} (A=U diag(s) V^T), "
+                                   f"bounded CPU sample m={rows} of m={args.m}",
+                       "m": args.m, "n": args.n, "kappa": args.kappa, "sample_rows": rows},
+            "cpu_baseline": {"value": val, "unit": "rows*cols/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{rows} x {args.n} matrix per step"},
+            "e2e": {"value": val, "unit": "rows*cols/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def time_factor(cq, torch, dA, dQ, dR, opts, steps, warmup):
+    for _ in range(warmup):
+        cq.factor(dA, Q=dQ, R=dR, opts=opts)
+    s = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    res = None
+    for _ in range(steps):
+        res = cq.factor(dA, Q=dQ, R=dR, opts=opts)
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, res
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2507_07788_gb300 as cq
+    from paper_2507_07788_gb300 import _build, synth
+
+    ws, rank, local = dist()
+    if ws > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group(backend="nccl")
+    torch.cuda.set_device(local)
+    _build.build()
+    m, n, kappa = args.m, args.n, args.kappa
+    opts = cq.default_opts(precision=cq.PREC_MIXED if args.precision == "mixed" else cq.PREC_FP64)
+
+    A = synth.test_matrix(m, n, kappa, rep=rank)
+    dA = cq.to_colmajor(A)
+    dQ = cq.colmajor(m, n)
+    dR = cq.colmajor(n, n)
+
+    for _ in range(args.warmup):
+        cq.factor(dA, Q=dQ, R=dR, opts=opts)
+    cq.cqr_timing_reset()
+    cq.cqr_timing_enable(True)
+    clocks = Clocks(local)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    res = None
+    for _ in range(args.steps):
+        res = cq.factor(dA, Q=dQ, R=dR, opts=opts)
+    e1.record(s)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    cq.cqr_timing_enable(False)
+    tm = cq.cqr_timing_read()
+    ms = e0.elapsed_time(e1) / args.steps
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * m * n / (ms * 1e-3)
+
+    # quality of the timed result (outside the timed region)
+    G = dQ.t() @ dQ
+    loo_f = float(torch.linalg.norm(G - torch.eye(n, dtype=G.dtype, device=G.device)))
+
+    hbm_peak, hbm_src = peaks()
+    fused_ms = tm["fused_ms"] / max(tm["fused_launches"], 1)
+    fused_flops = tm["fused_flops"] / max(tm["fused_launches"], 1)
+    fused_bytes = tm["fused_bytes"] / max(tm["fused_launches"], 1)
+    ach_flops = fused_flops / (fused_ms * 1e-3) if fused_ms > 0 else 0.0
+    ach_gbs = fused_bytes / (fused_ms * 1e-3) / 1e9 if fused_ms > 0 else 0.0
+    traffic, tinfo = traffic_per_launch(m)
+    roof = {"bound": "alu", "achieved": ach_flops / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
+            "frac": ach_flops / FP64_PEAK_FLOPS, "traffic": traffic,
+            "kernel": "rowsweep_kernel (fused triangular solve + Gramian sweep)",
+            "per_launch": {"ms": fused_ms, "algorithmic_flops": fused_flops, "algorithmic_bytes": fused_bytes},
+            "hbm": {"achieved_gbs": ach_gbs, "peak_gbs": hbm_peak, "frac": ach_gbs / hbm_peak,
+                    "peak_source": hbm_src},
+            "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz (FP64 CUDA cores)"}
+
+    line = {"metric": METRIC, "value": value, "unit": "rows*cols/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"sCholQR3 FP64 m={m} n={n} kappa={kappa:g} (A=U diag(s) V^T, Sec. 4.1)",
+                       "m": m, "n": n, "kappa": kappa, "precision": args.precision,
+                       "l2": f"inputs larger than L2 ({8 * m * n / 2**20:.0f} MiB per matrix)",
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "roofline": roof, "gpu_launches": int(tm["kernel_launches"]),
+            "quality": {"status": res.status, "iters": res.info["iters"], "loo_frob": loo_f,
+                        "orth_frob_last_gram": res.info["orth_frob"], "shifts": res.info["shifts"]},
+            "clocks": clk}
+
+    if rank == 0 and not args.no_e2e:
+        Ah = torch.from_numpy(np.asfortranarray(A)).t().contiguous().pin_memory().t()
+        for _ in range(2):
+            cq.factor_host(Ah, opts=opts)
+        t0 = time.perf_counter()
+        k = max(2, args.steps // 2)
+        for _ in range(k):
+            r2 = cq.factor_host(Ah, opts=opts)
+        dt = (time.perf_counter() - t0) / k
+        line["e2e"] = {"value": m * n / dt, "unit": "rows*cols/s", "h2d_bytes_per_step": 8 * m * n,
+                       "d2h_bytes_per_step": 8 * (m * n + n * n), "ms_per_step": dt * 1e3,
+                       "api": "cholqr_factor_host (pinned host buffers, H2D + factor + D2H in the timed region)"}
+
+    if rank == 0 and not args.no_sweep:
+        sweep = []
+        for nn in (16, 32, 64):
+            for kap in (1e4, 1e8, 1e12, 1e15):
+                As = synth.test_matrix(m, nn, kap, rep=11)
+                dAs, dQs, dRs = cq.to_colmajor(As), cq.colmajor(m, nn), cq.colmajor(nn, nn)
+                tms, rs = time_factor(cq, torch, dAs, dQs, dRs, opts, 3, 1)
+                sweep.append({"n": nn, "kappa": kap, "ms": tms, "rows_cols_per_s": m * nn / (tms * 1e-3),
+                              "iters": rs.info["iters"], "status": rs.status,
+                              "orth_frob": rs.info["orth_frob"]})
+                del dAs, dQs, dRs
+        line["sweep"] = sweep
+
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(A, min(args.cpu_rows, m), n)
+
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

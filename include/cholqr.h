@@ -181,6 +181,34 @@ int64_t basis_capacity(const cqr_basis *b);
 cqr_status basis_q(const cqr_basis *b, const double **Q, int64_t *ldq);
 cqr_status basis_r(const cqr_basis *b, const double **R, int64_t *ldr);
 
+/*
+ * Instrumentation (no counterpart in the paper).  When enabled, every call
+ * brackets each launch of the row-sweep kernels (the Gramian sweep and the
+ * fused solve + Gramian sweep) with CUDA events on the launching stream and,
+ * at the call's final synchronisation, adds the elapsed times of the sweeps
+ * that did work, with their algorithmic FLOPs and bytes, to process-wide
+ * counters.  All kernel launches of the library are counted whether or not
+ * timing is enabled.  Counters are protected by a mutex; reset clears them.
+ */
+typedef struct cqr_timing {
+  int64_t kernel_launches;   /* every kernel launch of the library */
+  int64_t sweep_launches;    /* timed row sweeps that did work */
+  double sweep_ms;           /* their summed event time */
+  double sweep_flops;        /* their algorithmic FLOPs */
+  double sweep_bytes;        /* their algorithmic HBM bytes (read + write) */
+  int64_t fused_launches;    /* of those, fused solve + Gramian sweeps */
+  double fused_ms;
+  double fused_flops;
+  double fused_bytes;
+} cqr_timing;
+
+/* Enables (1) or disables (0) event timing of the row sweeps. */
+cqr_status cqr_timing_enable(int enable);
+/* Copies the counters to *out (host pointer, not NULL). */
+cqr_status cqr_timing_read(cqr_timing *out);
+/* Clears the counters. */
+void cqr_timing_reset(void);
+
 #ifdef __cplusplus
 }
 #endif

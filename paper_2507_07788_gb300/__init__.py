@@ -47,6 +47,16 @@ class Info(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Timing(C.Structure):
+    _fields_ = [("kernel_launches", C.c_int64), ("sweep_launches", C.c_int64),
+                ("sweep_ms", C.c_double), ("sweep_flops", C.c_double), ("sweep_bytes", C.c_double),
+                ("fused_launches", C.c_int64), ("fused_ms", C.c_double),
+                ("fused_flops", C.c_double), ("fused_bytes", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class CholQRError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         self.status = status
@@ -72,6 +82,9 @@ _SIGNATURES = {
     "basis_capacity": (_I64, [_VP]),
     "basis_q": (C.c_int, [_VP, C.POINTER(_VP), C.POINTER(_I64)]),
     "basis_r": (C.c_int, [_VP, C.POINTER(_VP), C.POINTER(_I64)]),
+    "cqr_timing_enable": (C.c_int, [C.c_int]),
+    "cqr_timing_read": (C.c_int, [C.POINTER(Timing)]),
+    "cqr_timing_reset": (None, []),
 }
 
 
@@ -131,6 +144,22 @@ def basis_append(b, p, A_in, lda, info, stream) -> int:
 
 def basis_free(b) -> int:
     return lib().basis_free(b)
+
+
+def cqr_timing_enable(enable: bool) -> int:
+    return lib().cqr_timing_enable(1 if enable else 0)
+
+
+def cqr_timing_read() -> dict:
+    t = Timing()
+    st = lib().cqr_timing_read(C.byref(t))
+    if st != OK:
+        raise CholQRError(st, "cqr_timing_read")
+    return t.as_dict()
+
+
+def cqr_timing_reset() -> None:
+    lib().cqr_timing_reset()
 
 
 # ----------------------------------------------------------------- tensor helpers
@@ -213,8 +242,8 @@ def factor_host(A, opts: Opts | None = None, stream=None, check=True) -> Result:
     if t.stride(0) != 1:
         t = t.t().contiguous().t()
     lda = max(t.stride(1), m)
-    Q = torch.empty((n, m), dtype=torch.float64).t()
-    R = torch.empty((n, n), dtype=torch.float64).t()
+    Q = torch.empty((n, m), dtype=torch.float64, pin_memory=True).t()
+    R = torch.empty((n, n), dtype=torch.float64, pin_memory=True).t()
     info = Info()
     st = lib().cholqr_factor_host(C.byref(opts) if opts is not None else None, m, n, t.data_ptr(),
                                   lda, Q.data_ptr(), m, R.data_ptr(), n, C.byref(info),

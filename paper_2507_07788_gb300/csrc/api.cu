@@ -18,7 +18,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
+#include <vector>
 
 #include "cqr_internal.cuh"
 
@@ -35,6 +37,24 @@ struct cqr_basis {
 namespace {
 
 constexpr int kPrelaunch = 3;
+
+// ---- instrumentation (cqr_timing_*)
+std::mutex g_timing_mu;
+cqr_timing g_timing = {};
+std::atomic<int> g_timing_on{0};
+std::atomic<int64_t> g_launches{0};
+
+struct SweepMark {
+  cudaEvent_t a, b;
+  int pass;    // 0 = first Gramian sweep, k >= 1 = k-th solve + Gramian sweep
+  double flops, bytes;
+};
+
+// Thread-local pool of event pairs for the sweep marks of one call.
+std::vector<SweepMark> &marks_pool() {
+  thread_local std::vector<SweepMark> pool;
+  return pool;
+}
 
 cqr_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return CQR_OK;
@@ -153,6 +173,16 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
   CQR_TRY(scratch_alloc(s, q, p, G, E, str));
   DevState *hs = host_state();
   cqr_status result = CQR_OK;
+  const bool timing = g_timing_on.load() != 0;
+  std::vector<SweepMark> &pool = marks_pool();
+  size_t nmarks = 0;
+  int npass = 0;
+  // algorithmic work of one sweep (the minimum, whether or not it is split)
+  const double m_d = (double)P.m;
+  const double gram_flops = 2.0 * m_d * (double)E;
+  const double gram_bytes = 8.0 * m_d * (double)(q + p);
+  const double solve_flops = 2.0 * m_d * ((double)q * p + (double)p * (p - 1) / 2.0) + m_d * p;
+  const double solve_bytes = 8.0 * m_d * (double)p;  // the write of the new block
 
   auto sweep = [&](bool trsm, bool first) -> cudaError_t {
     RowSweep a{};
@@ -175,20 +205,43 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
     a.lds = lds;
     a.do_trsm = trsm ? 1 : 0;
     a.st = s.st;
+    SweepMark *mk = nullptr;
+    if (timing) {
+      if (nmarks == pool.size()) {
+        SweepMark nm{};
+        cudaEventCreate(&nm.a);
+        cudaEventCreate(&nm.b);
+        pool.push_back(nm);
+      }
+      mk = &pool[nmarks++];
+      mk->pass = trsm ? ++npass : 0;
+      mk->flops = gram_flops + (trsm ? solve_flops : 0.0);
+      mk->bytes = gram_bytes + (trsm ? solve_bytes : 0.0);
+      cudaEventRecord(mk->a, str);
+    } else if (trsm) {
+      ++npass;
+    }
+    cudaError_t e = cudaSuccess;
     if (trsm && split) {
       // transform only, then a separate Gram sweep over the result
       RowSweep t = a;
       t.E = 0;
-      cudaError_t e = launch_rowsweep(t, G, str);
-      if (e != cudaSuccess) return e;
+      e = launch_rowsweep(t, G, str);
+      g_launches++;
       a.do_trsm = 0;
       a.Yin = P.Y;
       a.ldyin = P.ldy;
     }
-    return launch_rowsweep(a, G, str);
+    if (e == cudaSuccess) {
+      e = launch_rowsweep(a, G, str);
+      g_launches++;
+    }
+    if (mk != nullptr) cudaEventRecord(mk->b, str);
+    return e;
   };
   auto reduce = [&]() -> cudaError_t {
     Reduce r{s.partials, G, E, q, p, s.C, s.st};
+    g_launches++;
     return launch_reduce(r, str);
   };
   auto ctrl = [&]() -> cudaError_t {
@@ -212,6 +265,7 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
     c.B = P.B;
     c.ldb = P.ldb;
     c.st = s.st;
+    g_launches++;
     return launch_ctrl(c, str);
   };
   auto pass = [&](bool first) -> cudaError_t {
@@ -222,6 +276,7 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
   };
 
   cudaError_t e = launch_init(P.R, P.ldr, p, P.B, P.ldb, q, s.st, str);
+  g_launches++;
   if (e == cudaSuccess) e = sweep(false, true);
   if (e == cudaSuccess) e = reduce();
   if (e == cudaSuccess) e = ctrl();
@@ -266,6 +321,29 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
     return cuda_status(e);
+  }
+  if (timing && hs->done) {
+    // sweeps that did work: the first Gramian sweep and passes 1 .. iters
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    for (size_t i = 0; i < nmarks; ++i) {
+      const SweepMark &mk = pool[i];
+      if (mk.pass > hs->iters) continue;
+      float ms = 0.0f;
+      if (cudaEventElapsedTime(&ms, mk.a, mk.b) != cudaSuccess) {
+        (void)cudaGetLastError();
+        continue;
+      }
+      g_timing.sweep_launches++;
+      g_timing.sweep_ms += ms;
+      g_timing.sweep_flops += mk.flops;
+      g_timing.sweep_bytes += mk.bytes;
+      if (mk.pass > 0) {
+        g_timing.fused_launches++;
+        g_timing.fused_ms += ms;
+        g_timing.fused_flops += mk.flops;
+        g_timing.fused_bytes += mk.bytes;
+      }
+    }
   }
   return result;
 }
@@ -447,6 +525,25 @@ cqr_status basis_free(cqr_basis *b) {
   free(b);
   if (e1 != cudaSuccess) return cuda_status(e1);
   return cuda_status(e2);
+}
+
+cqr_status cqr_timing_enable(int enable) {
+  g_timing_on.store(enable ? 1 : 0);
+  return CQR_OK;
+}
+
+cqr_status cqr_timing_read(cqr_timing *out) {
+  if (out == nullptr) return CQR_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(g_timing_mu);
+  *out = g_timing;
+  out->kernel_launches = g_launches.load();
+  return CQR_OK;
+}
+
+void cqr_timing_reset(void) {
+  std::lock_guard<std::mutex> lk(g_timing_mu);
+  g_timing = cqr_timing{};
+  g_launches.store(0);
 }
 
 int64_t basis_cols(const cqr_basis *b) { return b ? b->q : -1; }
