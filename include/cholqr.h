@@ -138,6 +138,32 @@ cqr_status cholqr_factor_host(const cqr_opts *opts, int64_t m, int64_t n, const 
                               int64_t lda, double *Q, int64_t ldq, double *R, int64_t ldr,
                               cqr_info *info, void *stream);
 
+/*
+ * cholqr_factor_noalloc -- cholqr_factor for callers that cannot allocate
+ * device memory.  The paper has no counterpart: this is a deployment variant.
+ * Some callers cannot call cudaMalloc: processes that have already handed all
+ * device memory to their own allocator (a framework caching allocator, or a
+ * serving loop that admits work against a fixed HBM budget), where a
+ * library-side allocation could fail or fragment their pool, and
+ * latency-critical loops that must never pay for, or risk the failure of, an
+ * allocation inside a call.  This entry point calls no allocating routine:
+ * all of its device scratch lives in one fixed 8 MiB array compiled into the
+ * library, which every GPU that loads the library holds until the process
+ * exits, and the status is read back into host stack memory.
+ *   Arguments, layout and results are those of cholqr_factor (same kernels,
+ *   same launch geometry).  Limit: n <= 64; larger n returns
+ *   CQR_ERR_CAPACITY without touching the device.
+ *   The first call on a device looks up the array's device address (with
+ *   that device current); make that first call before any stream capture.
+ *   All calls share the array and it keeps the last call's contents; each
+ *   call clears what must start at zero.  Calls whose work overlaps on the
+ *   GPU (for example on two streams at once) race on the array and must be
+ *   serialised by the caller.
+ */
+cqr_status cholqr_factor_noalloc(const cqr_opts *opts, int64_t m, int64_t n, const double *A,
+                                 int64_t lda, double *Q, int64_t ldq, double *R, int64_t ldr,
+                                 cqr_info *info, void *stream);
+
 /* Opaque growing orthonormal basis (Q_in m x q, R_in q x q) of Sec. 2.2. */
 typedef struct cqr_basis cqr_basis;
 

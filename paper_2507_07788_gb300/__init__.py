@@ -74,6 +74,8 @@ _SIGNATURES = {
                                 C.POINTER(Info), _VP]),
     "cholqr_factor_host": (C.c_int, [C.POINTER(Opts), _I64, _I64, _P, _I64, _P, _I64, _P, _I64,
                                      C.POINTER(Info), _VP]),
+    "cholqr_factor_noalloc": (C.c_int, [C.POINTER(Opts), _I64, _I64, _P, _I64, _P, _I64, _P,
+                                        _I64, C.POINTER(Info), _VP]),
     "basis_create": (C.c_int, [_I64, _I64, C.POINTER(Opts), _VP, C.POINTER(_VP)]),
     "basis_append": (C.c_int, [_VP, _I64, _P, _I64, C.POINTER(Info), _VP]),
     "basis_free": (C.c_int, [_VP]),
@@ -130,6 +132,12 @@ def cholqr_factor(opts, m, n, A, lda, Q, ldq, R, ldr, info, stream) -> int:
 
 def cholqr_factor_host(opts, m, n, A, lda, Q, ldq, R, ldr, info, stream) -> int:
     return lib().cholqr_factor_host(opts, m, n, A, lda, Q, ldq, R, ldr, info, stream)
+
+
+def cholqr_factor_noalloc(opts, m, n, A, lda, Q, ldq, R, ldr, info, stream) -> int:
+    """cholqr_factor with all scratch in the library's fixed device array (no
+    allocation; n <= 64); for callers that cannot allocate device memory."""
+    return lib().cholqr_factor_noalloc(opts, m, n, A, lda, Q, ldq, R, ldr, info, stream)
 
 
 def basis_create(m, n_max, opts, stream):
