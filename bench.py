@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=600_000)
+    ap.add_argument("--no-update", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--update-m", type=int, default=2_000_000)
+    ap.add_argument("--mixed-m", type=int, default=4_000_000)
     return ap.parse_args()
 
 
@@ -204,6 +208,78 @@ def time_factor(cq, torch, dA, dQ, dR, opts, steps, warmup):
     return e0.elapsed_time(e1) / steps, res
 
 
+def leg_update(cq, torch, m, p=8, count=32, seed=0):
+    """Basis growth (Alg. 2): 32 appends of 8 columns up to n = 256 at m rows.
+    block_k = Q_prev G 0.1 + N eta (eta log-uniform in [1e-12, 1]); the first
+    block is N.  Inputs are drawn on the device from a seeded generator; the
+    orthogonality of every new block against the whole basis is checked
+    right after its append."""
+    import numpy as np
+    from paper_2507_07788_gb300.synth import seed_for
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed_for(m, p, count, seed) & 0x7FFFFFFFFFFFFFFF)
+    rng = np.random.default_rng(seed_for(m, p, count, seed, 1))
+    b = cq.Basis(m, p * count)
+    blk = cq.colmajor(m, p)
+    times, worst, iters, shifts, statuses = [], 0.0, [], [], []
+    torch.cuda.synchronize()
+    for k in range(count):
+        N = torch.randn((p, m), generator=gen, device="cuda", dtype=torch.float64).t()
+        if k == 0:
+            blk.copy_(N)
+        else:
+            Qp = b.Q()
+            G = torch.randn((Qp.shape[1], p), generator=gen, device="cuda", dtype=torch.float64)
+            eta = 10.0 ** rng.uniform(-12.0, 0.0)
+            blk.copy_(Qp @ G * 0.1 + N * eta)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, info = b.append(blk)
+        times.append(time.perf_counter() - t0)
+        statuses.append(st)
+        iters.append(info["iters"])
+        shifts.append(info["shifts"])
+        Qa = b.Q()
+        Qn = Qa[:, -p:]
+        Gm = Qa.t() @ Qn
+        Gm[-p:, :] -= torch.eye(p, dtype=Gm.dtype, device=Gm.device)
+        worst = max(worst, float(torch.linalg.norm(Gm)))
+    q_end = b.cols
+    b.close()
+    bytes_alg = 0.0
+    tot = sum(times)
+    return {"workload": f"basis growth m={m}: {count} appends of p={p} to n={q_end}, blocks Q_prev G 0.1 + N eta",
+            "appends_per_s": count / tot, "ms_per_append_mean": 1e3 * tot / count,
+            "ms_per_append_last": 1e3 * times[-1], "rows_cols_per_s": m * q_end / tot,
+            "max_block_orth_frob": worst, "iters": iters, "shifts": shifts,
+            "status": sorted(set(statuses))}
+
+
+def leg_mixed(cq, torch, synth, m, n=128, kappas=(1e6, 1e10, 1e14), steps=3):
+    """Mixed precision vs plain FP64 at m x 128 on the same matrices."""
+    out = []
+    for kap in kappas:
+        A = synth.test_matrix(m, n, kap, rep=21)
+        dA = cq.to_colmajor(A)
+        del A
+        dQ, dR = cq.colmajor(m, n), cq.colmajor(n, n)
+        row = {"kappa": kap}
+        for prec, name in ((cq.PREC_FP64, "fp64"), (cq.PREC_MIXED, "mixed")):
+            o = cq.default_opts(precision=prec)
+            ms, res = time_factor(cq, torch, dA, dQ, dR, o, steps, 1)
+            Gm = dQ.t() @ dQ
+            loo = float(torch.linalg.norm(Gm - torch.eye(n, dtype=Gm.dtype, device=Gm.device)))
+            rrr = float(torch.linalg.norm(dA - dQ @ torch.triu(dR)) / torch.linalg.norm(dA))
+            row[name] = {"ms": ms, "rows_cols_per_s": m * n / (ms * 1e-3), "iters": res.info["iters"],
+                         "status": res.status, "loo_frob": loo, "rrr_frob": rrr,
+                         "sigma_first": res.info["sigma_first"]}
+        row["speedup_mixed_vs_fp64"] = row["fp64"]["ms"] / row["mixed"]["ms"]
+        out.append(row)
+        del dA, dQ, dR
+        torch.cuda.empty_cache()
+    return {"workload": f"mixed vs FP64 sCholQR3, m={m} n={n}, A=U diag(s) V^T", "rows": out}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -310,6 +386,12 @@ def run_ours(args):
                               "orth_frob": rs.info["orth_frob"]})
                 del dAs, dQs, dRs
         line["sweep"] = sweep
+
+    if rank == 0 and not args.no_update:
+        line["update"] = leg_update(cq, torch, args.update_m)
+
+    if rank == 0 and not args.no_mixed:
+        line["mixed"] = leg_mixed(cq, torch, synth, args.mixed_m)
 
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(A, min(args.cpu_rows, m), n)

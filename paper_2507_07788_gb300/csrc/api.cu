@@ -168,6 +168,18 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
   const int64_t rows_per_cta = ((tiles + G - 1) / G) * tile_rows;
   const int64_t E = (int64_t)q * p + (int64_t)p * (p + 1) / 2;
   const bool split = E > (int64_t)kThreads * 33;  // fused solve+Gram needs one entry group
+  // Mixed precision (factor only): the first Gramian from FP32 data, with the
+  // first shift sized for that roundoff:
+  //   sigma = 11 (n (2 u_in + d u_acc) + n (n + 1) u) ||X||,
+  // u_in = 2^-23 (truncation to FP32), u_acc = 2^-24, d = FP32 summation
+  // depth of one partial, u = 2^-53 for the FP64 Cholesky.
+  const bool mixed = (P.mode == MODE_FACTOR) && (P.o.precision == CQR_PREC_MIXED);
+  double mixed_coeff = 0.0;
+  if (mixed) {
+    const double u_in = 1.1920928955078125e-07, u_acc = 5.9604644775390625e-08;
+    mixed_coeff = 11.0 * ((double)p * (2.0 * u_in + kGram32Depth * u_acc) +
+                          (double)p * (p + 1.0) * kU64);
+  }
 
   Scratch s;
   CQR_TRY(scratch_alloc(s, q, p, G, E, str));
@@ -222,6 +234,18 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
       ++npass;
     }
     cudaError_t e = cudaSuccess;
+    if (!trsm && first && mixed) {
+      RowSweep g = a;
+      int tr32, lds32;
+      size_t smem32;
+      gram32_geometry(q, p, &tr32, &lds32, &smem32);
+      g.tile_rows = tr32;
+      g.lds = lds32;
+      e = launch_gram32(g, G, str);
+      g_launches++;
+      if (mk != nullptr) cudaEventRecord(mk->b, str);
+      return e;
+    }
     if (trsm && split) {
       // transform only, then a separate Gram sweep over the result
       RowSweep t = a;
@@ -256,6 +280,7 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
     c.max_escalations = P.o.max_escalations;
     c.stop_rule = P.o.stop_rule;
     c.tol = P.o.tol;
+    c.first_shift_coeff = mixed_coeff;
     c.C = s.C;
     c.Rt = s.Rt;
     c.Rdinv = s.Rdinv;

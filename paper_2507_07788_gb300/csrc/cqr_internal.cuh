@@ -73,6 +73,9 @@ struct Ctrl {
   int32_t mode;
   int32_t shift_policy, max_iter, min_iter, max_escalations, stop_rule;
   double tol;
+  // Mixed precision: when > 0 the first pass is always shifted by
+  // max(first_shift_coeff * ||X||, 2u) (the Gramian came from FP32 data).
+  double first_shift_coeff;
   const double *C;  // (q + p) x p, ld q + p
   double *Rt;       // p x p, ld p
   double *Rdinv;    // p
@@ -88,6 +91,13 @@ struct Ctrl {
 cudaError_t launch_init(double *R, int64_t ldr, int p, double *B, int64_t ldb, int q,
                         DevState *st, cudaStream_t s);
 cudaError_t launch_rowsweep(const RowSweep &a, int grid, cudaStream_t s);
+// FP32 Gramian sweep of the mixed-precision first pass (no solve): inputs
+// truncated to FP32 on the integer pipe, FP32 products summed per tile,
+// tiles combined with Kahan compensation, partials written as FP64.
+cudaError_t launch_gram32(const RowSweep &a, int grid, cudaStream_t s);
+void gram32_geometry(int q, int p, int *tile_rows, int *lds, size_t *smem);
+// Summation depth of one FP32 partial (tile rows + Kahan), for the shift.
+constexpr int kGram32Depth = 64 + 2;
 cudaError_t launch_reduce(const Reduce &a, cudaStream_t s);
 cudaError_t launch_ctrl(const Ctrl &a, cudaStream_t s);
 size_t ctrl_smem_bytes(int p);

@@ -234,10 +234,12 @@ __global__ void __launch_bounds__(kCtrlThreads) ctrl_kernel(Ctrl c) {
   double s_first = 0.0;
   bool fatal = false;
   if (c.mode == MODE_FACTOR) {
-    const bool shifted_first = (it == 0) && (c.shift_policy == CQR_SHIFT_SCHOLQR3);
+    const bool mixed_first = (it == 0) && (c.first_shift_coeff > 0.0);
+    const bool shifted_first =
+        mixed_first || ((it == 0) && (c.shift_policy == CQR_SHIFT_SCHOLQR3));
     if (shifted_first) {
       const double lam = norm_estimate(X, p, (float *)Rk, v, w, fred, red);
-      sigma = shift_alg1(c.m, p, lam);
+      sigma = mixed_first ? fmax(c.first_shift_coeff * lam, 2.0 * kU64) : shift_alg1(c.m, p, lam);
       ++shifts;
       s_first = sigma;
     }
