@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--update-m", type=int, default=2_000_000)
     ap.add_argument("--mixed-m", type=int, default=4_000_000)
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=512)
     return ap.parse_args()
 
 
@@ -280,6 +282,35 @@ def leg_mixed(cq, torch, synth, m, n=128, kappas=(1e6, 1e10, 1e14), steps=3):
     return {"workload": f"mixed vs FP64 sCholQR3, m={m} n={n}, A=U diag(s) V^T", "rows": out}
 
 
+def leg_serve(cq, torch, n_requests=512):
+    """Serving: Poisson arrivals (mean 2 ms, seed 0) of factor / append requests
+    over 64 device-resident bases (m log-uniform in [1e4, 2e6], capacity 256);
+    factors n in [8, 128], kappa log-uniform in [1e2, 1e14]; appends of 4..32
+    columns; 50/50 mix.  Latency = completion - arrival."""
+    from paper_2507_07788_gb300 import serve_driver as sd
+    t0 = time.perf_counter()
+    wl = sd.make_workload(n_bases=64, n_requests=n_requests, mean_gap_s=2e-3, seed=0)
+    sd.make_payloads(wl, seed=0)
+    bases = sd.make_bases(cq, wl)
+    gen_s = time.perf_counter() - t0
+    srv = cq.Server(slots=4, batch_max=16, hbm_budget_bytes=16 << 30, small_rows=262144)
+    info = sd.replay(cq, srv, bases, wl, realtime=True)
+    srv.close()
+    st = sd.latency_stats(wl)
+    st.update(info)
+    st["workload"] = (f"{n_requests} requests, Poisson mean 2 ms, 64 bases m log-uniform [1e4, 2e6], "
+                      "factor n U[8,128] kappa logU[1e2,1e14] / append p U[4,32], 50/50, FP64")
+    st["arrival_span_s"] = wl.reqs[-1].arrival
+    st["setup_s"] = gen_s
+    st["factors"] = sum(1 for r in wl.reqs if r.kind == "factor")
+    for b in bases:
+        b.close()
+    for r in wl.reqs:
+        r.payload = None
+    torch.cuda.empty_cache()
+    return st
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -392,6 +423,9 @@ def run_ours(args):
 
     if rank == 0 and not args.no_mixed:
         line["mixed"] = leg_mixed(cq, torch, synth, args.mixed_m)
+
+    if rank == 0 and not args.no_serve:
+        line["serve"] = leg_serve(cq, torch, args.serve_requests)
 
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(A, min(args.cpu_rows, m), n)

@@ -208,6 +208,64 @@ cqr_status basis_q(const cqr_basis *b, const double **Q, int64_t *ldq);
 cqr_status basis_r(const cqr_basis *b, const double **R, int64_t *ldr);
 
 /*
+ * Serving runtime (no counterpart in the paper; it serves the paper's two
+ * modes of use, M1 = full factorisation and M2 = repeated updates, Sec. 1).
+ * A server keeps many bases resident on the device and executes factor and
+ * append requests with continuous batching:
+ *   - requests are admitted in arrival order when their basis is idle, their
+ *     transient device memory fits `hbm_budget_bytes` and an executor is free;
+ *     requests on one basis run in submission order;
+ *   - factor requests and large appends run on `slots` worker streams
+ *     concurrently; appends of at most 32 columns to bases of at most
+ *     `small_rows` rows are batched: one persistent launch per step covers
+ *     every append of the batch, replayed from captured CUDA graphs;
+ *   - each result is bitwise the same alone and in the mix (a batched problem
+ *     uses the same per-CTA work and reduction order as alone).
+ * Timestamps are seconds on the server's steady clock (cqr_server_now).
+ */
+typedef struct cqr_server cqr_server;
+
+typedef struct cqr_server_opts {
+  int32_t slots;            /* worker streams for factors / large appends (4) */
+  int32_t batch_max;        /* appends per batched launch, 0 = no batching (16) */
+  int64_t hbm_budget_bytes; /* transient device memory of admitted requests (8 GiB) */
+  int64_t small_rows;       /* appends to bases with m <= small_rows are batched (262144) */
+} cqr_server_opts;
+
+typedef struct cqr_request_result {
+  int32_t status;     /* cqr_status of the request */
+  int32_t kind;       /* 0 factor, 1 append */
+  int32_t batched;    /* 1 if it ran in a batched launch */
+  int32_t batch_size; /* problems in that launch */
+  double t_submit;    /* arrival (submit) time */
+  double t_start;     /* admission time */
+  double t_done;      /* completion time */
+  cqr_info info;
+} cqr_request_result;
+
+void cqr_server_default_opts(cqr_server_opts *o);
+/* Creates a server on the current device (allocates the batch workspace,
+ * captures its graphs, starts the worker and batcher threads). */
+cqr_status cqr_server_create(const cqr_server_opts *opts, cqr_server **out);
+/* Factor request (M1): replaces basis b by the QR of A (device, b->m x n,
+ * lda >= m, caller-owned and unchanged until the request completes).
+ * n <= min(CQR_MAX_N, capacity).  *ticket identifies the request. */
+cqr_status cqr_server_submit_factor(cqr_server *s, cqr_basis *b, int64_t n, const double *A,
+                                    int64_t lda, const cqr_opts *opts, uint64_t *ticket);
+/* Append request (M2): basis_append(b, p, A_in) when admitted.  A_in stays
+ * caller-owned and unchanged until completion. */
+cqr_status cqr_server_submit_append(cqr_server *s, cqr_basis *b, int64_t p, const double *A_in,
+                                    int64_t lda, uint64_t *ticket);
+/* Blocks until the request completes and copies its result (out may be NULL). */
+cqr_status cqr_server_wait(cqr_server *s, uint64_t ticket, cqr_request_result *out);
+/* Blocks until every submitted request has completed. */
+cqr_status cqr_server_drain(cqr_server *s);
+/* Seconds since the server was created (the clock of the result stamps). */
+double cqr_server_now(const cqr_server *s);
+/* Drains, stops the threads and frees the server (not the bases). */
+cqr_status cqr_server_destroy(cqr_server *s);
+
+/*
  * Instrumentation (no counterpart in the paper).  When enabled, every call
  * brackets each launch of the row-sweep kernels (the Gramian sweep and the
  * fused solve + Gramian sweep) with CUDA events on the launching stream and,

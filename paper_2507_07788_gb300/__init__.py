@@ -57,6 +57,22 @@ class Timing(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ServerOpts(C.Structure):
+    _fields_ = [("slots", C.c_int32), ("batch_max", C.c_int32), ("hbm_budget_bytes", C.c_int64),
+                ("small_rows", C.c_int64)]
+
+
+class RequestResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("kind", C.c_int32), ("batched", C.c_int32),
+                ("batch_size", C.c_int32), ("t_submit", C.c_double), ("t_start", C.c_double),
+                ("t_done", C.c_double), ("info", Info)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "info"}
+        d["info"] = self.info.as_dict()
+        return d
+
+
 class CholQRError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         self.status = status
@@ -84,6 +100,15 @@ _SIGNATURES = {
     "basis_capacity": (_I64, [_VP]),
     "basis_q": (C.c_int, [_VP, C.POINTER(_VP), C.POINTER(_I64)]),
     "basis_r": (C.c_int, [_VP, C.POINTER(_VP), C.POINTER(_I64)]),
+    "cqr_server_default_opts": (None, [C.POINTER(ServerOpts)]),
+    "cqr_server_create": (C.c_int, [C.POINTER(ServerOpts), C.POINTER(_VP)]),
+    "cqr_server_submit_factor": (C.c_int, [_VP, _VP, _I64, _P, _I64, C.POINTER(Opts),
+                                           C.POINTER(C.c_uint64)]),
+    "cqr_server_submit_append": (C.c_int, [_VP, _VP, _I64, _P, _I64, C.POINTER(C.c_uint64)]),
+    "cqr_server_wait": (C.c_int, [_VP, C.c_uint64, C.POINTER(RequestResult)]),
+    "cqr_server_drain": (C.c_int, [_VP]),
+    "cqr_server_now": (C.c_double, [_VP]),
+    "cqr_server_destroy": (C.c_int, [_VP]),
     "cqr_timing_enable": (C.c_int, [C.c_int]),
     "cqr_timing_read": (C.c_int, [C.POINTER(Timing)]),
     "cqr_timing_reset": (None, []),
@@ -328,3 +353,59 @@ def _device_view(ptr: int, rows: int, cols: int, ld: int):
 
     flat = torch.as_tensor(_Arr(), device="cuda")
     return flat.as_strided((rows, cols), (1, ld))
+
+
+class Server:
+    """Continuous-batching request server over device-resident bases
+    (cqr_server_*).  Submissions return tickets; wait() returns the result
+    with its timestamps on the server clock."""
+
+    def __init__(self, slots=4, batch_max=16, hbm_budget_bytes=8 << 30, small_rows=262144):
+        o = ServerOpts(slots, batch_max, hbm_budget_bytes, small_rows)
+        h = _VP()
+        st = lib().cqr_server_create(C.byref(o), C.byref(h))
+        if st != OK:
+            raise CholQRError(st, "cqr_server_create")
+        self._h = h
+
+    def now(self) -> float:
+        return lib().cqr_server_now(self._h)
+
+    def submit_factor(self, basis: "Basis", A, opts: Opts | None = None) -> int:
+        lda = _check_colmajor(A, "A")
+        t = C.c_uint64()
+        st = lib().cqr_server_submit_factor(self._h, basis._h, A.shape[1], A.data_ptr(), lda,
+                                            C.byref(opts) if opts is not None else None, C.byref(t))
+        if st != OK:
+            raise CholQRError(st, "cqr_server_submit_factor")
+        return t.value
+
+    def submit_append(self, basis: "Basis", A_in) -> int:
+        lda = _check_colmajor(A_in, "A_in")
+        t = C.c_uint64()
+        st = lib().cqr_server_submit_append(self._h, basis._h, A_in.shape[1], A_in.data_ptr(), lda,
+                                            C.byref(t))
+        if st != OK:
+            raise CholQRError(st, "cqr_server_submit_append")
+        return t.value
+
+    def wait(self, ticket: int) -> dict:
+        r = RequestResult()
+        st = lib().cqr_server_wait(self._h, ticket, C.byref(r))
+        if st != OK:
+            raise CholQRError(st, "cqr_server_wait")
+        return r.as_dict()
+
+    def drain(self) -> None:
+        lib().cqr_server_drain(self._h)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().cqr_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -26,14 +26,6 @@
 
 using namespace cqr;
 
-struct cqr_basis {
-  int device;
-  int64_t m, n_max, q, ldq, ldr;
-  double *Q;
-  double *R;
-  cqr_opts opts;
-};
-
 namespace {
 
 constexpr int kPrelaunch = 3;

@@ -5,6 +5,15 @@
 
 #include "cholqr.h"
 
+// A growing basis (Q m x n_max with q valid columns, R n_max x n_max).
+struct cqr_basis {
+  int device;
+  int64_t m, n_max, q, ldq, ldr;
+  double *Q;
+  double *R;
+  cqr_opts opts;
+};
+
 namespace cqr {
 
 constexpr double kU64 = 1.1102230246251565404236316680908203125e-16;  // 2^-53
@@ -101,6 +110,18 @@ constexpr int kGram32Depth = 64 + 2;
 cudaError_t launch_reduce(const Reduce &a, cudaStream_t s);
 cudaError_t launch_ctrl(const Ctrl &a, cudaStream_t s);
 size_t ctrl_smem_bytes(int p);
+
+// Batched persistent variants (descriptor arrays and counts in device
+// memory, so a captured CUDA graph can be replayed with new contents).  A
+// problem in a batch runs the same per-CTA work, in the same order, as alone.
+constexpr int kBatchEPT = 33;  // entries per thread; problems need E <= 256 * 33
+cudaError_t launch_rowsweep_batched(const RowSweep *reqs, const int *item_req, const int *item_cta,
+                                    const int *nitems, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_reduce_batched(const Reduce *reqs, const int *item_req, const int *item_chunk,
+                                  const int *nitems, int grid, cudaStream_t s);
+cudaError_t launch_ctrl_batched(const Ctrl *reqs, const int *nreq, int grid, size_t smem,
+                                cudaStream_t s);
+cudaError_t launch_init_batched(const Ctrl *reqs, const int *nreq, int grid, cudaStream_t s);
 
 // Geometry of a row sweep for the given widths: tile rows, shared stride and
 // bytes of dynamic shared memory.

@@ -162,10 +162,10 @@ __device__ __forceinline__ double shift_alg2_first(int64_t m, int q, int p, doub
   return c * kU64 * normX;
 }
 
-__global__ void __launch_bounds__(kCtrlThreads) ctrl_kernel(Ctrl c) {
+// One control step of one problem; shared by the single and batched kernels.
+__device__ void ctrl_body(const Ctrl &c, double *sm) {
   DevState *st = c.st;
   if (st->done) return;
-  extern __shared__ double sm[];
   __shared__ double red[32];
   __shared__ float fred[32];
   __shared__ int s_fail;
@@ -342,6 +342,33 @@ __global__ void __launch_bounds__(kCtrlThreads) ctrl_kernel(Ctrl c) {
     st->proj_frob = projf;
     st->active = 1;
   }
+}
+
+__global__ void __launch_bounds__(kCtrlThreads) ctrl_kernel(Ctrl c) {
+  extern __shared__ double sm[];
+  ctrl_body(c, sm);
+}
+
+// Batched control: CTA b handles problems b, b + grid, ...
+__global__ void __launch_bounds__(kCtrlThreads) ctrl_batched_kernel(const Ctrl *reqs, const int *nreq) {
+  extern __shared__ double sm[];
+  const int n = *nreq;
+  for (int r = blockIdx.x; r < n; r += gridDim.x) {
+    const Ctrl c = reqs[r];
+    ctrl_body(c, sm);
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_ctrl_batched(const Ctrl *reqs, const int *nreq, int grid, size_t smem,
+                                cudaStream_t s) {
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaFuncSetAttribute(ctrl_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_done = true;
+  }
+  ctrl_batched_kernel<<<grid, kCtrlThreads, smem, s>>>(reqs, nreq);
+  return cudaGetLastError();
 }
 
 size_t ctrl_smem_bytes(int p) {

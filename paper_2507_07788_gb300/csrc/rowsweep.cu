@@ -38,18 +38,20 @@ __device__ __forceinline__ void entry_columns(int64_t e, int q, int p, int &ca, 
   }
 }
 
+// The work of CTA (bx, by) of one sweep.  Shared by the single-problem
+// kernel and the batched persistent kernel, so that a problem computes the
+// same partial sums in the same order whether it runs alone or in a batch.
 template <int EPT>
-__global__ void __launch_bounds__(kThreads) rowsweep_kernel(RowSweep a) {
+__device__ __forceinline__ void rowsweep_body(const RowSweep &a, int bx, int by, double *tile) {
   if (a.st != nullptr && a.st->done) return;
-  extern __shared__ double tile[];
   const int t = threadIdx.x;
   const int q = a.q, p = a.p, W = q + p, lds = a.lds, TR = a.tile_rows;
-  const int64_t row0 = (int64_t)blockIdx.x * a.rows_per_cta;
+  const int64_t row0 = (int64_t)bx * a.rows_per_cta;
   const int64_t row1 = min(a.m, row0 + a.rows_per_cta);
 
   uint32_t idx[EPT];
   double acc[EPT];
-  const int64_t ebase = (int64_t)blockIdx.y * (kThreads * EPT);
+  const int64_t ebase = (int64_t)by * (kThreads * EPT);
 #pragma unroll
   for (int k = 0; k < EPT; ++k) {
     const int64_t e = ebase + t + (int64_t)k * kThreads;
@@ -106,15 +108,35 @@ __global__ void __launch_bounds__(kThreads) rowsweep_kernel(RowSweep a) {
 #pragma unroll
   for (int k = 0; k < EPT; ++k) {
     const int64_t e = ebase + t + (int64_t)k * kThreads;
-    if (e < a.E) a.partials[(int64_t)blockIdx.x * a.E + e] = acc[k];
+    if (e < a.E) a.partials[(int64_t)bx * a.E + e] = acc[k];
+  }
+}
+
+template <int EPT>
+__global__ void __launch_bounds__(kThreads) rowsweep_kernel(RowSweep a) {
+  extern __shared__ double tile[];
+  rowsweep_body<EPT>(a, blockIdx.x, blockIdx.y, tile);
+}
+
+// Batched persistent sweep: work item w is CTA item_cta[w] of problem
+// item_req[w]; a fixed grid loops over the *nitems items.
+template <int EPT>
+__global__ void __launch_bounds__(kThreads)
+    rowsweep_batched_kernel(const RowSweep *reqs, const int *item_req, const int *item_cta,
+                            const int *nitems) {
+  extern __shared__ double tile[];
+  const int n = *nitems;
+  for (int w = blockIdx.x; w < n; w += gridDim.x) {
+    const RowSweep a = reqs[item_req[w]];
+    rowsweep_body<EPT>(a, item_cta[w], 0, tile);
+    __syncthreads();
   }
 }
 
 // Fixed-order sum of the per-CTA partials: C(e) = sum_{g=0}^{G-1} P[g][e];
 // the Y^T Y part is written to both triangles.
-__global__ void reduce_kernel(Reduce a) {
+__device__ __forceinline__ void reduce_body(const Reduce &a, int64_t e) {
   if (a.st != nullptr && a.st->done) return;
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= a.E) return;
   double s = 0.0;
   for (int g = 0; g < a.G; ++g) s += a.partials[(int64_t)g * a.E + e];
@@ -133,10 +155,21 @@ __global__ void reduce_kernel(Reduce a) {
   }
 }
 
-__global__ void init_kernel(double *R, int64_t ldr, int p, double *B, int64_t ldb, int q,
-                            DevState *st) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int nt = gridDim.x * blockDim.x;
+__global__ void reduce_kernel(Reduce a) {
+  reduce_body(a, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// Batched reduction: work item w covers entries [64 chunk, 64 chunk + 64) of
+// problem item_req[w] (chunk = item_chunk[w]).
+__global__ void reduce_batched_kernel(const Reduce *reqs, const int *item_req, const int *item_chunk,
+                                      const int *nitems) {
+  const int n = *nitems;
+  for (int w = blockIdx.x; w < n; w += gridDim.x)
+    reduce_body(reqs[item_req[w]], (int64_t)item_chunk[w] * blockDim.x + threadIdx.x);
+}
+
+__device__ __forceinline__ void init_body(double *R, int64_t ldr, int p, double *B, int64_t ldb,
+                                          int q, DevState *st, int t, int nt) {
   for (int e = t; e < p * p; e += nt) {
     const int i = e % p, j = e / p;
     R[i + (int64_t)j * ldr] = (i == j) ? 1.0 : 0.0;
@@ -146,6 +179,21 @@ __global__ void init_kernel(double *R, int64_t ldr, int p, double *B, int64_t ld
   if (t == 0) {
     DevState z = {};
     *st = z;
+  }
+}
+
+__global__ void init_kernel(double *R, int64_t ldr, int p, double *B, int64_t ldb, int q,
+                            DevState *st) {
+  init_body(R, ldr, p, B, ldb, q, st, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+// Batched init: CTA r (grid-stride) initialises problem r from its control
+// descriptor (R block = I, B block = 0, state cleared).
+__global__ void init_batched_kernel(const Ctrl *reqs, const int *nreq) {
+  const int n = *nreq;
+  for (int r = blockIdx.x; r < n; r += gridDim.x) {
+    const Ctrl c = reqs[r];
+    init_body(c.R, c.ldr, c.p, c.B, c.ldb, c.q, c.st, threadIdx.x, blockDim.x);
   }
 }
 
@@ -208,6 +256,29 @@ cudaError_t launch_rowsweep(const RowSweep &a, int grid, cudaStream_t s) {
     case 16: return launch_ept<16>(a, g, smem, s);
     default: return launch_ept<33>(a, g, smem, s);
   }
+}
+
+cudaError_t launch_rowsweep_batched(const RowSweep *reqs, const int *item_req, const int *item_cta,
+                                    const int *nitems, int grid, size_t smem, cudaStream_t s) {
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaFuncSetAttribute(rowsweep_batched_kernel<kBatchEPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+    attr_done = true;
+  }
+  rowsweep_batched_kernel<kBatchEPT><<<grid, kThreads, smem, s>>>(reqs, item_req, item_cta, nitems);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_batched(const Reduce *reqs, const int *item_req, const int *item_chunk,
+                                  const int *nitems, int grid, cudaStream_t s) {
+  reduce_batched_kernel<<<grid, 64, 0, s>>>(reqs, item_req, item_chunk, nitems);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_batched(const Ctrl *reqs, const int *nreq, int grid, cudaStream_t s) {
+  init_batched_kernel<<<grid, 256, 0, s>>>(reqs, nreq);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_reduce(const Reduce &a, cudaStream_t s) {
