@@ -78,8 +78,15 @@ typedef struct cqr_opts {
   int32_t shift_policy;    /* CQR_SHIFT_*                    (SCHOLQR3) */
   int32_t stop_rule;       /* CQR_STOP_*                     (FROB_TOL) */
   int32_t max_escalations; /* cap on x10 shift escalations           (40) */
-  int32_t reserved;
+  int32_t emulation;       /* CQR_EMU_*                          (AUTO) */
 } cqr_opts;
+
+/* How FP64 Gramians are formed.  CQR_EMU_AUTO: on the tensor cores with the
+ * Ozaki splitting scheme (exact digit products, FP64-class accuracy) where
+ * the kernels support it (cholqr_factor and cholqr_gram with n <= 64), FP64
+ * CUDA cores elsewhere (basis_append always).  CQR_EMU_OFF: FP64 CUDA cores
+ * everywhere. */
+enum { CQR_EMU_AUTO = 0, CQR_EMU_OFF = 1 };
 
 /* Per-call report.  orth_frob is ||X - I||_F of the last Gramian formed
  * (for basis_append: of the projected Gramian Q^T Q - B~^T B~), proj_frob is
@@ -127,6 +134,18 @@ const char *cqr_status_string(int status);
 cqr_status cholqr_factor(const cqr_opts *opts, int64_t m, int64_t n, const double *A,
                          int64_t lda, double *Q, int64_t ldq, double *R, int64_t ldr,
                          cqr_info *info, void *stream);
+
+/*
+ * cholqr_gram -- the Gramian X = A^T A of Alg. 1 line 3, formed by the same
+ * row sweep and fixed-order reduction as the factorisation's first pass
+ * (tensor-core digit arithmetic for n <= 64 unless opts->emulation is
+ * CQR_EMU_OFF; FP64 CUDA cores otherwise).
+ *   A, lda    device, m x n, lda >= m (read only).
+ *   X, ldx    device, n x n output (both triangles), ldx >= n.
+ *   1 <= n <= CQR_MAX_N, m >= 1.
+ */
+cqr_status cholqr_gram(const cqr_opts *opts, int64_t m, int64_t n, const double *A, int64_t lda,
+                       double *X, int64_t ldx, void *stream);
 
 /*
  * cholqr_factor_host -- the same factorisation on HOST buffers: copies A to

@@ -28,6 +28,7 @@ ERR_INVALID, ERR_BREAKDOWN, ERR_OOM, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT = -1, -
 SHIFT_SCHOLQR3, SHIFT_ON_BREAKDOWN, SHIFT_NONE = 0, 1, 2
 STOP_FROB_TOL, STOP_U_SQRT_N = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
+EMU_AUTO, EMU_OFF = 0, 1
 MAX_N, MAX_BASIS = 128, 1024
 
 
@@ -35,7 +36,7 @@ class Opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("min_iter", C.c_int32),
                 ("update_min_iter", C.c_int32), ("precision", C.c_int32),
                 ("shift_policy", C.c_int32), ("stop_rule", C.c_int32),
-                ("max_escalations", C.c_int32), ("reserved", C.c_int32)]
+                ("max_escalations", C.c_int32), ("emulation", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -90,6 +91,7 @@ _SIGNATURES = {
                                 C.POINTER(Info), _VP]),
     "cholqr_factor_host": (C.c_int, [C.POINTER(Opts), _I64, _I64, _P, _I64, _P, _I64, _P, _I64,
                                      C.POINTER(Info), _VP]),
+    "cholqr_gram": (C.c_int, [C.POINTER(Opts), _I64, _I64, _P, _I64, _P, _I64, _VP]),
     "cholqr_factor_noalloc": (C.c_int, [C.POINTER(Opts), _I64, _I64, _P, _I64, _P, _I64, _P,
                                         _I64, C.POINTER(Info), _VP]),
     "basis_create": (C.c_int, [_I64, _I64, C.POINTER(Opts), _VP, C.POINTER(_VP)]),
@@ -261,6 +263,18 @@ def factor(A, Q=None, R=None, opts: Opts | None = None, stream=None, check=True)
     if check and st < 0:
         raise CholQRError(st, "cholqr_factor")
     return Result(Q, R, st, info.as_dict())
+
+
+def gram(A, opts: Opts | None = None, stream=None):
+    """X = A^T A of a column-major CUDA tensor through cholqr_gram."""
+    lda = _check_colmajor(A, "A")
+    m, n = A.shape
+    X = colmajor(n, n, device=A.device)
+    st = lib().cholqr_gram(C.byref(opts) if opts is not None else None, m, n, A.data_ptr(), lda,
+                           X.data_ptr(), n, _stream_ptr(stream))
+    if st != OK:
+        raise CholQRError(st, "cholqr_gram")
+    return X
 
 
 def factor_host(A, opts: Opts | None = None, stream=None, check=True) -> Result:

@@ -42,6 +42,39 @@ struct SweepMark {
   double flops, bytes;
 };
 
+// Per host thread: an auxiliary stream and events for the chunked pass
+// pipeline (FP64 row solve of chunk c+1 on the caller's stream overlapping
+// the tensor-core Gramian of chunk c on the auxiliary stream).
+struct AuxCtx {
+  cudaStream_t aux = nullptr;
+  cudaEvent_t done = nullptr;
+  std::vector<cudaEvent_t> ev;
+};
+
+AuxCtx *aux_ctx(int nchunks) {
+  thread_local AuxCtx c;
+  if (c.aux == nullptr) {
+    if (cudaStreamCreateWithFlags(&c.aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming) != cudaSuccess) {
+      (void)cudaGetLastError();
+      c.aux = nullptr;
+      return nullptr;
+    }
+  }
+  while ((int)c.ev.size() < nchunks) {
+    cudaEvent_t e;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return nullptr;
+    }
+    c.ev.push_back(e);
+  }
+  return &c;
+}
+
+constexpr int kMaxChunks = 8;
+constexpr int64_t kMinChunkRows = 78 * 1024;
+
 // Thread-local pool of event pairs for the sweep marks of one call.
 std::vector<SweepMark> &marks_pool() {
   thread_local std::vector<SweepMark> pool;
@@ -68,7 +101,8 @@ bool opts_valid(const cqr_opts &o) {
          o.update_min_iter >= 0 && o.max_escalations >= 0 && o.max_escalations <= 400 &&
          (o.precision == CQR_PREC_FP64 || o.precision == CQR_PREC_MIXED) &&
          o.shift_policy >= CQR_SHIFT_SCHOLQR3 && o.shift_policy <= CQR_SHIFT_NONE &&
-         (o.stop_rule == CQR_STOP_FROB_TOL || o.stop_rule == CQR_STOP_U_SQRT_N);
+         (o.stop_rule == CQR_STOP_FROB_TOL || o.stop_rule == CQR_STOP_U_SQRT_N) &&
+         (o.emulation == CQR_EMU_AUTO || o.emulation == CQR_EMU_OFF);
 }
 
 // Pinned host mirror of the device state, one per host thread.
@@ -173,8 +207,36 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
                           (double)p * (p + 1.0) * kU64);
   }
 
+  // Tensor-core Gramian (Ozaki digits) for factorisations with n <= 64.
+  // (Updates, including the first block of an empty basis, keep the FP64
+  // sweep so that basis_append and the batched serving path agree bitwise.)
+  const bool oz = (P.mode == MODE_FACTOR) && (p <= kOzMaxN) && (P.o.emulation == CQR_EMU_AUTO);
+  const int Goz = oz ? ozgram_grid(P.m) : 0;
+  int64_t oz_rows_per_cta = 0;
+  if (oz) {
+    const int64_t tr = ozgram_tile_rows();
+    const int64_t tiles = (P.m + tr - 1) / tr;
+    oz_rows_per_cta = ((tiles + Goz - 1) / Goz) * tr;
+  }
+  // Chunked pipeline of the fused passes for large m (see AuxCtx).
+  const int nchunks = oz ? (int)std::max<int64_t>(1, std::min<int64_t>(kMaxChunks, P.m / kMinChunkRows)) : 1;
+  int64_t chunk_rows = 0, chunk_rpc = 0;
+  int Gc = 0;
+  if (oz && nchunks >= 2) {
+    const int64_t tr = ozgram_tile_rows();
+    chunk_rows = (((P.m + nchunks - 1) / nchunks + tr - 1) / tr) * tr;
+    Gc = ozgram_grid(chunk_rows);
+    const int64_t tiles = chunk_rows / tr;
+    chunk_rpc = ((tiles + Gc - 1) / Gc) * tr;
+  }
+  AuxCtx *ax = (nchunks >= 2) ? aux_ctx(nchunks) : nullptr;
+  const int64_t oz_parts = oz ? std::max<int64_t>((int64_t)Goz, (int64_t)nchunks * Gc) * p * p : 0;
+  const int64_t part_elems = std::max<int64_t>(E, (oz_parts + G - 1) / G);
+  bool last_oz = false;  // which reduction the last sweep needs
+  int last_oz_G = Goz;   // and over how many partials
+
   Scratch s;
-  CQR_TRY(scratch_alloc(s, q, p, G, E, str));
+  CQR_TRY(scratch_alloc(s, q, p, G, part_elems, str));
   DevState *hs = host_state();
   cqr_status result = CQR_OK;
   const bool timing = g_timing_on.load() != 0;
@@ -226,6 +288,52 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
       ++npass;
     }
     cudaError_t e = cudaSuccess;
+    last_oz = false;
+    if (oz && trsm && nchunks >= 2 && ax != nullptr) {
+      // chunked pipeline: solve chunk c on str; its Gramian on the aux stream
+      for (int c = 0; c < nchunks && e == cudaSuccess; ++c) {
+        const int64_t r0 = (int64_t)c * chunk_rows;
+        const int64_t rc = std::min(chunk_rows, P.m - r0);
+        if (rc <= 0) break;
+        RowSweep tr = a;
+        tr.m = rc;
+        tr.Yin = a.Yin + r0;
+        tr.Yout = a.Yout + r0;
+        e = launch_trsm_rows(tr, trsm_rows_grid(rc), str);
+        g_launches++;
+        if (e == cudaSuccess) e = cudaEventRecord(ax->ev[c], str);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ax->aux, ax->ev[c], 0);
+        RowSweep z = a;
+        z.m = rc;
+        z.Yin = a.Yout + r0;
+        z.ldyin = a.ldyout;
+        z.do_trsm = 0;
+        z.partials = s.partials + (int64_t)c * Gc * p * p;
+        z.rows_per_cta = chunk_rpc;
+        z.E = (int64_t)p * p;
+        if (e == cudaSuccess) e = launch_ozgram(z, Gc, ax->aux);
+        g_launches++;
+      }
+      // chunks past the end of m (none with the sizing above) would leave
+      // stale partials; all nchunks * Gc partials are written when rc > 0
+      if (e == cudaSuccess) e = cudaEventRecord(ax->done, ax->aux);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(str, ax->done, 0);
+      last_oz = true;
+      last_oz_G = nchunks * Gc;
+      if (mk != nullptr) cudaEventRecord(mk->b, str);
+      return e;
+    }
+    if (oz && !(first && !trsm && mixed)) {
+      RowSweep z = a;
+      z.rows_per_cta = oz_rows_per_cta;
+      z.E = (int64_t)p * p;
+      e = launch_ozgram(z, Goz, str);
+      g_launches++;
+      last_oz = true;
+      last_oz_G = Goz;
+      if (mk != nullptr) cudaEventRecord(mk->b, str);
+      return e;
+    }
     if (!trsm && first && mixed) {
       RowSweep g = a;
       int tr32, lds32;
@@ -256,8 +364,9 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
     return e;
   };
   auto reduce = [&]() -> cudaError_t {
-    Reduce r{s.partials, G, E, q, p, s.C, s.st};
     g_launches++;
+    if (last_oz) return launch_reduce_oz(s.partials, last_oz_G, p, s.C, s.st, str);
+    Reduce r{s.partials, G, E, q, p, s.C, s.st};
     return launch_reduce(r, str);
   };
   auto ctrl = [&]() -> cudaError_t {
@@ -379,7 +488,7 @@ void cqr_default_opts(cqr_opts *o) {
   o->shift_policy = CQR_SHIFT_SCHOLQR3;
   o->stop_rule = CQR_STOP_FROB_TOL;
   o->max_escalations = 40;
-  o->reserved = 0;
+  o->emulation = CQR_EMU_AUTO;
 }
 
 const char *cqr_status_string(int status) {
@@ -430,6 +539,64 @@ cqr_status cholqr_factor(const cqr_opts *opts, int64_t m, int64_t n, const doubl
   P.min_iter = o.min_iter;
   P.o = o;
   return run(P, info, (cudaStream_t)stream);
+}
+
+cqr_status cholqr_gram(const cqr_opts *opts, int64_t m, int64_t n, const double *A, int64_t lda,
+                       double *X, int64_t ldx, void *stream) {
+  cqr_opts o;
+  cqr_default_opts(&o);
+  if (opts != nullptr) o = *opts;
+  if (!opts_valid(o)) return CQR_ERR_INVALID;
+  if (n < 1 || n > CQR_MAX_N || m < 1 || lda < m || ldx < n) return CQR_ERR_INVALID;
+  if (A == nullptr || X == nullptr) return CQR_ERR_INVALID;
+  cudaStream_t str = (cudaStream_t)stream;
+  const int p = (int)n;
+  const bool oz = (p <= kOzMaxN) && (o.emulation == CQR_EMU_AUTO);
+  int tile_rows, lds;
+  size_t smem;
+  rowsweep_geometry(0, p, &tile_rows, &lds, &smem);
+  const int G = oz ? ozgram_grid(m) : rowsweep_grid(m, tile_rows);
+  const int64_t tr = oz ? ozgram_tile_rows() : tile_rows;
+  const int64_t tiles = (m + tr - 1) / tr;
+  const int64_t rows_per_cta = ((tiles + G - 1) / G) * tr;
+  const int64_t E = oz ? (int64_t)p * p : (int64_t)p * (p + 1) / 2;
+  Scratch s;
+  CQR_TRY(scratch_alloc(s, 0, p, G, E, str));
+  RowSweep a{};
+  a.m = m;
+  a.q = 0;
+  a.p = p;
+  a.Yin = A;
+  a.ldyin = lda;
+  a.partials = s.partials;
+  a.E = E;
+  a.rows_per_cta = rows_per_cta;
+  a.tile_rows = tile_rows;
+  a.lds = lds;
+  a.do_trsm = 0;
+  a.st = nullptr;
+  cudaError_t e = oz ? launch_ozgram(a, G, str) : launch_rowsweep(a, G, str);
+  g_launches++;
+  if (e == cudaSuccess) {
+    if (oz) {
+      e = launch_reduce_oz(s.partials, G, p, s.C, nullptr, str);
+    } else {
+      Reduce r{s.partials, G, E, 0, p, s.C, nullptr};
+      e = launch_reduce(r, str);
+    }
+    g_launches++;
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync(X, sizeof(double) * ldx, s.C, sizeof(double) * p, sizeof(double) * p, p,
+                          cudaMemcpyDeviceToDevice, str);
+  cudaError_t ef = cudaFreeAsync(s.base, str);
+  if (e == cudaSuccess) e = ef;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(str);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return cuda_status(e);
+  }
+  return CQR_OK;
 }
 
 cqr_status cholqr_factor_host(const cqr_opts *opts, int64_t m, int64_t n, const double *A,

@@ -123,6 +123,20 @@ cudaError_t launch_ctrl_batched(const Ctrl *reqs, const int *nreq, int grid, siz
                                 cudaStream_t s);
 cudaError_t launch_init_batched(const Ctrl *reqs, const int *nreq, int grid, cudaStream_t s);
 
+// Tensor-core (Ozaki digit) Gramian sweep for q = 0, p <= 64: optional FP64
+// row solve, then the exact-digit Gramian of the tile; per-CTA partials are
+// full p x p (ld p) and reduce_oz returns X = sum_g (P_g + P_g^T).
+cudaError_t launch_ozgram(const RowSweep &a, int grid, cudaStream_t s);
+cudaError_t launch_reduce_oz(const double *partials, int G, int n, double *C, const DevState *st,
+                             cudaStream_t s);
+int ozgram_grid(int64_t m);
+int ozgram_tile_rows();
+constexpr int kOzMaxN = 64;
+// FP64 row solve Q = Y R~^{-1} alone (one thread per row, registers); shares
+// SMs with ozgram_kernel when the two run on different streams.
+cudaError_t launch_trsm_rows(const RowSweep &a, int grid, cudaStream_t s);
+int trsm_rows_grid(int64_t m);
+
 // Geometry of a row sweep for the given widths: tile rows, shared stride and
 // bytes of dynamic shared memory.
 void rowsweep_geometry(int q, int p, int *tile_rows, int *lds, size_t *smem);

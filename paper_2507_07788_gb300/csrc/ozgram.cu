@@ -1,0 +1,459 @@
+// Gramian sweep on the tensor cores with exact digit arithmetic (the Ozaki
+// splitting scheme: Ozaki, Ogita, Oishi, Rump, "Error-free transformations of
+// matrix multiplication by using fast routines of matrix multiplication and
+// its applications", Numer. Algorithms 59, 2012), for the FP64 Gramian
+// X = Y^T Y of Alg. 1 lines 3 and 11.
+//
+// Why: GB300 retires ~1.6 FP64 FMAs per SM per clock but ~570 dense bf16
+// TFLOP/s through mma.sync, so the Gramian is computed from bf16 "digits"
+// whose products the tensor cores form and add exactly.
+//
+// Representation (per 64-row tile, per column j):
+//   E_j = running maximum of the biased exponent of column j over the rows
+//   this CTA has seen; every element is written as
+//     x = sign * V * 2^(E_j - 1078),   V = sum_{t=1..8} d_t 2^(56 - 7 t),
+//   with 8 digits d_t in [0, 127] (56 bits relative to the column maximum,
+//   truncated).  A digit with its sign is an integer of magnitude <= 127,
+//   exact in bf16.
+// Products: x_i x_j = 2^(E_i + E_j - 2156) sum_{s,t} d_s(i) d_t(j) 2^(112 - 7(s+t)).
+//   Orders s + t <= 9 are kept (the rest lies below 2^-53 of the leading
+//   term).  Using P_st^T = P_ts, only s <= t is formed; the CTA stores
+//   P = sum_d (B_d + C_d / 2) w_d with B_d = sum_{s<t, s+t=d} P_st and
+//   C_d = P_{d/2,d/2}, and the reduction returns X = P + P^T.
+// Exactness: one mma.sync accumulator sums at most four digit pairs over 64
+//   rows, |sum| <= 4 * 64 * 127^2 < 2^22, so FP32 accumulation is exact and
+//   the FP32 -> int conversion is the exact magic-number add.  Orders are
+//   combined in two int64 words per entry (orders 2..5 and 6..9), summed
+//   over the CTA's tiles (rescaled by right shifts when a column's running
+//   exponent grows), and rounded to FP64 once per CTA.
+// Non-finite inputs make every partial of the CTA NaN (the control kernel
+// then reports a breakdown, as the FP64 path does).
+#include <algorithm>
+
+#include <cuda_bf16.h>
+
+#include "cqr_internal.cuh"
+
+namespace cqr {
+
+namespace {
+
+constexpr int kOzTR = 64;            // tile rows (one exact accumulation window)
+constexpr int kOzLDK = kOzTR + 8;    // bf16 stride of a digit-plane column
+constexpr int kOzThreads = 256;      // 8 warps, one CTA per SM
+constexpr int kOzWarps = kOzThreads / 32;
+constexpr int kOzDigits = 8;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2,
+                                        uint32_t &r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+
+__device__ __forceinline__ void ldsm_x2(uint32_t addr, uint32_t &r0, uint32_t &r1) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n"
+               : "=r"(r0), "=r"(r1)
+               : "r"(addr));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// Asynchronous 8-byte global -> shared copy; src_bytes = 0 zero-fills.
+__device__ __forceinline__ void cp_async8(void *dst, const void *src, int src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(smem_u32(dst)), "l"(src),
+               "r"(src_bytes));
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Exact FP32 -> int for integer-valued |v| < 2^22 (magic-number add).
+__device__ __forceinline__ int f2i_exact(float v) {
+  return __float_as_int(v + 12582912.0f) - 0x4B400000;
+}
+
+// bf16 bit pattern of the integer d in [0, 127] with sign bit s (exact).
+__device__ __forceinline__ uint32_t digit_bf16(uint32_t d, uint32_t s) {
+  const float f = __int_as_float(0x4B000000 | (int)d) - 8388608.0f;
+  return ((uint32_t)__float_as_int(f) >> 16) | (s << 15);
+}
+
+// Biased exponent used for alignment (subnormals and zeros count as 1).
+__device__ __forceinline__ int align_exp(unsigned long long b) {
+  const int ef = (int)((b >> 52) & 0x7FF);
+  return ef ? ef : 1;
+}
+
+// Rescales an accumulator pair (value = hi * 2^28 u + lo * u) to a unit 2^D
+// times larger when a column's running exponent grows by D: the bits that
+// leave hi move into lo before lo is shifted, so only bits below the new
+// lo unit are dropped.  For D >= 62 the old value lies below 2^-62 of the
+// entry's new magnitude and is dropped.
+__device__ __forceinline__ void shift_pair(long long &hi, long long &lo, int D) {
+  if (D <= 0) return;
+  if (D >= 62) {
+    hi = 0;
+    lo = 0;
+    return;
+  }
+  const long long q = hi >> D;
+  const long long rm = hi - (q << D);  // 0 <= rm < 2^D
+  if (D <= 34) lo = (lo + (rm << 28)) >> D;
+  else lo = (lo >> D) + (rm >> (D - 28));
+  hi = q;
+}
+
+// Orders 2..9 split into g groups (each warp unit handles one group).
+// The order sets are balanced by the number of digit pairs they contain.
+__device__ __forceinline__ int group_orders(int g, int grp, int (&ord)[8]) {
+  // order lists for g = 1, 2, 4, 8
+  if (g == 1) {
+    for (int k = 0; k < 8; ++k) ord[k] = 2 + k;
+    return 8;
+  }
+  if (g == 2) {
+    const int o[2][4] = {{2, 4, 6, 8}, {3, 5, 7, 9}};
+    for (int k = 0; k < 4; ++k) ord[k] = o[grp][k];
+    return 4;
+  }
+  const int o[4][2] = {{2, 9}, {3, 8}, {4, 7}, {5, 6}};
+  ord[0] = o[grp][0];
+  ord[1] = o[grp][1];
+  return 2;
+}
+
+}  // namespace
+
+struct OzGeom {
+  int NI, NJ, JB, groups, units;
+};
+
+// Work units: strips of 16 output rows x JB output columns, times groups of
+// orders; NT in {16, 32, 64} gives 4, 8 and 8 units (one per warp).
+__host__ __device__ inline OzGeom oz_geom(int NT) {
+  OzGeom g;
+  g.JB = (NT >= 32) ? 32 : 16;
+  g.NI = NT / 16;
+  g.NJ = NT / g.JB;
+  const int strips = g.NI * g.NJ;
+  g.groups = strips >= 8 ? 1 : (strips >= 2 ? 4 : 4);
+  g.units = strips * g.groups;
+  return g;
+}
+
+// One CTA: rows [bx * rows_per_cta, ...) in tiles of 64; optional FP64 row
+// solve (Alg. 1 line 9) before the Gramian of the tile.  Writes the CTA's
+// partial P (n x n, ld n) to partials[bx * n * n].
+template <int NT>
+__global__ void __launch_bounds__(kOzThreads, 1) ozgram_kernel(RowSweep a) {
+  if (a.st != nullptr && a.st->done) return;
+  constexpr int JB = (NT >= 32) ? 32 : 16;
+  constexpr int NTILE = JB / 8;               // n8 tiles per unit
+  constexpr int SLOTS = 4 * NTILE;            // int64 accumulator slots per lane (one unit)
+  extern __shared__ __align__(16) unsigned char smem[];
+  double *tile = (double *)smem;                                   // [NT][kOzTR] column-major
+  uint16_t *planes = (uint16_t *)(smem + sizeof(double) * NT * kOzTR);  // [8][NT][kOzLDK]
+  int *Erun = (int *)(planes + (size_t)kOzDigits * NT * kOzLDK);        // [NT]
+  int *Edel = Erun + NT;                                                // [NT]
+  int *flag = Edel + NT;                                                // [1]
+
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int n = a.p;
+  const OzGeom gg = oz_geom(NT);
+  const int64_t row0 = (int64_t)blockIdx.x * a.rows_per_cta;
+  const int64_t row1 = min(a.m, row0 + a.rows_per_cta);
+
+  for (int j = t; j < NT; j += kOzThreads) {
+    Erun[j] = 1;
+    Edel[j] = 0;
+  }
+  if (t == 0) *flag = 0;
+
+  long long acc_hi[SLOTS], acc_lo[SLOTS];
+#pragma unroll
+  for (int k = 0; k < SLOTS; ++k) {
+    acc_hi[k] = 0;
+    acc_lo[k] = 0;
+  }
+  __syncthreads();
+
+  for (int64_t r0 = row0; r0 < row1; r0 += kOzTR) {
+    const int nr = (int)min((int64_t)kOzTR, row1 - r0);
+    // ---- stage the tile (column-major, zero padded): every copy of the
+    // tile is in flight at once
+    for (int e = t; e < kOzTR * NT; e += kOzThreads) {
+      const int i = e % kOzTR, j = e / kOzTR;
+      const bool in = (i < nr) && (j < n);
+      const double *src = in ? a.Yin + (r0 + i) + (int64_t)j * a.ldyin : a.Yin;
+      cp_async8(tile + j * kOzTR + i, src, in ? 8 : 0);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    // ---- optional FP64 row solve, then write the rows out
+    if (a.do_trsm) {
+      // forward substitution, 4 threads per row (64 rows x 4 = 256): thread
+      // sub of a row sums q_k R_kj over k = sub (mod 4); the four partial
+      // sums are combined as (s0 + s1) + (s2 + s3)
+      const int row = t >> 2, sub = t & 3;
+      for (int j = 0; j < n; ++j) {
+        double part = 0.0;
+        for (int k = sub; k < j; k += 4) part = fma(tile[k * kOzTR + row], a.Rt[k + (int64_t)j * n], part);
+        part += __shfl_xor_sync(0xffffffffu, part, 1);
+        part += __shfl_xor_sync(0xffffffffu, part, 2);
+        if (sub == 0 && row < nr) tile[j * kOzTR + row] = (tile[j * kOzTR + row] - part) * a.Rdinv[j];
+        __syncwarp();
+      }
+      __syncthreads();
+      for (int e = t; e < nr * n; e += kOzThreads) {
+        const int i = e % nr, j = e / nr;
+        a.Yout[(r0 + i) + (int64_t)j * a.ldyout] = tile[j * kOzTR + i];
+      }
+    }
+    // ---- column exponents: running maximum, growth since the last tile
+    for (int j = warp; j < NT; j += kOzWarps) {
+      int mx = 1, bad = 0;
+      for (int i = lane; i < kOzTR; i += 32) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(tile[j * kOzTR + i]);
+        const int ef = (int)((b >> 52) & 0x7FF);
+        bad |= (ef == 0x7FF);
+        mx = max(mx, align_exp(b));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+      }
+      if (lane == 0) {
+        const int old = Erun[j];
+        const int nw = max(old, mx);
+        Edel[j] = nw - old;
+        Erun[j] = nw;
+        if (bad) *flag = 1;
+      }
+    }
+    __syncthreads();
+    // ---- slice into 8 digit planes (two rows per thread step)
+    for (int e = t; e < (kOzTR / 2) * NT; e += kOzThreads) {
+      const int i = 2 * (e % (kOzTR / 2)), j = e / (kOzTR / 2);
+      const int Ej = Erun[j];
+      unsigned long long V[2];
+      uint32_t sgnmask = 0;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(tile[j * kOzTR + i + h]);
+        const int ef = (int)((b >> 52) & 0x7FF);
+        unsigned long long M = b & 0xFFFFFFFFFFFFFull;
+        if (ef) M |= 0x10000000000000ull;
+        if (ef == 0x7FF) M = 0;
+        const int sh = Ej - (ef ? ef : 1);
+        V[h] = (sh >= 56) ? 0ull : ((M << 3) >> sh);
+        sgnmask |= (uint32_t)(b >> 63) << (15 + 16 * h);
+      }
+#pragma unroll
+      for (int d = 0; d < kOzDigits; ++d) {
+        // two digits -> exact FP32 (magic add) -> one packed bf16x2, signs ORed in
+        const float f0 = __int_as_float(0x4B000000 | (int)((V[0] >> (49 - 7 * d)) & 127u)) - 8388608.0f;
+        const float f1 = __int_as_float(0x4B000000 | (int)((V[1] >> (49 - 7 * d)) & 127u)) - 8388608.0f;
+        const __nv_bfloat162 pr = __floats2bfloat162_rn(f0, f1);
+        *(uint32_t *)(planes + ((size_t)d * NT + j) * kOzLDK + i) = *(const uint32_t *)&pr | sgnmask;
+      }
+    }
+    __syncthreads();
+    // ---- tensor-core products, drained into the int64 accumulators
+    {
+      const int u = warp;
+      if (u < gg.units) {
+      const int slot_base = 0;
+      const int strip = u / gg.groups, grp = u % gg.groups;
+      const int ib = strip / gg.NJ, jb = strip % gg.NJ;
+      const int i0 = ib * 16, j0 = jb * JB;
+      // rescale this unit's accumulators where a column exponent grew
+#pragma unroll
+      for (int nt = 0; nt < NTILE; ++nt)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int gi = i0 + (lane >> 2) + ((r >> 1) << 3);
+          const int gj = j0 + nt * 8 + 2 * (lane & 3) + (r & 1);
+          const int k = slot_base + nt * 4 + r;
+          shift_pair(acc_hi[k], acc_lo[k], Edel[gi] + Edel[gj]);
+        }
+      int ord[8];
+      const int nord = group_orders(gg.groups, grp, ord);
+      for (int oi = 0; oi < nord; ++oi) {
+        const int d = ord[oi];
+        // pairs (s, t), 1 <= s <= t <= 8, s + t = d (at most four)
+        int npairs = 0;
+        int ps[4];
+        for (int s = 1; 2 * s <= d; ++s)
+          if (d - s <= 8) ps[npairs++] = s;
+        for (int pb = 0; pb < npairs; pb += 4) {
+          float c[NTILE][4];
+#pragma unroll
+          for (int nt = 0; nt < NTILE; ++nt) c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.0f;
+          float cd[NTILE][4];  // the s == t pair (weight 1/2)
+#pragma unroll
+          for (int nt = 0; nt < NTILE; ++nt) cd[nt][0] = cd[nt][1] = cd[nt][2] = cd[nt][3] = 0.0f;
+          bool has_diag = false, has_off = false;
+          for (int pp = pb; pp < min(npairs, pb + 4); ++pp) {
+            const int s = ps[pp], tt = d - s;
+            const bool diag = (s == tt);
+            has_diag |= diag;
+            has_off |= !diag;
+            const uint16_t *As = planes + ((size_t)(s - 1) * NT + i0) * kOzLDK;
+            const uint16_t *Bt = planes + ((size_t)(tt - 1) * NT + j0) * kOzLDK;
+            for (int ks = 0; ks < kOzTR; ks += 16) {
+              uint32_t a0, a1, a2, a3;
+              {
+                const int mi = lane >> 3, rr = lane & 7;
+                const uint16_t *pa = As + ((mi & 1) * 8 + rr) * kOzLDK + ks + (mi >> 1) * 8;
+                ldsm_x4(smem_u32(pa), a0, a1, a2, a3);
+              }
+#pragma unroll
+              for (int nt = 0; nt < NTILE; nt += 2) {
+                uint32_t b0, b1, b2, b3;
+                const int mi = lane >> 3, rr = lane & 7;
+                const uint16_t *pb2 = Bt + ((nt + (mi >> 1)) * 8 + rr) * kOzLDK + ks + (mi & 1) * 8;
+                ldsm_x4(smem_u32(pb2), b0, b1, b2, b3);
+                if (diag) {
+                  mma_bf16(cd[nt], a0, a1, a2, a3, b0, b1);
+                  mma_bf16(cd[nt + 1], a0, a1, a2, a3, b2, b3);
+                } else {
+                  mma_bf16(c[nt], a0, a1, a2, a3, b0, b1);
+                  mma_bf16(c[nt + 1], a0, a1, a2, a3, b2, b3);
+                }
+              }
+            }
+          }
+          // drain: T_d = 2 B + C, into the order word with weight 2^(7 (5 - d)) or 2^(7 (9 - d))
+          const bool hi = d <= 5;
+          const int shl = hi ? 7 * (5 - d) : 7 * (9 - d);
+#pragma unroll
+          for (int nt = 0; nt < NTILE; ++nt)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+              long long v = 0;
+              if (has_off) v += 2ll * f2i_exact(c[nt][r]);
+              if (has_diag) v += (long long)f2i_exact(cd[nt][r]);
+              const int k = slot_base + nt * 4 + r;
+              if (hi) acc_hi[k] += v << shl;
+              else acc_lo[k] += v << shl;
+            }
+        }
+      }
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- round to FP64 once; combine the order groups in a fixed order
+  double *outb = (double *)planes;  // NT x NT, reuses the plane storage
+  for (int e = t; e < NT * NT; e += kOzThreads) outb[e] = 0.0;
+  __syncthreads();
+  const bool bad = *flag != 0;
+  for (int g = 0; g < gg.groups; ++g) {
+    {
+      const int u = warp;
+      const int slot_base = 0;
+      if (u < gg.units && u % gg.groups == g) {
+      const int strip = u / gg.groups;
+      const int ib = strip / gg.NJ, jb = strip % gg.NJ;
+      const int i0 = ib * 16, j0 = jb * JB;
+#pragma unroll
+      for (int nt = 0; nt < NTILE; ++nt)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int gi = i0 + (lane >> 2) + ((r >> 1) << 3);
+          const int gj = j0 + nt * 8 + 2 * (lane & 3) + (r & 1);
+          const int k = slot_base + nt * 4 + r;
+          const int ex = Erun[gi] + Erun[gj];
+          // P = hi 2^(ex - 2080) + lo 2^(ex - 2108)
+          const double vh = ldexp((double)acc_hi[k], ex - 2080);
+          const double vl = ldexp((double)acc_lo[k], ex - 2108);
+          outb[gi + gj * NT] += vh + vl;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  double *P = a.partials + (int64_t)blockIdx.x * n * n;
+  for (int e = t; e < n * n; e += kOzThreads) {
+    const int i = e % n, j = e / n;
+    P[e] = bad ? __longlong_as_double(0x7FF8000000000000ll) : outb[i + j * NT];
+  }
+}
+
+size_t ozgram_smem_bytes(int NT) {
+  return sizeof(double) * NT * kOzTR + sizeof(uint16_t) * kOzDigits * NT * kOzLDK + sizeof(int) * (2 * NT + 4);
+}
+
+int ozgram_nt(int n) { return n <= 16 ? 16 : (n <= 32 ? 32 : 64); }
+
+template <int NT>
+static cudaError_t launch_oz(const RowSweep &a, int grid, cudaStream_t s) {
+  static bool attr_done = false;
+  const size_t smem = ozgram_smem_bytes(NT);
+  if (!attr_done) {
+    cudaFuncSetAttribute(ozgram_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_done = true;
+  }
+  ozgram_kernel<NT><<<grid, kOzThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ozgram(const RowSweep &a, int grid, cudaStream_t s) {
+  switch (ozgram_nt(a.p)) {
+    case 16: return launch_oz<16>(a, grid, s);
+    case 32: return launch_oz<32>(a, grid, s);
+    case 64: return launch_oz<64>(a, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int ozgram_grid(int64_t m) {
+  const int64_t tiles = (m + kOzTR - 1) / kOzTR;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, 2 * (int64_t)num_sms()));
+}
+
+int ozgram_tile_rows() { return kOzTR; }
+
+// Reduction of the symmetric-pair partials: X_ij = sum_g (P_g[i,j] + P_g[j,i]).
+__global__ void reduce_oz_kernel(const double *partials, int G, int n, double *C, const DevState *st) {
+  if (st != nullptr && st->done) return;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t E = (int64_t)n * (n + 1) / 2;
+  if (e >= E) return;
+  int j = (int)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
+  while ((int64_t)(j + 1) * (j + 2) / 2 <= e) ++j;
+  while ((int64_t)j * (j + 1) / 2 > e) --j;
+  const int i = (int)(e - (int64_t)j * (j + 1) / 2);
+  const int64_t nn = (int64_t)n * n;
+  double s = 0.0;
+  for (int g = 0; g < G; ++g) {
+    const double *P = partials + g * nn;
+    s += P[i + (int64_t)j * n] + P[j + (int64_t)i * n];
+  }
+  C[i + (int64_t)j * n] = s;
+  C[j + (int64_t)i * n] = s;
+}
+
+cudaError_t launch_reduce_oz(const double *partials, int G, int n, double *C, const DevState *st,
+                             cudaStream_t s) {
+  const int64_t E = (int64_t)n * (n + 1) / 2;
+  reduce_oz_kernel<<<(unsigned)((E + 63) / 64), 64, 0, s>>>(partials, G, n, C, st);
+  return cudaGetLastError();
+}
+
+}  // namespace cqr

@@ -192,3 +192,53 @@ def test_host_entry_point(cq, orc):
     Qd, Rd, _, _ = run_gpu(cq, A)
     assert res.status == cq.OK
     assert np.array_equal(Q, Qd) and np.array_equal(R, Rd)
+
+
+# ---- tensor-core (Ozaki digit) Gramian vs FP64 CUDA-core Gramian
+
+@pytest.mark.parametrize("kappa", [1e4, 1e12])
+@pytest.mark.parametrize("n", [1, 16, 20, 33, 48, 64])
+def test_emulated_and_native_gramian_agree(cq, orc, kappa, n):
+    m = 30011
+    A = synth.test_matrix(m, n, kappa, rep=12)
+    Qe, Re, ste, infoe = run_gpu(cq, A)
+    Qn, Rn, stn, infon = run_gpu(cq, A, opts=cq.default_opts(emulation=cq.EMU_OFF))
+    Qo, Ro, sto, info_o = orc.cholqr(A)
+    assert ste == stn == sto == cq.OK
+    assert infoe["iters"] == infon["iters"] == info_o.iters
+    for Q, R in ((Qe, Re), (Qn, Rn)):
+        assert orc.loo_frob(Q) <= 1e-13
+        assert orc.rrr(A, Q, R) <= 1e-13
+        assert np.max(np.abs(R - Ro)) <= r_tol(kappa, n, Ro)
+        assert np.max(np.abs(Q - Qo)) <= q_tol(kappa, m, n)
+
+
+def test_emulated_gramian_column_scaling(cq, orc):
+    # columns scaled over 12 orders of magnitude: each column has its own
+    # exponent in the digit representation; the result follows the oracle
+    # within the bounds of the scaled matrix's condition number
+    m, n = 20000, 8
+    A = synth.test_matrix(m, n, 1e3, rep=13)
+    As = A * np.array([1.0, 1e-6, 1e6, 1e-3, 1e3, 3.0, 1e-5, 1e5])
+    kap = np.linalg.cond(As)
+    Q, R, st, info = run_gpu(cq, As)
+    Qo, Ro, sto, info_o = orc.cholqr(As)
+    assert st == sto == cq.OK
+    assert orc.loo_frob(Q) <= 1e-13
+    assert orc.rrr(As, Q, R) <= 1e-13
+    assert np.max(np.abs(Q - Qo)) <= q_tol(kap, m, n)
+
+
+def test_emulated_gramian_row_dynamic_range(cq, orc):
+    # entries spanning 8 orders of magnitude inside each column
+    m, n = 9000, 12
+    rng = np.random.default_rng(14)
+    A = rng.standard_normal((m, n)) * 10.0 ** rng.uniform(-4, 4, size=(m, 1))
+    kap = np.linalg.cond(A)
+    Q, R, st, info = run_gpu(cq, A)
+    Qn, Rn, stn, _ = run_gpu(cq, A, opts=cq.default_opts(emulation=cq.EMU_OFF))
+    Qo, Ro, sto, _ = orc.cholqr(A)
+    assert st == stn == sto == cq.OK
+    assert orc.loo_frob(Q) <= 1e-13
+    assert orc.rrr(A, Q, R) <= 1e-13
+    assert np.max(np.abs(Q - Qo)) <= q_tol(kap, m, n)

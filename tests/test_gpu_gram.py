@@ -1,0 +1,78 @@
+"""The Gramian X = A^T A (Alg. 1 line 3) as the library forms it
+(cholqr_gram): tensor-core digit arithmetic (Ozaki splitting) for n <= 64 and
+FP64 CUDA cores otherwise, against the oracle's FP64 triple loop.
+
+Tolerance: both sides are within the FP64 dot-product bound, so
+|X_gpu - X_oracle|_ij <= 2 * gamma_m * (|A|^T |A|)_ij with gamma_m = m u / (1 - m u).
+(The digit scheme's own error is below 2^-53 (|A|^T|A|)_ij plus 2^-56 of
+the column maxima, far inside the bound.)"""
+import numpy as np
+import pytest
+
+from paper_2507_07788_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+U = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def cq():
+    import paper_2507_07788_gb300 as cq
+    from paper_2507_07788_gb300 import _build
+    _build.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return cq
+
+
+def check(cq, orc, A, emu):
+    m = A.shape[0]
+    X = cq.gram(cq.to_colmajor(A), opts=cq.default_opts(emulation=emu)).cpu().numpy()
+    Xo = orc.gram(A)
+    absA = np.abs(A)
+    bound = 2.0 * (m * U / (1 - m * U)) * (absA.T @ absA) + 1e-300
+    assert np.all(np.abs(X - Xo) <= bound), np.max(np.abs(X - Xo) / bound)
+    assert np.array_equal(X, X.T)
+    return X
+
+
+@pytest.mark.parametrize("emu", [0, 1])
+@pytest.mark.parametrize("m,n", [(1, 1), (17, 3), (128, 16), (129, 16), (5000, 20), (40000, 33),
+                                 (60000, 64), (3000, 100)])
+def test_gram_parity(cq, orc, emu, m, n):
+    A = synth.test_matrix(m, n, 1e6, rep=2)
+    check(cq, orc, A, emu)
+
+
+def test_gram_exponent_growth_across_tiles(cq, orc):
+    # every CTA sees several tiles whose column maxima grow from tile to tile
+    m, n = 80000, 24
+    rng = np.random.default_rng(3)
+    scale = 10.0 ** (np.arange(m) // 128 % 7 - 3.0)[:, None] * 10.0 ** rng.uniform(-2, 2, size=(1, n))
+    A = rng.standard_normal((m, n)) * scale
+    check(cq, orc, A, 0)
+
+
+def test_gram_extreme_column_scales(cq, orc):
+    # column scales from 1e-150 to 1e150 (all squares representable)
+    A = synth.test_matrix(20000, 8, 1e3, rep=13) * np.array([1.0, 1e-150, 1e150, 1e-30, 1e30, 3.0,
+                                                             2.0 ** -400, 2.0 ** 450])
+    check(cq, orc, A, 0)
+
+
+def test_gram_exact_on_small_integers(cq):
+    # small integer entries: every product and sum is exact in both paths
+    rng = np.random.default_rng(4)
+    A = rng.integers(-50, 51, size=(30000, 40)).astype(np.float64)
+    Xe = cq.gram(cq.to_colmajor(A)).cpu().numpy()
+    Xn = cq.gram(cq.to_colmajor(A), opts=cq.default_opts(emulation=cq.EMU_OFF)).cpu().numpy()
+    ref = A.T @ A  # exact: |sum| < 2^53
+    assert np.array_equal(Xe, ref) and np.array_equal(Xn, ref)
+
+
+def test_gram_nan_propagates(cq):
+    A = synth.gaussian(5000, 10, seed=1)
+    A[77, 4] = np.nan
+    X = cq.gram(cq.to_colmajor(A)).cpu().numpy()
+    assert np.isnan(X).any()
