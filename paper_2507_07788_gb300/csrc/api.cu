@@ -230,7 +230,7 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
     chunk_rpc = ((tiles + Gc - 1) / Gc) * tr;
   }
   AuxCtx *ax = (nchunks >= 2) ? aux_ctx(nchunks) : nullptr;
-  const int64_t oz_parts = oz ? std::max<int64_t>((int64_t)Goz, (int64_t)nchunks * Gc) * p * p : 0;
+  const int64_t oz_parts = oz ? std::max<int64_t>((int64_t)Goz, (int64_t)Gc) * p * p : 0;
   const int64_t part_elems = std::max<int64_t>(E, (oz_parts + G - 1) / G);
   bool last_oz = false;  // which reduction the last sweep needs
   int last_oz_G = Goz;   // and over how many partials
@@ -308,7 +308,8 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
         z.Yin = a.Yout + r0;
         z.ldyin = a.ldyout;
         z.do_trsm = 0;
-        z.partials = s.partials + (int64_t)c * Gc * p * p;
+        z.partials = s.partials;  // chunk c adds into chunk c-1's slots (in order on aux)
+        z.accumulate = (c > 0) ? 1 : 0;
         z.rows_per_cta = chunk_rpc;
         z.E = (int64_t)p * p;
         if (e == cudaSuccess) e = launch_ozgram(z, Gc, ax->aux);
@@ -319,7 +320,7 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
       if (e == cudaSuccess) e = cudaEventRecord(ax->done, ax->aux);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(str, ax->done, 0);
       last_oz = true;
-      last_oz_G = nchunks * Gc;
+      last_oz_G = Gc;
       if (mk != nullptr) cudaEventRecord(mk->b, str);
       return e;
     }

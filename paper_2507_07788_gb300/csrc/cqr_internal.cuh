@@ -62,6 +62,7 @@ struct RowSweep {
   int32_t tile_rows;
   int32_t lds;          // shared-memory row stride (doubles), odd
   int32_t do_trsm;
+  int32_t accumulate;  // tensor-core Gramian: add into the partials (later chunks of a pass)
   const DevState *st;
 };
 

@@ -391,7 +391,8 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozgram_kernel(RowSweep a) {
   double *P = a.partials + (int64_t)blockIdx.x * n * n;
   for (int e = t; e < n * n; e += kOzThreads) {
     const int i = e % n, j = e / n;
-    P[e] = bad ? __longlong_as_double(0x7FF8000000000000ll) : outb[i + j * NT];
+    const double v = bad ? __longlong_as_double(0x7FF8000000000000ll) : outb[i + j * NT];
+    P[e] = a.accumulate ? P[e] + v : v;
   }
 }
 
@@ -424,7 +425,7 @@ cudaError_t launch_ozgram(const RowSweep &a, int grid, cudaStream_t s) {
 
 int ozgram_grid(int64_t m) {
   const int64_t tiles = (m + kOzTR - 1) / kOzTR;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, 2 * (int64_t)num_sms()));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)num_sms()));
 }
 
 int ozgram_tile_rows() { return kOzTR; }

@@ -2,9 +2,9 @@
 // per row with the row held in registers.
 //
 // The solve is forward substitution on R~^T q^T = y^T: q_j = (y_j -
-// sum_{k<j} q_k R~_kj) / R~_jj, with the sum split into four interleaved
-// partial sums (k mod 4) combined as (s0 + s1) + (s2 + s3) for instruction-
-// level parallelism on GB300's narrow FP64 pipe, and the division done as a
+// sum_{k<j} q_k R~_kj) / R~_jj, with the sum split into eight interleaved
+// partial sums (k mod 8) added pairwise, for instruction-level parallelism on
+// GB300's narrow FP64 pipe, and the division done as a
 // multiplication by the precomputed 1 / R~_jj.  R~ and its inverse diagonal
 // sit in shared memory and every thread of a warp reads the same entry
 // (broadcast).  CTAs are small (64 threads, ~33 KB shared memory) so that
@@ -36,15 +36,13 @@ __global__ void __launch_bounds__(kTrsmThreads) trsm_rows_kernel(RowSweep a) {
     for (int j = 0; j < NT; ++j) {
       if (j < n) {
         const double *Rj = Rs + j * n;
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        double sp[8];
 #pragma unroll
-        for (int k = 0; k < j; k += 4) {
-          s0 = fma(q[k], Rj[k], s0);
-          if (k + 1 < j) s1 = fma(q[k + 1], Rj[k + 1], s1);
-          if (k + 2 < j) s2 = fma(q[k + 2], Rj[k + 2], s2);
-          if (k + 3 < j) s3 = fma(q[k + 3], Rj[k + 3], s3);
-        }
-        q[j] = (q[j] - ((s0 + s1) + (s2 + s3))) * Rd[j];
+        for (int u = 0; u < 8; ++u) sp[u] = 0.0;
+#pragma unroll
+        for (int k = 0; k < j; ++k) sp[k & 7] = fma(q[k], Rj[k], sp[k & 7]);
+        const double s = ((sp[0] + sp[1]) + (sp[2] + sp[3])) + ((sp[4] + sp[5]) + (sp[6] + sp[7]));
+        q[j] = (q[j] - s) * Rd[j];
       }
     }
 #pragma unroll
@@ -65,9 +63,11 @@ static cudaError_t launch_tr(const RowSweep &a, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Up to four CTAs per SM: the FP64 pipe needs several warps with
+// independent chains to stay busy.
 int trsm_rows_grid(int64_t m) {
   const int64_t blocks = (m + kTrsmThreads - 1) / kTrsmThreads;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(blocks, 2 * (int64_t)num_sms()));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(blocks, 4 * (int64_t)num_sms()));
 }
 
 cudaError_t launch_trsm_rows(const RowSweep &a, int grid, cudaStream_t s) {
