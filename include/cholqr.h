@@ -286,11 +286,12 @@ cqr_status cqr_server_destroy(cqr_server *s);
 
 /*
  * Instrumentation (no counterpart in the paper).  When enabled, every call
- * brackets each launch of the row-sweep kernels (the Gramian sweep and the
- * fused solve + Gramian sweep) with CUDA events on the launching stream and,
- * at the call's final synchronisation, adds the elapsed times of the sweeps
- * that did work, with their algorithmic FLOPs and bytes, to process-wide
- * counters.  All kernel launches of the library are counted whether or not
+ * brackets each row sweep (the Gramian sweep and each solve + Gramian pass)
+ * with CUDA events on the caller's stream, and each FP64 row-solve kernel
+ * and each tensor-core Gramian kernel with events on the stream it is
+ * launched on; at the call's final synchronisation the elapsed times of the
+ * launches that did work, with their algorithmic FLOPs and bytes, are added
+ * to process-wide counters.  All kernel launches of the library are counted whether or not
  * timing is enabled.  Counters are protected by a mutex; reset clears them.
  */
 typedef struct cqr_timing {
@@ -303,6 +304,14 @@ typedef struct cqr_timing {
   double fused_ms;
   double fused_flops;
   double fused_bytes;
+  int64_t solve_launches;    /* FP64 row-solve kernels of the pass pipeline */
+  double solve_ms;
+  double solve_flops;
+  double solve_bytes;
+  int64_t gram_launches;     /* tensor-core Gramian kernels (each timed alone) */
+  double gram_ms;
+  double gram_flops;
+  double gram_bytes;
 } cqr_timing;
 
 /* Enables (1) or disables (0) event timing of the row sweeps. */

@@ -52,7 +52,11 @@ class Timing(C.Structure):
     _fields_ = [("kernel_launches", C.c_int64), ("sweep_launches", C.c_int64),
                 ("sweep_ms", C.c_double), ("sweep_flops", C.c_double), ("sweep_bytes", C.c_double),
                 ("fused_launches", C.c_int64), ("fused_ms", C.c_double),
-                ("fused_flops", C.c_double), ("fused_bytes", C.c_double)]
+                ("fused_flops", C.c_double), ("fused_bytes", C.c_double),
+                ("solve_launches", C.c_int64), ("solve_ms", C.c_double),
+                ("solve_flops", C.c_double), ("solve_bytes", C.c_double),
+                ("gram_launches", C.c_int64), ("gram_ms", C.c_double),
+                ("gram_flops", C.c_double), ("gram_bytes", C.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

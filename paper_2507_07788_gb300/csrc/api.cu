@@ -19,6 +19,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <deque>
 #include <mutex>
 #include <vector>
 
@@ -36,9 +37,12 @@ cqr_timing g_timing = {};
 std::atomic<int> g_timing_on{0};
 std::atomic<int64_t> g_launches{0};
 
+enum { MARK_SWEEP = 0, MARK_SOLVE = 1, MARK_GRAM = 2 };
+
 struct SweepMark {
   cudaEvent_t a, b;
   int pass;    // 0 = first Gramian sweep, k >= 1 = k-th solve + Gramian sweep
+  int kind;    // MARK_*
   double flops, bytes;
 };
 
@@ -75,9 +79,10 @@ AuxCtx *aux_ctx(int nchunks) {
 constexpr int kMaxChunks = 8;
 constexpr int64_t kMinChunkRows = 78 * 1024;
 
-// Thread-local pool of event pairs for the sweep marks of one call.
-std::vector<SweepMark> &marks_pool() {
-  thread_local std::vector<SweepMark> pool;
+// Thread-local pool of event pairs for the sweep marks of one call.  A deque:
+// a mark taken before a later one is added must keep its address.
+std::deque<SweepMark> &marks_pool() {
+  thread_local std::deque<SweepMark> pool;
   return pool;
 }
 
@@ -240,7 +245,7 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
   DevState *hs = host_state();
   cqr_status result = CQR_OK;
   const bool timing = g_timing_on.load() != 0;
-  std::vector<SweepMark> &pool = marks_pool();
+  std::deque<SweepMark> &pool = marks_pool();
   size_t nmarks = 0;
   int npass = 0;
   // algorithmic work of one sweep (the minimum, whether or not it is split)
@@ -250,6 +255,22 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
   const double solve_flops = 2.0 * m_d * ((double)q * p + (double)p * (p - 1) / 2.0) + m_d * p;
   const double solve_bytes = 8.0 * m_d * (double)p;  // the write of the new block
 
+  // a mark around one kernel launch on stream `on` (timing only)
+  auto kmark = [&](int kind, int pass, double flops, double bytes) -> SweepMark * {
+    if (!timing) return nullptr;
+    if (nmarks == pool.size()) {
+      SweepMark nm{};
+      cudaEventCreate(&nm.a);
+      cudaEventCreate(&nm.b);
+      pool.push_back(nm);
+    }
+    SweepMark *k = &pool[nmarks++];
+    k->kind = kind;
+    k->pass = pass;
+    k->flops = flops;
+    k->bytes = bytes;
+    return k;
+  };
   auto sweep = [&](bool trsm, bool first) -> cudaError_t {
     RowSweep a{};
     a.m = P.m;
@@ -280,6 +301,7 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
         pool.push_back(nm);
       }
       mk = &pool[nmarks++];
+      mk->kind = MARK_SWEEP;
       mk->pass = trsm ? ++npass : 0;
       mk->flops = gram_flops + (trsm ? solve_flops : 0.0);
       mk->bytes = gram_bytes + (trsm ? solve_bytes : 0.0);
@@ -299,7 +321,11 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
         tr.m = rc;
         tr.Yin = a.Yin + r0;
         tr.Yout = a.Yout + r0;
+        const double rcd = (double)rc;
+        SweepMark *ms = kmark(MARK_SOLVE, npass, rcd * p * p, 16.0 * rcd * p);
+        if (ms) cudaEventRecord(ms->a, str);
         e = launch_trsm_rows(tr, trsm_rows_grid(rc), str);
+        if (ms) cudaEventRecord(ms->b, str);
         g_launches++;
         if (e == cudaSuccess) e = cudaEventRecord(ax->ev[c], str);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(ax->aux, ax->ev[c], 0);
@@ -312,7 +338,10 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
         z.accumulate = (c > 0) ? 1 : 0;
         z.rows_per_cta = chunk_rpc;
         z.E = (int64_t)p * p;
+        SweepMark *mg = kmark(MARK_GRAM, npass, rcd * p * (p + 1.0), 8.0 * rcd * p);
+        if (mg && e == cudaSuccess) cudaEventRecord(mg->a, ax->aux);
         if (e == cudaSuccess) e = launch_ozgram(z, Gc, ax->aux);
+        if (mg && e == cudaSuccess) cudaEventRecord(mg->b, ax->aux);
         g_launches++;
       }
       // chunks past the end of m (none with the sizing above) would leave
@@ -328,7 +357,10 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
       RowSweep z = a;
       z.rows_per_cta = oz_rows_per_cta;
       z.E = (int64_t)p * p;
+      SweepMark *mg = trsm ? nullptr : kmark(MARK_GRAM, 0, m_d * p * (p + 1.0), 8.0 * m_d * p);
+      if (mg) cudaEventRecord(mg->a, str);
       e = launch_ozgram(z, Goz, str);
+      if (mg) cudaEventRecord(mg->b, str);
       g_launches++;
       last_oz = true;
       last_oz_G = Goz;
@@ -458,6 +490,20 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
       float ms = 0.0f;
       if (cudaEventElapsedTime(&ms, mk.a, mk.b) != cudaSuccess) {
         (void)cudaGetLastError();
+        continue;
+      }
+      if (mk.kind == MARK_SOLVE) {
+        g_timing.solve_launches++;
+        g_timing.solve_ms += ms;
+        g_timing.solve_flops += mk.flops;
+        g_timing.solve_bytes += mk.bytes;
+        continue;
+      }
+      if (mk.kind == MARK_GRAM) {
+        g_timing.gram_launches++;
+        g_timing.gram_ms += ms;
+        g_timing.gram_flops += mk.flops;
+        g_timing.gram_bytes += mk.bytes;
         continue;
       }
       g_timing.sweep_launches++;
