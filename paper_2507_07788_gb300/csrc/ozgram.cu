@@ -20,10 +20,12 @@
 //   term).  Using P_st^T = P_ts, only s <= t is formed; the CTA stores
 //   P = sum_d (B_d + C_d / 2) w_d with B_d = sum_{s<t, s+t=d} P_st and
 //   C_d = P_{d/2,d/2}, and the reduction returns X = P + P^T.
-// Exactness: one mma.sync accumulator sums at most four digit pairs over 64
-//   rows, |sum| <= 4 * 64 * 127^2 < 2^22, so FP32 accumulation is exact and
-//   the FP32 -> int conversion is the exact magic-number add.  Orders are
-//   combined in two int64 words per entry (orders 2..5 and 6..9), summed
+// Exactness: each order d has one FP32 mma.sync accumulator holding
+//   T_d = 2 B_d + C_d over a 64-row tile (the off-diagonal pairs enter with
+//   their A digits doubled, exact in bf16); |T_d| <= 8 * 64 * 127^2 < 2^23,
+//   so the FP32 sums are exact and the FP32 -> int conversion is exact.
+//   Adjacent orders are combined exactly in int32 (T_d 2^7 + T_{d+1} < 2^31)
+//   and added into two int64 words per entry (orders 2..5 and 6..9), summed
 //   over the CTA's tiles (rescaled by right shifts when a column's running
 //   exponent grows), and rounded to FP64 once per CTA.
 // Non-finite inputs make every partial of the CTA NaN (the control kernel
@@ -40,7 +42,8 @@ namespace {
 
 constexpr int kOzTR = 64;            // tile rows (one exact accumulation window)
 constexpr int kOzLDK = kOzTR + 8;    // bf16 stride of a digit-plane column
-constexpr int kOzThreads = 256;      // 8 warps, one CTA per SM
+constexpr int kOzThreads = 256;      // 8 warps
+constexpr int kOzCtasPerSm = 2;     // two CTAs per SM hide each other's latency
 constexpr int kOzWarps = kOzThreads / 32;
 constexpr int kOzDigits = 8;
 
@@ -80,9 +83,18 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
-// Exact FP32 -> int for integer-valued |v| < 2^22 (magic-number add).
-__device__ __forceinline__ int f2i_exact(float v) {
-  return __float_as_int(v + 12582912.0f) - 0x4B400000;
+// FP32 -> int32 for an integer-valued FP32 (exact: the value is an integer).
+__device__ __forceinline__ int f2i(float v) {
+  int r;
+  asm("cvt.rzi.s32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return r;
+}
+
+// Doubles both bf16 halves (exact for the integer digits, |2 d| <= 254).
+__device__ __forceinline__ uint32_t bf16x2_twice(uint32_t x) {
+  __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162 *>(&x);
+  h = __hadd2(h, h);
+  return *reinterpret_cast<uint32_t *>(&h);
 }
 
 // bf16 bit pattern of the integer d in [0, 127] with sign bit s (exact).
@@ -116,23 +128,10 @@ __device__ __forceinline__ void shift_pair(long long &hi, long long &lo, int D) 
   hi = q;
 }
 
-// Orders 2..9 split into g groups (each warp unit handles one group).
-// The order sets are balanced by the number of digit pairs they contain.
-__device__ __forceinline__ int group_orders(int g, int grp, int (&ord)[8]) {
-  // order lists for g = 1, 2, 4, 8
-  if (g == 1) {
-    for (int k = 0; k < 8; ++k) ord[k] = 2 + k;
-    return 8;
-  }
-  if (g == 2) {
-    const int o[2][4] = {{2, 4, 6, 8}, {3, 5, 7, 9}};
-    for (int k = 0; k < 4; ++k) ord[k] = o[grp][k];
-    return 4;
-  }
-  const int o[4][2] = {{2, 9}, {3, 8}, {4, 7}, {5, 6}};
-  ord[0] = o[grp][0];
-  ord[1] = o[grp][1];
-  return 2;
+// Orders 2..9 split into `groups` groups, balanced by the number of digit
+// pairs they contain (5 each for four groups): does group grp own order d?
+__device__ __forceinline__ bool order_in_group(int groups, int grp, int d) {
+  return groups == 1 || d == 2 + grp || d == 9 - grp;
 }
 
 }  // namespace
@@ -143,22 +142,18 @@ struct OzGeom {
 
 // Work units: strips of 16 output rows x JB output columns, times groups of
 // orders; NT in {16, 32, 64} gives 4, 8 and 8 units (one per warp).
-__host__ __device__ inline OzGeom oz_geom(int NT) {
-  OzGeom g;
-  g.JB = (NT >= 32) ? 32 : 16;
-  g.NI = NT / 16;
-  g.NJ = NT / g.JB;
-  const int strips = g.NI * g.NJ;
-  g.groups = strips >= 8 ? 1 : (strips >= 2 ? 4 : 4);
-  g.units = strips * g.groups;
-  return g;
+__host__ __device__ constexpr OzGeom oz_geom(int NT) {
+  return OzGeom{NT / 16, NT / ((NT >= 32) ? 32 : 16), (NT >= 32) ? 32 : 16,
+                (NT / 16) * (NT / ((NT >= 32) ? 32 : 16)) >= 8 ? 1 : 4,
+                (NT / 16) * (NT / ((NT >= 32) ? 32 : 16)) *
+                    ((NT / 16) * (NT / ((NT >= 32) ? 32 : 16)) >= 8 ? 1 : 4)};
 }
 
 // One CTA: rows [bx * rows_per_cta, ...) in tiles of 64; optional FP64 row
 // solve (Alg. 1 line 9) before the Gramian of the tile.  Writes the CTA's
 // partial P (n x n, ld n) to partials[bx * n * n].
 template <int NT>
-__global__ void __launch_bounds__(kOzThreads, 1) ozgram_kernel(RowSweep a) {
+__global__ void __launch_bounds__(kOzThreads, kOzCtasPerSm) ozgram_kernel(RowSweep a) {
   if (a.st != nullptr && a.st->done) return;
   constexpr int JB = (NT >= 32) ? 32 : 16;
   constexpr int NTILE = JB / 8;               // n8 tiles per unit
@@ -172,7 +167,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozgram_kernel(RowSweep a) {
 
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int n = a.p;
-  const OzGeom gg = oz_geom(NT);
+  constexpr OzGeom gg = oz_geom(NT);
   const int64_t row0 = (int64_t)blockIdx.x * a.rows_per_cta;
   const int64_t row1 = min(a.m, row0 + a.rows_per_cta);
 
@@ -290,67 +285,70 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozgram_kernel(RowSweep a) {
           const int k = slot_base + nt * 4 + r;
           shift_pair(acc_hi[k], acc_lo[k], Edel[gi] + Edel[gj]);
         }
-      int ord[8];
-      const int nord = group_orders(gg.groups, grp, ord);
-      for (int oi = 0; oi < nord; ++oi) {
-        const int d = ord[oi];
-        // pairs (s, t), 1 <= s <= t <= 8, s + t = d (at most four)
-        int npairs = 0;
-        int ps[4];
-        for (int s = 1; 2 * s <= d; ++s)
-          if (d - s <= 8) ps[npairs++] = s;
-        for (int pb = 0; pb < npairs; pb += 4) {
-          float c[NTILE][4];
+      // order d: T_d = sum over pairs s <= t, s + t = d of (2 if s < t else 1)
+      // D_s^T D_t; adjacent orders (2k, 2k+1) combined in int32, then added
+      // to the int64 word of their order group with its weight
+      int pend = 0;  // T of the even order of the current pair of orders, per slot
+      int tv[NTILE][4];
 #pragma unroll
-          for (int nt = 0; nt < NTILE; ++nt) c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.0f;
-          float cd[NTILE][4];  // the s == t pair (weight 1/2)
+      for (int d = 2; d <= 9; ++d) {
+        if (!order_in_group(gg.groups, grp, d)) continue;
+        float c[NTILE][4];
 #pragma unroll
-          for (int nt = 0; nt < NTILE; ++nt) cd[nt][0] = cd[nt][1] = cd[nt][2] = cd[nt][3] = 0.0f;
-          bool has_diag = false, has_off = false;
-          for (int pp = pb; pp < min(npairs, pb + 4); ++pp) {
-            const int s = ps[pp], tt = d - s;
-            const bool diag = (s == tt);
-            has_diag |= diag;
-            has_off |= !diag;
-            const uint16_t *As = planes + ((size_t)(s - 1) * NT + i0) * kOzLDK;
-            const uint16_t *Bt = planes + ((size_t)(tt - 1) * NT + j0) * kOzLDK;
-            for (int ks = 0; ks < kOzTR; ks += 16) {
-              uint32_t a0, a1, a2, a3;
-              {
-                const int mi = lane >> 3, rr = lane & 7;
-                const uint16_t *pa = As + ((mi & 1) * 8 + rr) * kOzLDK + ks + (mi >> 1) * 8;
-                ldsm_x4(smem_u32(pa), a0, a1, a2, a3);
-              }
+        for (int nt = 0; nt < NTILE; ++nt) c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.0f;
+#pragma unroll 1
+        for (int s = (d > kOzDigits + 1) ? d - kOzDigits : 1; 2 * s <= d; ++s) {
+          const int tt = d - s;
+          const bool diag = (s == tt);
+          const uint16_t *As = planes + ((size_t)(s - 1) * NT + i0) * kOzLDK;
+          const uint16_t *Bt = planes + ((size_t)(tt - 1) * NT + j0) * kOzLDK;
+#pragma unroll 2
+          for (int ks = 0; ks < kOzTR; ks += 16) {
+            uint32_t a0, a1, a2, a3;
+            {
+              const int mi = lane >> 3, rr = lane & 7;
+              const uint16_t *pa = As + ((mi & 1) * 8 + rr) * kOzLDK + ks + (mi >> 1) * 8;
+              ldsm_x4(smem_u32(pa), a0, a1, a2, a3);
+            }
+            if (!diag) {
+              a0 = bf16x2_twice(a0);
+              a1 = bf16x2_twice(a1);
+              a2 = bf16x2_twice(a2);
+              a3 = bf16x2_twice(a3);
+            }
 #pragma unroll
-              for (int nt = 0; nt < NTILE; nt += 2) {
-                uint32_t b0, b1, b2, b3;
-                const int mi = lane >> 3, rr = lane & 7;
-                const uint16_t *pb2 = Bt + ((nt + (mi >> 1)) * 8 + rr) * kOzLDK + ks + (mi & 1) * 8;
-                ldsm_x4(smem_u32(pb2), b0, b1, b2, b3);
-                if (diag) {
-                  mma_bf16(cd[nt], a0, a1, a2, a3, b0, b1);
-                  mma_bf16(cd[nt + 1], a0, a1, a2, a3, b2, b3);
-                } else {
-                  mma_bf16(c[nt], a0, a1, a2, a3, b0, b1);
-                  mma_bf16(c[nt + 1], a0, a1, a2, a3, b2, b3);
-                }
-              }
+            for (int nt = 0; nt < NTILE; nt += 2) {
+              uint32_t b0, b1, b2, b3;
+              const int mi = lane >> 3, rr = lane & 7;
+              const uint16_t *pb2 = Bt + ((nt + (mi >> 1)) * 8 + rr) * kOzLDK + ks + (mi & 1) * 8;
+              ldsm_x4(smem_u32(pb2), b0, b1, b2, b3);
+              mma_bf16(c[nt], a0, a1, a2, a3, b0, b1);
+              mma_bf16(c[nt + 1], a0, a1, a2, a3, b2, b3);
             }
           }
-          // drain: T_d = 2 B + C, into the order word with weight 2^(7 (5 - d)) or 2^(7 (9 - d))
-          const bool hi = d <= 5;
+        }
+        // drain: with one group every order pair (2k, 2k+1) is combined as
+        // T_2k 2^7 + T_2k+1 in int32; with four groups each order alone
+        const bool hi = d <= 5;
+        if (gg.groups == 1 && (d & 1) == 0) {
+#pragma unroll
+          for (int nt = 0; nt < NTILE; ++nt)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) tv[nt][r] = f2i(c[nt][r]);
+          pend = 1;
+        } else {
           const int shl = hi ? 7 * (5 - d) : 7 * (9 - d);
 #pragma unroll
           for (int nt = 0; nt < NTILE; ++nt)
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
-              long long v = 0;
-              if (has_off) v += 2ll * f2i_exact(c[nt][r]);
-              if (has_diag) v += (long long)f2i_exact(cd[nt][r]);
+              const int v = f2i(c[nt][r]);
+              const long long w = pend ? (long long)(tv[nt][r] * 128 + v) : (long long)v;
               const int k = slot_base + nt * 4 + r;
-              if (hi) acc_hi[k] += v << shl;
-              else acc_lo[k] += v << shl;
+              if (hi) acc_hi[k] += w << shl;
+              else acc_lo[k] += w << shl;
             }
+          pend = 0;
         }
       }
       }
@@ -408,6 +406,8 @@ static cudaError_t launch_oz(const RowSweep &a, int grid, cudaStream_t s) {
   const size_t smem = ozgram_smem_bytes(NT);
   if (!attr_done) {
     cudaFuncSetAttribute(ozgram_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(ozgram_kernel<NT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
     attr_done = true;
   }
   ozgram_kernel<NT><<<grid, kOzThreads, smem, s>>>(a);
@@ -425,7 +425,7 @@ cudaError_t launch_ozgram(const RowSweep &a, int grid, cudaStream_t s) {
 
 int ozgram_grid(int64_t m) {
   const int64_t tiles = (m + kOzTR - 1) / kOzTR;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)num_sms()));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)kOzCtasPerSm * num_sms()));
 }
 
 int ozgram_tile_rows() { return kOzTR; }
