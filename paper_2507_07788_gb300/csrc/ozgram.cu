@@ -134,6 +134,44 @@ __device__ __forceinline__ bool order_in_group(int groups, int grp, int d) {
   return groups == 1 || d == 2 + grp || d == 9 - grp;
 }
 
+// (hi 2^28 + lo) 2^e rounded to the nearest FP64 (ties to even), on the
+// integer pipe: the two words are combined exactly in 128 bits and rounded
+// once.  Results outside the normal range (rare: entries below 2^-1022 or
+// above 2^1023) take the FP64 path, whose ldexp rounds subnormals correctly.
+__device__ __forceinline__ double fixed_to_double(long long hi, long long lo, int e) {
+  const __int128 v = ((__int128)hi << 28) + (__int128)lo;
+  if (v == 0) return 0.0;
+  const unsigned long long sign = (v < 0) ? 0x8000000000000000ull : 0ull;
+  const unsigned __int128 a = (v < 0) ? (unsigned __int128)(-v) : (unsigned __int128)v;
+  const unsigned long long ah = (unsigned long long)(a >> 64), al = (unsigned long long)a;
+  const int msb = ah ? 127 - __clzll((long long)ah) : 63 - __clzll((long long)al);
+  unsigned long long mant;
+  int E = msb + e;  // a in [2^msb, 2^(msb+1)): value in [2^E, 2^(E+1))
+  if (msb <= 52) {
+    mant = (unsigned long long)a << (52 - msb);
+  } else {
+    const int sh = msb - 52;
+    const unsigned __int128 q = a >> sh;
+    const unsigned __int128 rem = a - (q << sh);
+    const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
+    mant = (unsigned long long)q;
+    if (rem > half || (rem == half && (mant & 1ull))) {
+      ++mant;
+      if (mant == (1ull << 53)) {
+        mant >>= 1;
+        ++E;
+      }
+    }
+  }
+  if (E < -1022 || E > 1023) {
+    const double vh = ldexp((double)hi, e + 28);
+    const double vl = ldexp((double)lo, e);
+    return vh + vl;
+  }
+  return __longlong_as_double((long long)(sign | ((unsigned long long)(E + 1023) << 52) |
+                                          (mant & 0xFFFFFFFFFFFFFull)));
+}
+
 }  // namespace
 
 struct OzGeom {
@@ -356,11 +394,14 @@ __global__ void __launch_bounds__(kOzThreads, kOzCtasPerSm) ozgram_kernel(RowSwe
     __syncthreads();
   }
 
-  // ---- round to FP64 once; combine the order groups in a fixed order
-  double *outb = (double *)planes;  // NT x NT, reuses the plane storage
-  for (int e = t; e < NT * NT; e += kOzThreads) outb[e] = 0.0;
+  // ---- combine the order groups exactly, round to FP64 once per entry
+  long long *ohi = (long long *)planes;  // NT x NT, reuses the plane storage
+  long long *olo = ohi + NT * NT;        // NT x NT
+  for (int e = t; e < NT * NT; e += kOzThreads) {
+    ohi[e] = 0;
+    olo[e] = 0;
+  }
   __syncthreads();
-  const bool bad = *flag != 0;
   for (int g = 0; g < gg.groups; ++g) {
     {
       const int u = warp;
@@ -376,20 +417,20 @@ __global__ void __launch_bounds__(kOzThreads, kOzCtasPerSm) ozgram_kernel(RowSwe
           const int gi = i0 + (lane >> 2) + ((r >> 1) << 3);
           const int gj = j0 + nt * 8 + 2 * (lane & 3) + (r & 1);
           const int k = slot_base + nt * 4 + r;
-          const int ex = Erun[gi] + Erun[gj];
-          // P = hi 2^(ex - 2080) + lo 2^(ex - 2108)
-          const double vh = ldexp((double)acc_hi[k], ex - 2080);
-          const double vl = ldexp((double)acc_lo[k], ex - 2108);
-          outb[gi + gj * NT] += vh + vl;
+          ohi[gi + gj * NT] += acc_hi[k];
+          olo[gi + gj * NT] += acc_lo[k];
         }
       }
     }
     __syncthreads();
   }
+  const bool bad = *flag != 0;
   double *P = a.partials + (int64_t)blockIdx.x * n * n;
   for (int e = t; e < n * n; e += kOzThreads) {
     const int i = e % n, j = e / n;
-    const double v = bad ? __longlong_as_double(0x7FF8000000000000ll) : outb[i + j * NT];
+    // P_ij = (hi 2^28 + lo) 2^(Erun_i + Erun_j - 2108)
+    const double v = bad ? __longlong_as_double(0x7FF8000000000000ll)
+                         : fixed_to_double(ohi[i + j * NT], olo[i + j * NT], Erun[i] + Erun[j] - 2108);
     P[e] = a.accumulate ? P[e] + v : v;
   }
 }

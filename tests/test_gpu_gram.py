@@ -6,6 +6,8 @@ Tolerance: both sides are within the FP64 dot-product bound, so
 |X_gpu - X_oracle|_ij <= 2 * gamma_m * (|A|^T |A|)_ij with gamma_m = m u / (1 - m u).
 (The digit scheme's own error is below 2^-53 (|A|^T|A|)_ij plus 2^-56 of
 the column maxima, far inside the bound.)"""
+import itertools
+
 import numpy as np
 import pytest
 
@@ -76,3 +78,42 @@ def test_gram_nan_propagates(cq):
     A[77, 4] = np.nan
     X = cq.gram(cq.to_colmajor(A)).cpu().numpy()
     assert np.isnan(X).any()
+
+
+def _rne(S: int, scale: int) -> float:
+    """S * 2^scale rounded to FP64, ties to even (Python's int -> float
+    conversion rounds to nearest even; the power-of-two scale is exact)."""
+    return float(S) * 2.0 ** scale
+
+
+def test_gram_diagonal_is_correctly_rounded(cq):
+    # One 64-row tile: a single digit-Gramian CTA rounds each entry once from
+    # the exact sum, and the reduction doubles P_jj exactly, so X_jj must be
+    # the correctly rounded sum of squares.  Entries are M 2^(k_j - 25) with
+    # |M| < 2^26: the squares are exact, their sum needs up to 58 bits, and
+    # every element lies within the top 28 bits of its column (4 digits), so
+    # no digit product is dropped.  The last entry of some columns is chosen
+    # so that the exact sum is a tie between two doubles.
+    rng = np.random.default_rng(11)
+    m, n = 64, 16
+    M = rng.integers(-(2 ** 26) + 1, 2 ** 26, size=(m, n), dtype=np.int64)
+    k = rng.integers(-40, 41, size=n)
+    ties = 0
+    for j in range(0, n, 2):
+        # the last four entries (0..15 each; every residue is a sum of four
+        # squares) are chosen so that the exact sum sits halfway between
+        # two doubles
+        S60 = sum(int(x) * int(x) for x in M[:-4, j])
+        for e in itertools.product(range(16), repeat=4):
+            S = S60 + sum(v * v for v in e)
+            drop = S.bit_length() - 53
+            if drop > 1 and S % (1 << drop) == 1 << (drop - 1):
+                M[-4:, j] = e
+                ties += 1
+                break
+    assert ties >= 6
+    A = M.astype(np.float64) * np.exp2(k - 25)[None, :]
+    X = cq.gram(cq.to_colmajor(A)).cpu().numpy()
+    for j in range(n):
+        S = sum(int(x) * int(x) for x in M[:, j])
+        assert X[j, j] == _rne(S, 2 * (int(k[j]) - 25)), (j, X[j, j], _rne(S, 2 * (int(k[j]) - 25)))
