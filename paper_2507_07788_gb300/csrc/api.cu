@@ -212,29 +212,33 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
                           (double)p * (p + 1.0) * kU64);
   }
 
-  // Tensor-core Gramian (Ozaki digits) for factorisations with n <= 64.
+  // Tensor-core Gramian (Ozaki digits) for factorisations with n <= 128.
   // (Updates, including the first block of an empty basis, keep the FP64
   // sweep so that basis_append and the batched serving path agree bitwise.)
   const bool oz = (P.mode == MODE_FACTOR) && (p <= kOzMaxN) && (P.o.emulation == CQR_EMU_AUTO);
-  const int Goz = oz ? ozgram_grid(P.m) : 0;
+  const int Goz = oz ? ozgram_grid(P.m, p) : 0;
   int64_t oz_rows_per_cta = 0;
   if (oz) {
     const int64_t tr = ozgram_tile_rows();
     const int64_t tiles = (P.m + tr - 1) / tr;
     oz_rows_per_cta = ((tiles + Goz - 1) / Goz) * tr;
   }
-  // Chunked pipeline of the fused passes for large m (see AuxCtx).
-  const int nchunks = oz ? (int)std::max<int64_t>(1, std::min<int64_t>(kMaxChunks, P.m / kMinChunkRows)) : 1;
+  // Chunked pipeline of the passes for large m (see AuxCtx); for n > 64 the
+  // solve and the Gramian always run as separate kernels (one chunk for small
+  // m), with chunks half as tall since each row is twice as wide.
+  const int64_t min_chunk = (p > 64) ? kMinChunkRows / 2 : kMinChunkRows;
+  const int nchunks = oz ? (int)std::max<int64_t>(1, std::min<int64_t>(kMaxChunks, P.m / min_chunk)) : 1;
+  const bool pipe = oz && (nchunks >= 2 || p > 64);
   int64_t chunk_rows = 0, chunk_rpc = 0;
   int Gc = 0;
-  if (oz && nchunks >= 2) {
+  if (pipe) {
     const int64_t tr = ozgram_tile_rows();
     chunk_rows = (((P.m + nchunks - 1) / nchunks + tr - 1) / tr) * tr;
-    Gc = ozgram_grid(chunk_rows);
+    Gc = ozgram_grid(chunk_rows, p);
     const int64_t tiles = chunk_rows / tr;
     chunk_rpc = ((tiles + Gc - 1) / Gc) * tr;
   }
-  AuxCtx *ax = (nchunks >= 2) ? aux_ctx(nchunks) : nullptr;
+  AuxCtx *ax = pipe ? aux_ctx(nchunks) : nullptr;
   const int64_t oz_parts = oz ? std::max<int64_t>((int64_t)Goz, (int64_t)Gc) * p * p : 0;
   const int64_t part_elems = std::max<int64_t>(E, (oz_parts + G - 1) / G);
   bool last_oz = false;  // which reduction the last sweep needs
@@ -311,7 +315,7 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
     }
     cudaError_t e = cudaSuccess;
     last_oz = false;
-    if (oz && trsm && nchunks >= 2 && ax != nullptr) {
+    if (pipe && trsm && ax != nullptr) {
       // chunked pipeline: solve chunk c on str; its Gramian on the aux stream
       for (int c = 0; c < nchunks && e == cudaSuccess; ++c) {
         const int64_t r0 = (int64_t)c * chunk_rows;
@@ -602,7 +606,7 @@ cqr_status cholqr_gram(const cqr_opts *opts, int64_t m, int64_t n, const double 
   int tile_rows, lds;
   size_t smem;
   rowsweep_geometry(0, p, &tile_rows, &lds, &smem);
-  const int G = oz ? ozgram_grid(m) : rowsweep_grid(m, tile_rows);
+  const int G = oz ? ozgram_grid(m, p) : rowsweep_grid(m, tile_rows);
   const int64_t tr = oz ? ozgram_tile_rows() : tile_rows;
   const int64_t tiles = (m + tr - 1) / tr;
   const int64_t rows_per_cta = ((tiles + G - 1) / G) * tr;

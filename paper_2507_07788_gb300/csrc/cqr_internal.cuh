@@ -130,9 +130,9 @@ cudaError_t launch_init_batched(const Ctrl *reqs, const int *nreq, int grid, cud
 cudaError_t launch_ozgram(const RowSweep &a, int grid, cudaStream_t s);
 cudaError_t launch_reduce_oz(const double *partials, int G, int n, double *C, const DevState *st,
                              cudaStream_t s);
-int ozgram_grid(int64_t m);
+int ozgram_grid(int64_t m, int n);
 int ozgram_tile_rows();
-constexpr int kOzMaxN = 64;
+constexpr int kOzMaxN = 128;
 // FP64 row solve Q = Y R~^{-1} alone (one thread per row, registers); shares
 // SMs with ozgram_kernel when the two run on different streams.
 cudaError_t launch_trsm_rows(const RowSweep &a, int grid, cudaStream_t s);

@@ -42,9 +42,17 @@ namespace {
 
 constexpr int kOzTR = 64;            // tile rows (one exact accumulation window)
 constexpr int kOzLDK = kOzTR + 8;    // bf16 stride of a digit-plane column
-constexpr int kOzThreads = 256;      // 8 warps
-constexpr int kOzCtasPerSm = 2;     // two CTAs per SM hide each other's latency
-constexpr int kOzWarps = kOzThreads / 32;
+// Launch shape per width: n <= 64: 8 warps, two CTAs per SM (they hide each
+// other's latency), one CTA per row group.  n in (64, 128]: two CTAs per row
+// group, each forming one 64-row half of P with 16 warps, one CTA per SM.
+template <int NT>
+struct OzCfg {
+  static constexpr int halves = (NT > 64) ? 2 : 1;   // CTAs per row group
+  static constexpr int PR = NT / halves;             // rows of P per CTA
+  static constexpr int threads = (NT > 64) ? 512 : 256;
+  static constexpr int warps = threads / 32;
+  static constexpr int ctas = (NT > 64) ? 1 : 2;     // CTAs per SM
+};
 constexpr int kOzDigits = 8;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -178,20 +186,22 @@ struct OzGeom {
   int NI, NJ, JB, groups, units;
 };
 
-// Work units: strips of 16 output rows x JB output columns, times groups of
-// orders; NT in {16, 32, 64} gives 4, 8 and 8 units (one per warp).
-__host__ __device__ constexpr OzGeom oz_geom(int NT) {
-  return OzGeom{NT / 16, NT / ((NT >= 32) ? 32 : 16), (NT >= 32) ? 32 : 16,
-                (NT / 16) * (NT / ((NT >= 32) ? 32 : 16)) >= 8 ? 1 : 4,
-                (NT / 16) * (NT / ((NT >= 32) ? 32 : 16)) *
-                    ((NT / 16) * (NT / ((NT >= 32) ? 32 : 16)) >= 8 ? 1 : 4)};
+// Work units of one CTA (PR rows of P by NT columns): strips of 16 rows x JB
+// columns, times groups of orders.  NT = 16, 32, 64, 128 give 4, 8, 8 and 16
+// units (one per warp).
+__host__ __device__ constexpr OzGeom oz_geom(int NT, int PR) {
+  return OzGeom{PR / 16, NT / ((NT >= 32) ? 32 : 16), (NT >= 32) ? 32 : 16,
+                (PR / 16) * (NT / ((NT >= 32) ? 32 : 16)) >= 8 ? 1 : 4,
+                (PR / 16) * (NT / ((NT >= 32) ? 32 : 16)) *
+                    ((PR / 16) * (NT / ((NT >= 32) ? 32 : 16)) >= 8 ? 1 : 4)};
 }
 
-// One CTA: rows [bx * rows_per_cta, ...) in tiles of 64; optional FP64 row
-// solve (Alg. 1 line 9) before the Gramian of the tile.  Writes the CTA's
-// partial P (n x n, ld n) to partials[bx * n * n].
+// One CTA: rows [g * rows_per_cta, ...) of row group g in tiles of 64;
+// optional FP64 row solve (Alg. 1 line 9, n <= 64) before the Gramian of the
+// tile.  Writes rows [h PR, (h+1) PR) of the group's partial P (n x n, ld n)
+// to partials[g * n * n], h = the CTA's half.
 template <int NT>
-__global__ void __launch_bounds__(kOzThreads, kOzCtasPerSm) ozgram_kernel(RowSweep a) {
+__global__ void __launch_bounds__(OzCfg<NT>::threads, OzCfg<NT>::ctas) ozgram_kernel(RowSweep a) {
   if (a.st != nullptr && a.st->done) return;
   constexpr int JB = (NT >= 32) ? 32 : 16;
   constexpr int NTILE = JB / 8;               // n8 tiles per unit
@@ -205,8 +215,11 @@ __global__ void __launch_bounds__(kOzThreads, kOzCtasPerSm) ozgram_kernel(RowSwe
 
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int n = a.p;
-  constexpr OzGeom gg = oz_geom(NT);
-  const int64_t row0 = (int64_t)blockIdx.x * a.rows_per_cta;
+  constexpr int kOzThreads = OzCfg<NT>::threads, kOzWarps = OzCfg<NT>::warps, PR = OzCfg<NT>::PR;
+  constexpr OzGeom gg = oz_geom(NT, PR);
+  const int half = (int)(blockIdx.x % OzCfg<NT>::halves);
+  const int64_t grp_id = blockIdx.x / OzCfg<NT>::halves;
+  const int64_t row0 = grp_id * a.rows_per_cta;
   const int64_t row1 = min(a.m, row0 + a.rows_per_cta);
 
   for (int j = t; j < NT; j += kOzThreads) {
@@ -236,7 +249,7 @@ __global__ void __launch_bounds__(kOzThreads, kOzCtasPerSm) ozgram_kernel(RowSwe
     cp_async_wait_all();
     __syncthreads();
     // ---- optional FP64 row solve, then write the rows out
-    if (a.do_trsm) {
+    if (NT <= 64 && a.do_trsm) {
       // forward substitution, 4 threads per row (64 rows x 4 = 256): thread
       // sub of a row sums q_k R_kj over k = sub (mod 4); the four partial
       // sums are combined as (s0 + s1) + (s2 + s3)
@@ -312,7 +325,7 @@ __global__ void __launch_bounds__(kOzThreads, kOzCtasPerSm) ozgram_kernel(RowSwe
       const int slot_base = 0;
       const int strip = u / gg.groups, grp = u % gg.groups;
       const int ib = strip / gg.NJ, jb = strip % gg.NJ;
-      const int i0 = ib * 16, j0 = jb * JB;
+      const int i0 = half * PR + ib * 16, j0 = jb * JB;
       // rescale this unit's accumulators where a column exponent grew
 #pragma unroll
       for (int nt = 0; nt < NTILE; ++nt)
@@ -395,9 +408,9 @@ __global__ void __launch_bounds__(kOzThreads, kOzCtasPerSm) ozgram_kernel(RowSwe
   }
 
   // ---- combine the order groups exactly, round to FP64 once per entry
-  long long *ohi = (long long *)planes;  // NT x NT, reuses the plane storage
-  long long *olo = ohi + NT * NT;        // NT x NT
-  for (int e = t; e < NT * NT; e += kOzThreads) {
+  long long *ohi = (long long *)planes;  // PR x NT, reuses the plane storage
+  long long *olo = ohi + PR * NT;        // PR x NT
+  for (int e = t; e < PR * NT; e += kOzThreads) {
     ohi[e] = 0;
     olo[e] = 0;
   }
@@ -409,29 +422,31 @@ __global__ void __launch_bounds__(kOzThreads, kOzCtasPerSm) ozgram_kernel(RowSwe
       if (u < gg.units && u % gg.groups == g) {
       const int strip = u / gg.groups;
       const int ib = strip / gg.NJ, jb = strip % gg.NJ;
-      const int i0 = ib * 16, j0 = jb * JB;
+      const int i0 = ib * 16, j0 = jb * JB;  // local row of P
 #pragma unroll
       for (int nt = 0; nt < NTILE; ++nt)
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-          const int gi = i0 + (lane >> 2) + ((r >> 1) << 3);
+          const int li = i0 + (lane >> 2) + ((r >> 1) << 3);
           const int gj = j0 + nt * 8 + 2 * (lane & 3) + (r & 1);
           const int k = slot_base + nt * 4 + r;
-          ohi[gi + gj * NT] += acc_hi[k];
-          olo[gi + gj * NT] += acc_lo[k];
+          ohi[li + gj * PR] += acc_hi[k];
+          olo[li + gj * PR] += acc_lo[k];
         }
       }
     }
     __syncthreads();
   }
   const bool bad = *flag != 0;
-  double *P = a.partials + (int64_t)blockIdx.x * n * n;
-  for (int e = t; e < n * n; e += kOzThreads) {
-    const int i = e % n, j = e / n;
+  double *P = a.partials + grp_id * n * n;
+  for (int e = t; e < PR * n; e += kOzThreads) {
+    const int li = e % PR, j = e / PR, i = half * PR + li;
+    if (i >= n) continue;
     // P_ij = (hi 2^28 + lo) 2^(Erun_i + Erun_j - 2108)
     const double v = bad ? __longlong_as_double(0x7FF8000000000000ll)
-                         : fixed_to_double(ohi[i + j * NT], olo[i + j * NT], Erun[i] + Erun[j] - 2108);
-    P[e] = a.accumulate ? P[e] + v : v;
+                         : fixed_to_double(ohi[li + j * PR], olo[li + j * PR], Erun[i] + Erun[j] - 2108);
+    const int64_t pe = i + (int64_t)j * n;
+    P[pe] = a.accumulate ? P[pe] + v : v;
   }
 }
 
@@ -439,7 +454,7 @@ size_t ozgram_smem_bytes(int NT) {
   return sizeof(double) * NT * kOzTR + sizeof(uint16_t) * kOzDigits * NT * kOzLDK + sizeof(int) * (2 * NT + 4);
 }
 
-int ozgram_nt(int n) { return n <= 16 ? 16 : (n <= 32 ? 32 : 64); }
+int ozgram_nt(int n) { return n <= 16 ? 16 : (n <= 32 ? 32 : (n <= 64 ? 64 : 128)); }
 
 template <int NT>
 static cudaError_t launch_oz(const RowSweep &a, int grid, cudaStream_t s) {
@@ -451,7 +466,9 @@ static cudaError_t launch_oz(const RowSweep &a, int grid, cudaStream_t s) {
                          cudaSharedmemCarveoutMaxShared);
     attr_done = true;
   }
-  ozgram_kernel<NT><<<grid, kOzThreads, smem, s>>>(a);
+  // the fused solve exists for n <= 64 only
+  if (NT > 64 && a.do_trsm) return cudaErrorInvalidValue;
+  ozgram_kernel<NT><<<grid * OzCfg<NT>::halves, OzCfg<NT>::threads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -460,13 +477,17 @@ cudaError_t launch_ozgram(const RowSweep &a, int grid, cudaStream_t s) {
     case 16: return launch_oz<16>(a, grid, s);
     case 32: return launch_oz<32>(a, grid, s);
     case 64: return launch_oz<64>(a, grid, s);
+    case 128: return launch_oz<128>(a, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-int ozgram_grid(int64_t m) {
+// Number of row groups (= partials) for m rows at width n: every SM holds
+// OzCfg::ctas CTAs, a row group takes OzCfg::halves of them.
+int ozgram_grid(int64_t m, int n) {
   const int64_t tiles = (m + kOzTR - 1) / kOzTR;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)kOzCtasPerSm * num_sms()));
+  const int64_t per_sm = (n > 64) ? 1 : 2, halves = (n > 64) ? 2 : 1;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, per_sm * num_sms() / halves));
 }
 
 int ozgram_tile_rows() { return kOzTR; }

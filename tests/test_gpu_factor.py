@@ -197,7 +197,7 @@ def test_host_entry_point(cq, orc):
 # ---- tensor-core (Ozaki digit) Gramian vs FP64 CUDA-core Gramian
 
 @pytest.mark.parametrize("kappa", [1e4, 1e12])
-@pytest.mark.parametrize("n", [1, 16, 20, 33, 48, 64])
+@pytest.mark.parametrize("n", [1, 16, 20, 33, 48, 64, 65, 100, 128])
 def test_emulated_and_native_gramian_agree(cq, orc, kappa, n):
     m = 30011
     A = synth.test_matrix(m, n, kappa, rep=12)
@@ -205,12 +205,38 @@ def test_emulated_and_native_gramian_agree(cq, orc, kappa, n):
     Qn, Rn, stn, infon = run_gpu(cq, A, opts=cq.default_opts(emulation=cq.EMU_OFF))
     Qo, Ro, sto, info_o = orc.cholqr(A)
     assert ste == stn == sto == cq.OK
-    assert infoe["iters"] == infon["iters"] == info_o.iters
+    # An unshifted pass whose Gramian sits at the Cholesky breakdown threshold
+    # may break down (and take a recomputed shift, then one more pass) on one
+    # side only: pass counts may then differ by one, with the shift counts
+    # differing too.  Otherwise they agree.
+    its = (infoe["iters"], infon["iters"], info_o.iters)
+    shs = (infoe["shifts"], infon["shifts"], info_o.shifts)
+    assert max(its) - min(its) <= 1
+    assert len(set(its)) == 1 or len(set(shs)) > 1, (its, shs)
     for Q, R in ((Qe, Re), (Qn, Rn)):
         assert orc.loo_frob(Q) <= 1e-13
         assert orc.rrr(A, Q, R) <= 1e-13
         assert np.max(np.abs(R - Ro)) <= r_tol(kappa, n, Ro)
         assert np.max(np.abs(Q - Qo)) <= q_tol(kappa, m, n)
+
+
+@pytest.mark.parametrize("n", [64, 100])
+def test_chunked_pipeline_parity(cq, orc, n):
+    # m large enough that each pass runs as several row chunks (solve of
+    # chunk c beside the Gramian of chunk c-1, partials accumulated across
+    # chunks): 2 chunks at n = 64, 4 at n = 100, with a ragged last chunk
+    m = 160003
+    A = synth.test_matrix(m, n, 1e10, rep=15)
+    Q, R, st, info = run_gpu(cq, A)
+    Qo, Ro, sto, info_o = orc.cholqr(A)
+    assert st == sto == cq.OK
+    # at this size ||Q^T Q - I||_F after the third pass lies near the 1e-13
+    # stop tolerance, so the two sides may stop one pass apart
+    assert abs(info["iters"] - info_o.iters) <= 1
+    assert orc.loo_frob(Q) <= 1e-13
+    assert orc.rrr(A, Q, R) <= 1e-13
+    assert np.max(np.abs(R - Ro)) <= r_tol(1e10, n, Ro)
+    assert np.max(np.abs(Q - Qo)) <= q_tol(1e10, m, n)
 
 
 def test_emulated_gramian_column_scaling(cq, orc):

@@ -41,7 +41,7 @@ def check(cq, orc, A, emu):
 
 @pytest.mark.parametrize("emu", [0, 1])
 @pytest.mark.parametrize("m,n", [(1, 1), (17, 3), (128, 16), (129, 16), (5000, 20), (40000, 33),
-                                 (60000, 64), (3000, 100)])
+                                 (60000, 64), (3000, 100), (5000, 65), (70000, 128)])
 def test_gram_parity(cq, orc, emu, m, n):
     A = synth.test_matrix(m, n, 1e6, rep=2)
     check(cq, orc, A, emu)
