@@ -15,7 +15,9 @@ Prints ONE JSON line (rank 0) with the contract keys plus:
   e2e           the same metric through cholqr_factor_host (host buffers,
                 copies inside the timed region);
   clocks        nvidia-smi samples taken during the timed region;
-  sweep         a short n x kappa sweep at the same m.
+  sweep         a short n x kappa sweep at the same m;
+  update / mixed / pn / serve   the basis-growth, mixed-precision, pnCholQR
+                and serving legs (each skippable with --no-<leg>).
 ``--impl reference`` times the CPU oracle instead (rank 0 only).
 """
 from __future__ import annotations
@@ -58,6 +60,7 @@ def parse():
     ap.add_argument("--update-m", type=int, default=2_000_000)
     ap.add_argument("--mixed-m", type=int, default=4_000_000)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-pn", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=512)
     return ap.parse_args()
 
@@ -328,6 +331,37 @@ def leg_mixed(cq, torch, synth, m, n=128, kappas=(1e6, 1e10, 1e14), steps=3):
     return {"workload": f"mixed vs FP64 sCholQR3, m={m} n={n}, A=U diag(s) V^T", "rows": out}
 
 
+def leg_pn(cq, torch, synth, m, n=64, kappa=1e12, rs=(1, 2, 4, 8), steps=2):
+    """pnCholQR (Alg. 3) with r panels against sCholQR3 on the same matrix.
+    The paper's flop model puts pnCholQR at G(r) = 1/2 + 1/(2r) of the
+    one-shot method's flops (its flop comparison of Alg. 3)."""
+    A = synth.test_matrix(m, n, kappa, rep=41)
+    dA = cq.to_colmajor(A)
+    del A
+    dQ, dR = cq.colmajor(m, n), cq.colmajor(n, n)
+    ms_f, rf = time_factor(cq, torch, dA, dQ, dR, None, steps, 1)
+    rows = []
+    for r in rs:
+        cq.pn(dA, r, Q=dQ, R=dR)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            res = cq.pn(dA, r, Q=dQ, R=dR)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        G = dQ.t() @ dQ
+        loo = float(torch.linalg.norm(G - torch.eye(n, dtype=G.dtype, device=G.device)))
+        rows.append({"r": r, "ms": ms, "rows_cols_per_s": m * n / (ms * 1e-3), "status": res.status,
+                     "iters_total": res.info["iters"], "loo_frob": loo, "time_vs_scholqr3": ms / ms_f,
+                     "paper_flop_ratio": 0.5 + 0.5 / r})
+    del dA, dQ, dR
+    torch.cuda.empty_cache()
+    return {"workload": f"pnCholQR vs sCholQR3, m={m} n={n} kappa={kappa:g}, A=U diag(s) V^T",
+            "scholqr3_ms": ms_f, "scholqr3_iters": rf.info["iters"], "rows": rows}
+
+
 def leg_serve(cq, torch, n_requests=512):
     """Serving: Poisson arrivals (mean 2 ms, seed 0) of factor / append requests
     over 64 device-resident bases (m log-uniform in [1e4, 2e6], capacity 256);
@@ -457,6 +491,9 @@ def run_ours(args):
 
     if rank == 0 and not args.no_mixed:
         line["mixed"] = leg_mixed(cq, torch, synth, args.mixed_m)
+
+    if rank == 0 and not args.no_pn:
+        line["pn"] = leg_pn(cq, torch, synth, m)
 
     if rank == 0 and not args.no_serve:
         line["serve"] = leg_serve(cq, torch, args.serve_requests)

@@ -183,6 +183,30 @@ cqr_status cholqr_factor_noalloc(const cqr_opts *opts, int64_t m, int64_t n, con
                                  int64_t lda, double *Q, int64_t ldq, double *R, int64_t ldr,
                                  cqr_info *info, void *stream);
 
+/*
+ * cholqr_pn -- pnCholQR, Alg. 3 (Sec. 2.3): QR of A (m x n) by r column
+ * panels, the first factored and each later one appended to the growing
+ * basis by the Cholesky-QR update (Alg. 2, as basis_append).  Panel k has
+ * n/r columns, plus one for k < n mod r.
+ *   opts      host pointer, may be NULL (defaults; update_min_iter applies to
+ *             every panel).
+ *   m, n, r   1 <= r <= n <= CQR_MAX_BASIS, m >= n, every panel at most
+ *             CQR_MAX_N columns (ceil(n/r) <= CQR_MAX_N).
+ *   A, lda    device, m x n, lda >= m, read only; must not overlap Q.
+ *   Q, ldq    device, m x n output, ldq >= m.
+ *   R, ldr    device, n x n output, ldr >= n; upper triangular (the
+ *             strictly lower part is set to zero).
+ *   info      host pointer, may be NULL: iters, chol_attempts, shifts and
+ *             escalations summed over the panels; sigma_first = the first
+ *             nonzero shift, sigma_last = the last; orth_frob and proj_frob of
+ *             the last panel.
+ * Returns the first error of a panel (later panels are not run), else
+ * CQR_NOT_CONVERGED if any panel did not converge, else CQR_OK.
+ */
+cqr_status cholqr_pn(const cqr_opts *opts, int64_t m, int64_t n, int64_t r, const double *A,
+                     int64_t lda, double *Q, int64_t ldq, double *R, int64_t ldr, cqr_info *info,
+                     void *stream);
+
 /* Opaque growing orthonormal basis (Q_in m x q, R_in q x q) of Sec. 2.2. */
 typedef struct cqr_basis cqr_basis;
 

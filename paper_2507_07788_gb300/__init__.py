@@ -96,6 +96,8 @@ _SIGNATURES = {
     "cholqr_factor_host": (C.c_int, [C.POINTER(Opts), _I64, _I64, _P, _I64, _P, _I64, _P, _I64,
                                      C.POINTER(Info), _VP]),
     "cholqr_gram": (C.c_int, [C.POINTER(Opts), _I64, _I64, _P, _I64, _P, _I64, _VP]),
+    "cholqr_pn": (C.c_int, [C.POINTER(Opts), _I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64,
+                            C.POINTER(Info), _VP]),
     "cholqr_factor_noalloc": (C.c_int, [C.POINTER(Opts), _I64, _I64, _P, _I64, _P, _I64, _P,
                                         _I64, C.POINTER(Info), _VP]),
     "basis_create": (C.c_int, [_I64, _I64, C.POINTER(Opts), _VP, C.POINTER(_VP)]),
@@ -266,6 +268,28 @@ def factor(A, Q=None, R=None, opts: Opts | None = None, stream=None, check=True)
                                  _stream_ptr(stream))
     if check and st < 0:
         raise CholQRError(st, "cholqr_factor")
+    return Result(Q, R, st, info.as_dict())
+
+
+def pn(A, r: int, Q=None, R=None, opts: Opts | None = None, stream=None, check=True) -> Result:
+    """pnCholQR (Alg. 3) of a column-major CUDA tensor A (m x n) in r column
+    panels through cholqr_pn.  Returns Result(Q, R, status, info)."""
+    torch = _torch()
+    lda = _check_colmajor(A, "A")
+    m, n = A.shape
+    if Q is None:
+        Q = colmajor(m, n, device=A.device)
+    if R is None:
+        R = colmajor(n, n, device=A.device)
+    ldq = _check_colmajor(Q, "Q")
+    ldr = _check_colmajor(R, "R")
+    info = Info()
+    with torch.cuda.device(A.device):
+        st = lib().cholqr_pn(C.byref(opts) if opts is not None else None, m, n, int(r), A.data_ptr(),
+                             lda, Q.data_ptr(), ldq, R.data_ptr(), ldr, C.byref(info),
+                             _stream_ptr(stream))
+    if check and st < 0:
+        raise CholQRError(st, "cholqr_pn")
     return Result(Q, R, st, info.as_dict())
 
 

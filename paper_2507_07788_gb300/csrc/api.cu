@@ -753,6 +753,73 @@ cqr_status basis_append(cqr_basis *b, int64_t p, const double *A_in, int64_t lda
   return st;
 }
 
+cqr_status cholqr_pn(const cqr_opts *opts, int64_t m, int64_t n, int64_t r, const double *A,
+                     int64_t lda, double *Q, int64_t ldq, double *R, int64_t ldr, cqr_info *info,
+                     void *stream) {
+  cqr_opts o;
+  cqr_default_opts(&o);
+  if (opts != nullptr) o = *opts;
+  if (!opts_valid(o)) return CQR_ERR_INVALID;
+  if (n < 1 || n > CQR_MAX_BASIS || r < 1 || r > n || m < n) return CQR_ERR_INVALID;
+  if ((n + r - 1) / r > CQR_MAX_N) return CQR_ERR_INVALID;
+  if (lda < m || ldq < m || ldr < n) return CQR_ERR_INVALID;
+  if (A == nullptr || Q == nullptr || R == nullptr) return CQR_ERR_INVALID;
+  {
+    const char *a0 = (const char *)A, *a1 = (const char *)(A + lda * (n - 1) + m);
+    const char *q0 = (const char *)Q, *q1 = (const char *)(Q + ldq * (n - 1) + m);
+    if (a0 < q1 && q0 < a1) return CQR_ERR_INVALID;
+  }
+  if (host_state() == nullptr) return CQR_ERR_CUDA;
+  cudaStream_t str = (cudaStream_t)stream;
+  cudaError_t e = cudaMemset2DAsync(R, sizeof(double) * ldr, 0, sizeof(double) * n, n, str);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return cuda_status(e);
+  }
+  cqr_info tot{};
+  cqr_status status = CQR_OK;
+  int64_t q = 0;
+  for (int64_t k = 0; k < r; ++k) {
+    const int64_t p = n / r + (k < n % r ? 1 : 0);
+    // panel k = columns q .. q+p-1 of A, appended to Q's first q columns
+    Problem P{};
+    P.m = m;
+    P.q = (int)q;
+    P.p = (int)p;
+    P.Qin = Q;
+    P.ldqin = ldq;
+    P.Y0 = A + q * lda;
+    P.ldy0 = lda;
+    P.Y = Q + q * ldq;
+    P.ldy = ldq;
+    P.R = R + q + q * ldr;
+    P.ldr = ldr;
+    P.B = (q > 0) ? R + q * ldr : nullptr;
+    P.ldb = ldr;
+    P.mode = MODE_UPDATE;
+    P.min_iter = o.update_min_iter;
+    P.o = o;
+    cqr_info pi{};
+    const cqr_status st = run(P, &pi, str);
+    tot.iters += pi.iters;
+    tot.chol_attempts += pi.chol_attempts;
+    tot.shifts += pi.shifts;
+    tot.escalations += pi.escalations;
+    if (tot.sigma_first == 0.0) tot.sigma_first = pi.sigma_first;
+    if (pi.sigma_last != 0.0) tot.sigma_last = pi.sigma_last;
+    tot.orth_frob = pi.orth_frob;
+    tot.proj_frob = pi.proj_frob;
+    if (st < 0) {
+      status = st;
+      break;
+    }
+    if (st == CQR_NOT_CONVERGED) status = CQR_NOT_CONVERGED;
+    q += p;
+  }
+  if (info != nullptr) *info = tot;
+  return status;
+}
+
 cqr_status basis_free(cqr_basis *b) {
   if (b == nullptr) return CQR_OK;
   cudaError_t e1 = cudaFree(b->Q);

@@ -90,6 +90,28 @@ def test_factor_rejects_partial_overlap(cq):
     assert st == cq.ERR_INVALID
 
 
+@pytest.mark.parametrize("m,n,r,lda,ldq,ldr", [
+    (100, 8, 0, 100, 100, 8),       # r = 0
+    (100, 8, 9, 100, 100, 8),       # r > n
+    (1000, 300, 2, 1000, 1000, 300),  # panel of 150 columns > CQR_MAX_N
+    (5, 8, 2, 5, 5, 8),             # m < n
+    (100, 8, 2, 99, 100, 8),        # lda < m
+    (100, 8, 2, 100, 100, 7),       # ldr < n
+    (5000, 1100, 10, 5000, 5000, 1100),  # n > CQR_MAX_BASIS
+])
+def test_pn_rejects_bad_sizes_without_gpu(cq, m, n, r, lda, ldq, ldr):
+    st = cq.lib().cholqr_pn(None, m, n, r, C.c_void_p(0x1000), lda, C.c_void_p(0x20000000), ldq,
+                            C.c_void_p(0x30000000), ldr, None, None)
+    assert st == cq.ERR_INVALID
+
+
+def test_pn_rejects_overlap_without_gpu(cq):
+    base = 0x100000
+    st = cq.lib().cholqr_pn(None, 100, 4, 2, C.c_void_p(base), 100, C.c_void_p(base), 100,
+                            C.c_void_p(0x900000), 4, None, None)
+    assert st == cq.ERR_INVALID
+
+
 def test_basis_null_handles(cq):
     L = cq.lib()
     assert L.basis_free(None) == cq.OK
