@@ -140,7 +140,8 @@ void keep_pool_memory() {
 struct Scratch {
   char *base = nullptr;
   DevState *st;
-  double *C, *Rt, *Rdinv, *Bt, *partials;
+  double *C, *Rt, *Rdinv, *Bt, *Tinv, *partials;
+  int *Tscale;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -153,7 +154,8 @@ cudaError_t scratch_alloc(Scratch &s, int q, int p, int G, int64_t E, cudaStream
   const size_t b_Bt = align256(sizeof(double) * (size_t)std::max(q, 1) * p);
   const size_t b_P = align256(sizeof(double) * (size_t)G * (size_t)E);
   keep_pool_memory();
-  cudaError_t e = cudaMallocAsync((void **)&s.base, b_st + b_C + b_Rt + b_Rd + b_Bt + b_P, str);
+  const size_t b_Ts = align256(sizeof(int) * (size_t)p);
+  cudaError_t e = cudaMallocAsync((void **)&s.base, b_st + b_C + 2 * b_Rt + b_Rd + b_Bt + b_Ts + b_P, str);
   if (e != cudaSuccess) return e;
   char *p0 = s.base;
   s.st = (DevState *)p0;
@@ -166,6 +168,10 @@ cudaError_t scratch_alloc(Scratch &s, int q, int p, int G, int64_t E, cudaStream
   p0 += b_Rd;
   s.Bt = (double *)p0;
   p0 += b_Bt;
+  s.Tinv = (double *)p0;
+  p0 += b_Rt;
+  s.Tscale = (int *)p0;
+  p0 += b_Ts;
   s.partials = (double *)p0;
   return cudaSuccess;
 }
@@ -228,7 +234,11 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
   // m), with chunks half as tall since each row is twice as wide.
   const int64_t min_chunk = (p > 64) ? kMinChunkRows / 2 : kMinChunkRows;
   const int nchunks = oz ? (int)std::max<int64_t>(1, std::min<int64_t>(kMaxChunks, P.m / min_chunk)) : 1;
-  const bool pipe = oz && (nchunks >= 2 || p > 64);
+  const bool pipe = oz;
+  // the solve of the pipelined passes: Q = Y T on the tensor cores (T = R~^{-1}
+  // formed by the control kernel) for 33 <= n <= 64, FP64 substitution
+  // otherwise
+  const bool gemm = pipe && p >= kOzGemmMinN && p <= kOzGemmMaxN;
   int64_t chunk_rows = 0, chunk_rpc = 0;
   int Gc = 0;
   if (pipe) {
@@ -328,7 +338,16 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
         const double rcd = (double)rc;
         SweepMark *ms = kmark(MARK_SOLVE, npass, rcd * p * p, 16.0 * rcd * p);
         if (ms) cudaEventRecord(ms->a, str);
-        e = launch_trsm_rows(tr, trsm_rows_grid(rc), str);
+        if (gemm) {
+          const int Gg = ozgemm_grid(rc);
+          const int64_t tg = ozgemm_tile_rows();
+          tr.rows_per_cta = (((rc + tg - 1) / tg + Gg - 1) / Gg) * tg;
+          tr.Tinv = s.Tinv;
+          tr.Tscale = s.Tscale;
+          e = launch_ozgemm(tr, Gg, str);
+        } else {
+          e = launch_trsm_rows(tr, trsm_rows_grid(rc), str);
+        }
         if (ms) cudaEventRecord(ms->b, str);
         g_launches++;
         if (e == cudaSuccess) e = cudaEventRecord(ax->ev[c], str);
@@ -423,6 +442,8 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
     c.Rt = s.Rt;
     c.Rdinv = s.Rdinv;
     c.Bt = s.Bt;
+    c.Tinv = gemm ? s.Tinv : nullptr;
+    c.Tscale = s.Tscale;
     c.R = P.R;
     c.ldr = P.ldr;
     c.B = P.B;

@@ -63,6 +63,8 @@ struct RowSweep {
   int32_t lds;          // shared-memory row stride (doubles), odd
   int32_t do_trsm;
   int32_t accumulate;  // tensor-core Gramian: add into the partials (later chunks of a pass)
+  const double *Tinv;   // p x p upper (ld p): D R~^{-1} (tensor-core product Q = (Y D^-1)(D T))
+  const int *Tscale;    // p: log2 of D (column k of Y is divided, row k of T multiplied, by 2^Tscale[k])
   const DevState *st;
 };
 
@@ -90,6 +92,8 @@ struct Ctrl {
   double *Rt;       // p x p, ld p
   double *Rdinv;    // p
   double *Bt;       // q x p, ld q (update only)
+  double *Tinv;     // p x p, ld p: D R~^{-1}, formed when not null
+  int *Tscale;      // p: D = diag(2^Tscale), from the Gramian's diagonal
   double *R;        // accumulated R (p x p block), ld ldr
   int64_t ldr;
   double *B;        // accumulated B (q x p block), ld ldb (update only)
@@ -131,6 +135,14 @@ cudaError_t launch_ozgram(const RowSweep &a, int grid, cudaStream_t s);
 cudaError_t launch_reduce_oz(const double *partials, int G, int n, double *C, const DevState *st,
                              cudaStream_t s);
 int ozgram_grid(int64_t m, int n);
+// Q = Y T (T = R~^{-1}) on the tensor cores, exact digit products, n <= 64.
+cudaError_t launch_ozgemm(const RowSweep &a, int grid, cudaStream_t s);
+int ozgemm_grid(int64_t m);
+int ozgemm_tile_rows();
+constexpr int kOzGemmMaxN = 64;
+// Below this width the FP64 substitution (n^2 FP64 instructions per row) is
+// cheaper than the digit product's fixed per-row work.
+constexpr int kOzGemmMinN = 33;
 int ozgram_tile_rows();
 constexpr int kOzMaxN = 128;
 // FP64 row solve Q = Y R~^{-1} alone (one thread per row, registers); shares

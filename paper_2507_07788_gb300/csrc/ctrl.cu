@@ -305,6 +305,28 @@ __device__ void ctrl_body(const Ctrl &c, double *sm) {
     c.Rt[e] = (i <= j) ? Rk[pk(i, j)] : 0.0;
   }
   for (int j = t; j < p; j += NT) c.Rdinv[j] = 1.0 / Rk[pk(j, j)];
+  if (c.Tinv != nullptr) {
+    // T = R~^{-1} (the explicit inverse of App. A): row i of T solves
+    // t R~ = e_i^T by forward substitution, T_ij = -(sum_{i<=k<j} T_ik R~_kj)
+    // / R~_jj, one thread per row (no row depends on another).  The row is
+    // then scaled by 2^c_i with c_i = floor(log2 sqrt(X_ii)): the product
+    // Q = Y T is formed as (Y D^-1)(D T), D = diag(2^c), which balances the
+    // columns of Y and the rows of T (exact: powers of two).
+    for (int i = t; i < p; i += NT) {
+      double *Ti = c.Tinv + i;  // row i, stride p
+      for (int j = 0; j < i; ++j) Ti[(int64_t)j * p] = 0.0;
+      Ti[(int64_t)i * p] = 1.0 / Rk[pk(i, i)];
+      for (int j = i + 1; j < p; ++j) {
+        double s = 0.0;
+        for (int k = i; k < j; ++k) s = fma(Ti[(int64_t)k * p], Rk[pk(k, j)], s);
+        Ti[(int64_t)j * p] = -s * (1.0 / Rk[pk(j, j)]);
+      }
+      const double xii = c.C[(q + i) + (int64_t)i * ldc];
+      const int ci = (xii > 0.0 && isfinite(xii)) ? (ilogb(xii) >> 1) : 0;
+      c.Tscale[i] = ci;
+      for (int j = i; j < p; ++j) Ti[(int64_t)j * p] = ldexp(Ti[(int64_t)j * p], ci);
+    }
+  }
   __syncthreads();
   // R_old into the (no longer needed) X region
   double *Rold = X;

@@ -1,0 +1,103 @@
+// Building blocks of the tensor-core kernels that do FP64 arithmetic exactly
+// on bf16 digits (the Ozaki splitting scheme: Ozaki, Ogita, Oishi, Rump,
+// "Error-free transformations of matrix multiplication by using fast routines
+// of matrix multiplication and its applications", Numer. Algorithms 59, 2012):
+// shared-memory staging, ldmatrix / mma.sync wrappers, exact conversions.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace cqr {
+namespace oz {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2,
+                                        uint32_t &r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// Asynchronous 8-byte global -> shared copy; src_bytes = 0 zero-fills.
+__device__ __forceinline__ void cp_async8(void *dst, const void *src, int src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(smem_u32(dst)), "l"(src),
+               "r"(src_bytes));
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// FP32 -> int32 for an integer-valued FP32 (exact: the value is an integer).
+__device__ __forceinline__ int f2i(float v) {
+  int r;
+  asm("cvt.rzi.s32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return r;
+}
+
+// Doubles both bf16 halves (exact for the integer digits, |2 d| <= 254).
+__device__ __forceinline__ uint32_t bf16x2_twice(uint32_t x) {
+  __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162 *>(&x);
+  h = __hadd2(h, h);
+  return *reinterpret_cast<uint32_t *>(&h);
+}
+
+// Biased exponent used for alignment (subnormals and zeros count as 1).
+__device__ __forceinline__ int align_exp(unsigned long long b) {
+  const int ef = (int)((b >> 52) & 0x7FF);
+  return ef ? ef : 1;
+}
+
+// (hi 2^hs + lo) 2^e rounded to the nearest FP64 (ties to even), on the
+// integer pipe: the two words are combined exactly in 128 bits and rounded
+// once.  Results outside the normal range (rare: entries below 2^-1022 or
+// above 2^1023) take the FP64 path, whose ldexp rounds subnormals correctly.
+__device__ __forceinline__ double fixed_to_double(long long hi, long long lo, int hs, int e) {
+  const __int128 v = ((__int128)hi << hs) + (__int128)lo;
+  if (v == 0) return 0.0;
+  const unsigned long long sign = (v < 0) ? 0x8000000000000000ull : 0ull;
+  const unsigned __int128 a = (v < 0) ? (unsigned __int128)(-v) : (unsigned __int128)v;
+  const unsigned long long ah = (unsigned long long)(a >> 64), al = (unsigned long long)a;
+  const int msb = ah ? 127 - __clzll((long long)ah) : 63 - __clzll((long long)al);
+  unsigned long long mant;
+  int E = msb + e;  // a in [2^msb, 2^(msb+1)): value in [2^E, 2^(E+1))
+  if (msb <= 52) {
+    mant = (unsigned long long)a << (52 - msb);
+  } else {
+    const int sh = msb - 52;
+    const unsigned __int128 q = a >> sh;
+    const unsigned __int128 rem = a - (q << sh);
+    const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
+    mant = (unsigned long long)q;
+    if (rem > half || (rem == half && (mant & 1ull))) {
+      ++mant;
+      if (mant == (1ull << 53)) {
+        mant >>= 1;
+        ++E;
+      }
+    }
+  }
+  if (E < -1022 || E > 1023) {
+    const double vh = ldexp((double)hi, e + hs);
+    const double vl = ldexp((double)lo, e);
+    return vh + vl;
+  }
+  return __longlong_as_double((long long)(sign | ((unsigned long long)(E + 1023) << 52) |
+                                          (mant & 0xFFFFFFFFFFFFFull)));
+}
+
+}  // namespace oz
+}  // namespace cqr

@@ -32,11 +32,12 @@
 // then reports a breakdown, as the FP64 path does).
 #include <algorithm>
 
-#include <cuda_bf16.h>
-
 #include "cqr_internal.cuh"
+#include "ozdigits.cuh"
 
 namespace cqr {
+
+using namespace oz;
 
 namespace {
 
@@ -54,68 +55,6 @@ struct OzCfg {
   static constexpr int ctas = (NT > 64) ? 1 : 2;     // CTAs per SM
 };
 constexpr int kOzDigits = 8;
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2,
-                                        uint32_t &r3) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-               : "r"(addr));
-}
-
-__device__ __forceinline__ void ldsm_x2(uint32_t addr, uint32_t &r0, uint32_t &r1) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n"
-               : "=r"(r0), "=r"(r1)
-               : "r"(addr));
-}
-
-__device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                         uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-// Asynchronous 8-byte global -> shared copy; src_bytes = 0 zero-fills.
-__device__ __forceinline__ void cp_async8(void *dst, const void *src, int src_bytes) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(smem_u32(dst)), "l"(src),
-               "r"(src_bytes));
-}
-
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-}
-
-// FP32 -> int32 for an integer-valued FP32 (exact: the value is an integer).
-__device__ __forceinline__ int f2i(float v) {
-  int r;
-  asm("cvt.rzi.s32.f32 %0, %1;" : "=r"(r) : "f"(v));
-  return r;
-}
-
-// Doubles both bf16 halves (exact for the integer digits, |2 d| <= 254).
-__device__ __forceinline__ uint32_t bf16x2_twice(uint32_t x) {
-  __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162 *>(&x);
-  h = __hadd2(h, h);
-  return *reinterpret_cast<uint32_t *>(&h);
-}
-
-// bf16 bit pattern of the integer d in [0, 127] with sign bit s (exact).
-__device__ __forceinline__ uint32_t digit_bf16(uint32_t d, uint32_t s) {
-  const float f = __int_as_float(0x4B000000 | (int)d) - 8388608.0f;
-  return ((uint32_t)__float_as_int(f) >> 16) | (s << 15);
-}
-
-// Biased exponent used for alignment (subnormals and zeros count as 1).
-__device__ __forceinline__ int align_exp(unsigned long long b) {
-  const int ef = (int)((b >> 52) & 0x7FF);
-  return ef ? ef : 1;
-}
 
 // Rescales an accumulator pair (value = hi * 2^28 u + lo * u) to a unit 2^D
 // times larger when a column's running exponent grows by D: the bits that
@@ -140,44 +79,6 @@ __device__ __forceinline__ void shift_pair(long long &hi, long long &lo, int D) 
 // pairs they contain (5 each for four groups): does group grp own order d?
 __device__ __forceinline__ bool order_in_group(int groups, int grp, int d) {
   return groups == 1 || d == 2 + grp || d == 9 - grp;
-}
-
-// (hi 2^28 + lo) 2^e rounded to the nearest FP64 (ties to even), on the
-// integer pipe: the two words are combined exactly in 128 bits and rounded
-// once.  Results outside the normal range (rare: entries below 2^-1022 or
-// above 2^1023) take the FP64 path, whose ldexp rounds subnormals correctly.
-__device__ __forceinline__ double fixed_to_double(long long hi, long long lo, int e) {
-  const __int128 v = ((__int128)hi << 28) + (__int128)lo;
-  if (v == 0) return 0.0;
-  const unsigned long long sign = (v < 0) ? 0x8000000000000000ull : 0ull;
-  const unsigned __int128 a = (v < 0) ? (unsigned __int128)(-v) : (unsigned __int128)v;
-  const unsigned long long ah = (unsigned long long)(a >> 64), al = (unsigned long long)a;
-  const int msb = ah ? 127 - __clzll((long long)ah) : 63 - __clzll((long long)al);
-  unsigned long long mant;
-  int E = msb + e;  // a in [2^msb, 2^(msb+1)): value in [2^E, 2^(E+1))
-  if (msb <= 52) {
-    mant = (unsigned long long)a << (52 - msb);
-  } else {
-    const int sh = msb - 52;
-    const unsigned __int128 q = a >> sh;
-    const unsigned __int128 rem = a - (q << sh);
-    const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
-    mant = (unsigned long long)q;
-    if (rem > half || (rem == half && (mant & 1ull))) {
-      ++mant;
-      if (mant == (1ull << 53)) {
-        mant >>= 1;
-        ++E;
-      }
-    }
-  }
-  if (E < -1022 || E > 1023) {
-    const double vh = ldexp((double)hi, e + 28);
-    const double vl = ldexp((double)lo, e);
-    return vh + vl;
-  }
-  return __longlong_as_double((long long)(sign | ((unsigned long long)(E + 1023) << 52) |
-                                          (mant & 0xFFFFFFFFFFFFFull)));
 }
 
 }  // namespace
@@ -444,7 +345,7 @@ __global__ void __launch_bounds__(OzCfg<NT>::threads, OzCfg<NT>::ctas) ozgram_ke
     if (i >= n) continue;
     // P_ij = (hi 2^28 + lo) 2^(Erun_i + Erun_j - 2108)
     const double v = bad ? __longlong_as_double(0x7FF8000000000000ll)
-                         : fixed_to_double(ohi[li + j * PR], olo[li + j * PR], Erun[i] + Erun[j] - 2108);
+                         : fixed_to_double(ohi[li + j * PR], olo[li + j * PR], 28, Erun[i] + Erun[j] - 2108);
     const int64_t pe = i + (int64_t)j * n;
     P[pe] = a.accumulate ? P[pe] + v : v;
   }

@@ -239,13 +239,16 @@ def test_chunked_pipeline_parity(cq, orc, n):
     assert np.max(np.abs(Q - Qo)) <= q_tol(1e10, m, n)
 
 
-def test_emulated_gramian_column_scaling(cq, orc):
+@pytest.mark.parametrize("n", [8, 48])
+def test_emulated_gramian_column_scaling(cq, orc, n):
     # columns scaled over 12 orders of magnitude: each column has its own
-    # exponent in the digit representation; the result follows the oracle
-    # within the bounds of the scaled matrix's condition number
-    m, n = 20000, 8
+    # exponent in the digit Gramian, and the tensor-core solve (n >= 33)
+    # balances the columns of Y and the rows of T before splitting them; the
+    # result follows the oracle within the bounds of the scaled matrix's
+    # condition number
+    m = 20000
     A = synth.test_matrix(m, n, 1e3, rep=13)
-    As = A * np.array([1.0, 1e-6, 1e6, 1e-3, 1e3, 3.0, 1e-5, 1e5])
+    As = A * np.resize(np.array([1.0, 1e-6, 1e6, 1e-3, 1e3, 3.0, 1e-5, 1e5]), n)
     kap = np.linalg.cond(As)
     Q, R, st, info = run_gpu(cq, As)
     Qo, Ro, sto, info_o = orc.cholqr(As)
@@ -255,9 +258,10 @@ def test_emulated_gramian_column_scaling(cq, orc):
     assert np.max(np.abs(Q - Qo)) <= q_tol(kap, m, n)
 
 
-def test_emulated_gramian_row_dynamic_range(cq, orc):
+@pytest.mark.parametrize("n", [12, 40])
+def test_emulated_gramian_row_dynamic_range(cq, orc, n):
     # entries spanning 8 orders of magnitude inside each column
-    m, n = 9000, 12
+    m = 9000
     rng = np.random.default_rng(14)
     A = rng.standard_normal((m, n)) * 10.0 ** rng.uniform(-4, 4, size=(m, 1))
     kap = np.linalg.cond(A)
