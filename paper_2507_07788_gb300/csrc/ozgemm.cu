@@ -61,7 +61,7 @@ template <int NT>
 __host__ __device__ constexpr size_t ozgemm_smem(void) {
   return sizeof(uint16_t) * (size_t)kGmDigits * (NT + kGmTR) * GmGeom<NT>::LDK  // T and Y digit planes
          + sizeof(double) * (size_t)NT * kGmTR                                   // FP64 Y tile
-         + sizeof(int) * (size_t)(2 * NT + 2 * kGmTR);                          // exponents, flags, scales
+         + sizeof(int) * (size_t)(2 * NT + 10 * kGmTR);                         // exponents, flags, scales
 }
 
 constexpr int kNoExp = -(1 << 28);  // scaled exponent of a zero (below any real one)
@@ -109,6 +109,8 @@ __global__ void __launch_bounds__(kGmThreads, 1) ozgemm_kernel(RowSweep a) {
   int *erow = fcol + NT;                                                 // [64]
   int *bad = erow + kGmTR;                                               // [64]
   int *cs = bad + kGmTR;                                                 // [NT] column scales
+  int *epart = cs + NT;                                                  // [4][64] partial row maxima
+  int *bpart = epart + 4 * kGmTR;                                        // [4][64] partial flags
 
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int n = a.p;
@@ -160,35 +162,49 @@ __global__ void __launch_bounds__(kGmThreads, 1) ozgemm_kernel(RowSweep a) {
     const int nr = (int)min((int64_t)kGmTR, row1 - r0);
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
-    // ---- row exponents (4 threads per row) and non-finite rows
+    // ---- row exponents and non-finite rows: thread (r, quarter) scans 1/4
+    // of row r (lanes read consecutive rows: no bank conflicts)
     {
-      const int r = t >> 2, q4 = t & 3;
+      constexpr int KQ = NT / 4;
+      const int r = t & (kGmTR - 1), qk = t >> 6;
       int mx = kNoExp, bd = 0;
-      for (int k = q4; k < NT; k += 4) {
+#pragma unroll 4
+      for (int k = qk * KQ; k < (qk + 1) * KQ; ++k) {
         const unsigned long long b = (unsigned long long)__double_as_longlong(tile[k * kGmTR + r]);
         bd |= (((b >> 52) & 0x7FF) == 0x7FF);
         mx = max(mx, scaled_exp(b, cs[k]));
       }
-      mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-      mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
-      bd |= __shfl_xor_sync(0xffffffffu, bd, 1);
-      bd |= __shfl_xor_sync(0xffffffffu, bd, 2);
-      if (q4 == 0) {
-        erow[r] = mx;
-        bad[r] = bd;
-      }
+      epart[qk * kGmTR + r] = mx;
+      bpart[qk * kGmTR + r] = bd;
     }
     __syncthreads();
-    // ---- split the tile into 9 digit planes (row r, k contiguous)
-    for (int e = t; e < kGmTR * (NT / 2); e += kGmThreads) {
-      const int r = e / (NT / 2), k = 2 * (e % (NT / 2));
-      const unsigned long long b0 = (unsigned long long)__double_as_longlong(tile[k * kGmTR + r]);
-      const unsigned long long b1 = (unsigned long long)__double_as_longlong(tile[(k + 1) * kGmTR + r]);
-      const unsigned long long V0 = digits63(b0, erow[r], cs[k]), V1 = digits63(b1, erow[r], cs[k + 1]);
-      const uint32_t sg = ((uint32_t)(b0 >> 63) << 15) | ((uint32_t)(b1 >> 63) << 31);
+    // ---- split the tile into 9 digit planes (row r, k contiguous): a thread
+    // takes 8 consecutive k of one row and writes one 16-byte word per digit
+    for (int e = t; e < kGmTR * (NT / 8); e += kGmThreads) {
+      const int r = e & (kGmTR - 1), k0 = 8 * (e / kGmTR);
+      const int er = max(max(epart[r], epart[kGmTR + r]), max(epart[2 * kGmTR + r], epart[3 * kGmTR + r]));
+      if (k0 == 0) {
+        erow[r] = er;
+        bad[r] = bpart[r] | bpart[kGmTR + r] | bpart[2 * kGmTR + r] | bpart[3 * kGmTR + r];
+      }
+      unsigned long long V[8];
+      uint32_t sg[4];
 #pragma unroll
-      for (int d = 0; d < kGmDigits; ++d)
-        *(uint32_t *)(planesY + ((size_t)d * kGmTR + r) * LDK + k) = digit_pair_bf16(V0, V1, d, sg);
+      for (int h = 0; h < 8; ++h) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(tile[(k0 + h) * kGmTR + r]);
+        V[h] = digits63(b, er, cs[k0 + h]);
+        if (h & 1) sg[h >> 1] |= (uint32_t)(b >> 63) << 31;
+        else sg[h >> 1] = (uint32_t)(b >> 63) << 15;
+      }
+#pragma unroll
+      for (int d = 0; d < kGmDigits; ++d) {
+        uint4 w;
+        w.x = digit_pair_bf16(V[0], V[1], d, sg[0]);
+        w.y = digit_pair_bf16(V[2], V[3], d, sg[1]);
+        w.z = digit_pair_bf16(V[4], V[5], d, sg[2]);
+        w.w = digit_pair_bf16(V[6], V[7], d, sg[3]);
+        *(uint4 *)(planesY + ((size_t)d * kGmTR + r) * LDK + k0) = w;
+      }
     }
     __syncthreads();
     // ---- the next tile loads while this one is multiplied
@@ -213,8 +229,10 @@ __global__ void __launch_bounds__(kGmThreads, 1) ozgemm_kernel(RowSweep a) {
         const int tt = d - s;
         const uint16_t *As = planesY + ((size_t)(s - 1) * kGmTR + i0) * LDK;
         const uint16_t *Bt = planesT + ((size_t)(tt - 1) * NT + j0) * LDK;
+        // T is upper triangular: rows k >= j0 + JB of its strip are zero
+        const int kend = min(NT, j0 + G::JB);
 #pragma unroll 2
-        for (int ks = 0; ks < NT; ks += 16) {
+        for (int ks = 0; ks < kend; ks += 16) {
           uint32_t a0, a1, a2, a3;
           {
             const int mi = lane >> 3, rr = lane & 7;
