@@ -39,6 +39,7 @@ METRIC = ("sCholQR3 rows·cols/s & %HBM roofline at ‖QᵀQ−I‖≤1e-13; "
           "serve p50/p99 latency")
 FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9   # SMs x DFMA/clk/SM x 2 FLOP x max SM clock
 FALLBACK_HBM_GBS = 6800.0
+FALLBACK_BF16_TFLOPS = 1700.0
 
 
 def parse():
@@ -66,11 +67,13 @@ def parse():
 
 
 def peaks():
+    """(HBM GB/s, source, bf16 TFLOP/s sustained, source)."""
     try:
         d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        return float(d["hbm_gbs"]), "measured"
+        return (float(d["hbm_gbs"]), "measured", float(d["bf16_tflops_sustained"]),
+                "measured (cuBLAS bf16 GEMM, sustained: the kernel runs inside a multi-kernel step)")
     except Exception:
-        return FALLBACK_HBM_GBS, "fallback"
+        return FALLBACK_HBM_GBS, "fallback", FALLBACK_BF16_TFLOPS, "fallback"
 
 
 def dist():
@@ -126,15 +129,16 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-KERNEL_FILES = {"rowsweep": "rowsweep.cu", "trsm_rows": "trsm.cu", "ozgram": "ozgram.cu"}
+KERNEL_FILES = {"rowsweep": ("rowsweep.cu",), "trsm_rows": ("trsm.cu",),
+                "ozgram": ("ozgram.cu", "ozdigits.cuh"), "ozgemm": ("ozgemm.cu", "ozdigits.cuh")}
 
 
 def kernel_source_hash(name: str) -> str:
-    """Hash of one kernel's source file and the shared internal header: the
-    DRAM counters of a kernel stay valid while neither changes."""
+    """Hash of one kernel's source files: the DRAM counters of a kernel stay
+    valid while they do not change."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2507_07788_gb300", "csrc")
-    for f in (KERNEL_FILES[name], "cqr_internal.cuh"):
+    for f in KERNEL_FILES[name]:
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -218,12 +222,15 @@ def time_factor(cq, torch, dA, dQ, dR, opts, steps, warmup):
     return e0.elapsed_time(e1) / steps, res
 
 
-def roofline_from(tm, m, n, hbm_peak, hbm_src):
+def roofline_from(tm, m, n, hbm_peak, hbm_src, tc_peak, tc_src):
     """Roofline of the dominant kernel from the library's per-launch events.
 
-    With the tensor-core Gramian the pass pipeline runs two kernels: the FP64
-    row solve (dominant, bound by the FP64 pipe) and the digit Gramian.  The
-    solve is reported against the FP64 peak; the Gramian goes in "gram"."""
+    The pass pipeline runs a solve kernel and the tensor-core digit Gramian
+    per row chunk.  The solve is the dominant kernel: for 33 <= n <= 64 it is
+    the tensor-core product Q = Y R~^-1 (reported against the bf16 tensor
+    peak, with its FP64-equivalent rate beside it), otherwise the FP64 row
+    substitution (reported against the FP64 peak).  The Gramian goes in
+    "gram"."""
     def per(k):
         nl = max(tm[f"{k}_launches"], 1)
         ms = tm[f"{k}_ms"] / nl
@@ -232,6 +239,33 @@ def roofline_from(tm, m, n, hbm_peak, hbm_src):
         return ms, fl, by, (fl / (ms * 1e-3) if ms > 0 else 0.0), (by / (ms * 1e-3) / 1e9 if ms > 0 else 0.0)
 
     fp64_src = "derived: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz (FP64 CUDA cores)"
+    gram = None
+    if tm["gram_launches"] > 0:
+        gms, gfl, gby, gaf, gag = per("gram")
+        gtraffic, _ = traffic_per_launch(int(round(gby / (8.0 * n))), "ozgram")
+        gram = {"kernel": "ozgram_kernel (exact bf16 digit Gramian on tensor cores)",
+                "per_launch_ms": gms, "algorithmic_fp64_flops": gfl, "algorithmic_bytes": gby,
+                "fp64_equiv_tflops": gaf / 1e12, "hbm_gbs": gag, "hbm_frac": gag / hbm_peak,
+                "traffic": gtraffic}
+    if tm["tsolve_launches"] > 0:
+        ms, fl, by, af, ag = per("tsolve")
+        tcf = tm["tsolve_tc_flops"] / max(tm["tsolve_launches"], 1)
+        tca = tcf / (ms * 1e-3) if ms > 0 else 0.0
+        traffic, _ = traffic_per_launch(int(round(by / (16.0 * n))), "ozgemm")
+        roof = {"bound": "tensor", "achieved": tca / 1e12, "peak": tc_peak, "unit": "TFLOP/s",
+                "frac": tca / 1e12 / tc_peak, "traffic": traffic,
+                "kernel": "ozgemm_kernel (Q = Y R~^-1 as an exact bf16 digit product on the tensor cores, "
+                          "one launch per row chunk)",
+                "per_launch": {"ms": ms, "bf16_digit_flops": tcf, "algorithmic_fp64_flops": fl,
+                               "algorithmic_bytes": by},
+                "peak_source": tc_src,
+                "fp64_equiv": {"achieved_tflops": af / 1e12, "fp64_peak_tflops": FP64_PEAK_FLOPS / 1e12,
+                               "ratio": af / FP64_PEAK_FLOPS, "peak_source": fp64_src},
+                "hbm": {"achieved_gbs": ag, "peak_gbs": hbm_peak, "frac": ag / hbm_peak,
+                        "peak_source": hbm_src}}
+        if gram:
+            roof["gram"] = gram
+        return roof
     if tm["solve_launches"] > 0:
         ms, fl, by, af, ag = per("solve")
         traffic, _ = traffic_per_launch(int(round(by / (16.0 * n))), "trsm_rows")  # 16 B per row entry
@@ -241,13 +275,8 @@ def roofline_from(tm, m, n, hbm_peak, hbm_src):
                 "per_launch": {"ms": ms, "algorithmic_flops": fl, "algorithmic_bytes": by},
                 "hbm": {"achieved_gbs": ag, "peak_gbs": hbm_peak, "frac": ag / hbm_peak, "peak_source": hbm_src},
                 "peak_source": fp64_src}
-        if tm["gram_launches"] > 0:
-            gms, gfl, gby, gaf, gag = per("gram")
-            gtraffic, _ = traffic_per_launch(int(round(gby / (8.0 * n))), "ozgram")
-            roof["gram"] = {"kernel": "ozgram_kernel (exact bf16 digit Gramian on tensor cores)",
-                            "per_launch_ms": gms, "algorithmic_fp64_flops": gfl, "algorithmic_bytes": gby,
-                            "fp64_equiv_tflops": gaf / 1e12, "hbm_gbs": gag, "hbm_frac": gag / hbm_peak,
-                            "traffic": gtraffic}
+        if gram:
+            roof["gram"] = gram
         return roof
     ms, fl, by, af, ag = per("fused")
     traffic, _ = traffic_per_launch(int(round(m)), "rowsweep")
@@ -445,8 +474,8 @@ def run_ours(args):
     G = dQ.t() @ dQ
     loo_f = float(torch.linalg.norm(G - torch.eye(n, dtype=G.dtype, device=G.device)))
 
-    hbm_peak, hbm_src = peaks()
-    roof = roofline_from(tm, m, n, hbm_peak, hbm_src)
+    hbm_peak, hbm_src, tc_peak, tc_src = peaks()
+    roof = roofline_from(tm, m, n, hbm_peak, hbm_src, tc_peak, tc_src)
 
     line = {"metric": METRIC, "value": value, "unit": "rows*cols/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -462,16 +491,18 @@ def run_ours(args):
 
     if rank == 0 and not args.no_e2e:
         Ah = torch.from_numpy(np.asfortranarray(A)).t().contiguous().pin_memory().t()
+        Qh = torch.empty((n, m), dtype=torch.float64, pin_memory=True).t()
+        Rh = torch.empty((n, n), dtype=torch.float64, pin_memory=True).t()
         for _ in range(2):
-            cq.factor_host(Ah, opts=opts)
+            cq.factor_host(Ah, Q=Qh, R=Rh, opts=opts)
         t0 = time.perf_counter()
         k = max(2, args.steps // 2)
         for _ in range(k):
-            r2 = cq.factor_host(Ah, opts=opts)
+            r2 = cq.factor_host(Ah, Q=Qh, R=Rh, opts=opts)
         dt = (time.perf_counter() - t0) / k
         line["e2e"] = {"value": m * n / dt, "unit": "rows*cols/s", "h2d_bytes_per_step": 8 * m * n,
                        "d2h_bytes_per_step": 8 * (m * n + n * n), "ms_per_step": dt * 1e3,
-                       "api": "cholqr_factor_host (pinned host buffers, H2D + factor + D2H in the timed region)"}
+                       "api": "cholqr_factor_host (pinned host A, Q, R allocated once; H2D + factor + D2H in the timed region)"}
 
     if rank == 0 and not args.no_sweep:
         sweep = []

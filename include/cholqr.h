@@ -336,6 +336,11 @@ typedef struct cqr_timing {
   double gram_ms;
   double gram_flops;
   double gram_bytes;
+  int64_t tsolve_launches;   /* tensor-core solve kernels Q = Y R~^{-1} */
+  double tsolve_ms;
+  double tsolve_flops;       /* FP64-equivalent FLOPs (n^2 per row) */
+  double tsolve_bytes;
+  double tsolve_tc_flops;    /* bf16 digit-product FLOPs on the tensor pipe */
 } cqr_timing;
 
 /* Enables (1) or disables (0) event timing of the row sweeps. */

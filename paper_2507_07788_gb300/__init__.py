@@ -56,7 +56,10 @@ class Timing(C.Structure):
                 ("solve_launches", C.c_int64), ("solve_ms", C.c_double),
                 ("solve_flops", C.c_double), ("solve_bytes", C.c_double),
                 ("gram_launches", C.c_int64), ("gram_ms", C.c_double),
-                ("gram_flops", C.c_double), ("gram_bytes", C.c_double)]
+                ("gram_flops", C.c_double), ("gram_bytes", C.c_double),
+                ("tsolve_launches", C.c_int64), ("tsolve_ms", C.c_double),
+                ("tsolve_flops", C.c_double), ("tsolve_bytes", C.c_double),
+                ("tsolve_tc_flops", C.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -305,9 +308,11 @@ def gram(A, opts: Opts | None = None, stream=None):
     return X
 
 
-def factor_host(A, opts: Opts | None = None, stream=None, check=True) -> Result:
+def factor_host(A, Q=None, R=None, opts: Opts | None = None, stream=None, check=True) -> Result:
     """QR of a host matrix (numpy array or CPU tensor, float64) through
     cholqr_factor_host: copies in, factors on the GPU, copies Q and R out.
+    Q (m x n) and R (n x n) may be given as column-major host tensors (pinned
+    memory gives full copy bandwidth); otherwise pinned ones are allocated.
     Returns host (CPU tensor) Q and R."""
     torch = _torch()
     t = A if isinstance(A, torch.Tensor) else torch.from_numpy(A)
@@ -317,12 +322,18 @@ def factor_host(A, opts: Opts | None = None, stream=None, check=True) -> Result:
     if t.stride(0) != 1:
         t = t.t().contiguous().t()
     lda = max(t.stride(1), m)
-    Q = torch.empty((n, m), dtype=torch.float64, pin_memory=True).t()
-    R = torch.empty((n, n), dtype=torch.float64, pin_memory=True).t()
+    if Q is None:
+        Q = torch.empty((n, m), dtype=torch.float64, pin_memory=True).t()
+    if R is None:
+        R = torch.empty((n, n), dtype=torch.float64, pin_memory=True).t()
+    for M, name, rows, cols in ((Q, "Q", m, n), (R, "R", n, n)):
+        if (M.dtype != torch.float64 or M.device.type != "cpu" or tuple(M.shape) != (rows, cols)
+                or M.stride(0) != 1 or (cols > 1 and M.stride(1) < rows)):
+            raise TypeError(f"{name} must be a column-major {rows} x {cols} float64 host tensor")
     info = Info()
     st = lib().cholqr_factor_host(C.byref(opts) if opts is not None else None, m, n, t.data_ptr(),
-                                  lda, Q.data_ptr(), m, R.data_ptr(), n, C.byref(info),
-                                  _stream_ptr(stream))
+                                  lda, Q.data_ptr(), max(Q.stride(1), m), R.data_ptr(),
+                                  max(R.stride(1), n), C.byref(info), _stream_ptr(stream))
     if check and st < 0:
         raise CholQRError(st, "cholqr_factor_host")
     return Result(Q, R, st, info.as_dict())

@@ -37,13 +37,14 @@ cqr_timing g_timing = {};
 std::atomic<int> g_timing_on{0};
 std::atomic<int64_t> g_launches{0};
 
-enum { MARK_SWEEP = 0, MARK_SOLVE = 1, MARK_GRAM = 2 };
+enum { MARK_SWEEP = 0, MARK_SOLVE = 1, MARK_GRAM = 2, MARK_TSOLVE = 3 };
 
 struct SweepMark {
   cudaEvent_t a, b;
   int pass;    // 0 = first Gramian sweep, k >= 1 = k-th solve + Gramian sweep
   int kind;    // MARK_*
   double flops, bytes;
+  double tc_flops;  // MARK_TSOLVE: digit-product FLOPs on the tensor pipe
 };
 
 // Per host thread: an auxiliary stream and events for the chunked pass
@@ -336,7 +337,8 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
         tr.Yin = a.Yin + r0;
         tr.Yout = a.Yout + r0;
         const double rcd = (double)rc;
-        SweepMark *ms = kmark(MARK_SOLVE, npass, rcd * p * p, 16.0 * rcd * p);
+        SweepMark *ms = kmark(gemm ? MARK_TSOLVE : MARK_SOLVE, npass, rcd * p * p, 16.0 * rcd * p);
+        if (ms) ms->tc_flops = gemm ? rcd * ozgemm_tc_flops_per_row(p) : 0.0;
         if (ms) cudaEventRecord(ms->a, str);
         if (gemm) {
           const int Gg = ozgemm_grid(rc);
@@ -522,6 +524,14 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
         g_timing.solve_ms += ms;
         g_timing.solve_flops += mk.flops;
         g_timing.solve_bytes += mk.bytes;
+        continue;
+      }
+      if (mk.kind == MARK_TSOLVE) {
+        g_timing.tsolve_launches++;
+        g_timing.tsolve_ms += ms;
+        g_timing.tsolve_flops += mk.flops;
+        g_timing.tsolve_bytes += mk.bytes;
+        g_timing.tsolve_tc_flops += mk.tc_flops;
         continue;
       }
       if (mk.kind == MARK_GRAM) {

@@ -114,7 +114,7 @@ void gram32_geometry(int q, int p, int *tile_rows, int *lds, size_t *smem);
 constexpr int kGram32Depth = 64 + 2;
 cudaError_t launch_reduce(const Reduce &a, cudaStream_t s);
 cudaError_t launch_ctrl(const Ctrl &a, cudaStream_t s);
-size_t ctrl_smem_bytes(int p);
+size_t ctrl_smem_bytes(int p, bool with_t);
 
 // Batched persistent variants (descriptor arrays and counts in device
 // memory, so a captured CUDA graph can be replayed with new contents).  A
@@ -139,6 +139,9 @@ int ozgram_grid(int64_t m, int n);
 cudaError_t launch_ozgemm(const RowSweep &a, int grid, cudaStream_t s);
 int ozgemm_grid(int64_t m);
 int ozgemm_tile_rows();
+// bf16 FLOPs the tensor-core solve issues per row at width n (digit pairs x
+// the k-blocks its upper-triangular T does not skip).
+double ozgemm_tc_flops_per_row(int n);
 constexpr int kOzGemmMaxN = 64;
 // Below this width the FP64 substitution (n^2 FP64 instructions per row) is
 // cheaper than the digit product's fixed per-row work.

@@ -306,25 +306,53 @@ __device__ void ctrl_body(const Ctrl &c, double *sm) {
   }
   for (int j = t; j < p; j += NT) c.Rdinv[j] = 1.0 / Rk[pk(j, j)];
   if (c.Tinv != nullptr) {
-    // T = R~^{-1} (the explicit inverse of App. A): row i of T solves
-    // t R~ = e_i^T by forward substitution, T_ij = -(sum_{i<=k<j} T_ik R~_kj)
-    // / R~_jj, one thread per row (no row depends on another).  The row is
-    // then scaled by 2^c_i with c_i = floor(log2 sqrt(X_ii)): the product
-    // Q = Y T is formed as (Y D^-1)(D T), D = diag(2^c), which balances the
-    // columns of Y and the rows of T (exact: powers of two).
+    // T = R~^{-1} (the explicit inverse of App. A): T_jj = 1 / R~_jj and
+    // T_ij = -T_jj sum_{i<=k<j} T_ik R~_kj for i < j, in increasing j.  Row i
+    // depends only on itself, so 8 lanes of one warp own it (each sum split
+    // over them in a fixed order) and synchronise as a warp.  Row i of T then
+    // satisfies t R~ = e_i^T to working accuracy, so T R~ - I stays small.
+    // The row is scaled by 2^c_i with c_i = floor(log2 sqrt(X_ii)): the
+    // product Q = Y T is formed as (Y D^-1)(D T), D = diag(2^c), which
+    // balances the columns of Y and the rows of T (exact: powers of two).
+    double *Ts = (double *)(vecs + 2 * p);  // p x (p + 1), row-major with a padded stride
+    const int ldt = p + 1;
+    int *cexp = (int *)(Ts + (size_t)p * ldt);  // c_i
+    for (int e = t; e < p * ldt; e += NT) Ts[e] = 0.0;
+    __syncthreads();
     for (int i = t; i < p; i += NT) {
-      double *Ti = c.Tinv + i;  // row i, stride p
-      for (int j = 0; j < i; ++j) Ti[(int64_t)j * p] = 0.0;
-      Ti[(int64_t)i * p] = 1.0 / Rk[pk(i, i)];
-      for (int j = i + 1; j < p; ++j) {
-        double s = 0.0;
-        for (int k = i; k < j; ++k) s = fma(Ti[(int64_t)k * p], Rk[pk(k, j)], s);
-        Ti[(int64_t)j * p] = -s * (1.0 / Rk[pk(j, j)]);
-      }
+      Ts[i * ldt + i] = 1.0 / Rk[pk(i, i)];  // each reciprocal once
       const double xii = c.C[(q + i) + (int64_t)i * ldc];
       const int ci = (xii > 0.0 && isfinite(xii)) ? (ilogb(xii) >> 1) : 0;
+      cexp[i] = ci;
       c.Tscale[i] = ci;
-      for (int j = i; j < p; ++j) Ti[(int64_t)j * p] = ldexp(Ti[(int64_t)j * p], ci);
+    }
+    __syncthreads();
+    const int sub = t & 7, ir = t >> 3;
+    for (int j = 1; j < p; ++j) {
+      const double tjj = Ts[j * ldt + j];
+      double s = 0.0;
+      if (ir < j)
+        for (int k = ir + sub; k < j; k += 8) s = fma(Ts[ir * ldt + k], Rk[pk(k, j)], s);
+      s += __shfl_xor_sync(0xffffffffu, s, 1);
+      s += __shfl_xor_sync(0xffffffffu, s, 2);
+      s += __shfl_xor_sync(0xffffffffu, s, 4);
+      if (sub == 0 && ir < j) Ts[ir * ldt + j] = -s * tjj;
+      // row ir is written and read only by its own 8 lanes, all in one warp
+      __syncwarp();
+    }
+    __syncthreads();
+    for (int e = t; e < p * p; e += NT) {
+      const int i = e % p, j = e / p;
+      const int ci = cexp[i];
+      double v = 0.0;
+      if (i <= j) {
+        // times 2^c_i: one multiplication by an exact power of two when
+        // 2^c_i is a normal number, ldexp otherwise
+        v = (ci >= -1022 && ci <= 1023)
+                ? Ts[i * ldt + j] * __longlong_as_double((long long)(1023 + ci) << 52)
+                : ldexp(Ts[i * ldt + j], ci);
+      }
+      c.Tinv[e] = v;
     }
   }
   __syncthreads();
@@ -393,9 +421,12 @@ cudaError_t launch_ctrl_batched(const Ctrl *reqs, const int *nreq, int grid, siz
   return cudaGetLastError();
 }
 
-size_t ctrl_smem_bytes(int p) {
+// X (p x p), packed R~, two float vectors, then (when the pass forms it)
+// T = R~^{-1} (p x (p + 1)).
+size_t ctrl_smem_bytes(int p, bool with_t) {
   return (size_t)p * p * sizeof(double) + (size_t)(p * (p + 1) / 2 + 1) * sizeof(double) +
-         (size_t)2 * p * sizeof(float) + 64;
+         (size_t)2 * p * sizeof(float) +
+         (with_t ? (size_t)p * (p + 1) * sizeof(double) + (size_t)p * sizeof(int) : 0) + 64;
 }
 
 cudaError_t launch_ctrl(const Ctrl &a, cudaStream_t s) {
@@ -404,7 +435,10 @@ cudaError_t launch_ctrl(const Ctrl &a, cudaStream_t s) {
     cudaFuncSetAttribute(ctrl_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_done = true;
   }
-  ctrl_kernel<<<1, kCtrlThreads, ctrl_smem_bytes(a.p), s>>>(a);
+  // T is formed only for p <= 64 (the tensor-core solve), where 512 threads
+  // cover one row of T per 8 lanes
+  if (a.Tinv != nullptr && a.p > 64) return cudaErrorInvalidValue;
+  ctrl_kernel<<<1, kCtrlThreads, ctrl_smem_bytes(a.p, a.Tinv != nullptr), s>>>(a);
   return cudaGetLastError();
 }
 

@@ -337,6 +337,16 @@ int ozgemm_grid(int64_t m) {
 
 int ozgemm_tile_rows() { return kGmTR; }
 
+double ozgemm_tc_flops_per_row(int n) {
+  (void)n;  // one kernel shape (NT = 64) serves 33 <= n <= 64
+  constexpr int NT = 64, JB = GmGeom<NT>::JB;
+  double kcols = 0.0;  // sum over column strips of (strip width x k extent)
+  for (int j0 = 0; j0 < NT; j0 += JB) kcols += (double)JB * std::min(NT, j0 + JB);
+  int pairs = 0;
+  for (int d = 2; d <= 10; ++d) pairs += std::min(d - 1, kGmDigits) - std::max(1, d - kGmDigits) + 1;
+  return 2.0 * pairs * kcols;
+}
+
 // Q = Y T for 33 <= n <= 64 (a.Yin, a.Yout, a.Tinv, a.Tscale, a.m, a.p,
 // a.rows_per_cta); narrower blocks use the FP64 substitution.
 cudaError_t launch_ozgemm(const RowSweep &a, int grid, cudaStream_t s) {
