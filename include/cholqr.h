@@ -55,8 +55,22 @@ typedef enum cqr_status {
  *                           lines 5-7).  Default.
  *   CQR_SHIFT_ON_BREAKDOWN  Alg. 1 exactly as printed.
  *   CQR_SHIFT_NONE          no shift at all (CholQR / CholQR2); a breakdown
- *                           returns CQR_ERR_BREAKDOWN. */
-enum { CQR_SHIFT_SCHOLQR3 = 0, CQR_SHIFT_ON_BREAKDOWN = 1, CQR_SHIFT_NONE = 2 };
+ *                           returns CQR_ERR_BREAKDOWN.
+ *   CQR_SHIFT_SCHOLQR3_STRICT  first pass shifted, a later breakdown returns
+ *                           CQR_ERR_BREAKDOWN (the sCholQR3 of Fukaya et al.
+ *                           that Fig. 1 compares against).
+ *   CQR_SHIFT_ISCHOLQR      no first shift; the shift is computed once, from
+ *                           the Gramian of the first breakdown, and reused at
+ *                           every later breakdown (isCholQR, Fig. 1).
+ * The last two are comparison policies for Fig. 1; the factorisation's
+ * other rules (stop test, x10 escalation of a failing shift) are shared. */
+enum {
+  CQR_SHIFT_SCHOLQR3 = 0,
+  CQR_SHIFT_ON_BREAKDOWN = 1,
+  CQR_SHIFT_NONE = 2,
+  CQR_SHIFT_SCHOLQR3_STRICT = 3,
+  CQR_SHIFT_ISCHOLQR = 4
+};
 
 /* Stopping rule: ||X - I||_F < tol (Sec. 4.1, default tol = 1e-13), or the
  * literal u*sqrt(n) of Alg. 1 line 4 / Alg. 2 line 6. */

@@ -25,7 +25,7 @@ LIB_PATH = os.path.join(_HERE, "libcholqr.so")
 # status codes (cqr_status)
 OK, NOT_CONVERGED = 0, 1
 ERR_INVALID, ERR_BREAKDOWN, ERR_OOM, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT = -1, -2, -3, -4, -5, -6
-SHIFT_SCHOLQR3, SHIFT_ON_BREAKDOWN, SHIFT_NONE = 0, 1, 2
+SHIFT_SCHOLQR3, SHIFT_ON_BREAKDOWN, SHIFT_NONE, SHIFT_SCHOLQR3_STRICT, SHIFT_ISCHOLQR = 0, 1, 2, 3, 4
 STOP_FROB_TOL, STOP_U_SQRT_N = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 EMU_AUTO, EMU_OFF = 0, 1

@@ -36,6 +36,7 @@ struct DevState {
   double sigma_last;
   double orth_frob;
   double proj_frob;
+  double sigma_once;  // isCholQR: the one shift, 0 until the first breakdown
 };
 
 // One sweep over the m rows.  The block being orthogonalised is Y (m x p);

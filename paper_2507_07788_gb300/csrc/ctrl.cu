@@ -236,7 +236,9 @@ __device__ void ctrl_body(const Ctrl &c, double *sm) {
   if (c.mode == MODE_FACTOR) {
     const bool mixed_first = (it == 0) && (c.first_shift_coeff > 0.0);
     const bool shifted_first =
-        mixed_first || ((it == 0) && (c.shift_policy == CQR_SHIFT_SCHOLQR3));
+        mixed_first || ((it == 0) && (c.shift_policy == CQR_SHIFT_SCHOLQR3 ||
+                                      c.shift_policy == CQR_SHIFT_SCHOLQR3_STRICT));
+    const double sigma_once = st->sigma_once;  // read before thread 0 may set it
     if (shifted_first) {
       const double lam = norm_estimate(X, p, (float *)Rk, v, w, fred, red);
       sigma = mixed_first ? fmax(c.first_shift_coeff * lam, 2.0 * kU64) : shift_alg1(c.m, p, lam);
@@ -246,11 +248,16 @@ __device__ void ctrl_body(const Ctrl &c, double *sm) {
     rc = cholesky(X, p, sigma, Rk, &s_inv, &s_fail);
     ++attempts;
     if (rc != 0 && !shifted_first) {
-      if (c.shift_policy == CQR_SHIFT_NONE) {
+      if (c.shift_policy == CQR_SHIFT_NONE || c.shift_policy == CQR_SHIFT_SCHOLQR3_STRICT) {
         fatal = true;
       } else {
-        const double lam = norm_estimate(X, p, (float *)Rk, v, w, fred, red);
-        sigma = shift_alg1(c.m, p, lam);
+        if (c.shift_policy == CQR_SHIFT_ISCHOLQR && sigma_once > 0.0) {
+          sigma = sigma_once;
+        } else {
+          const double lam = norm_estimate(X, p, (float *)Rk, v, w, fred, red);
+          sigma = shift_alg1(c.m, p, lam);
+          if (c.shift_policy == CQR_SHIFT_ISCHOLQR && t == 0) st->sigma_once = sigma;
+        }
         ++shifts;
         s_first = sigma;
         rc = cholesky(X, p, sigma, Rk, &s_inv, &s_fail);

@@ -80,7 +80,7 @@ extern "C" cqr_status cholqr_factor_noalloc(const cqr_opts *opts, int64_t m, int
       o.tol >= 0.0 && o.max_iter >= 1 && o.max_iter <= 100 && o.min_iter >= 0 &&
       o.max_escalations >= 0 && o.max_escalations <= 400 &&
       (o.precision == CQR_PREC_FP64 || o.precision == CQR_PREC_MIXED) &&
-      o.shift_policy >= CQR_SHIFT_SCHOLQR3 && o.shift_policy <= CQR_SHIFT_NONE &&
+      o.shift_policy >= CQR_SHIFT_SCHOLQR3 && o.shift_policy <= CQR_SHIFT_ISCHOLQR &&
       (o.stop_rule == CQR_STOP_FROB_TOL || o.stop_rule == CQR_STOP_U_SQRT_N) &&
       (o.emulation == CQR_EMU_AUTO || o.emulation == CQR_EMU_OFF);
   if (!opts_ok) return CQR_ERR_INVALID;
