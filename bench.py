@@ -176,6 +176,19 @@ def cpu_baseline(A, rows, n):
             "seconds": dt}
 
 
+def replica_throughput(ms_local: float, ws: int, m: int, n: int, device: str):
+    """Whole-job throughput of ws independent replicas, each factoring its own
+    m x n matrix: the slowest rank's time per step (max over ranks) and the
+    rows*cols all ranks processed per second."""
+    ms = ms_local
+    if ws > 1:
+        import torch
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, ws * m * n / (ms * 1e-3)
+
+
 def run_reference(args):
     ws, rank, _ = dist()
     if rank != 0:
@@ -463,12 +476,7 @@ def run_ours(args):
     clk = clocks.stop()
     cq.cqr_timing_enable(False)
     tm = cq.cqr_timing_read()
-    ms = e0.elapsed_time(e1) / args.steps
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * m * n / (ms * 1e-3)
+    ms, value = replica_throughput(e0.elapsed_time(e1) / args.steps, ws, m, n, "cuda")
 
     # quality of the timed result (outside the timed region)
     G = dQ.t() @ dQ
