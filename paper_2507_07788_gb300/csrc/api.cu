@@ -444,15 +444,19 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
     c.Rt = s.Rt;
     c.Rdinv = s.Rdinv;
     c.Bt = s.Bt;
-    c.Tinv = gemm ? s.Tinv : nullptr;
-    c.Tscale = s.Tscale;
     c.R = P.R;
     c.ldr = P.ldr;
     c.B = P.B;
     c.ldb = P.ldb;
     c.st = s.st;
     g_launches++;
-    return launch_ctrl(c, str);
+    cudaError_t e = launch_ctrl(c, str);
+    // T = D R~^{-1} for the next pass's tensor-core solve
+    if (e == cudaSuccess && gemm) {
+      g_launches++;
+      e = launch_tinv(s.Rt, s.Rdinv, s.C, q + p, q, p, s.Tinv, s.Tscale, s.st, str);
+    }
+    return e;
   };
   auto pass = [&](bool first) -> cudaError_t {
     cudaError_t e = sweep(true, first);

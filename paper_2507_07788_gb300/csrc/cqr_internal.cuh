@@ -93,8 +93,6 @@ struct Ctrl {
   double *Rt;       // p x p, ld p
   double *Rdinv;    // p
   double *Bt;       // q x p, ld q (update only)
-  double *Tinv;     // p x p, ld p: D R~^{-1}, formed when not null
-  int *Tscale;      // p: D = diag(2^Tscale), from the Gramian's diagonal
   double *R;        // accumulated R (p x p block), ld ldr
   int64_t ldr;
   double *B;        // accumulated B (q x p block), ld ldb (update only)
@@ -115,7 +113,11 @@ void gram32_geometry(int q, int p, int *tile_rows, int *lds, size_t *smem);
 constexpr int kGram32Depth = 64 + 2;
 cudaError_t launch_reduce(const Reduce &a, cudaStream_t s);
 cudaError_t launch_ctrl(const Ctrl &a, cudaStream_t s);
-size_t ctrl_smem_bytes(int p, bool with_t);
+size_t ctrl_smem_bytes(int p);
+// T = D R~^{-1} and the exponents of D (for the tensor-core solve), one
+// warp per row, after the control kernel of a pass.
+cudaError_t launch_tinv(const double *Rt, const double *Rdinv, const double *C, int ldc, int q, int p,
+                        double *Tinv, int *Tscale, const DevState *st, cudaStream_t s);
 
 // Batched persistent variants (descriptor arrays and counts in device
 // memory, so a captured CUDA graph can be replayed with new contents).  A

@@ -108,43 +108,45 @@ __device__ double norm_estimate(const double *X, int p, float *Xf, float *v, flo
   return fmax(l, dmax);
 }
 
-// Cholesky R^T R = X + sigma I into packed upper storage Rk (row-oriented,
-// pivot d_j = X_jj + sigma - sum_{k<j} R_kj^2).  Breakdown: d_j not strictly
-// positive or not finite.  Returns 0 or j + 1 of the failing pivot.
+// Cholesky R^T R = X + sigma I into packed upper storage Rk, right-looking:
+// Rk starts as the upper triangle of X + sigma I; step j takes the pivot
+// d_j = the updated (j, j) entry, scales row j by 1 / sqrt(d_j) and
+// subtracts R_ji R_jk from the trailing entries (i, k), j < i <= k.  Each
+// entry thus receives X_ik - R_0i R_0k - R_1i R_1k - ... in increasing j.
+// Breakdown: d_j not strictly positive or not finite.  Returns 0 or j + 1 of
+// the failing pivot.  All of the block's threads share the trailing update
+// (8 lanes per column), so a step costs one FP64 instruction per entry.
 __device__ int cholesky(const double *X, int p, double sigma, double *Rk, double *s_inv,
                         int *s_fail) {
   const int t = threadIdx.x, NT = blockDim.x;
   __syncthreads();  // every thread has read the previous call's *s_fail
+  for (int e = t; e < p * p; e += NT) {
+    const int i = e % p, j = e / p;
+    if (i <= j) Rk[pk(i, j)] = X[i + j * p] + (i == j ? sigma : 0.0);
+  }
   if (t == 0) *s_fail = 0;
   __syncthreads();
+  const int cl = t >> 3, rl = t & 7, cstep = NT >> 3;
   for (int j = 0; j < p; ++j) {
-    if (t < 32) {
-      double s = 0.0;
-      for (int k = t; k < j; k += 32) {
-        const double r = Rk[pk(k, j)];
-        s = fma(r, r, s);
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (t == 0) {
-        const double d = (X[j + j * p] + sigma) - s;
-        if (!(d > 0.0) || !isfinite(d)) {
-          *s_fail = j + 1;
-        } else {
-          const double r = sqrt(d);
-          Rk[pk(j, j)] = r;
-          *s_inv = 1.0 / r;
-        }
+    if (t == 0) {
+      const double d = Rk[pk(j, j)];
+      if (!(d > 0.0) || !isfinite(d)) {
+        *s_fail = j + 1;
+      } else {
+        const double r = sqrt(d);
+        Rk[pk(j, j)] = r;
+        *s_inv = 1.0 / r;
       }
     }
     __syncthreads();
-    const int fail = *s_fail;
-    if (fail) return fail;
+    if (*s_fail) return *s_fail;
     const double inv = *s_inv;
-    for (int i = j + 1 + t; i < p; i += NT) {
-      double s = X[j + i * p];
-      for (int k = 0; k < j; ++k) s -= Rk[pk(k, j)] * Rk[pk(k, i)];
-      Rk[pk(j, i)] = s * inv;
+    for (int k = j + 1 + t; k < p; k += NT) Rk[pk(j, k)] *= inv;
+    __syncthreads();
+    // trailing update of column k (rows j < i <= k) by its 8 lanes
+    for (int k = j + 1 + cl; k < p; k += cstep) {
+      const double rjk = Rk[pk(j, k)];
+      for (int i = j + 1 + rl; i <= k; i += 8) Rk[pk(i, k)] -= Rk[pk(j, i)] * rjk;
     }
     __syncthreads();
   }
@@ -312,56 +314,6 @@ __device__ void ctrl_body(const Ctrl &c, double *sm) {
     c.Rt[e] = (i <= j) ? Rk[pk(i, j)] : 0.0;
   }
   for (int j = t; j < p; j += NT) c.Rdinv[j] = 1.0 / Rk[pk(j, j)];
-  if (c.Tinv != nullptr) {
-    // T = R~^{-1} (the explicit inverse of App. A): T_jj = 1 / R~_jj and
-    // T_ij = -T_jj sum_{i<=k<j} T_ik R~_kj for i < j, in increasing j.  Row i
-    // depends only on itself, so 8 lanes of one warp own it (each sum split
-    // over them in a fixed order) and synchronise as a warp.  Row i of T then
-    // satisfies t R~ = e_i^T to working accuracy, so T R~ - I stays small.
-    // The row is scaled by 2^c_i with c_i = floor(log2 sqrt(X_ii)): the
-    // product Q = Y T is formed as (Y D^-1)(D T), D = diag(2^c), which
-    // balances the columns of Y and the rows of T (exact: powers of two).
-    double *Ts = (double *)(vecs + 2 * p);  // p x (p + 1), row-major with a padded stride
-    const int ldt = p + 1;
-    int *cexp = (int *)(Ts + (size_t)p * ldt);  // c_i
-    for (int e = t; e < p * ldt; e += NT) Ts[e] = 0.0;
-    __syncthreads();
-    for (int i = t; i < p; i += NT) {
-      Ts[i * ldt + i] = 1.0 / Rk[pk(i, i)];  // each reciprocal once
-      const double xii = c.C[(q + i) + (int64_t)i * ldc];
-      const int ci = (xii > 0.0 && isfinite(xii)) ? (ilogb(xii) >> 1) : 0;
-      cexp[i] = ci;
-      c.Tscale[i] = ci;
-    }
-    __syncthreads();
-    const int sub = t & 7, ir = t >> 3;
-    for (int j = 1; j < p; ++j) {
-      const double tjj = Ts[j * ldt + j];
-      double s = 0.0;
-      if (ir < j)
-        for (int k = ir + sub; k < j; k += 8) s = fma(Ts[ir * ldt + k], Rk[pk(k, j)], s);
-      s += __shfl_xor_sync(0xffffffffu, s, 1);
-      s += __shfl_xor_sync(0xffffffffu, s, 2);
-      s += __shfl_xor_sync(0xffffffffu, s, 4);
-      if (sub == 0 && ir < j) Ts[ir * ldt + j] = -s * tjj;
-      // row ir is written and read only by its own 8 lanes, all in one warp
-      __syncwarp();
-    }
-    __syncthreads();
-    for (int e = t; e < p * p; e += NT) {
-      const int i = e % p, j = e / p;
-      const int ci = cexp[i];
-      double v = 0.0;
-      if (i <= j) {
-        // times 2^c_i: one multiplication by an exact power of two when
-        // 2^c_i is a normal number, ldexp otherwise
-        v = (ci >= -1022 && ci <= 1023)
-                ? Ts[i * ldt + j] * __longlong_as_double((long long)(1023 + ci) << 52)
-                : ldexp(Ts[i * ldt + j], ci);
-      }
-      c.Tinv[e] = v;
-    }
-  }
   __syncthreads();
   // R_old into the (no longer needed) X region
   double *Rold = X;
@@ -428,12 +380,57 @@ cudaError_t launch_ctrl_batched(const Ctrl *reqs, const int *nreq, int grid, siz
   return cudaGetLastError();
 }
 
-// X (p x p), packed R~, two float vectors, then (when the pass forms it)
-// T = R~^{-1} (p x (p + 1)).
-size_t ctrl_smem_bytes(int p, bool with_t) {
+// X (p x p), packed R~, two float vectors.
+size_t ctrl_smem_bytes(int p) {
   return (size_t)p * p * sizeof(double) + (size_t)(p * (p + 1) / 2 + 1) * sizeof(double) +
-         (size_t)2 * p * sizeof(float) +
-         (with_t ? (size_t)p * (p + 1) * sizeof(double) + (size_t)p * sizeof(int) : 0) + 64;
+         (size_t)2 * p * sizeof(float) + 64;
+}
+
+// T = D R~^{-1} for the tensor-core solve (the explicit inverse of App. A),
+// one single-warp CTA per row: row i of T solves t R~ = e_i^T by forward
+// substitution, T_ii = 1 / R~_ii and T_ij = -(sum_{i<=k<j} T_ik R~_kj) / R~_jj
+// in increasing j (each sum split over the 32 lanes, combined in a fixed
+// butterfly), so T R~ - I stays at working accuracy.  The row is then scaled
+// by 2^c_i, c_i = floor(log2 sqrt(X_ii)): the product Q = Y T is formed as
+// (Y D^-1)(D T), D = diag(2^c), which balances the columns of Y and the rows
+// of T (exact: powers of two).  Rows are independent, so they run on
+// separate SMs.
+__global__ void __launch_bounds__(32) tinv_kernel(const double *Rt, const double *Rdinv, const double *C,
+                                                  int ldc, int q, int p, double *Tinv, int *Tscale,
+                                                  const DevState *st) {
+  if (st != nullptr && st->done) return;
+  extern __shared__ double tr[];  // row i of T, p entries
+  const int i = blockIdx.x, lane = threadIdx.x;
+  if (i >= p) return;
+  for (int j = lane; j < p; j += 32) tr[j] = 0.0;
+  __syncwarp();
+  if (lane == 0) tr[i] = Rdinv[i];
+  __syncwarp();
+  for (int j = i + 1; j < p; ++j) {
+    double s = 0.0;
+    for (int k = i + lane; k < j; k += 32) s = fma(tr[k], Rt[k + (int64_t)j * p], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) tr[j] = -s * Rdinv[j];
+    __syncwarp();
+  }
+  const double xii = C[(q + i) + (int64_t)i * ldc];
+  const int ci = (xii > 0.0 && isfinite(xii)) ? (ilogb(xii) >> 1) : 0;
+  if (lane == 0) Tscale[i] = ci;
+  // times 2^c_i: one multiplication by an exact power of two when 2^c_i is
+  // a normal number, ldexp otherwise
+  const bool normal = (ci >= -1022 && ci <= 1023);
+  const double sc = normal ? __longlong_as_double((long long)(1023 + ci) << 52) : 1.0;
+  for (int j = lane; j < p; j += 32) {
+    const double v = tr[j];
+    Tinv[i + (int64_t)j * p] = (j < i) ? 0.0 : (normal ? v * sc : ldexp(v, ci));
+  }
+}
+
+cudaError_t launch_tinv(const double *Rt, const double *Rdinv, const double *C, int ldc, int q, int p,
+                        double *Tinv, int *Tscale, const DevState *st, cudaStream_t s) {
+  tinv_kernel<<<p, 32, sizeof(double) * (size_t)p, s>>>(Rt, Rdinv, C, ldc, q, p, Tinv, Tscale, st);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_ctrl(const Ctrl &a, cudaStream_t s) {
@@ -442,10 +439,7 @@ cudaError_t launch_ctrl(const Ctrl &a, cudaStream_t s) {
     cudaFuncSetAttribute(ctrl_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_done = true;
   }
-  // T is formed only for p <= 64 (the tensor-core solve), where 512 threads
-  // cover one row of T per 8 lanes
-  if (a.Tinv != nullptr && a.p > 64) return cudaErrorInvalidValue;
-  ctrl_kernel<<<1, kCtrlThreads, ctrl_smem_bytes(a.p, a.Tinv != nullptr), s>>>(a);
+  ctrl_kernel<<<1, kCtrlThreads, ctrl_smem_bytes(a.p), s>>>(a);
   return cudaGetLastError();
 }
 

@@ -294,7 +294,7 @@ cudaError_t batch_ws_create(BatchWS &w, int cap, int device) {
 cudaError_t batch_launches(BatchWS &w, bool start, int passes) {
   const int grid = 2 * num_sms();
   const size_t smem_tile = 196608;
-  const size_t smem_ctrl = ctrl_smem_bytes(kSmallMaxP, false);
+  const size_t smem_ctrl = ctrl_smem_bytes(kSmallMaxP);
   cudaError_t e = cudaSuccess;
   auto red = [&]() {
     return launch_reduce_batched(w.d_red, w.d_red_req, w.d_red_chunk, w.d_counts + 1, grid, w.stream);
