@@ -449,8 +449,13 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
     c.B = P.B;
     c.ldb = P.ldb;
     c.st = s.st;
+    c.r_external = (P.mode == MODE_FACTOR) ? 1 : 0;
     g_launches++;
     cudaError_t e = launch_ctrl(c, str);
+    if (e == cudaSuccess && c.r_external) {
+      g_launches++;
+      e = launch_rupdate(s.Rt, p, P.R, P.ldr, s.st, str);
+    }
     // T = D R~^{-1} for the next pass's tensor-core solve
     if (e == cudaSuccess && gemm) {
       g_launches++;

@@ -89,6 +89,7 @@ struct Ctrl {
   // Mixed precision: when > 0 the first pass is always shifted by
   // max(first_shift_coeff * ||X||, 2u) (the Gramian came from FP32 data).
   double first_shift_coeff;
+  int32_t r_external;  // 1: R <- R~ R is left to launch_rupdate (factor mode)
   const double *C;  // (q + p) x p, ld q + p
   double *Rt;       // p x p, ld p
   double *Rdinv;    // p
@@ -114,6 +115,10 @@ constexpr int kGram32Depth = 64 + 2;
 cudaError_t launch_reduce(const Reduce &a, cudaStream_t s);
 cudaError_t launch_ctrl(const Ctrl &a, cudaStream_t s);
 size_t ctrl_smem_bytes(int p);
+// R <- R~ R (Alg. 1 line 10) with one CTA per column of R, after the control
+// kernel of a pass that continues (for controls run with r_external = 1).
+cudaError_t launch_rupdate(const double *Rt, int p, double *R, int64_t ldr, const DevState *st,
+                           cudaStream_t s);
 // T = D R~^{-1} and the exponents of D (for the tensor-core solve), one
 // warp per row, after the control kernel of a pass.
 cudaError_t launch_tinv(const double *Rt, const double *Rdinv, const double *C, int ldc, int q, int p,

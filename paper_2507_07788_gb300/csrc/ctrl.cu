@@ -17,6 +17,8 @@
 
 namespace cqr {
 
+constexpr int kCqrMaxN = CQR_MAX_N;
+
 __device__ __forceinline__ int pk(int i, int j) { return i + j * (j + 1) / 2; }  // i <= j
 
 // Sum over the block, fixed butterfly + fixed warp order: deterministic.
@@ -332,8 +334,10 @@ __device__ void ctrl_body(const Ctrl &c, double *sm) {
       c.B[i + (int64_t)j * c.ldb] = c.B[i + (int64_t)j * c.ldb] + s;
     }
   }
-  // R <- R~ R_old  (Alg. 1 line 10, Alg. 2 line 14)
-  for (int e = t; e < p * p; e += NT) {
+  // R <- R~ R_old  (Alg. 1 line 10, Alg. 2 line 14); with r_external the
+  // factorisation leaves it to rupdate_kernel, which spreads the columns of
+  // R over SMs
+  for (int e = t; e < (c.r_external ? 0 : p * p); e += NT) {
     const int i = e % p, j = e / p;
     double s = 0.0;
     if (i <= j)
@@ -395,23 +399,30 @@ size_t ctrl_smem_bytes(int p) {
 // (Y D^-1)(D T), D = diag(2^c), which balances the columns of Y and the rows
 // of T (exact: powers of two).  Rows are independent, so they run on
 // separate SMs.
-__global__ void __launch_bounds__(32) tinv_kernel(const double *Rt, const double *Rdinv, const double *C,
-                                                  int ldc, int q, int p, double *Tinv, int *Tscale,
-                                                  const DevState *st) {
+__global__ void __launch_bounds__(128) tinv_kernel(const double *Rt, const double *Rdinv, const double *C,
+                                                   int ldc, int q, int p, double *Tinv, int *Tscale,
+                                                   const DevState *st) {
   if (st != nullptr && st->done) return;
-  extern __shared__ double tr[];  // row i of T, p entries
-  const int i = blockIdx.x, lane = threadIdx.x;
+  extern __shared__ double sh[];  // R~ (p x p, ld p), 1 / diag, then row i of T
+  double *Rs = sh, *rd = sh + (size_t)p * p, *tr = rd + p;
+  const int i = blockIdx.x, t = threadIdx.x, lane = t & 31;
   if (i >= p) return;
-  for (int j = lane; j < p; j += 32) tr[j] = 0.0;
-  __syncwarp();
-  if (lane == 0) tr[i] = Rdinv[i];
+  // the dependent steps below read only shared memory
+  for (int e = t; e < p * p; e += blockDim.x) Rs[e] = Rt[e];
+  for (int j = t; j < p; j += blockDim.x) {
+    rd[j] = Rdinv[j];
+    tr[j] = 0.0;
+  }
+  __syncthreads();
+  if (t >= 32) return;
+  if (lane == 0) tr[i] = rd[i];
   __syncwarp();
   for (int j = i + 1; j < p; ++j) {
     double s = 0.0;
-    for (int k = i + lane; k < j; k += 32) s = fma(tr[k], Rt[k + (int64_t)j * p], s);
+    for (int k = i + lane; k < j; k += 32) s = fma(tr[k], Rs[k + j * p], s);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) tr[j] = -s * Rdinv[j];
+    if (lane == 0) tr[j] = -s * rd[j];
     __syncwarp();
   }
   const double xii = C[(q + i) + (int64_t)i * ldc];
@@ -427,9 +438,36 @@ __global__ void __launch_bounds__(32) tinv_kernel(const double *Rt, const double
   }
 }
 
+// R <- R~ R for a factorisation pass that continues: column j of the new R
+// is R~ times column j of the old one (rows i <= j, the sum over k = i..j in
+// increasing k), so each CTA updates its own column in place.
+__global__ void __launch_bounds__(128) rupdate_kernel(const double *Rt, int p, double *R, int64_t ldr,
+                                                      const DevState *st) {
+  if (st != nullptr && st->done) return;  // the pass stopped: R is final
+  __shared__ double col[kCqrMaxN];
+  const int j = blockIdx.x, t = threadIdx.x;
+  if (j >= p) return;
+  for (int k = t; k <= j; k += blockDim.x) col[k] = R[k + (int64_t)j * ldr];
+  __syncthreads();
+  for (int i = t; i <= j; i += blockDim.x) {
+    double s = 0.0;
+    for (int k = i; k <= j; ++k) s += Rt[i + (int64_t)k * p] * col[k];
+    R[i + (int64_t)j * ldr] = s;
+  }
+}
+
+cudaError_t launch_rupdate(const double *Rt, int p, double *R, int64_t ldr, const DevState *st,
+                           cudaStream_t s) {
+  if (p > kCqrMaxN) return cudaErrorInvalidValue;
+  rupdate_kernel<<<p, 128, 0, s>>>(Rt, p, R, ldr, st);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_tinv(const double *Rt, const double *Rdinv, const double *C, int ldc, int q, int p,
                         double *Tinv, int *Tscale, const DevState *st, cudaStream_t s) {
-  tinv_kernel<<<p, 32, sizeof(double) * (size_t)p, s>>>(Rt, Rdinv, C, ldc, q, p, Tinv, Tscale, st);
+  if (p > 64) return cudaErrorInvalidValue;  // R~ and a row of T in shared memory
+  tinv_kernel<<<p, 128, sizeof(double) * ((size_t)p * p + 2 * p), s>>>(Rt, Rdinv, C, ldc, q, p, Tinv, Tscale,
+                                                                      st);
   return cudaGetLastError();
 }
 
