@@ -220,8 +220,19 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
   }
 
   // Tensor-core Gramian (Ozaki digits) for factorisations with n <= 128.
-  // (Updates, including the first block of an empty basis, keep the FP64
-  // sweep so that basis_append and the batched serving path agree bitwise.)
+  // Wide appends to tall bases (m >= kOzUpdMinRows, 32 <= p <= 64) form
+  // their cross Gramian [Q_in Y]^T Y on the tensor cores too (xoz) and keep
+  // the FP64 projection + solve; the others keep the fused FP64 sweep.
+  const bool xoz = (P.mode == MODE_UPDATE) && (P.o.emulation == CQR_EMU_AUTO) &&
+                   (P.m >= kOzUpdMinRows) && (p >= kOzUpdMinP) && (p <= 64);
+  int Gx = 0;
+  int64_t x_rows_per_cta = 0;
+  if (xoz) {
+    Gx = ozxgram_grid(P.m, q, p);
+    const int64_t tr = ozxgram_tile_rows();
+    const int64_t tiles = (P.m + tr - 1) / tr;
+    x_rows_per_cta = ((tiles + Gx - 1) / Gx) * tr;
+  }
   const bool oz = (P.mode == MODE_FACTOR) && (p <= kOzMaxN) && (P.o.emulation == CQR_EMU_AUTO);
   const int Goz = oz ? ozgram_grid(P.m, p) : 0;
   int64_t oz_rows_per_cta = 0;
@@ -251,7 +262,9 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
   }
   AuxCtx *ax = pipe ? aux_ctx(nchunks) : nullptr;
   const int64_t oz_parts = oz ? std::max<int64_t>((int64_t)Goz, (int64_t)Gc) * p * p : 0;
-  const int64_t part_elems = std::max<int64_t>(E, (oz_parts + G - 1) / G);
+  const int64_t x_parts = xoz ? (int64_t)Gx * (q + p) * p : 0;
+  const int64_t part_elems = std::max<int64_t>(E, (std::max(oz_parts, x_parts) + G - 1) / G);
+  bool last_x = false;   // the last sweep left dense cross-Gramian partials
   bool last_oz = false;  // which reduction the last sweep needs
   int last_oz_G = Goz;   // and over how many partials
 
@@ -326,6 +339,30 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
     }
     cudaError_t e = cudaSuccess;
     last_oz = false;
+    last_x = false;
+    if (xoz) {
+      // projection + solve on the FP64 sweep (transform only), then the
+      // cross Gramian of the new block on the tensor cores
+      if (trsm) {
+        RowSweep tf = a;
+        tf.E = 0;
+        e = launch_rowsweep(tf, G, str);
+        g_launches++;
+      }
+      RowSweep x = a;
+      x.Yin = trsm ? P.Y : a.Yin;
+      x.ldyin = trsm ? P.ldy : a.ldyin;
+      x.do_trsm = 0;
+      x.rows_per_cta = x_rows_per_cta;
+      SweepMark *mg = kmark(MARK_GRAM, npass, 2.0 * m_d * (q + p) * p, 8.0 * m_d * (q + p));
+      if (mg && e == cudaSuccess) cudaEventRecord(mg->a, str);
+      if (e == cudaSuccess) e = launch_ozxgram(x, Gx, str);
+      if (mg && e == cudaSuccess) cudaEventRecord(mg->b, str);
+      g_launches++;
+      last_x = true;
+      if (mk != nullptr) cudaEventRecord(mk->b, str);
+      return e;
+    }
     if (pipe && trsm && ax != nullptr) {
       // chunked pipeline: solve chunk c on str; its Gramian on the aux stream
       for (int c = 0; c < nchunks && e == cudaSuccess; ++c) {
@@ -423,6 +460,7 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
   };
   auto reduce = [&]() -> cudaError_t {
     g_launches++;
+    if (last_x) return launch_reduce_dense(s.partials, Gx, (int64_t)(q + p) * p, s.C, s.st, str);
     if (last_oz) return launch_reduce_oz(s.partials, last_oz_G, p, s.C, s.st, str);
     Reduce r{s.partials, G, E, q, p, s.C, s.st};
     return launch_reduce(r, str);

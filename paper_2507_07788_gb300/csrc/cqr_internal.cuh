@@ -151,6 +151,20 @@ int ozgemm_tile_rows();
 // the k-blocks its upper-triangular T does not skip).
 double ozgemm_tc_flops_per_row(int n);
 constexpr int kOzGemmMaxN = 64;
+// Cross Gramian of the update, C = [Q_in Y]^T Y, on the tensor cores (exact
+// digit products, p <= 64): partials of `groups` row groups, each (q + p) x p.
+cudaError_t launch_ozxgram(const RowSweep &a, int groups, cudaStream_t s);
+int ozxgram_grid(int64_t m, int q, int p);
+int ozxgram_tile_rows();
+cudaError_t launch_reduce_dense(const double *partials, int G, int64_t E, double *C, const DevState *st,
+                                cudaStream_t s);
+// Appends of at least kOzUpdMinP columns to bases of at least kOzUpdMinRows
+// rows take the tensor-core cross Gramian.  Narrower blocks keep the fused
+// FP64 sweep (its projection and Gramian share one read, and their FP64 work
+// is small); shorter bases keep it too (the serving runtime's batched appends
+// use it, so a batched append and a direct one agree bitwise).
+constexpr int64_t kOzUpdMinRows = 262144;
+constexpr int kOzUpdMinP = 32;
 // Below this width the FP64 substitution (n^2 FP64 instructions per row) is
 // cheaper than the digit product's fixed per-row work.
 constexpr int kOzGemmMinN = 33;

@@ -56,25 +56,6 @@ struct OzCfg {
 };
 constexpr int kOzDigits = 8;
 
-// Rescales an accumulator pair (value = hi * 2^28 u + lo * u) to a unit 2^D
-// times larger when a column's running exponent grows by D: the bits that
-// leave hi move into lo before lo is shifted, so only bits below the new
-// lo unit are dropped.  For D >= 62 the old value lies below 2^-62 of the
-// entry's new magnitude and is dropped.
-__device__ __forceinline__ void shift_pair(long long &hi, long long &lo, int D) {
-  if (D <= 0) return;
-  if (D >= 62) {
-    hi = 0;
-    lo = 0;
-    return;
-  }
-  const long long q = hi >> D;
-  const long long rm = hi - (q << D);  // 0 <= rm < 2^D
-  if (D <= 34) lo = (lo + (rm << 28)) >> D;
-  else lo = (lo >> D) + (rm >> (D - 28));
-  hi = q;
-}
-
 // Orders 2..9 split into `groups` groups, balanced by the number of digit
 // pairs they contain (5 each for four groups): does group grp own order d?
 __device__ __forceinline__ bool order_in_group(int groups, int grp, int d) {

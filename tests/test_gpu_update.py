@@ -128,3 +128,63 @@ def test_wide_basis_split_sweep(cq, orc):
     assert Qg.shape[1] == 288
     assert orc.loo_frob(Qg) <= 1e-12
     b.close()
+
+
+def _check_append(orc, Qo, Ro, blk, Qg, Rg, m, info, k):
+    """One append against the oracle's Alg. 2 (as in the growth test)."""
+    p = blk.shape[1]
+    Qn, Bn, Rn, sto, info_o = orc.cholqr_update(Qo, blk, min_iter=2)
+    q = Qo.shape[1]
+    Qo2 = np.hstack([Qo, Qn])
+    Ro2 = np.block([[Ro, Bn], [np.zeros((p, q)), Rn]])
+    assert Qg.shape == (m, q + p)
+    assert orc.loo_frob(Qg) <= 1e-12, k
+    scale = max(np.max(np.abs(Rn)), np.max(np.abs(Bn)) if q else 0.0)
+    dR = np.max(np.abs(Rg[: q + p, q:] - Ro2[: q + p, q:]))
+    dQ = np.max(np.abs(Qg[:, q:] - Qn))
+    return Qo2, Ro2, dR, dQ, scale, sto, info_o
+
+
+@pytest.mark.parametrize("widths", [(32, 40), (64, 8, 32), (8, 20)])
+def test_tall_basis_tensor_cross_gramian(cq, orc, widths):
+    # m above the row limit of the serving runtime's batched appends: appends
+    # of 32..64 columns form the cross Gramian [Q_in Y]^T Y of every iteration
+    # on the tensor cores (p = 32: 32-wide kernel; 40, 64: 64-wide), narrower
+    # ones keep the fused FP64 sweep; both must follow the oracle
+    m = 300007
+    b = cq.Basis(m, sum(widths))
+    Qo = np.zeros((m, 0))
+    Ro = np.zeros((0, 0))
+    blocks = []
+    rng = np.random.default_rng(77)
+    for k, p in enumerate(widths):
+        if k == 0:
+            blk = synth.gaussian(m, p, seed=70 + k)
+        else:
+            # near-dependent on the basis so far (the growth recipe)
+            blk = Qo @ rng.standard_normal((Qo.shape[1], p)) * 0.1 + synth.gaussian(m, p, seed=70 + k) * 1e-6
+        blocks.append(blk)
+        st, info = b.append(cq.to_colmajor(blk))
+        Qg, Rg = b.Q().cpu().numpy(), b.R().cpu().numpy()
+        Qo, Ro, dR, dQ, scale, sto, info_o = _check_append(orc, Qo, Ro, blk, Qg, Rg, m, info, k)
+        assert st == sto and st >= 0, (k, st, info, info_o)
+        Afull = np.hstack(blocks)
+        assert orc.rrr(Afull, Qg, Rg) <= 1e-13, k
+        sv = np.linalg.svd(Afull, compute_uv=False)
+        kap = sv[0] / sv[-1]
+        q = Qg.shape[1] - p
+        print(f"append {k} p={p}: iters={info['iters']}/{info_o.iters} dR={dR:.2e} dQ={dQ:.2e} kappa={kap:.1e}")
+        assert dR <= 200 * kap * U * math.sqrt(q + p) * scale + 1e-15
+        assert dQ <= max(1e-12, 200 * kap * U * math.sqrt(p) / math.sqrt(m))
+    b.close()
+
+
+def test_tall_basis_nan_breaks_down(cq):
+    m = 300007
+    b = cq.Basis(m, 16, opts=cq.default_opts(max_escalations=0))
+    b.append(cq.to_colmajor(synth.gaussian(m, 8, seed=80)))
+    bad = synth.gaussian(m, 8, seed=81)
+    bad[123456, 3] = np.nan
+    st, info = b.append(cq.to_colmajor(bad), check=False)
+    assert st == cq.ERR_BREAKDOWN and b.cols == 8
+    b.close()
