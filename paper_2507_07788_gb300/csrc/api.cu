@@ -56,8 +56,19 @@ struct AuxCtx {
   std::vector<cudaEvent_t> ev;
 };
 
+constexpr int kMaxDevices = 64;
+
+int current_device() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return (dev >= 0 && dev < kMaxDevices) ? dev : 0;
+}
+
+// One auxiliary stream per host thread and device (streams and events belong
+// to the device that was current when they were created).
 AuxCtx *aux_ctx(int nchunks) {
-  thread_local AuxCtx c;
+  thread_local AuxCtx per_device[kMaxDevices];
+  AuxCtx &c = per_device[current_device()];
   if (c.aux == nullptr) {
     if (cudaStreamCreateWithFlags(&c.aux, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming) != cudaSuccess) {
@@ -80,11 +91,12 @@ AuxCtx *aux_ctx(int nchunks) {
 constexpr int kMaxChunks = 8;
 constexpr int64_t kMinChunkRows = 78 * 1024;
 
-// Thread-local pool of event pairs for the sweep marks of one call.  A deque:
-// a mark taken before a later one is added must keep its address.
+// Thread-local pool of event pairs for the sweep marks of one call, per
+// device.  A deque: a mark taken before a later one is added must keep its
+// address.
 std::deque<SweepMark> &marks_pool() {
-  thread_local std::deque<SweepMark> pool;
-  return pool;
+  thread_local std::deque<SweepMark> pool[kMaxDevices];
+  return pool[current_device()];
 }
 
 cqr_status cuda_status(cudaError_t e) {

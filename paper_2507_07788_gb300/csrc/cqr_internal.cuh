@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "cholqr.h"
 
 // A growing basis (Q m x n_max with q valid columns, R n_max x n_max).
@@ -15,6 +17,24 @@ struct cqr_basis {
 };
 
 namespace cqr {
+
+// Shared-memory attributes of a kernel belong to each device's context: this
+// sets them once per device (bit d of `done` for device d < 64; devices
+// beyond 64 set them on every launch).  Safe from several host threads.
+struct KernelAttr {
+  std::atomic<uint64_t> done{0};
+};
+template <typename K>
+inline void set_smem_attr(KernelAttr &ka, K *kernel, int bytes, bool max_carveout) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const uint64_t bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0ull;
+  if (bit != 0 && (ka.done.load(std::memory_order_acquire) & bit) != 0) return;
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (max_carveout)
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  if (bit != 0) ka.done.fetch_or(bit, std::memory_order_release);
+}
 
 constexpr double kU64 = 1.1102230246251565404236316680908203125e-16;  // 2^-53
 constexpr int kThreads = 256;        // block size of the row-sweeping kernels

@@ -375,11 +375,8 @@ __global__ void __launch_bounds__(kCtrlThreads) ctrl_batched_kernel(const Ctrl *
 
 cudaError_t launch_ctrl_batched(const Ctrl *reqs, const int *nreq, int grid, size_t smem,
                                 cudaStream_t s) {
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaFuncSetAttribute(ctrl_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_done = true;
-  }
+  static KernelAttr attr;
+  set_smem_attr(attr, ctrl_batched_kernel, 200 * 1024, false);
   ctrl_batched_kernel<<<grid, kCtrlThreads, smem, s>>>(reqs, nreq);
   return cudaGetLastError();
 }
@@ -472,11 +469,8 @@ cudaError_t launch_tinv(const double *Rt, const double *Rdinv, const double *C, 
 }
 
 cudaError_t launch_ctrl(const Ctrl &a, cudaStream_t s) {
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaFuncSetAttribute(ctrl_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_done = true;
-  }
+  static KernelAttr attr;
+  set_smem_attr(attr, ctrl_kernel, 200 * 1024, false);
   ctrl_kernel<<<1, kCtrlThreads, ctrl_smem_bytes(a.p), s>>>(a);
   return cudaGetLastError();
 }

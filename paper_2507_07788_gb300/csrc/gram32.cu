@@ -136,11 +136,8 @@ void gram32_geometry(int q, int p, int *tile_rows, int *lds, size_t *smem) {
 
 template <int EPT>
 static cudaError_t launch32_ept(const RowSweep &a, dim3 grid, size_t smem, cudaStream_t s) {
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaFuncSetAttribute(gram32_kernel<EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_done = true;
-  }
+  static KernelAttr attr;
+  set_smem_attr(attr, gram32_kernel<EPT>, 200 * 1024, false);
   gram32_kernel<EPT><<<grid, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }

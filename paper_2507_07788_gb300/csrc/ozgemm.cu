@@ -301,13 +301,8 @@ __global__ void __launch_bounds__(kGmThreads, 2) ozgemm_kernel(RowSweep a) {
 }
 
 static cudaError_t launch_gm(const RowSweep &a, int grid, cudaStream_t s) {
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaFuncSetAttribute(ozgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGmSmem);
-    cudaFuncSetAttribute(ozgemm_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                         cudaSharedmemCarveoutMaxShared);
-    attr_done = true;
-  }
+  static KernelAttr attr;
+  set_smem_attr(attr, ozgemm_kernel, (int)kGmSmem, true);
   ozgemm_kernel<<<grid, kGmThreads, kGmSmem, s>>>(a);
   return cudaGetLastError();
 }

@@ -340,14 +340,9 @@ int ozgram_nt(int n) { return n <= 16 ? 16 : (n <= 32 ? 32 : (n <= 64 ? 64 : 128
 
 template <int NT>
 static cudaError_t launch_oz(const RowSweep &a, int grid, cudaStream_t s) {
-  static bool attr_done = false;
+  static KernelAttr attr;
   const size_t smem = ozgram_smem_bytes(NT);
-  if (!attr_done) {
-    cudaFuncSetAttribute(ozgram_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(ozgram_kernel<NT>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                         cudaSharedmemCarveoutMaxShared);
-    attr_done = true;
-  }
+  set_smem_attr(attr, ozgram_kernel<NT>, (int)smem, true);
   // the fused solve exists for n <= 64 only
   if (NT > 64 && a.do_trsm) return cudaErrorInvalidValue;
   ozgram_kernel<NT><<<grid * OzCfg<NT>::halves, OzCfg<NT>::threads, smem, s>>>(a);

@@ -286,11 +286,8 @@ __global__ void __launch_bounds__(kXThreads, 1) ozxgram_kernel(RowSweep a, int n
 template <int NY>
 static cudaError_t launch_x(const RowSweep &a, int groups, int nzb, cudaStream_t s) {
   constexpr size_t smem = xgram_smem<NY>();
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaFuncSetAttribute(ozxgram_kernel<NY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr_done = true;
-  }
+  static KernelAttr attr;
+  set_smem_attr(attr, ozxgram_kernel<NY>, (int)smem, false);
   ozxgram_kernel<NY><<<groups * nzb, kXThreads, smem, s>>>(a, nzb);
   return cudaGetLastError();
 }

@@ -197,13 +197,17 @@ __global__ void init_batched_kernel(const Ctrl *reqs, const int *nreq) {
   }
 }
 
+// SM count of the current device (cached per device).
 int num_sms() {
-  static int sms = 0;
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const bool cached = dev >= 0 && dev < 64;
+  int sms = cached ? cache[dev].load(std::memory_order_relaxed) : 0;
   if (sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 1;
+    if (cached) cache[dev].store(sms, std::memory_order_relaxed);
   }
   return sms;
 }
@@ -226,11 +230,8 @@ int rowsweep_grid(int64_t m, int tile_rows) {
 
 template <int EPT>
 static cudaError_t launch_ept(const RowSweep &a, dim3 grid, size_t smem, cudaStream_t s) {
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaFuncSetAttribute(rowsweep_kernel<EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_done = true;
-  }
+  static KernelAttr attr;
+  set_smem_attr(attr, rowsweep_kernel<EPT>, 200 * 1024, false);
   rowsweep_kernel<EPT><<<grid, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
@@ -260,12 +261,8 @@ cudaError_t launch_rowsweep(const RowSweep &a, int grid, cudaStream_t s) {
 
 cudaError_t launch_rowsweep_batched(const RowSweep *reqs, const int *item_req, const int *item_cta,
                                     const int *nitems, int grid, size_t smem, cudaStream_t s) {
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaFuncSetAttribute(rowsweep_batched_kernel<kBatchEPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         200 * 1024);
-    attr_done = true;
-  }
+  static KernelAttr attr;
+  set_smem_attr(attr, rowsweep_batched_kernel<kBatchEPT>, 200 * 1024, false);
   rowsweep_batched_kernel<kBatchEPT><<<grid, kThreads, smem, s>>>(reqs, item_req, item_cta, nitems);
   return cudaGetLastError();
 }

@@ -121,11 +121,8 @@ __global__ void __launch_bounds__(kTrsm4Threads, 1) trsm_rows4_kernel(RowSweep a
 template <int NT>
 static cudaError_t launch_tr(const RowSweep &a, int grid, cudaStream_t s) {
   const size_t smem = sizeof(double) * ((size_t)NT * NT + NT);
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaFuncSetAttribute(trsm_rows_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-    attr_done = true;
-  }
+  static KernelAttr attr;
+  set_smem_attr(attr, trsm_rows_kernel<NT>, 64 * 1024, false);
   trsm_rows_kernel<NT><<<grid, kTrsmThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
@@ -133,11 +130,8 @@ static cudaError_t launch_tr(const RowSweep &a, int grid, cudaStream_t s) {
 static cudaError_t launch_tr4(const RowSweep &a, cudaStream_t s) {
   constexpr int NT = kTrsm4NT;
   const size_t smem = sizeof(double) * ((size_t)NT * NT + NT);
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaFuncSetAttribute(trsm_rows4_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr_done = true;
-  }
+  static KernelAttr attr;
+  set_smem_attr(attr, trsm_rows4_kernel, (int)smem, false);
   const int64_t rows_per_cta = kTrsm4Threads / 4;
   const int grid = (int)std::max<int64_t>(
       1, std::min<int64_t>((a.m + rows_per_cta - 1) / rows_per_cta, (int64_t)num_sms()));
