@@ -162,10 +162,22 @@ cqr_status cholqr_gram(const cqr_opts *opts, int64_t m, int64_t n, const double 
                        double *X, int64_t ldx, void *stream);
 
 /*
- * cholqr_factor_host -- the same factorisation on HOST buffers: copies A to
- * the device, factors it there with cholqr_factor and copies Q and R back.
- * A, Q, R are host pointers (pinned memory gives full copy bandwidth); the
- * device copies are stream-ordered scratch freed before return.
+ * cholqr_factor_host -- the same factorisation on HOST buffers, with the
+ * copies overlapped with the passes where the tensor-core path runs
+ * (n <= 128, CQR_PREC_FP64, emulation CQR_EMU_AUTO): A goes to the device in
+ * row chunks while the first Gramian consumes the chunks that have landed,
+ * and when Q is page-locked (cudaHostAlloc / cudaHostRegister) each pass
+ * writes its Q chunks straight into it as they are solved, so only the last
+ * chunk's copy trails the last pass.  Otherwise A is copied whole first and
+ * Q copied whole after.  The first Gramian sums its partials by row chunk,
+ * so Q and R agree with cholqr_factor on the same data to rounding, not bit
+ * for bit.
+ *   A, lda    host, m x n, lda >= m (read only; pinned for full bandwidth).
+ *   Q, ldq    host, m x n output, ldq >= m; must not overlap A.  Its contents
+ *             are undefined while the call runs and after an error.
+ *   R, ldr    host, n x n output, ldr >= n.
+ * The device copies are stream-ordered scratch freed before return; the call
+ * returns after the stream has drained.  Status as cholqr_factor.
  */
 cqr_status cholqr_factor_host(const cqr_opts *opts, int64_t m, int64_t n, const double *A,
                               int64_t lda, double *Q, int64_t ldq, double *R, int64_t ldr,

@@ -88,6 +88,72 @@ AuxCtx *aux_ctx(int nchunks) {
   return &c;
 }
 
+// Copy stream of the host-staged factorisation, per host thread and device,
+// with an event per row chunk for its host->device copy (h) and for the
+// device->host copy of Q after a pass (c), and a page-locked record of the
+// pass whose Q each chunk last received.
+struct CopyCtx {
+  cudaStream_t st = nullptr;
+  cudaEvent_t start = nullptr;
+  std::vector<cudaEvent_t> h, c;
+  int *copied = nullptr;    // host view
+  int *copied_d = nullptr;  // device view
+};
+
+constexpr int kCopyGrid = 16, kCopyThreads = 1024;
+
+// Q chunk -> host after pass k's solve of that chunk, speculatively: pass k
+// is taken to be the last when its input was already orthonormal to
+// ||Q^T Q - I||_F < kCopyAheadOrth (one Cholesky QR pass of such a Q lands
+// on the roundoff floor).  It copies iff pass k ran (the control step sets
+// iters to the index of the pass it admits; iters never decreases) and that
+// test holds; the control step after pass k waits for these copies, so the
+// state it reads is the one before pass k.  `copied` records the pass.
+constexpr double kCopyAheadOrth = 1e-2;
+
+__global__ void __launch_bounds__(kCopyThreads) copy_out_kernel(const double *src, int64_t lds, int64_t rows,
+                                                                int cols, double *dst, int64_t ldd, int k,
+                                                                const DevState *st, int *copied) {
+  if (st->iters < k || !(st->orth_frob < kCopyAheadOrth)) return;
+  const int64_t n = rows * cols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % rows, j = e / rows;
+    dst[i + j * ldd] = src[i + j * lds];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *copied = k;
+}
+
+CopyCtx *copy_ctx(int nchunks) {
+  thread_local CopyCtx per_device[kMaxDevices];
+  CopyCtx &x = per_device[current_device()];
+  if (x.st == nullptr) {
+    if (cudaStreamCreateWithFlags(&x.st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&x.start, cudaEventDisableTiming) != cudaSuccess ||
+        cudaHostAlloc((void **)&x.copied, sizeof(int) * 64, cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void **)&x.copied_d, x.copied, 0) != cudaSuccess) {
+      (void)cudaGetLastError();
+      x.st = nullptr;
+      return nullptr;
+    }
+  }
+  while ((int)x.h.size() < nchunks) {
+    cudaEvent_t a, b;
+    if (cudaEventCreateWithFlags(&a, cudaEventDisableTiming) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return nullptr;
+    }
+    if (cudaEventCreateWithFlags(&b, cudaEventDisableTiming) != cudaSuccess) {
+      (void)cudaGetLastError();
+      cudaEventDestroy(a);
+      return nullptr;
+    }
+    x.h.push_back(a);
+    x.c.push_back(b);
+  }
+  return &x;
+}
+
 constexpr int kMaxChunks = 8;
 constexpr int64_t kMinChunkRows = 78 * 1024;
 
@@ -206,6 +272,16 @@ struct Problem {
   int mode;
   int min_iter;
   cqr_opts o;
+  // Host staging (cholqr_factor_host): Y0 == Y is the device copy of hA,
+  // filled by row chunks on a copy stream while the first Gramian runs; hQ
+  // (host memory the device can write, or null) receives Q chunk by chunk as
+  // each pass's solve finishes, and *hq_written tells the caller whether it
+  // holds the final Q.
+  const double *hA = nullptr;
+  int64_t ldha = 0;
+  double *hQ = nullptr;
+  int64_t ldhq = 0;
+  bool *hq_written = nullptr;
 };
 
 cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
@@ -273,6 +349,10 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
     chunk_rpc = ((tiles + Gc - 1) / Gc) * tr;
   }
   AuxCtx *ax = pipe ? aux_ctx(nchunks) : nullptr;
+  // host staging pipelined with the passes (the tensor-core pipeline only)
+  CopyCtx *cx = (P.hA != nullptr && pipe && !mixed && ax != nullptr) ? copy_ctx(nchunks) : nullptr;
+  const bool stage = cx != nullptr;
+  if (P.hq_written != nullptr) *P.hq_written = false;
   const int64_t oz_parts = oz ? std::max<int64_t>((int64_t)Goz, (int64_t)Gc) * p * p : 0;
   const int64_t x_parts = xoz ? (int64_t)Gx * (q + p) * p : 0;
   const int64_t part_elems = std::max<int64_t>(E, (std::max(oz_parts, x_parts) + G - 1) / G);
@@ -377,6 +457,7 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
     }
     if (pipe && trsm && ax != nullptr) {
       // chunked pipeline: solve chunk c on str; its Gramian on the aux stream
+      int last_c = -1;  // the last chunk copied to the host
       for (int c = 0; c < nchunks && e == cudaSuccess; ++c) {
         const int64_t r0 = (int64_t)c * chunk_rows;
         const int64_t rc = std::min(chunk_rows, P.m - r0);
@@ -403,6 +484,18 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
         g_launches++;
         if (e == cudaSuccess) e = cudaEventRecord(ax->ev[c], str);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(ax->aux, ax->ev[c], 0);
+        if (stage && P.hQ != nullptr && e == cudaSuccess) {
+          // chunk c of this pass's Q to the host while the next chunks run
+          e = cudaStreamWaitEvent(cx->st, ax->ev[c], 0);
+          if (e == cudaSuccess) {
+            copy_out_kernel<<<kCopyGrid, kCopyThreads, 0, cx->st>>>(tr.Yout, tr.ldyout, rc, p, P.hQ + r0,
+                                                                      P.ldhq, npass, s.st, cx->copied_d + c);
+            e = cudaGetLastError();
+            g_launches++;
+          }
+          if (e == cudaSuccess) e = cudaEventRecord(cx->c[c], cx->st);
+          last_c = c;
+        }
         RowSweep z = a;
         z.m = rc;
         z.Yin = a.Yout + r0;
@@ -422,6 +515,35 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
       // stale partials; all nchunks * Gc partials are written when rc > 0
       if (e == cudaSuccess) e = cudaEventRecord(ax->done, ax->aux);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(str, ax->done, 0);
+      // the control step reads the state the copies test, and the next pass
+      // overwrites the chunks they read
+      if (stage && P.hQ != nullptr && e == cudaSuccess && last_c >= 0)
+        e = cudaStreamWaitEvent(str, cx->c[last_c], 0);
+      last_oz = true;
+      last_oz_G = Gc;
+      if (mk != nullptr) cudaEventRecord(mk->b, str);
+      return e;
+    }
+    if (stage && !trsm) {
+      // first Gramian by row chunks, each as soon as its copy has landed
+      for (int c = 0; c < nchunks && e == cudaSuccess; ++c) {
+        const int64_t r0 = (int64_t)c * chunk_rows;
+        const int64_t rc = std::min(chunk_rows, P.m - r0);
+        if (rc <= 0) break;
+        e = cudaStreamWaitEvent(str, cx->h[c], 0);
+        RowSweep z = a;
+        z.m = rc;
+        z.Yin = a.Yin + r0;
+        z.do_trsm = 0;
+        z.accumulate = (c > 0) ? 1 : 0;
+        z.rows_per_cta = chunk_rpc;
+        z.E = (int64_t)p * p;
+        SweepMark *mg = kmark(MARK_GRAM, 0, (double)rc * p * (p + 1.0), 8.0 * (double)rc * p);
+        if (mg && e == cudaSuccess) cudaEventRecord(mg->a, str);
+        if (e == cudaSuccess) e = launch_ozgram(z, Gc, str);
+        if (mg && e == cudaSuccess) cudaEventRecord(mg->b, str);
+        g_launches++;
+      }
       last_oz = true;
       last_oz_G = Gc;
       if (mk != nullptr) cudaEventRecord(mk->b, str);
@@ -520,7 +642,27 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
     return e;
   };
 
-  cudaError_t e = launch_init(P.R, P.ldr, p, P.B, P.ldb, q, s.st, str);
+  cudaError_t e = cudaSuccess;
+  if (P.hA != nullptr && !stage) {
+    // host input without the pipeline: one copy before everything
+    e = cudaMemcpy2DAsync(const_cast<double *>(P.Y0), sizeof(double) * P.ldy0, P.hA,
+                          sizeof(double) * P.ldha, sizeof(double) * P.m, p, cudaMemcpyHostToDevice, str);
+  } else if (stage) {
+    for (int c = 0; c < nchunks; ++c) cx->copied[c] = -1;
+    // row chunk c of A on the copy stream, after the caller's stream has
+    // reached this point (the device buffer is allocated there)
+    e = cudaEventRecord(cx->start, str);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cx->st, cx->start, 0);
+    for (int c = 0; c < nchunks && e == cudaSuccess; ++c) {
+      const int64_t r0 = (int64_t)c * chunk_rows;
+      const int64_t rc = std::min(chunk_rows, P.m - r0);
+      if (rc <= 0) break;
+      e = cudaMemcpy2DAsync(const_cast<double *>(P.Y0) + r0, sizeof(double) * P.ldy0, P.hA + r0,
+                            sizeof(double) * P.ldha, sizeof(double) * rc, p, cudaMemcpyHostToDevice, cx->st);
+      if (e == cudaSuccess) e = cudaEventRecord(cx->h[c], cx->st);
+    }
+  }
+  if (e == cudaSuccess) e = launch_init(P.R, P.ldr, p, P.B, P.ldb, q, s.st, str);
   g_launches++;
   if (e == cudaSuccess) e = sweep(false, true);
   if (e == cudaSuccess) e = reduce();
@@ -537,6 +679,7 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
   }
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
+    if (stage) (void)cudaStreamSynchronize(cx->st);
     cudaFreeAsync(s.base, str);
     return cuda_status(e);
   }
@@ -559,6 +702,23 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
     info->sigma_last = hs->sigma_last;
     info->orth_frob = hs->orth_frob;
     info->proj_frob = hs->proj_frob;
+  }
+  if (stage) {
+    // the copies read the device state and Q: finish them before the
+    // scratch (and the caller's buffers) can go
+    cudaError_t ec = cudaStreamSynchronize(cx->st);
+    if (e == cudaSuccess) e = ec;
+    if (e == cudaSuccess && P.hQ != nullptr && hs->done) {
+      // chunks whose last copy is not of the final pass (or none ran: Q = A)
+      for (int c = 0; c < nchunks && e == cudaSuccess; ++c) {
+        const int64_t r0 = (int64_t)c * chunk_rows;
+        const int64_t rc = std::min(chunk_rows, P.m - r0);
+        if (rc <= 0 || cx->copied[c] == hs->iters) continue;
+        e = cudaMemcpy2DAsync(P.hQ + r0, sizeof(double) * P.ldhq, P.Y + r0, sizeof(double) * P.ldy,
+                              sizeof(double) * rc, p, cudaMemcpyDefault, str);
+      }
+      if (e == cudaSuccess && P.hq_written != nullptr) *P.hq_written = true;
+    }
   }
   cudaError_t ef = cudaFreeAsync(s.base, str);
   if (e == cudaSuccess) e = ef;
@@ -743,10 +903,25 @@ cqr_status cholqr_gram(const cqr_opts *opts, int64_t m, int64_t n, const double 
 cqr_status cholqr_factor_host(const cqr_opts *opts, int64_t m, int64_t n, const double *A,
                               int64_t lda, double *Q, int64_t ldq, double *R, int64_t ldr,
                               cqr_info *info, void *stream) {
+  cqr_opts o;
+  cqr_default_opts(&o);
+  if (opts != nullptr) o = *opts;
+  if (!opts_valid(o)) return CQR_ERR_INVALID;
   if (n < 1 || n > CQR_MAX_N || m < n || lda < m || ldq < m || ldr < n) return CQR_ERR_INVALID;
   if (A == nullptr || Q == nullptr || R == nullptr) return CQR_ERR_INVALID;
+  if (host_state() == nullptr) return CQR_ERR_CUDA;
   cudaStream_t str = (cudaStream_t)stream;
   keep_pool_memory();
+  // Q written by the device as each pass ends needs page-locked host memory
+  // the device can address
+  double *dQh = nullptr;
+  {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, Q) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+        at.devicePointer != nullptr)
+      dQh = (double *)at.devicePointer;
+    (void)cudaGetLastError();
+  }
   double *dA = nullptr, *dR = nullptr;
   const int64_t ldd = m;
   CQR_TRY(cudaMallocAsync((void **)&dA, sizeof(double) * (size_t)m * n, str));
@@ -755,13 +930,35 @@ cqr_status cholqr_factor_host(const cqr_opts *opts, int64_t m, int64_t n, const 
     cudaFreeAsync(dA, str);
     return cuda_status(e);
   }
-  e = cudaMemcpy2DAsync(dA, sizeof(double) * ldd, A, sizeof(double) * lda, sizeof(double) * m, n,
-                        cudaMemcpyHostToDevice, str);
-  cqr_status st = CQR_ERR_CUDA;
-  if (e == cudaSuccess) st = cholqr_factor(opts, m, n, dA, ldd, dA, ldd, dR, n, info, stream);
+  bool q_written = false;
+  Problem P{};
+  P.m = m;
+  P.q = 0;
+  P.p = (int)n;
+  P.Qin = nullptr;
+  P.ldqin = 1;
+  P.Y0 = dA;
+  P.ldy0 = ldd;
+  P.Y = dA;
+  P.ldy = ldd;
+  P.R = dR;
+  P.ldr = n;
+  P.B = nullptr;
+  P.ldb = 1;
+  P.mode = MODE_FACTOR;
+  P.min_iter = o.min_iter;
+  P.o = o;
+  P.hA = A;
+  P.ldha = lda;
+  P.hQ = dQh;
+  P.ldhq = ldq;
+  P.hq_written = &q_written;
+  cqr_status st = run(P, info, str);
   if (st >= 0) {
-    e = cudaMemcpy2DAsync(Q, sizeof(double) * ldq, dA, sizeof(double) * ldd, sizeof(double) * m, n,
-                          cudaMemcpyDeviceToHost, str);
+    e = cudaSuccess;
+    if (!q_written)
+      e = cudaMemcpy2DAsync(Q, sizeof(double) * ldq, dA, sizeof(double) * ldd, sizeof(double) * m, n,
+                            cudaMemcpyDeviceToHost, str);
     if (e == cudaSuccess)
       e = cudaMemcpy2DAsync(R, sizeof(double) * ldr, dR, sizeof(double) * n, sizeof(double) * n, n,
                             cudaMemcpyDeviceToHost, str);

@@ -42,6 +42,19 @@ def r_tol(kappa, n, R):
     return 20.0 * max(kappa, 1.0) * U * math.sqrt(n) * np.max(np.abs(R))
 
 
+def loo_blocked(Q, rows=2048):
+    # ||Q^T Q - I||_F with the Gramian summed over row blocks of 2048: the
+    # oracle's row-by-row sum carries a rounding error near u sqrt(m/3) on
+    # each diagonal entry (3e-14 at m = 2e5), the size of the 1e-13 bound
+    # itself at n = 100; blocking cuts it to u (sqrt(rows) + m / rows)
+    m, n = Q.shape
+    G = np.zeros((n, n))
+    for r0 in range(0, m, rows):
+        B = Q[r0:r0 + rows]
+        G += B.T @ B
+    return float(np.linalg.norm(G - np.eye(n)))
+
+
 def run_gpu(cq, A, opts=None, inplace=False):
     dA = cq.to_colmajor(A)
     if inplace:
@@ -185,13 +198,81 @@ def test_deterministic(cq):
     assert np.array_equal(Q1, Q2) and np.array_equal(R1, R2)
 
 
-def test_host_entry_point(cq, orc):
-    A = synth.test_matrix(12345, 16, 1e8, rep=9)
-    res = cq.factor_host(A)
-    Q, R = res.Q.numpy(), res.R.numpy()
-    Qd, Rd, _, _ = run_gpu(cq, A)
-    assert res.status == cq.OK
-    assert np.array_equal(Q, Qd) and np.array_equal(R, Rd)
+@pytest.mark.parametrize("m,n,kappa,q_kind", [
+    (12345, 16, 1e8, "pinned"),      # one row chunk
+    (200003, 48, 1e12, "pinned"),    # two row chunks, tensor-core solve, ragged tail
+    (200003, 16, 1.0, "pinned"),     # converges before the pre-launched passes end
+    (200003, 48, 1e4, "pageable"),   # Q not device-addressable: one copy at the end
+    (170001, 40, 1e10, "strided"),   # ldq > m, lda > m
+    (200003, 100, 1e12, "pinned"),   # n > 64: FP64 substitution, half-height chunks
+])
+def test_host_entry_point(cq, orc, m, n, kappa, q_kind):
+    # cholqr_factor_host copies A in by row chunks while the first Gramian
+    # runs and writes each pass's Q chunks to a pinned host Q as they are
+    # solved; the result matches the device entry point to rounding (the
+    # first Gramian sums its partials by chunk) with the same pass count
+    A = synth.test_matrix(m, n, kappa, rep=9)
+    Ah = torch.from_numpy(np.asfortranarray(A)).t()
+    lda_pad = 5 if q_kind == "strided" else 0
+    Abig = torch.zeros((n, m + lda_pad), dtype=torch.float64)
+    Abig[:, :m] = Ah
+    Ah = Abig.t()[:m]
+    if q_kind == "pinned":
+        Q = torch.full((n, m), np.nan, dtype=torch.float64, pin_memory=True).t()
+    elif q_kind == "pageable":
+        Q = torch.full((n, m), np.nan, dtype=torch.float64).t()
+    else:
+        Q = torch.full((n, m + 7), np.nan, dtype=torch.float64, pin_memory=True).t()[:m]
+    res = cq.factor_host(Ah, Q=Q)
+    Qh, Rh = res.Q.numpy(), res.R.numpy()
+    Qd, Rd, std, infod = run_gpu(cq, A)
+    assert res.status == std == cq.OK
+    # the two first Gramians round differently: where an unshifted pass sits
+    # at the Cholesky breakdown threshold (one side shifts, then takes one
+    # more pass) or the stop test lands near the tolerance (the run that
+    # stopped first ended within 10x of it), the two may stop one pass apart
+    its = (res.info["iters"], infod["iters"])
+    if its[0] != its[1]:
+        first = res.info if its[0] < its[1] else infod
+        assert abs(its[0] - its[1]) == 1, (its, res.info, infod)
+        assert (res.info["shifts"] != infod["shifts"]
+                or first["orth_frob"] >= 1e-14), (res.info, infod)
+    assert np.all(np.isfinite(Qh))
+    assert loo_blocked(Qh) <= 1e-13
+    assert orc.rrr(A, Qh, Rh) <= 1e-13
+    assert np.max(np.abs(Rh - Rd)) <= r_tol(kappa, n, Rd)
+    assert np.max(np.abs(Qh - Qd)) <= q_tol(kappa, m, n)
+    assert np.array_equal(Ah.numpy(), A)  # input untouched
+    if q_kind == "strided":
+        assert torch.isnan(Q.as_strided((7, n), (1, m + 7), m)).all()  # padding untouched
+
+
+def test_host_entry_point_last_pass_not_foreseen(cq):
+    # orthogonal columns of norms 1..2 with no shift: one pass is the last,
+    # although its input was far from orthonormal, so no Q chunk reaches the
+    # host during it and every chunk is copied after the stop
+    m, n = 200003, 48
+    A = synth.orthonormal(m, n, 3) * np.linspace(1.0, 2.0, n)
+    opts = cq.default_opts(shift_policy=cq.SHIFT_NONE)
+    Q = torch.full((n, m), np.nan, dtype=torch.float64, pin_memory=True).t()
+    res = cq.factor_host(A, Q=Q, opts=opts)
+    Qd, Rd, std, infod = run_gpu(cq, A, opts=opts)
+    assert res.status == std == cq.OK and res.info["iters"] == infod["iters"] == 1
+    assert loo_blocked(res.Q.numpy()) <= 1e-13
+    assert np.max(np.abs(res.Q.numpy() - Qd)) <= 1e-13
+    assert np.max(np.abs(res.R.numpy() - Rd)) <= 1e-13
+
+
+def test_host_entry_point_orthonormal_input(cq):
+    # X = I on the first Gramian: no pass runs and Q = A, R = I (Alg. 1 line 1)
+    m, n = 160003, 8
+    A = np.zeros((m, n))
+    A[np.arange(n) * 1000, np.arange(n)] = 1.0
+    Q = torch.full((n, m), np.nan, dtype=torch.float64, pin_memory=True).t()
+    res = cq.factor_host(A, Q=Q)
+    assert res.status == cq.OK and res.info["iters"] == 0
+    assert np.array_equal(res.Q.numpy(), A)
+    assert np.array_equal(res.R.numpy(), np.eye(n))
 
 
 # ---- tensor-core (Ozaki digit) Gramian vs FP64 CUDA-core Gramian
