@@ -7,6 +7,8 @@
 
 #include <cuda_bf16.h>
 #include <stdint.h>
+#include <string.h>
+#include <math.h>
 
 namespace cqr {
 namespace oz {
@@ -22,9 +24,15 @@ __device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t &r0, uint32_t &r
                : "r"(addr));
 }
 
+__device__ __forceinline__ void ldsm_x2(uint32_t addr, uint32_t &r0, uint32_t &r1) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(addr));
+}
+
+// A register-only operation: not volatile, so the compiler may interleave it
+// with the fragment loads.
 __device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
                                          uint32_t b0, uint32_t b1) {
-  asm volatile(
+  asm(
       "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
       "{%0,%1,%2,%3};\n"
       : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
@@ -61,42 +69,73 @@ __device__ __forceinline__ int align_exp(unsigned long long b) {
   return ef ? ef : 1;
 }
 
+__host__ __device__ __forceinline__ int clz64(unsigned long long x) {
+#ifdef __CUDA_ARCH__
+  return __clzll((long long)x);
+#else
+  return x ? __builtin_clzll(x) : 64;
+#endif
+}
+
 // (hi 2^hs + lo) 2^e rounded to the nearest FP64 (ties to even), on the
-// integer pipe: the two words are combined exactly in 128 bits and rounded
-// once.  Results outside the normal range (rare: entries below 2^-1022 or
-// above 2^1023) take the FP64 path, whose ldexp rounds subnormals correctly.
-__device__ __forceinline__ double fixed_to_double(long long hi, long long lo, int hs, int e) {
-  const __int128 v = ((__int128)hi << hs) + (__int128)lo;
-  if (v == 0) return 0.0;
-  const unsigned long long sign = (v < 0) ? 0x8000000000000000ull : 0ull;
-  const unsigned __int128 a = (v < 0) ? (unsigned __int128)(-v) : (unsigned __int128)v;
-  const unsigned long long ah = (unsigned long long)(a >> 64), al = (unsigned long long)a;
-  const int msb = ah ? 127 - __clzll((long long)ah) : 63 - __clzll((long long)al);
-  unsigned long long mant;
-  int E = msb + e;  // a in [2^msb, 2^(msb+1)): value in [2^E, 2^(E+1))
-  if (msb <= 52) {
-    mant = (unsigned long long)a << (52 - msb);
+// integer pipe in 64-bit words, 0 < hs < 63, |hi| + |lo| 2^-hs < 2^62:
+//   v = a 2^hs + r with a = hi + floor(lo / 2^hs), 0 <= r < 2^hs;
+//   |v| = A 2^hs + R (for v < 0, A = -a - 1, R = 2^hs - r when r > 0);
+//   the top 64 bits of |v| (msb at bit 63) and a sticky bit for the bits of
+//   R below them give the 53-bit significand and its rounding.
+// Results outside the normal range (rare: entries below 2^-1022 or above
+// 2^1023) take the FP64 path, whose ldexp rounds subnormals correctly.
+__host__ __device__ __forceinline__ double fixed_to_double(long long hi, long long lo, int hs, int e) {
+  const unsigned long long rmask = (1ull << hs) - 1ull;
+  const long long a = hi + (lo >> hs);
+  const unsigned long long r = (unsigned long long)lo & rmask;
+  if (a == 0 && r == 0) return 0.0;
+  unsigned long long A, R, sign = 0ull;
+  if (a < 0) {
+    sign = 0x8000000000000000ull;
+    A = (unsigned long long)(-a) - (r ? 1ull : 0ull);
+    R = r ? (1ull << hs) - r : 0ull;
   } else {
-    const int sh = msb - 52;
-    const unsigned __int128 q = a >> sh;
-    const unsigned __int128 rem = a - (q << sh);
-    const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
-    mant = (unsigned long long)q;
-    if (rem > half || (rem == half && (mant & 1ull))) {
-      ++mant;
-      if (mant == (1ull << 53)) {
-        mant >>= 1;
-        ++E;
-      }
+    A = (unsigned long long)a;
+    R = r;
+  }
+  unsigned long long W;
+  bool sticky = false;
+  int M;  // |v| in [2^M, 2^(M+1))
+  if (A == 0) {
+    M = 63 - clz64(R);
+    W = R << (63 - M);
+  } else {
+    const int mA = 63 - clz64(A);
+    M = mA + hs;
+    W = A << (63 - mA);
+    if (M <= 63) {
+      W |= R << (63 - M);
+    } else {
+      const int k = M - 63;  // 0 < k < hs
+      W |= R >> k;
+      sticky = (R & ((1ull << k) - 1ull)) != 0ull;
     }
   }
+  unsigned long long mant = W >> 11;
+  const unsigned long long rb = W & 0x7FFull;
+  if (rb > 0x400ull || (rb == 0x400ull && (sticky || (mant & 1ull)))) {
+    ++mant;
+    if (mant == (1ull << 53)) {
+      mant >>= 1;
+      ++M;
+    }
+  }
+  const int E = M + e;
   if (E < -1022 || E > 1023) {
     const double vh = ldexp((double)hi, e + hs);
     const double vl = ldexp((double)lo, e);
     return vh + vl;
   }
-  return __longlong_as_double((long long)(sign | ((unsigned long long)(E + 1023) << 52) |
-                                          (mant & 0xFFFFFFFFFFFFFull)));
+  unsigned long long bits = sign | ((unsigned long long)(E + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull);
+  double out;
+  memcpy(&out, &bits, sizeof(out));
+  return out;
 }
 
 // Rescales an accumulator pair (value = hi * 2^28 u + lo * u) to a unit 2^D

@@ -21,13 +21,16 @@
 // Exactness: for an order d the sum over k of its (d - 1) digit pairs is at
 //   most 9 * 64 * 127^2 < 2^24: one FP32 mma.sync accumulator holds it
 //   exactly.  Orders are combined exactly in int32 pairs and two int64 words
-//   (orders 2..6 with unit 2^84, 7..10 with unit 2^56), the two warps that
-//   share an output strip (one order group each) are summed exactly, and
-//   each entry is rounded to FP64 once.
+//   (orders 2..6 with unit 2^84, 7..10 with unit 2^56), and each entry is
+//   rounded to FP64 once.
 // Geometry: 32-row tiles, loaded straight from global memory into registers
 //   (lanes read consecutive rows), 9 digit planes of the tile and of T in
 //   shared memory (T's first 32 columns only keep k < 32: T is upper
-//   triangular), 106 KB: two CTAs of 8 warps per SM.
+//   triangular), 106 KB: two CTAs of 8 warps per SM.  A warp owns 16 rows
+//   and two 8-column tiles whose triangle extents add up to the same five
+//   k-steps of 16 for every warp; it forms all orders itself, in two rounds
+//   (orders 2..6, then 7..10) whose accumulators fit in registers, loading
+//   each Y digit and each T digit once per k-step.
 // Error: the dropped digits (beyond 63 bits of the row or column maximum)
 //   and the dropped orders (s + t >= 11) change an entry by at most about
 //   2^-54 max_k |y_rk| max_k |T_kj|, below the error bound of an FP64 dot
@@ -83,14 +86,57 @@ __device__ __forceinline__ uint32_t digit_pair_bf16(unsigned long long V0, unsig
   return *(const uint32_t *)&pr | sgnmask;
 }
 
-// The 9 orders d = s + t in {2..10} split over two warps per output strip,
-// balanced by their digit pairs (d - 1 each): {3, 4, 9, 10} (22 pairs) and
-// {2, 5, 6, 7, 8} (23).  Within a group, (3,4), (9,10), (5,6) and (7,8) are
-// combined in int32 as T_d 2^7 + T_(d+1) before the int64 words: hi holds
-// orders 2..6 (weight 2^(7 (6 - d))), lo orders 7..10 (2^(7 (10 - d))).
-__device__ __forceinline__ bool in_group(int grp, int d) {
-  const bool g0 = (d == 3 || d == 4 || d == 9 || d == 10);
-  return grp == 0 ? g0 : !g0;
+// The products of orders DLO..DHI (digits 1..NS of both operands) for one
+// warp's 16 rows, over k-steps kk0..kk1-1: c[d - DLO][tile] accumulates
+// sum_{s + t = d} d_s(Y) d_t(D T) exactly.  MODE 0: both column tiles (one
+// x4 load of a T digit covers both); 1: tile B alone; 2: tile A alone.
+template <int DLO, int DHI, int NS, int MODE>
+__device__ __forceinline__ void gm_steps(float (&c)[DHI - DLO + 1][2][4], uint32_t aY, uint32_t strY,
+                                         uint32_t bT, uint32_t strT, int kk0, int kk1) {
+#pragma unroll 1
+  for (int kk = kk0; kk < kk1; ++kk) {
+    const uint32_t ko = 32u * kk;
+    uint32_t A[NS][4];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) ldsm_x4(aY + s * strY + ko, A[s][0], A[s][1], A[s][2], A[s][3]);
+#pragma unroll
+    for (int t = 0; t < NS; ++t) {
+      // digit t + 1 of T meets digits s + 1 with DLO <= s + t + 2 <= DHI
+      const int slo = max(0, DLO - 2 - t), shi = min(NS - 1, DHI - 2 - t);
+      if (slo > shi) continue;
+      uint32_t b0, b1, b2, b3;
+      if (MODE == 0) ldsm_x4(bT + t * strT + ko, b0, b1, b2, b3);
+      else ldsm_x2(bT + t * strT + ko, b0, b1);
+#pragma unroll
+      for (int s = slo; s <= shi; ++s) {
+        const int d = s + t + 2 - DLO;
+        if (MODE == 0) {
+          mma_bf16(c[d][0], A[s][0], A[s][1], A[s][2], A[s][3], b0, b1);
+          mma_bf16(c[d][1], A[s][0], A[s][1], A[s][2], A[s][3], b2, b3);
+        } else {
+          mma_bf16(c[d][MODE == 1 ? 1 : 0], A[s][0], A[s][1], A[s][2], A[s][3], b0, b1);
+        }
+      }
+    }
+  }
+}
+
+// All of one round of orders for a warp: both tiles below tile A's extent
+// kA, tile B alone up to kB; or tile A alone when tile B lies past n.
+template <int DLO, int DHI, int NS>
+__device__ __forceinline__ void gm_orders(float (&c)[DHI - DLO + 1][2][4], uint32_t aY, uint32_t strY,
+                                          uint32_t bA, uint32_t bB, uint32_t bAB, uint32_t strAB,
+                                          uint32_t strT0, uint32_t strT1, int kA, int kB, bool needB) {
+#pragma unroll
+  for (int d = 0; d <= DHI - DLO; ++d)
+#pragma unroll
+    for (int tl = 0; tl < 2; ++tl) c[d][tl][0] = c[d][tl][1] = c[d][tl][2] = c[d][tl][3] = 0.0f;
+  if (needB) {
+    gm_steps<DLO, DHI, NS, 0>(c, aY, strY, bAB, strAB, 0, kA);
+    gm_steps<DLO, DHI, NS, 1>(c, aY, strY, bB, strT1, kA, kB);
+  } else {
+    gm_steps<DLO, DHI, NS, 2>(c, aY, strY, bA, strT0, 0, kA);
+  }
 }
 
 }  // namespace
@@ -144,19 +190,29 @@ __global__ void __launch_bounds__(kGmThreads, 2) ozgemm_kernel(RowSweep a) {
     for (int d = 0; d < kGmDigits; ++d) *(uint32_t *)(dst + d * dstep) = digit_pair_bf16(V0, V1, d, sg);
   }
 
-  // warp -> strip (16 rows x 32 columns) and order group
-  const int strip = warp >> 1, grp = warp & 1;
-  const int ib = strip >> 1, jb = strip & 1;
-  const int i0 = ib * 16;
-  const uint16_t *Tbase = jb ? planesT1 : planesT0;
-  const int ldt = jb ? kLdB : kLdA;
-  const int kend = jb ? 64 : 32;  // T is upper triangular
+  // warp -> 16 rows (ib) and two 8-column tiles of equal triangle work: tile
+  // tA = cp (columns 8 cp .. 8 cp + 7, k < 16 (cp / 2 + 1)) and tile
+  // tB = 7 - cp (k < 16 (tB / 2 + 1)): five k-steps of 16 per digit pair
+  const int ib = warp & 1, cp = warp >> 1;
+  const int i0 = ib * 16, tA = cp, tB = 7 - cp;
+  const bool needB = 8 * tB < n;
+  const int kA = tA / 2 + 1;
+  const int kB = min(tB / 2 + 1, (n + 15) / 16);
+  const int mi = lane >> 3, rr = lane & 7;
+  // per-lane ldmatrix addresses at digit 1, k-step 0 (the k-step adds 32 bytes)
+  const uint32_t aY = smem_u32(planesY + (size_t)(i0 + (mi & 1) * 8 + rr) * kLdB + (mi >> 1) * 8);
+  const uint32_t bA = smem_u32(planesT0 + (size_t)(8 * tA + rr) * kLdA + (mi & 1) * 8);
+  const uint32_t bB = smem_u32(planesT1 + (size_t)(8 * (tB - 4) + rr) * kLdB + (mi & 1) * 8);
+  const uint32_t bAB = (mi < 2) ? bA : bB;  // x4: tile A (lanes 0-15), tile B (16-31)
+  constexpr uint32_t kStrY = 2u * kGmTR * kLdB, kStrT0 = 2u * 32 * kLdA, kStrT1 = 2u * 32 * kLdB;
+  const uint32_t strAB = (mi < 2) ? kStrT0 : kStrT1;
   // loader: thread (r, kc) holds 8 consecutive k of row r (lanes = rows)
   const int lr = t & (kGmTR - 1), kc = t >> 5, k0 = 8 * kc;
 
   for (int64_t r0 = row0; r0 < row1; r0 += kGmTR) {
     const int nr = (int)min((int64_t)kGmTR, row1 - r0);
-    // ---- load 8 entries per thread (coalesced along rows), partial maxima
+    // ---- load 8 entries per thread (coalesced along rows), partial maxima.
+    // The previous tile's readers of epart/bpart passed the barrier below.
     unsigned long long bv[8];
     int mx = kNoExp, bd = 0;
 #pragma unroll
@@ -169,7 +225,7 @@ __global__ void __launch_bounds__(kGmThreads, 2) ozgemm_kernel(RowSweep a) {
     }
     epart[kc * kGmTR + lr] = mx;
     bpart[kc * kGmTR + lr] = bd;
-    __syncthreads();
+    __syncthreads();  // also: every warp is done with the previous tile's planes
     // ---- row exponent, then 9 digit planes (row r, k contiguous)
     {
       int er = kNoExp, bb = 0;
@@ -202,101 +258,45 @@ __global__ void __launch_bounds__(kGmThreads, 2) ozgemm_kernel(RowSweep a) {
     }
     __syncthreads();
 
-    // ---- tensor-core products of this warp's order group
-    long long acc_hi[16], acc_lo[16];
+    // ---- orders 2..6 (digits 1..5), drained into hi; then orders 7..10
+    // (all 9 digits), drained into lo.  Each k-step loads the warp's Y
+    // digits once and each T digit once.
+    long long hi[8], lo[8];
+    {
+      float c[5][2][4];
+      gm_orders<2, 6, 5>(c, aY, kStrY, bA, bB, bAB, strAB, kStrT0, kStrT1, kA, kB, needB);
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      acc_hi[k] = 0;
-      acc_lo[k] = 0;
-    }
-    int tv[4][4];
-#pragma unroll
-    for (int d = 2; d <= 10; ++d) {
-      if (!in_group(grp, d)) continue;
-      float c[4][4];
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt) c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.0f;
-#pragma unroll 1
-      for (int s = 1; s < d && s <= kGmDigits; ++s) {
-        const int tt = d - s;
-        const uint16_t *As = planesY + ((size_t)(s - 1) * kGmTR + i0) * kLdB;
-        const uint16_t *Bt = Tbase + (size_t)(tt - 1) * 32 * ldt;
-#pragma unroll 2
-        for (int ks = 0; ks < kend; ks += 16) {
-          uint32_t a0, a1, a2, a3;
-          {
-            const int mi = lane >> 3, rr = lane & 7;
-            const uint16_t *pa = As + ((mi & 1) * 8 + rr) * kLdB + ks + (mi >> 1) * 8;
-            ldsm_x4(smem_u32(pa), a0, a1, a2, a3);
-          }
-#pragma unroll
-          for (int nt = 0; nt < 4; nt += 2) {
-            uint32_t b0, b1, b2, b3;
-            const int mi = lane >> 3, rr = lane & 7;
-            const uint16_t *pb = Bt + ((nt + (mi >> 1)) * 8 + rr) * ldt + ks + (mi & 1) * 8;
-            ldsm_x4(smem_u32(pb), b0, b1, b2, b3);
-            mma_bf16(c[nt], a0, a1, a2, a3, b0, b1);
-            mma_bf16(c[nt + 1], a0, a1, a2, a3, b2, b3);
-          }
-        }
-      }
-      // drain (see in_group): the first order of a pair waits in tv
-      if (d == 3 || d == 5 || d == 7 || d == 9) {
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-          for (int r = 0; r < 4; ++r) tv[nt][r] = f2i(c[nt][r]);
-      } else {
-        const bool paired = (d != 2);
-        const bool hi = d <= 6;
-        const int shl = hi ? 7 * (6 - d) : 7 * (10 - d);
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-          for (int r = 0; r < 4; ++r) {
-            const int v = f2i(c[nt][r]);
-            const long long w = paired ? (long long)(tv[nt][r] * 128 + v) : (long long)v;
-            const int k = nt * 4 + r;
-            if (hi) acc_hi[k] += w << shl;
-            else acc_lo[k] += w << shl;
-          }
+      for (int o = 0; o < 8; ++o) {
+        const int tl = o >> 2, r = o & 3;
+        const int t2 = f2i(c[0][tl][r]), t3 = f2i(c[1][tl][r]), t4 = f2i(c[2][tl][r]);
+        const int t5 = f2i(c[3][tl][r]), t6 = f2i(c[4][tl][r]);
+        hi[o] = ((long long)t2 << 28) + ((long long)(t3 * 128 + t4) << 14) + (long long)(t5 * 128 + t6);
       }
     }
-    // ---- combine the two order groups exactly (reusing the Y planes), round once
-    __syncthreads();  // every warp is done reading planesY
-    constexpr int kLdO = kGmTR + 1;  // odd stride: the four column lanes of a fragment hit distinct banks
-    long long *ohi = (long long *)planesY;  // [64 j][kLdO]
-    long long *olo = ohi + (size_t)NT * kLdO;
-    for (int g = 0; g < 2; ++g) {
-      if (grp == g) {
+    {
+      float c[4][2][4];
+      gm_orders<7, 10, 9>(c, aY, kStrY, bA, bB, bAB, strAB, kStrT0, kStrT1, kA, kB, needB);
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-          for (int r = 0; r < 4; ++r) {
-            const int rr = i0 + (lane >> 2) + ((r >> 1) << 3);
-            const int jj = jb * 32 + nt * 8 + 2 * (lane & 3) + (r & 1);
-            const int k = nt * 4 + r;
-            if (g == 0) {
-              ohi[rr + jj * kLdO] = acc_hi[k];
-              olo[rr + jj * kLdO] = acc_lo[k];
-            } else {
-              ohi[rr + jj * kLdO] += acc_hi[k];
-              olo[rr + jj * kLdO] += acc_lo[k];
-            }
-          }
+      for (int o = 0; o < 8; ++o) {
+        const int tl = o >> 2, r = o & 3;
+        const int t7 = f2i(c[0][tl][r]), t8 = f2i(c[1][tl][r]), t9 = f2i(c[2][tl][r]);
+        const int t10 = f2i(c[3][tl][r]);
+        lo[o] = ((long long)(t7 * 128 + t8) << 14) + (long long)(t9 * 128 + t10);
       }
-      __syncthreads();
     }
-    // Q_rj = (hi 2^28 + lo) 2^(e_r + f_j - 2114); one column's rows per warp
-    for (int e = t; e < kGmTR * n; e += kGmThreads) {
-      const int r = e % kGmTR, j = e / kGmTR;
-      if (r >= nr) continue;
-      const double v = bad[r] ? __longlong_as_double(0x7FF8000000000000ll)
-                              : fixed_to_double(ohi[r + j * kLdO], olo[r + j * kLdO], 28,
-                                                erow[r] + fcol[j] - 2114);
-      a.Yout[(r0 + r) + (int64_t)j * a.ldyout] = v;
+    // ---- Q_rj = (hi 2^28 + lo) 2^(e_r + f_j - 2114), rounded once, stored
+    // straight from the fragment (8 consecutive rows per column segment)
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+      const int tl = o >> 2, r = o & 3;
+      if (tl == 1 && !needB) continue;
+      const int row = i0 + (lane >> 2) + ((r >> 1) << 3);
+      const int col = 8 * (tl ? tB : tA) + 2 * (lane & 3) + (r & 1);
+      if (row >= nr || col >= n) continue;
+      const double v = bad[row] ? __longlong_as_double(0x7FF8000000000000ll)
+                                : fixed_to_double(hi[o], lo[o], 28, erow[row] + fcol[col] - 2114);
+      a.Yout[(r0 + row) + (int64_t)col * a.ldyout] = v;
     }
-    __syncthreads();  // planesY (ohi/olo), epart and erow are rewritten by the next tile
   }
 }
 

@@ -1,0 +1,100 @@
+"""The exact fixed-point -> FP64 rounding used by every tensor-core epilogue
+(fixed_to_double in csrc/ozdigits.cuh), compiled for the host and checked
+against exact rational arithmetic: (hi 2^hs + lo) 2^e must come back as the
+nearest FP64, ties to even, for every input in the normal range.  The cases
+cover both signs, carries between the two words, ties with and without
+bits below the rounding position, and results with no high word."""
+import os
+import random
+import shutil
+import struct
+import subprocess
+from fractions import Fraction
+
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "..", "paper_2507_07788_gb300", "csrc")
+
+HARNESS = r'''
+#include <stdio.h>
+#include "ozdigits.cuh"
+int main() {
+  long long hi, lo; int hs, e;
+  while (scanf("%lld %lld %d %d", &hi, &lo, &hs, &e) == 4) {
+    double d = cqr::oz::fixed_to_double(hi, lo, hs, e);
+    unsigned long long b; memcpy(&b, &d, 8);
+    printf("%016llx\n", b);
+  }
+  return 0;
+}
+'''
+
+
+@pytest.fixture(scope="module")
+def harness(tmp_path_factory):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not found")
+    d = tmp_path_factory.mktemp("f2d")
+    src = d / "h.cu"
+    src.write_text(HARNESS)
+    exe = d / "h"
+    subprocess.check_call([nvcc, "-O2", "-std=c++17", "-I", CSRC, "-o", str(exe), str(src)])
+    return str(exe)
+
+
+def exact(hi, lo, hs, e):
+    v = Fraction(hi * 2 ** hs + lo) * Fraction(2) ** e
+    return struct.unpack("<Q", struct.pack("<d", float(v)))[0]
+
+
+def cases():
+    rng = random.Random(20250710)
+    out = []
+    hs = 28
+    for _ in range(4000):
+        bh, bl = rng.randint(0, 60), rng.randint(0, 60)
+        hi = rng.randint(-(2 ** bh), 2 ** bh)
+        lo = rng.randint(-(2 ** bl), 2 ** bl)
+        out.append((hi, lo, hs, rng.randint(-900, 900)))
+    # no high word; carries across the word boundary; a = -1 with r > 0
+    for lo in (1, -1, 2 ** 27, -(2 ** 27), 2 ** 28 - 1, -(2 ** 28) + 1, 2 ** 60, -(2 ** 60)):
+        out.append((0, lo, hs, 0))
+    for hi, lo in ((1, -1), (-1, 1), (-1, 2 ** 28 - 1), (2 ** 40, -(2 ** 28)), (-(2 ** 40), 2 ** 28)):
+        out.append((hi, lo, hs, -3))
+    # ties: the bit below the 53-bit significand set, with and without
+    # sticky bits below it, on even and odd significands
+    for mant in (2 ** 52, 2 ** 52 + 1, 2 ** 53 - 1):
+        for extra in range(1, 28):
+            for sticky in (0, 1):
+                v = (mant << extra) | (1 << (extra - 1)) | (sticky if extra > 1 else 0)
+                for sgn in (1, -1):
+                    vv = sgn * v
+                    out.append((vv >> hs, vv - ((vv >> hs) << hs), hs, -40))
+    # the 80-bit range of the solve's words: hi < 2^53, |lo| < 2^46
+    for _ in range(2000):
+        hi = rng.randint(-(2 ** 53), 2 ** 53)
+        lo = rng.randint(-(2 ** 46), 2 ** 46)
+        out.append((hi, lo, hs, rng.randint(-1100, -1000)))
+    return out
+
+
+def test_fixed_to_double_rounds_exactly(harness):
+    cs = cases()
+    inp = "".join(f"{h} {l} {s} {e}\n" for h, l, s, e in cs)
+    res = subprocess.run([harness], input=inp, capture_output=True, text=True, check=True)
+    got = [int(x, 16) for x in res.stdout.split()]
+    assert len(got) == len(cs)
+    checked = 0
+    for (h, l, s, e), g in zip(cs, got):
+        v = Fraction(h * 2 ** s + l) * Fraction(2) ** e
+        if v == 0:
+            assert g == 0
+            continue
+        # the normal range only (outside it the FP64 fallback applies)
+        if not (Fraction(2) ** -1022 <= abs(v) < Fraction(2) ** 1023):
+            continue
+        assert g == exact(h, l, s, e), (h, l, s, e, hex(g), hex(exact(h, l, s, e)))
+        checked += 1
+    assert checked > 5000
