@@ -471,8 +471,8 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
         if (ms) ms->tc_flops = gemm ? rcd * ozgemm_tc_flops_per_row(p) : 0.0;
         if (ms) cudaEventRecord(ms->a, str);
         if (gemm) {
-          const int Gg = ozgemm_grid(rc);
-          const int64_t tg = ozgemm_tile_rows();
+          const int Gg = ozgemm_grid(rc, p);
+          const int64_t tg = ozgemm_tile_rows(p);
           tr.rows_per_cta = (((rc + tg - 1) / tg + Gg - 1) / Gg) * tg;
           tr.Tinv = s.Tinv;
           tr.Tscale = s.Tscale;

@@ -163,14 +163,14 @@ cudaError_t launch_ozgram(const RowSweep &a, int grid, cudaStream_t s);
 cudaError_t launch_reduce_oz(const double *partials, int G, int n, double *C, const DevState *st,
                              cudaStream_t s);
 int ozgram_grid(int64_t m, int n);
-// Q = Y T (T = R~^{-1}) on the tensor cores, exact digit products, n <= 64.
+// Q = Y T (T = R~^{-1}) on the tensor cores, exact digit products, 33 <= n <= 128.
 cudaError_t launch_ozgemm(const RowSweep &a, int grid, cudaStream_t s);
-int ozgemm_grid(int64_t m);
-int ozgemm_tile_rows();
+int ozgemm_grid(int64_t m, int n);
+int ozgemm_tile_rows(int n);
 // bf16 FLOPs the tensor-core solve issues per row at width n (digit pairs x
 // the k-blocks its upper-triangular T does not skip).
 double ozgemm_tc_flops_per_row(int n);
-constexpr int kOzGemmMaxN = 64;
+constexpr int kOzGemmMaxN = 128;
 // Cross Gramian of the update, C = [Q_in Y]^T Y, on the tensor cores (exact
 // digit products, p <= 64): partials of `groups` row groups, each (q + p) x p.
 cudaError_t launch_ozxgram(const RowSweep &a, int groups, cudaStream_t s);

@@ -462,7 +462,10 @@ cudaError_t launch_rupdate(const double *Rt, int p, double *R, int64_t ldr, cons
 
 cudaError_t launch_tinv(const double *Rt, const double *Rdinv, const double *C, int ldc, int q, int p,
                         double *Tinv, int *Tscale, const DevState *st, cudaStream_t s) {
-  if (p > 64) return cudaErrorInvalidValue;  // R~ and a row of T in shared memory
+  if (p > kCqrMaxN) return cudaErrorInvalidValue;  // R~ and a row of T in shared memory (133 KB at 128)
+  static KernelAttr attr;
+  const size_t smem = sizeof(double) * ((size_t)kCqrMaxN * kCqrMaxN + 2 * kCqrMaxN);
+  set_smem_attr(attr, tinv_kernel, (int)smem, false);
   tinv_kernel<<<p, 128, sizeof(double) * ((size_t)p * p + 2 * p), s>>>(Rt, Rdinv, C, ldc, q, p, Tinv, Tscale,
                                                                       st);
   return cudaGetLastError();

@@ -78,12 +78,14 @@ __device__ __forceinline__ unsigned long long digits63(unsigned long long b, int
   return (sh >= 63) ? 0ull : ((M << 10) >> sh);
 }
 
+// Digit d of two elements as a packed bf16 pair, each with the sign of its
+// element (s = +-1): s (2^23 + x) - s 2^23 = s x exactly in one FMA.
 __device__ __forceinline__ uint32_t digit_pair_bf16(unsigned long long V0, unsigned long long V1, int d,
-                                                    uint32_t sgnmask) {
-  const float f0 = __int_as_float(0x4B000000 | (int)((V0 >> (56 - 7 * d)) & 127u)) - 8388608.0f;
-  const float f1 = __int_as_float(0x4B000000 | (int)((V1 >> (56 - 7 * d)) & 127u)) - 8388608.0f;
+                                                    float s0, float s1) {
+  const float f0 = fmaf(__int_as_float(0x4B000000 | (int)((V0 >> (56 - 7 * d)) & 127u)), s0, -8388608.0f * s0);
+  const float f1 = fmaf(__int_as_float(0x4B000000 | (int)((V1 >> (56 - 7 * d)) & 127u)), s1, -8388608.0f * s1);
   const __nv_bfloat162 pr = __floats2bfloat162_rn(f0, f1);
-  return *(const uint32_t *)&pr | sgnmask;
+  return *(const uint32_t *)&pr;
 }
 
 // The products of orders DLO..DHI (digits 1..NS of both operands) for one
@@ -183,11 +185,11 @@ __global__ void __launch_bounds__(kGmThreads, 2) ozgemm_kernel(RowSweep a) {
     for (int h = 0; h < 2; ++h)
       if (j < n && k + h < n) b[h] = (unsigned long long)__double_as_longlong(a.Tinv[(k + h) + (int64_t)j * n]);
     const unsigned long long V0 = digits63(b[0], fcol[j], 0), V1 = digits63(b[1], fcol[j], 0);
-    const uint32_t sg = ((uint32_t)(b[0] >> 63) << 15) | ((uint32_t)(b[1] >> 63) << 31);
+    const float sg0 = (b[0] >> 63) ? -1.0f : 1.0f, sg1 = (b[1] >> 63) ? -1.0f : 1.0f;
     uint16_t *dst = lo ? planesT0 + (size_t)jl * kLdA + k : planesT1 + (size_t)jl * kLdB + k;
     const size_t dstep = lo ? (size_t)32 * kLdA : (size_t)32 * kLdB;
 #pragma unroll
-    for (int d = 0; d < kGmDigits; ++d) *(uint32_t *)(dst + d * dstep) = digit_pair_bf16(V0, V1, d, sg);
+    for (int d = 0; d < kGmDigits; ++d) *(uint32_t *)(dst + d * dstep) = digit_pair_bf16(V0, V1, d, sg0, sg1);
   }
 
   // warp -> 16 rows (ib) and two 8-column tiles of equal triangle work: tile
@@ -239,20 +241,19 @@ __global__ void __launch_bounds__(kGmThreads, 2) ozgemm_kernel(RowSweep a) {
         bad[lr] = bb;
       }
       unsigned long long V[8];
-      uint32_t sg[4];
+      float sg[8];
 #pragma unroll
       for (int h = 0; h < 8; ++h) {
         V[h] = digits63(bv[h], er, cs[k0 + h]);
-        if (h & 1) sg[h >> 1] |= (uint32_t)(bv[h] >> 63) << 31;
-        else sg[h >> 1] = (uint32_t)(bv[h] >> 63) << 15;
+        sg[h] = (bv[h] >> 63) ? -1.0f : 1.0f;
       }
 #pragma unroll
       for (int d = 0; d < kGmDigits; ++d) {
         uint4 w;
-        w.x = digit_pair_bf16(V[0], V[1], d, sg[0]);
-        w.y = digit_pair_bf16(V[2], V[3], d, sg[1]);
-        w.z = digit_pair_bf16(V[4], V[5], d, sg[2]);
-        w.w = digit_pair_bf16(V[6], V[7], d, sg[3]);
+        w.x = digit_pair_bf16(V[0], V[1], d, sg[0], sg[1]);
+        w.y = digit_pair_bf16(V[2], V[3], d, sg[2], sg[3]);
+        w.z = digit_pair_bf16(V[4], V[5], d, sg[4], sg[5]);
+        w.w = digit_pair_bf16(V[6], V[7], d, sg[6], sg[7]);
         *(uint4 *)(planesY + ((size_t)d * kGmTR + lr) * kLdB + k0) = w;
       }
     }
@@ -300,6 +301,168 @@ __global__ void __launch_bounds__(kGmThreads, 2) ozgemm_kernel(RowSweep a) {
   }
 }
 
+// ---- 65 <= n <= 128: 16-row tiles, one CTA of 8 warps per SM.  Warp w owns
+// column tiles w and 15 - w (nine k-steps together); D T is kept compact in
+// shared memory per 8-column tile (tile u keeps k < 16 (u / 2 + 1)), 180 KB
+// for the 9 digits, beside 38 KB of Y digits.
+constexpr int kWT = 16;                 // tile rows
+constexpr int kWNT = 128;               // padded width
+constexpr int kWLdY = kWNT + 8;         // bf16 stride of a Y digit-plane row
+__host__ __device__ constexpr int wide_ldt(int u) { return 16 * (u / 2 + 1) + 8; }  // bf16 stride, tile u
+__host__ __device__ constexpr int wide_off(int u) {  // bf16 offset of tile u in a digit plane
+  return u <= 0 ? 0 : wide_off(u - 1) + 8 * wide_ldt(u - 1);
+}
+constexpr int kWPlane = wide_off(16);  // bf16 per T digit plane (10240)
+constexpr size_t kWSmem = sizeof(uint16_t) * (size_t)kGmDigits * kWPlane      // D T
+                          + sizeof(uint16_t) * (size_t)kGmDigits * kWT * kWLdY  // Y tile digits
+                          + sizeof(int) * (size_t)(2 * kWNT + 2 * kWT + 2 * 16 * kWT);
+
+__global__ void __launch_bounds__(kGmThreads, 1) ozgemm_wide_kernel(RowSweep a) {
+  if (a.st != nullptr && a.st->done) return;
+  constexpr int NT = kWNT;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint16_t *planesT = (uint16_t *)smem;                                // [9][kWPlane]
+  uint16_t *planesY = planesT + (size_t)kGmDigits * kWPlane;           // [9][16 rows][kWLdY]
+  int *fcol = (int *)(planesY + (size_t)kGmDigits * kWT * kWLdY);      // [128]
+  int *cs = fcol + NT;                                                 // [128] column scales
+  int *erow = cs + NT;                                                 // [16]
+  int *bad = erow + kWT;                                               // [16]
+  int *epart = bad + kWT;                                              // [16][16] partial row maxima
+  int *bpart = epart + 16 * kWT;                                       // [16][16] partial flags
+
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int n = a.p;
+  const int64_t row0 = (int64_t)blockIdx.x * a.rows_per_cta;
+  const int64_t row1 = min(a.m, row0 + a.rows_per_cta);
+  if (row0 >= row1) return;
+
+  // ---- D T: column exponents, then 9 compact digit planes per column tile
+  for (int k = t; k < NT; k += kGmThreads) cs[k] = (k < n) ? a.Tscale[k] : 0;
+  for (int j = warp; j < NT; j += kGmThreads / 32) {
+    int mx = 1;
+    for (int k = lane; k < n; k += 32)
+      if (j < n) mx = max(mx, align_exp((unsigned long long)__double_as_longlong(a.Tinv[k + (int64_t)j * n])));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) fcol[j] = mx;
+  }
+  __syncthreads();
+  // items: (tile u, column c of the tile, k pair); tile u has 8 (u / 2 + 1)
+  // k pairs per column
+  for (int e = t; e < 64 * 72; e += kGmThreads) {
+    int u = 0, rem = e;
+    while (rem >= 64 * (u / 2 + 1)) {
+      rem -= 64 * (u / 2 + 1);
+      ++u;
+    }
+    const int kp = 8 * (u / 2 + 1);  // k pairs per column of tile u
+    const int c = rem / kp, k = 2 * (rem % kp), j = 8 * u + c;
+    unsigned long long b[2] = {0ull, 0ull};
+    for (int h = 0; h < 2; ++h)
+      if (j < n && k + h < n) b[h] = (unsigned long long)__double_as_longlong(a.Tinv[(k + h) + (int64_t)j * n]);
+    const unsigned long long V0 = digits63(b[0], fcol[j], 0), V1 = digits63(b[1], fcol[j], 0);
+    const float sg0 = (b[0] >> 63) ? -1.0f : 1.0f, sg1 = (b[1] >> 63) ? -1.0f : 1.0f;
+    uint16_t *dst = planesT + wide_off(u) + c * wide_ldt(u) + k;
+#pragma unroll
+    for (int d = 0; d < kGmDigits; ++d) *(uint32_t *)(dst + (size_t)d * kWPlane) = digit_pair_bf16(V0, V1, d, sg0, sg1);
+  }
+
+  // warp -> column tiles tA = w (k-steps kA) and tB = 15 - w (kB), all 16 rows
+  const int tA = warp, tB = 15 - warp;
+  const bool needB = 8 * tB < n;
+  const int kA = tA / 2 + 1;
+  const int kB = min(tB / 2 + 1, (n + 15) / 16);
+  const int mi = lane >> 3, rr = lane & 7;
+  const uint32_t aY = smem_u32(planesY + (size_t)((mi & 1) * 8 + rr) * kWLdY + (mi >> 1) * 8);
+  const uint32_t bA = smem_u32(planesT + wide_off(tA) + rr * wide_ldt(tA) + (mi & 1) * 8);
+  const uint32_t bB = smem_u32(planesT + wide_off(tB) + rr * wide_ldt(tB) + (mi & 1) * 8);
+  const uint32_t bAB = (mi < 2) ? bA : bB;
+  constexpr uint32_t kStrY = 2u * kWT * kWLdY, kStrT = 2u * kWPlane;
+  // loader: thread (r, kc) holds 8 consecutive k of row r
+  const int lr = t & (kWT - 1), kc = t >> 4, k0 = 8 * kc;
+
+  for (int64_t r0 = row0; r0 < row1; r0 += kWT) {
+    const int nr = (int)min((int64_t)kWT, row1 - r0);
+    unsigned long long bv[8];
+    int mx = kNoExp, bd = 0;
+#pragma unroll
+    for (int h = 0; h < 8; ++h) {
+      const int k = k0 + h;
+      bv[h] = (lr < nr && k < n) ? (unsigned long long)__double_as_longlong(a.Yin[(r0 + lr) + (int64_t)k * a.ldyin])
+                                 : 0ull;
+      bd |= (((bv[h] >> 52) & 0x7FF) == 0x7FF);
+      mx = max(mx, scaled_exp(bv[h], cs[k]));
+    }
+    epart[kc * kWT + lr] = mx;
+    bpart[kc * kWT + lr] = bd;
+    __syncthreads();  // also: every warp is done with the previous tile's planes
+    {
+      int er = kNoExp, bb = 0;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        er = max(er, epart[q * kWT + lr]);
+        bb |= bpart[q * kWT + lr];
+      }
+      if (kc == 0) {
+        erow[lr] = er;
+        bad[lr] = bb;
+      }
+      unsigned long long V[8];
+      float sg[8];
+#pragma unroll
+      for (int h = 0; h < 8; ++h) {
+        V[h] = digits63(bv[h], er, cs[k0 + h]);
+        sg[h] = (bv[h] >> 63) ? -1.0f : 1.0f;
+      }
+#pragma unroll
+      for (int d = 0; d < kGmDigits; ++d) {
+        uint4 w;
+        w.x = digit_pair_bf16(V[0], V[1], d, sg[0], sg[1]);
+        w.y = digit_pair_bf16(V[2], V[3], d, sg[2], sg[3]);
+        w.z = digit_pair_bf16(V[4], V[5], d, sg[4], sg[5]);
+        w.w = digit_pair_bf16(V[6], V[7], d, sg[6], sg[7]);
+        *(uint4 *)(planesY + ((size_t)d * kWT + lr) * kWLdY + k0) = w;
+      }
+    }
+    __syncthreads();
+
+    long long hi[8], lo[8];
+    {
+      float c[5][2][4];
+      gm_orders<2, 6, 5>(c, aY, kStrY, bA, bB, bAB, kStrT, kStrT, kStrT, kA, kB, needB);
+#pragma unroll
+      for (int o = 0; o < 8; ++o) {
+        const int tl = o >> 2, r = o & 3;
+        const int t2 = f2i(c[0][tl][r]), t3 = f2i(c[1][tl][r]), t4 = f2i(c[2][tl][r]);
+        const int t5 = f2i(c[3][tl][r]), t6 = f2i(c[4][tl][r]);
+        hi[o] = ((long long)t2 << 28) + ((long long)(t3 * 128 + t4) << 14) + (long long)(t5 * 128 + t6);
+      }
+    }
+    {
+      float c[4][2][4];
+      gm_orders<7, 10, 9>(c, aY, kStrY, bA, bB, bAB, kStrT, kStrT, kStrT, kA, kB, needB);
+#pragma unroll
+      for (int o = 0; o < 8; ++o) {
+        const int tl = o >> 2, r = o & 3;
+        const int t7 = f2i(c[0][tl][r]), t8 = f2i(c[1][tl][r]), t9 = f2i(c[2][tl][r]);
+        const int t10 = f2i(c[3][tl][r]);
+        lo[o] = ((long long)(t7 * 128 + t8) << 14) + (long long)(t9 * 128 + t10);
+      }
+    }
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+      const int tl = o >> 2, r = o & 3;
+      if (tl == 1 && !needB) continue;
+      const int row = (lane >> 2) + ((r >> 1) << 3);
+      const int col = 8 * (tl ? tB : tA) + 2 * (lane & 3) + (r & 1);
+      if (row >= nr || col >= n) continue;
+      const double v = bad[row] ? __longlong_as_double(0x7FF8000000000000ll)
+                                : fixed_to_double(hi[o], lo[o], 28, erow[row] + fcol[col] - 2114);
+      a.Yout[(r0 + row) + (int64_t)col * a.ldyout] = v;
+    }
+  }
+}
+
 static cudaError_t launch_gm(const RowSweep &a, int grid, cudaStream_t s) {
   static KernelAttr attr;
   set_smem_attr(attr, ozgemm_kernel, (int)kGmSmem, true);
@@ -307,26 +470,42 @@ static cudaError_t launch_gm(const RowSweep &a, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-int ozgemm_grid(int64_t m) {
-  const int64_t tiles = (m + kGmTR - 1) / kGmTR;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, 2 * (int64_t)num_sms()));
+static cudaError_t launch_gm_wide(const RowSweep &a, int grid, cudaStream_t s) {
+  static KernelAttr attr;
+  set_smem_attr(attr, ozgemm_wide_kernel, (int)kWSmem, false);
+  ozgemm_wide_kernel<<<grid, kGmThreads, kWSmem, s>>>(a);
+  return cudaGetLastError();
 }
 
-int ozgemm_tile_rows() { return kGmTR; }
+int ozgemm_tile_rows(int n) { return n > kGmNT ? kWT : kGmTR; }
+
+int ozgemm_grid(int64_t m, int n) {
+  const int64_t tr = ozgemm_tile_rows(n);
+  const int64_t tiles = (m + tr - 1) / tr;
+  const int64_t per_sm = n > kGmNT ? 1 : 2;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, per_sm * (int64_t)num_sms()));
+}
 
 double ozgemm_tc_flops_per_row(int n) {
-  (void)n;  // one kernel shape (64 columns) serves 33 <= n <= 64
-  const double kcols = 32.0 * 32 + 32.0 * 64;  // column halves x their k extent
   int pairs = 0;
   for (int d = 2; d <= 10; ++d) pairs += std::min(d - 1, kGmDigits) - std::max(1, d - kGmDigits) + 1;
+  // m16n8k16 products per row: 8-column tiles times their k extent
+  double kcols = 0.0;
+  if (n > kGmNT) {
+    for (int u = 0; u < 16; ++u)
+      if (8 * u < n) kcols += 8.0 * 16 * std::min(u / 2 + 1, (n + 15) / 16);
+  } else {
+    kcols = 32.0 * 32 + 32.0 * 64;  // one shape serves 33 <= n <= 64
+  }
   return 2.0 * pairs * kcols;
 }
 
-// Q = Y T for 33 <= n <= 64 (a.Yin, a.Yout, a.Tinv, a.Tscale, a.m, a.p,
+// Q = Y T for 33 <= n <= 128 (a.Yin, a.Yout, a.Tinv, a.Tscale, a.m, a.p,
 // a.rows_per_cta); narrower blocks use the FP64 substitution.
 cudaError_t launch_ozgemm(const RowSweep &a, int grid, cudaStream_t s) {
   if (a.Tinv == nullptr || a.Tscale == nullptr) return cudaErrorInvalidValue;
   if (a.p >= kOzGemmMinN && a.p <= kGmNT) return launch_gm(a, grid, s);
+  if (a.p > kGmNT && a.p <= kWNT) return launch_gm_wide(a, grid, s);
   return cudaErrorInvalidValue;
 }
 

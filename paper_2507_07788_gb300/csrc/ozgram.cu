@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(OzCfg<NT>::threads, OzCfg<NT>::ctas) ozgram_ke
       const int i = 2 * (e % (kOzTR / 2)), j = e / (kOzTR / 2);
       const int Ej = Erun[j];
       unsigned long long V[2];
-      uint32_t sgnmask = 0;
+      float sg[2];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const unsigned long long b = (unsigned long long)__double_as_longlong(tile[j * kOzTR + i + h]);
@@ -188,15 +188,18 @@ __global__ void __launch_bounds__(OzCfg<NT>::threads, OzCfg<NT>::ctas) ozgram_ke
         if (ef == 0x7FF) M = 0;
         const int sh = Ej - (ef ? ef : 1);
         V[h] = (sh >= 56) ? 0ull : ((M << 3) >> sh);
-        sgnmask |= (uint32_t)(b >> 63) << (15 + 16 * h);
+        sg[h] = (b >> 63) ? -1.0f : 1.0f;
       }
 #pragma unroll
       for (int d = 0; d < kOzDigits; ++d) {
-        // two digits -> exact FP32 (magic add) -> one packed bf16x2, signs ORed in
-        const float f0 = __int_as_float(0x4B000000 | (int)((V[0] >> (49 - 7 * d)) & 127u)) - 8388608.0f;
-        const float f1 = __int_as_float(0x4B000000 | (int)((V[1] >> (49 - 7 * d)) & 127u)) - 8388608.0f;
+        // two signed digits -> exact FP32 (s (2^23 + x) - s 2^23 = s x in one
+        // FMA) -> one packed bf16x2
+        const float f0 = fmaf(__int_as_float(0x4B000000 | (int)((V[0] >> (49 - 7 * d)) & 127u)), sg[0],
+                              -8388608.0f * sg[0]);
+        const float f1 = fmaf(__int_as_float(0x4B000000 | (int)((V[1] >> (49 - 7 * d)) & 127u)), sg[1],
+                              -8388608.0f * sg[1]);
         const __nv_bfloat162 pr = __floats2bfloat162_rn(f0, f1);
-        *(uint32_t *)(planes + ((size_t)d * NT + j) * kOzLDK + i) = *(const uint32_t *)&pr | sgnmask;
+        *(uint32_t *)(planes + ((size_t)d * NT + j) * kOzLDK + i) = *(const uint32_t *)&pr;
       }
     }
     __syncthreads();
