@@ -185,9 +185,9 @@ cudaError_t launch_reduce_dense(const double *partials, int G, int64_t E, double
 // use it, so a batched append and a direct one agree bitwise).
 constexpr int64_t kOzUpdMinRows = 262144;
 constexpr int kOzUpdMinP = 32;
-// Below this width the FP64 substitution (n^2 FP64 instructions per row) is
-// cheaper than the digit product's fixed per-row work.
-constexpr int kOzGemmMinN = 33;
+// From this width on the solve is the digit product (padded to 32, 64 or 128
+// columns); at n <= 16 the FP64 substitution's n^2 / 2 FMAs per row stay.
+constexpr int kOzGemmMinN = 17;
 int ozgram_tile_rows();
 constexpr int kOzMaxN = 128;
 // FP64 row solve Q = Y R~^{-1} alone (one thread per row, registers); shares

@@ -301,34 +301,40 @@ __global__ void __launch_bounds__(kGmThreads, 2) ozgemm_kernel(RowSweep a) {
   }
 }
 
-// ---- 65 <= n <= 128: 16-row tiles, one CTA of 8 warps per SM.  Warp w owns
-// column tiles w and 15 - w (nine k-steps together); D T is kept compact in
-// shared memory per 8-column tile (tile u keeps k < 16 (u / 2 + 1)), 180 KB
-// for the 9 digits, beside 38 KB of Y digits.
-constexpr int kWT = 16;                 // tile rows
-constexpr int kWNT = 128;               // padded width
-constexpr int kWLdY = kWNT + 8;         // bf16 stride of a Y digit-plane row
+// ---- The same product with D T kept compact per 8-column tile (tile u keeps
+// k < 16 (u / 2 + 1)), for a padded width NT in {32, 64, 128}: the CTA's
+// 8 warps cover NT / 16 pairs of column tiles (u, NT / 8 - 1 - u, equal
+// triangle work) times 128 / NT strips of 16 rows, so a tile has 2048 / NT
+// rows.  NT = 128 needs 180 KB for the nine digits of D T (one CTA per SM).
 __host__ __device__ constexpr int wide_ldt(int u) { return 16 * (u / 2 + 1) + 8; }  // bf16 stride, tile u
 __host__ __device__ constexpr int wide_off(int u) {  // bf16 offset of tile u in a digit plane
   return u <= 0 ? 0 : wide_off(u - 1) + 8 * wide_ldt(u - 1);
 }
-constexpr int kWPlane = wide_off(16);  // bf16 per T digit plane (10240)
-constexpr size_t kWSmem = sizeof(uint16_t) * (size_t)kGmDigits * kWPlane      // D T
-                          + sizeof(uint16_t) * (size_t)kGmDigits * kWT * kWLdY  // Y tile digits
-                          + sizeof(int) * (size_t)(2 * kWNT + 2 * kWT + 2 * 16 * kWT);
+template <int NT>
+struct TiledCfg {
+  static constexpr int ntiles = NT / 8, ncp = NT / 16, nib = 8 / ncp, tr = 16 * nib, kc = NT / 8;
+  static constexpr int ldy = NT + 8;
+  static constexpr int plane = wide_off(ntiles);  // bf16 per T digit plane
+  static constexpr size_t smem = sizeof(uint16_t) * (size_t)kGmDigits * plane
+                                 + sizeof(uint16_t) * (size_t)kGmDigits * tr * ldy
+                                 + sizeof(int) * (size_t)(2 * NT + 2 * tr + 2 * 256);
+  static constexpr int ctas = NT > 64 ? 1 : 2;
+};
 
-__global__ void __launch_bounds__(kGmThreads, 1) ozgemm_wide_kernel(RowSweep a) {
+template <int NT>
+__global__ void __launch_bounds__(kGmThreads, TiledCfg<NT>::ctas) ozgemm_tiled_kernel(RowSweep a) {
   if (a.st != nullptr && a.st->done) return;
-  constexpr int NT = kWNT;
+  using Cfg = TiledCfg<NT>;
+  constexpr int TR = Cfg::tr, LDY = Cfg::ldy, PL = Cfg::plane;
   extern __shared__ __align__(16) unsigned char smem[];
-  uint16_t *planesT = (uint16_t *)smem;                                // [9][kWPlane]
-  uint16_t *planesY = planesT + (size_t)kGmDigits * kWPlane;           // [9][16 rows][kWLdY]
-  int *fcol = (int *)(planesY + (size_t)kGmDigits * kWT * kWLdY);      // [128]
-  int *cs = fcol + NT;                                                 // [128] column scales
-  int *erow = cs + NT;                                                 // [16]
-  int *bad = erow + kWT;                                               // [16]
-  int *epart = bad + kWT;                                              // [16][16] partial row maxima
-  int *bpart = epart + 16 * kWT;                                       // [16][16] partial flags
+  uint16_t *planesT = (uint16_t *)smem;                          // [9][PL]
+  uint16_t *planesY = planesT + (size_t)kGmDigits * PL;          // [9][TR rows][LDY]
+  int *fcol = (int *)(planesY + (size_t)kGmDigits * TR * LDY);  // [NT]
+  int *cs = fcol + NT;                                           // [NT] column scales
+  int *erow = cs + NT;                                           // [TR]
+  int *bad = erow + TR;                                          // [TR]
+  int *epart = bad + TR;                                         // [KC][TR] partial row maxima
+  int *bpart = epart + 256;                                      // [KC][TR] partial flags
 
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int n = a.p;
@@ -348,8 +354,9 @@ __global__ void __launch_bounds__(kGmThreads, 1) ozgemm_wide_kernel(RowSweep a) 
   }
   __syncthreads();
   // items: (tile u, column c of the tile, k pair); tile u has 8 (u / 2 + 1)
-  // k pairs per column
-  for (int e = t; e < 64 * 72; e += kGmThreads) {
+  // k pairs per column, 64 (u / 2 + 1) items
+  constexpr int items = 64 * (Cfg::ncp * (Cfg::ncp + 1));  // 64 * sum_u (u / 2 + 1)
+  for (int e = t; e < items; e += kGmThreads) {
     int u = 0, rem = e;
     while (rem >= 64 * (u / 2 + 1)) {
       rem -= 64 * (u / 2 + 1);
@@ -364,25 +371,27 @@ __global__ void __launch_bounds__(kGmThreads, 1) ozgemm_wide_kernel(RowSweep a) 
     const float sg0 = (b[0] >> 63) ? -1.0f : 1.0f, sg1 = (b[1] >> 63) ? -1.0f : 1.0f;
     uint16_t *dst = planesT + wide_off(u) + c * wide_ldt(u) + k;
 #pragma unroll
-    for (int d = 0; d < kGmDigits; ++d) *(uint32_t *)(dst + (size_t)d * kWPlane) = digit_pair_bf16(V0, V1, d, sg0, sg1);
+    for (int d = 0; d < kGmDigits; ++d) *(uint32_t *)(dst + (size_t)d * PL) = digit_pair_bf16(V0, V1, d, sg0, sg1);
   }
 
-  // warp -> column tiles tA = w (k-steps kA) and tB = 15 - w (kB), all 16 rows
-  const int tA = warp, tB = 15 - warp;
+  // warp -> strip ib (16 rows) and column tiles tA = cp (k-steps kA),
+  // tB = NT / 8 - 1 - cp (kB)
+  const int cp = warp % Cfg::ncp, ib = warp / Cfg::ncp;
+  const int i0 = 16 * ib, tA = cp, tB = Cfg::ntiles - 1 - cp;
   const bool needB = 8 * tB < n;
   const int kA = tA / 2 + 1;
   const int kB = min(tB / 2 + 1, (n + 15) / 16);
   const int mi = lane >> 3, rr = lane & 7;
-  const uint32_t aY = smem_u32(planesY + (size_t)((mi & 1) * 8 + rr) * kWLdY + (mi >> 1) * 8);
+  const uint32_t aY = smem_u32(planesY + (size_t)(i0 + (mi & 1) * 8 + rr) * LDY + (mi >> 1) * 8);
   const uint32_t bA = smem_u32(planesT + wide_off(tA) + rr * wide_ldt(tA) + (mi & 1) * 8);
   const uint32_t bB = smem_u32(planesT + wide_off(tB) + rr * wide_ldt(tB) + (mi & 1) * 8);
   const uint32_t bAB = (mi < 2) ? bA : bB;
-  constexpr uint32_t kStrY = 2u * kWT * kWLdY, kStrT = 2u * kWPlane;
-  // loader: thread (r, kc) holds 8 consecutive k of row r
-  const int lr = t & (kWT - 1), kc = t >> 4, k0 = 8 * kc;
+  constexpr uint32_t kStrY = 2u * TR * LDY, kStrT = 2u * PL;
+  // loader: thread (r, kc) holds 8 consecutive k of row r (lanes = rows)
+  const int lr = t % TR, kc = t / TR, k0 = 8 * kc;
 
-  for (int64_t r0 = row0; r0 < row1; r0 += kWT) {
-    const int nr = (int)min((int64_t)kWT, row1 - r0);
+  for (int64_t r0 = row0; r0 < row1; r0 += TR) {
+    const int nr = (int)min((int64_t)TR, row1 - r0);
     unsigned long long bv[8];
     int mx = kNoExp, bd = 0;
 #pragma unroll
@@ -393,15 +402,15 @@ __global__ void __launch_bounds__(kGmThreads, 1) ozgemm_wide_kernel(RowSweep a) 
       bd |= (((bv[h] >> 52) & 0x7FF) == 0x7FF);
       mx = max(mx, scaled_exp(bv[h], cs[k]));
     }
-    epart[kc * kWT + lr] = mx;
-    bpart[kc * kWT + lr] = bd;
+    epart[kc * TR + lr] = mx;
+    bpart[kc * TR + lr] = bd;
     __syncthreads();  // also: every warp is done with the previous tile's planes
     {
       int er = kNoExp, bb = 0;
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        er = max(er, epart[q * kWT + lr]);
-        bb |= bpart[q * kWT + lr];
+      for (int q = 0; q < Cfg::kc; ++q) {
+        er = max(er, epart[q * TR + lr]);
+        bb |= bpart[q * TR + lr];
       }
       if (kc == 0) {
         erow[lr] = er;
@@ -421,7 +430,7 @@ __global__ void __launch_bounds__(kGmThreads, 1) ozgemm_wide_kernel(RowSweep a) 
         w.y = digit_pair_bf16(V[2], V[3], d, sg[2], sg[3]);
         w.z = digit_pair_bf16(V[4], V[5], d, sg[4], sg[5]);
         w.w = digit_pair_bf16(V[6], V[7], d, sg[6], sg[7]);
-        *(uint4 *)(planesY + ((size_t)d * kWT + lr) * kWLdY + k0) = w;
+        *(uint4 *)(planesY + ((size_t)d * TR + lr) * LDY + k0) = w;
       }
     }
     __syncthreads();
@@ -453,7 +462,7 @@ __global__ void __launch_bounds__(kGmThreads, 1) ozgemm_wide_kernel(RowSweep a) 
     for (int o = 0; o < 8; ++o) {
       const int tl = o >> 2, r = o & 3;
       if (tl == 1 && !needB) continue;
-      const int row = (lane >> 2) + ((r >> 1) << 3);
+      const int row = i0 + (lane >> 2) + ((r >> 1) << 3);
       const int col = 8 * (tl ? tB : tA) + 2 * (lane & 3) + (r & 1);
       if (row >= nr || col >= n) continue;
       const double v = bad[row] ? __longlong_as_double(0x7FF8000000000000ll)
@@ -470,19 +479,22 @@ static cudaError_t launch_gm(const RowSweep &a, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-static cudaError_t launch_gm_wide(const RowSweep &a, int grid, cudaStream_t s) {
+template <int NT>
+static cudaError_t launch_gm_tiled(const RowSweep &a, int grid, cudaStream_t s) {
   static KernelAttr attr;
-  set_smem_attr(attr, ozgemm_wide_kernel, (int)kWSmem, false);
-  ozgemm_wide_kernel<<<grid, kGmThreads, kWSmem, s>>>(a);
+  set_smem_attr(attr, ozgemm_tiled_kernel<NT>, (int)TiledCfg<NT>::smem, true);
+  ozgemm_tiled_kernel<NT><<<grid, kGmThreads, TiledCfg<NT>::smem, s>>>(a);
   return cudaGetLastError();
 }
 
-int ozgemm_tile_rows(int n) { return n > kGmNT ? kWT : kGmTR; }
+int ozgemm_tile_rows(int n) {
+  return n > kGmNT ? TiledCfg<128>::tr : (n > 32 ? kGmTR : TiledCfg<32>::tr);
+}
 
 int ozgemm_grid(int64_t m, int n) {
   const int64_t tr = ozgemm_tile_rows(n);
   const int64_t tiles = (m + tr - 1) / tr;
-  const int64_t per_sm = n > kGmNT ? 1 : 2;
+  const int64_t per_sm = n > kGmNT ? TiledCfg<128>::ctas : 2;
   return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, per_sm * (int64_t)num_sms()));
 }
 
@@ -491,8 +503,9 @@ double ozgemm_tc_flops_per_row(int n) {
   for (int d = 2; d <= 10; ++d) pairs += std::min(d - 1, kGmDigits) - std::max(1, d - kGmDigits) + 1;
   // m16n8k16 products per row: 8-column tiles times their k extent
   double kcols = 0.0;
-  if (n > kGmNT) {
-    for (int u = 0; u < 16; ++u)
+  if (n > kGmNT || n <= 32) {
+    const int nt = n > kGmNT ? 128 : 32;
+    for (int u = 0; u < nt / 8; ++u)
       if (8 * u < n) kcols += 8.0 * 16 * std::min(u / 2 + 1, (n + 15) / 16);
   } else {
     kcols = 32.0 * 32 + 32.0 * 64;  // one shape serves 33 <= n <= 64
@@ -500,13 +513,14 @@ double ozgemm_tc_flops_per_row(int n) {
   return 2.0 * pairs * kcols;
 }
 
-// Q = Y T for 33 <= n <= 128 (a.Yin, a.Yout, a.Tinv, a.Tscale, a.m, a.p,
-// a.rows_per_cta); narrower blocks use the FP64 substitution.
+// Q = Y T for kOzGemmMinN <= n <= 128 (a.Yin, a.Yout, a.Tinv, a.Tscale, a.m,
+// a.p, a.rows_per_cta); narrower blocks use the FP64 substitution.
 cudaError_t launch_ozgemm(const RowSweep &a, int grid, cudaStream_t s) {
   if (a.Tinv == nullptr || a.Tscale == nullptr) return cudaErrorInvalidValue;
-  if (a.p >= kOzGemmMinN && a.p <= kGmNT) return launch_gm(a, grid, s);
-  if (a.p > kGmNT && a.p <= kWNT) return launch_gm_wide(a, grid, s);
-  return cudaErrorInvalidValue;
+  if (a.p < kOzGemmMinN || a.p > 128) return cudaErrorInvalidValue;
+  if (a.p <= 32) return launch_gm_tiled<32>(a, grid, s);
+  if (a.p <= kGmNT) return launch_gm(a, grid, s);
+  return launch_gm_tiled<128>(a, grid, s);
 }
 
 }  // namespace cqr

@@ -278,7 +278,7 @@ def test_host_entry_point_orthonormal_input(cq):
 # ---- tensor-core (Ozaki digit) Gramian vs FP64 CUDA-core Gramian
 
 @pytest.mark.parametrize("kappa", [1e4, 1e12])
-@pytest.mark.parametrize("n", [1, 16, 20, 33, 48, 64, 65, 100, 128])
+@pytest.mark.parametrize("n", [1, 16, 17, 20, 25, 32, 33, 48, 64, 65, 100, 128])
 def test_emulated_and_native_gramian_agree(cq, orc, kappa, n):
     m = 30011
     A = synth.test_matrix(m, n, kappa, rep=12)
@@ -320,10 +320,10 @@ def test_chunked_pipeline_parity(cq, orc, n):
     assert np.max(np.abs(Q - Qo)) <= q_tol(1e10, m, n)
 
 
-@pytest.mark.parametrize("n", [8, 48])
+@pytest.mark.parametrize("n", [8, 24, 48, 100])
 def test_emulated_gramian_column_scaling(cq, orc, n):
     # columns scaled over 12 orders of magnitude: each column has its own
-    # exponent in the digit Gramian, and the tensor-core solve (n >= 33)
+    # exponent in the digit Gramian, and the tensor-core solve (n >= 17)
     # balances the columns of Y and the rows of T before splitting them; the
     # result follows the oracle within the bounds of the scaled matrix's
     # condition number
@@ -339,7 +339,7 @@ def test_emulated_gramian_column_scaling(cq, orc, n):
     assert np.max(np.abs(Q - Qo)) <= q_tol(kap, m, n)
 
 
-@pytest.mark.parametrize("n", [12, 40])
+@pytest.mark.parametrize("n", [12, 24, 40, 120])
 def test_emulated_gramian_row_dynamic_range(cq, orc, n):
     # entries spanning 8 orders of magnitude inside each column
     m = 9000
