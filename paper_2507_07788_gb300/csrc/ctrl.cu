@@ -404,8 +404,21 @@ __global__ void __launch_bounds__(128) tinv_kernel(const double *Rt, const doubl
   double *Rs = sh, *rd = sh + (size_t)p * p, *tr = rd + p;
   const int i = blockIdx.x, t = threadIdx.x, lane = t & 31;
   if (i >= p) return;
-  // the dependent steps below read only shared memory
-  for (int e = t; e < p * p; e += blockDim.x) Rs[e] = Rt[e];
+  // the dependent steps below read only shared memory; the copy issues 8
+  // loads before it stores (the loads are then in flight together)
+  for (int e0 = 0; e0 < p * p; e0 += 8 * 128) {
+    double v[8];
+#pragma unroll
+    for (int h = 0; h < 8; ++h) {
+      const int e = e0 + h * 128 + t;
+      v[h] = (e < p * p) ? Rt[e] : 0.0;
+    }
+#pragma unroll
+    for (int h = 0; h < 8; ++h) {
+      const int e = e0 + h * 128 + t;
+      if (e < p * p) Rs[e] = v[h];
+    }
+  }
   for (int j = t; j < p; j += blockDim.x) {
     rd[j] = Rdinv[j];
     tr[j] = 0.0;

@@ -373,29 +373,39 @@ int ozgram_grid(int64_t m, int n) {
 int ozgram_tile_rows() { return kOzTR; }
 
 // Reduction of the symmetric-pair partials: X_ij = sum_g (P_g[i,j] + P_g[j,i]).
-__global__ void reduce_oz_kernel(const double *partials, int G, int n, double *C, const DevState *st) {
+// CTA j forms column j: thread (i, gq) sums the partials g = gq (mod NG) in
+// increasing g, the NG sums are added in increasing gq.  X_ji (CTA i) adds
+// the same terms in the same order (a + b = b + a), so X is exactly
+// symmetric.  The partials are L2-resident; the loads of a thread are
+// independent, so they overlap.
+__global__ void __launch_bounds__(256) reduce_oz_kernel(const double *partials, int G, int n, double *C,
+                                                        const DevState *st) {
   if (st != nullptr && st->done) return;
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t E = (int64_t)n * (n + 1) / 2;
-  if (e >= E) return;
-  int j = (int)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
-  while ((int64_t)(j + 1) * (j + 2) / 2 <= e) ++j;
-  while ((int64_t)j * (j + 1) / 2 > e) --j;
-  const int i = (int)(e - (int64_t)j * (j + 1) / 2);
+  __shared__ double part[256];
+  const int j = blockIdx.x, t = threadIdx.x;
+  const int ni = n <= 32 ? 32 : (n <= 64 ? 64 : 128);
+  const int ng = 256 / ni, i = t % ni, gq = t / ni;
   const int64_t nn = (int64_t)n * n;
   double s = 0.0;
-  for (int g = 0; g < G; ++g) {
-    const double *P = partials + g * nn;
-    s += P[i + (int64_t)j * n] + P[j + (int64_t)i * n];
+  if (i < n) {
+    const double *P0 = partials + i + (int64_t)j * n;
+    const double *P1 = partials + j + (int64_t)i * n;
+#pragma unroll 4
+    for (int g = gq; g < G; g += ng) s += P0[g * nn] + P1[g * nn];
   }
-  C[i + (int64_t)j * n] = s;
-  C[j + (int64_t)i * n] = s;
+  part[t] = s;
+  __syncthreads();
+  if (gq == 0 && i < n) {
+    double tot = 0.0;
+    for (int h = 0; h < ng; ++h) tot += part[h * ni + i];
+    C[i + (int64_t)j * n] = tot;
+  }
 }
 
 cudaError_t launch_reduce_oz(const double *partials, int G, int n, double *C, const DevState *st,
                              cudaStream_t s) {
-  const int64_t E = (int64_t)n * (n + 1) / 2;
-  reduce_oz_kernel<<<(unsigned)((E + 63) / 64), 64, 0, s>>>(partials, G, n, C, st);
+  if (n < 1 || n > 128) return cudaErrorInvalidValue;
+  reduce_oz_kernel<<<n, 256, 0, s>>>(partials, G, n, C, st);
   return cudaGetLastError();
 }
 
