@@ -13,27 +13,31 @@
 // Representation:
 //   row r of the scaled Y tile, with e_r = the largest scaled exponent in the
 //   row (biased exponent of y_rk minus c_k, zeros ignored):
-//     y_rk 2^-c_k = sign * V * 2^(e_r - 1085),  V = sum_{s=1..9} d_s 2^(63 - 7 s),
-//   9 digits d_s in [0, 127] (63 bits below the row maximum, truncated);
-//   column j of D T likewise with f_j = the largest exponent in the column.
-// Products: Q_rj = 2^(e_r + f_j - 2170) sum_{s,t} sum_k d_s(y_rk) d_t(T_kj)
-//   2^(126 - 7(s+t)); all ordered digit pairs with s + t <= 10 are kept.
-// Exactness: for an order d the sum over k of its (d - 1) digit pairs is at
-//   most 9 * 64 * 127^2 < 2^24: one FP32 mma.sync accumulator holds it
+//     y_rk 2^-c_k = sign * V * 2^(e_r - 1085),  V < 2^63 (63 bits below the
+//     row maximum, truncated),
+//   V written in 8 balanced base-256 digits, V = sum_{i=0..7} D_i 2^(8 (7 - i)),
+//   D_0 in [0, 128] and D_i in [-128, 127] for i >= 1 (add 128 to each of
+//   the 7 low bytes, then take bytes minus 128: one byte permute per digit);
+//   signed digits of magnitude <= 128 are exact in bf16.  Column j of D T
+//   likewise with f_j = the largest exponent in the column.
+// Products: Q_rj = 2^(e_r + f_j - 2170) sum_{i,i'} sum_k D_i(y_rk) D_i'(T_kj)
+//   2^(8 (14 - i - i')); the 36 ordered digit pairs of order o = i + i' <= 7
+//   are kept.
+// Exactness: for an order o the sum over k of its o + 1 digit pairs is at
+//   most 8 * 64 * 128^2 = 2^23: one FP32 mma.sync accumulator holds it
 //   exactly.  Orders are combined exactly in int32 pairs and two int64 words
-//   (orders 2..6 with unit 2^84, 7..10 with unit 2^56), and each entry is
+//   (orders 0..3 with unit 2^88, 4..7 with unit 2^56), and each entry is
 //   rounded to FP64 once.
 // Geometry: 32-row tiles, loaded straight from global memory into registers
-//   (lanes read consecutive rows), 9 digit planes of the tile and of T in
+//   (lanes read consecutive rows), 8 digit planes of the tile and of T in
 //   shared memory (T's first 32 columns only keep k < 32: T is upper
-//   triangular), 106 KB: two CTAs of 8 warps per SM.  A warp owns 16 rows
+//   triangular), 96 KB: two CTAs of 8 warps per SM.  A warp owns 16 rows
 //   and two 8-column tiles whose triangle extents add up to the same five
 //   k-steps of 16 for every warp; it forms all orders itself, in two rounds
-//   (orders 2..6, then 7..10) whose accumulators fit in registers, loading
+//   (orders 0..3, then 4..7) whose accumulators fit in registers, loading
 //   each Y digit and each T digit once per k-step.
-// Error: the dropped digits (beyond 63 bits of the row or column maximum)
-//   and the dropped orders (s + t >= 11) change an entry by at most about
-//   2^-54 max_k |y_rk| max_k |T_kj|, below the error bound of an FP64 dot
+// Error: the dropped orders (o >= 8) change an entry by at most about
+//   2^-55 max_k |y_rk| max_k |T_kj|, below the error bound of an FP64 dot
 //   product of length n.
 // A row with a NaN or Inf entry gives a NaN row of Q.
 #include <algorithm>
@@ -48,7 +52,7 @@ using namespace oz;
 namespace {
 
 constexpr int kGmTR = 32;              // tile rows
-constexpr int kGmDigits = 9;
+constexpr int kGmDigits = 8;   // balanced base-256 digits of 63 bits
 constexpr int kGmThreads = 256;        // 8 warps, two CTAs per SM
 constexpr int kGmNT = 64;              // padded width (33 <= n <= 64)
 constexpr int kLdA = 40;               // bf16 stride of T's first 32 columns (k < 32 only)
@@ -68,7 +72,7 @@ __device__ __forceinline__ int scaled_exp(unsigned long long b, int c) {
 }
 
 // Splits x (bit pattern b, column scale 2^-c) against the reference exponent
-// eref into 9 digit magnitudes, V = (M << 10) >> (eref - (ev - c)).
+// eref into its 63-bit magnitude V = (M << 10) >> (eref - (ev - c)).
 __device__ __forceinline__ unsigned long long digits63(unsigned long long b, int eref, int c) {
   const int ef = (int)((b >> 52) & 0x7FF);
   unsigned long long M = b & 0xFFFFFFFFFFFFFull;
@@ -78,13 +82,22 @@ __device__ __forceinline__ unsigned long long digits63(unsigned long long b, int
   return (sh >= 63) ? 0ull : ((M << 10) >> sh);
 }
 
-// Digit d of two elements as a packed bf16 pair, each with the sign of its
-// element (s = +-1): s (2^23 + x) - s 2^23 = s x exactly in one FMA.
-__device__ __forceinline__ uint32_t digit_pair_bf16(unsigned long long V0, unsigned long long V1, int d,
+// Balanced digit i of two elements as a packed bf16 pair, each with the
+// sign of its element (s = +-1).  W = V + 0x0080808080808080 (128 added to
+// each of the seven low bytes; V < 2^63, so no carry leaves the top byte);
+// digit i is byte 7 - i of W, minus 128 for i >= 1.  The byte is placed in
+// an FP32 2^23 + x by one byte permute, and s (2^23 + x) - s (2^23 + b) =
+// s (x - b) exactly in one FMA.
+constexpr unsigned long long kBalance = 0x0080808080808080ull;
+__device__ __forceinline__ float balanced_digit(unsigned long long W, int i, float s) {
+  const uint32_t word = (i < 4) ? (uint32_t)(W >> 32) : (uint32_t)W;
+  const uint32_t byte = 3 - (i & 3);
+  const float x = __int_as_float((int)__byte_perm(word, 0x4B000000u, 0x7440u | byte));
+  return fmaf(x, s, -s * (i == 0 ? 8388608.0f : 8388736.0f));
+}
+__device__ __forceinline__ uint32_t digit_pair_bf16(unsigned long long W0, unsigned long long W1, int i,
                                                     float s0, float s1) {
-  const float f0 = fmaf(__int_as_float(0x4B000000 | (int)((V0 >> (56 - 7 * d)) & 127u)), s0, -8388608.0f * s0);
-  const float f1 = fmaf(__int_as_float(0x4B000000 | (int)((V1 >> (56 - 7 * d)) & 127u)), s1, -8388608.0f * s1);
-  const __nv_bfloat162 pr = __floats2bfloat162_rn(f0, f1);
+  const __nv_bfloat162 pr = __floats2bfloat162_rn(balanced_digit(W0, i, s0), balanced_digit(W1, i, s1));
   return *(const uint32_t *)&pr;
 }
 
@@ -148,9 +161,9 @@ __global__ void __launch_bounds__(kGmThreads, 2) ozgemm_kernel(RowSweep a) {
   if (a.st != nullptr && a.st->done) return;
   constexpr int NT = kGmNT;
   extern __shared__ __align__(16) unsigned char smem[];
-  uint16_t *planesT0 = (uint16_t *)smem;                                 // [9][32 cols][kLdA]
-  uint16_t *planesT1 = planesT0 + (size_t)kGmDigits * 32 * kLdA;         // [9][32 cols][kLdB]
-  uint16_t *planesY = planesT1 + (size_t)kGmDigits * 32 * kLdB;          // [9][32 rows][kLdB]
+  uint16_t *planesT0 = (uint16_t *)smem;                                 // [8][32 cols][kLdA]
+  uint16_t *planesT1 = planesT0 + (size_t)kGmDigits * 32 * kLdA;         // [8][32 cols][kLdB]
+  uint16_t *planesY = planesT1 + (size_t)kGmDigits * 32 * kLdB;          // [8][32 rows][kLdB]
   int *fcol = (int *)(planesY + (size_t)kGmDigits * kGmTR * kLdB);      // [64]
   int *cs = fcol + NT;                                                   // [64] column scales
   int *erow = cs + NT;                                                   // [32]
@@ -164,7 +177,7 @@ __global__ void __launch_bounds__(kGmThreads, 2) ozgemm_kernel(RowSweep a) {
   const int64_t row1 = min(a.m, row0 + a.rows_per_cta);
   if (row0 >= row1) return;
 
-  // ---- D T (n x n, upper, ld n): column exponents, then 9 digit planes
+  // ---- D T (n x n, upper, ld n): column exponents, then 8 digit planes
   // (columns j < 32 only meet rows k < 32 of the triangle)
   for (int k = t; k < NT; k += kGmThreads) cs[k] = (k < n) ? a.Tscale[k] : 0;
   for (int j = warp; j < NT; j += kGmThreads / 32) {
@@ -184,7 +197,7 @@ __global__ void __launch_bounds__(kGmThreads, 2) ozgemm_kernel(RowSweep a) {
     unsigned long long b[2] = {0ull, 0ull};
     for (int h = 0; h < 2; ++h)
       if (j < n && k + h < n) b[h] = (unsigned long long)__double_as_longlong(a.Tinv[(k + h) + (int64_t)j * n]);
-    const unsigned long long V0 = digits63(b[0], fcol[j], 0), V1 = digits63(b[1], fcol[j], 0);
+    const unsigned long long V0 = digits63(b[0], fcol[j], 0) + kBalance, V1 = digits63(b[1], fcol[j], 0) + kBalance;
     const float sg0 = (b[0] >> 63) ? -1.0f : 1.0f, sg1 = (b[1] >> 63) ? -1.0f : 1.0f;
     uint16_t *dst = lo ? planesT0 + (size_t)jl * kLdA + k : planesT1 + (size_t)jl * kLdB + k;
     const size_t dstep = lo ? (size_t)32 * kLdA : (size_t)32 * kLdB;
@@ -228,7 +241,7 @@ __global__ void __launch_bounds__(kGmThreads, 2) ozgemm_kernel(RowSweep a) {
     epart[kc * kGmTR + lr] = mx;
     bpart[kc * kGmTR + lr] = bd;
     __syncthreads();  // also: every warp is done with the previous tile's planes
-    // ---- row exponent, then 9 digit planes (row r, k contiguous)
+    // ---- row exponent, then 8 digit planes (row r, k contiguous)
     {
       int er = kNoExp, bb = 0;
 #pragma unroll
@@ -244,7 +257,7 @@ __global__ void __launch_bounds__(kGmThreads, 2) ozgemm_kernel(RowSweep a) {
       float sg[8];
 #pragma unroll
       for (int h = 0; h < 8; ++h) {
-        V[h] = digits63(bv[h], er, cs[k0 + h]);
+        V[h] = digits63(bv[h], er, cs[k0 + h]) + kBalance;
         sg[h] = (bv[h] >> 63) ? -1.0f : 1.0f;
       }
 #pragma unroll
@@ -259,33 +272,33 @@ __global__ void __launch_bounds__(kGmThreads, 2) ozgemm_kernel(RowSweep a) {
     }
     __syncthreads();
 
-    // ---- orders 2..6 (digits 1..5), drained into hi; then orders 7..10
-    // (all 9 digits), drained into lo.  Each k-step loads the warp's Y
+    // ---- orders 0..3 (digits 0..3), drained into hi; then orders 4..7
+    // (all 8 digits), drained into lo.  Each k-step loads the warp's Y
     // digits once and each T digit once.
     long long hi[8], lo[8];
     {
-      float c[5][2][4];
-      gm_orders<2, 6, 5>(c, aY, kStrY, bA, bB, bAB, strAB, kStrT0, kStrT1, kA, kB, needB);
+      float c[4][2][4];
+      gm_orders<2, 5, 4>(c, aY, kStrY, bA, bB, bAB, strAB, kStrT0, kStrT1, kA, kB, needB);
 #pragma unroll
       for (int o = 0; o < 8; ++o) {
         const int tl = o >> 2, r = o & 3;
-        const int t2 = f2i(c[0][tl][r]), t3 = f2i(c[1][tl][r]), t4 = f2i(c[2][tl][r]);
-        const int t5 = f2i(c[3][tl][r]), t6 = f2i(c[4][tl][r]);
-        hi[o] = ((long long)t2 << 28) + ((long long)(t3 * 128 + t4) << 14) + (long long)(t5 * 128 + t6);
+        const int t0 = f2i(c[0][tl][r]), t1 = f2i(c[1][tl][r]), t2 = f2i(c[2][tl][r]);
+        const int t3 = f2i(c[3][tl][r]);
+        hi[o] = ((long long)(t0 * 256 + t1) << 16) + (long long)(t2 * 256 + t3);
       }
     }
     {
       float c[4][2][4];
-      gm_orders<7, 10, 9>(c, aY, kStrY, bA, bB, bAB, strAB, kStrT0, kStrT1, kA, kB, needB);
+      gm_orders<6, 9, 8>(c, aY, kStrY, bA, bB, bAB, strAB, kStrT0, kStrT1, kA, kB, needB);
 #pragma unroll
       for (int o = 0; o < 8; ++o) {
         const int tl = o >> 2, r = o & 3;
-        const int t7 = f2i(c[0][tl][r]), t8 = f2i(c[1][tl][r]), t9 = f2i(c[2][tl][r]);
-        const int t10 = f2i(c[3][tl][r]);
-        lo[o] = ((long long)(t7 * 128 + t8) << 14) + (long long)(t9 * 128 + t10);
+        const int t4 = f2i(c[0][tl][r]), t5 = f2i(c[1][tl][r]), t6 = f2i(c[2][tl][r]);
+        const int t7 = f2i(c[3][tl][r]);
+        lo[o] = ((long long)(t4 * 256 + t5) << 16) + (long long)(t6 * 256 + t7);
       }
     }
-    // ---- Q_rj = (hi 2^28 + lo) 2^(e_r + f_j - 2114), rounded once, stored
+    // ---- Q_rj = (hi 2^32 + lo) 2^(e_r + f_j - 2114), rounded once, stored
     // straight from the fragment (8 consecutive rows per column segment)
 #pragma unroll
     for (int o = 0; o < 8; ++o) {
@@ -295,7 +308,7 @@ __global__ void __launch_bounds__(kGmThreads, 2) ozgemm_kernel(RowSweep a) {
       const int col = 8 * (tl ? tB : tA) + 2 * (lane & 3) + (r & 1);
       if (row >= nr || col >= n) continue;
       const double v = bad[row] ? __longlong_as_double(0x7FF8000000000000ll)
-                                : fixed_to_double(hi[o], lo[o], 28, erow[row] + fcol[col] - 2114);
+                                : fixed_to_double(hi[o], lo[o], 32, erow[row] + fcol[col] - 2114);
       a.Yout[(r0 + row) + (int64_t)col * a.ldyout] = v;
     }
   }
@@ -305,7 +318,7 @@ __global__ void __launch_bounds__(kGmThreads, 2) ozgemm_kernel(RowSweep a) {
 // k < 16 (u / 2 + 1)), for a padded width NT in {32, 64, 128}: the CTA's
 // 8 warps cover NT / 16 pairs of column tiles (u, NT / 8 - 1 - u, equal
 // triangle work) times 128 / NT strips of 16 rows, so a tile has 2048 / NT
-// rows.  NT = 128 needs 180 KB for the nine digits of D T (one CTA per SM).
+// rows.  NT = 128 needs 160 KB for the eight digits of D T (one CTA per SM).
 __host__ __device__ constexpr int wide_ldt(int u) { return 16 * (u / 2 + 1) + 8; }  // bf16 stride, tile u
 __host__ __device__ constexpr int wide_off(int u) {  // bf16 offset of tile u in a digit plane
   return u <= 0 ? 0 : wide_off(u - 1) + 8 * wide_ldt(u - 1);
@@ -327,8 +340,8 @@ __global__ void __launch_bounds__(kGmThreads, TiledCfg<NT>::ctas) ozgemm_tiled_k
   using Cfg = TiledCfg<NT>;
   constexpr int TR = Cfg::tr, LDY = Cfg::ldy, PL = Cfg::plane;
   extern __shared__ __align__(16) unsigned char smem[];
-  uint16_t *planesT = (uint16_t *)smem;                          // [9][PL]
-  uint16_t *planesY = planesT + (size_t)kGmDigits * PL;          // [9][TR rows][LDY]
+  uint16_t *planesT = (uint16_t *)smem;                          // [8][PL]
+  uint16_t *planesY = planesT + (size_t)kGmDigits * PL;          // [8][TR rows][LDY]
   int *fcol = (int *)(planesY + (size_t)kGmDigits * TR * LDY);  // [NT]
   int *cs = fcol + NT;                                           // [NT] column scales
   int *erow = cs + NT;                                           // [TR]
@@ -342,7 +355,7 @@ __global__ void __launch_bounds__(kGmThreads, TiledCfg<NT>::ctas) ozgemm_tiled_k
   const int64_t row1 = min(a.m, row0 + a.rows_per_cta);
   if (row0 >= row1) return;
 
-  // ---- D T: column exponents, then 9 compact digit planes per column tile
+  // ---- D T: column exponents, then 8 compact digit planes per column tile
   for (int k = t; k < NT; k += kGmThreads) cs[k] = (k < n) ? a.Tscale[k] : 0;
   for (int j = warp; j < NT; j += kGmThreads / 32) {
     int mx = 1;
@@ -367,7 +380,7 @@ __global__ void __launch_bounds__(kGmThreads, TiledCfg<NT>::ctas) ozgemm_tiled_k
     unsigned long long b[2] = {0ull, 0ull};
     for (int h = 0; h < 2; ++h)
       if (j < n && k + h < n) b[h] = (unsigned long long)__double_as_longlong(a.Tinv[(k + h) + (int64_t)j * n]);
-    const unsigned long long V0 = digits63(b[0], fcol[j], 0), V1 = digits63(b[1], fcol[j], 0);
+    const unsigned long long V0 = digits63(b[0], fcol[j], 0) + kBalance, V1 = digits63(b[1], fcol[j], 0) + kBalance;
     const float sg0 = (b[0] >> 63) ? -1.0f : 1.0f, sg1 = (b[1] >> 63) ? -1.0f : 1.0f;
     uint16_t *dst = planesT + wide_off(u) + c * wide_ldt(u) + k;
 #pragma unroll
@@ -420,7 +433,7 @@ __global__ void __launch_bounds__(kGmThreads, TiledCfg<NT>::ctas) ozgemm_tiled_k
       float sg[8];
 #pragma unroll
       for (int h = 0; h < 8; ++h) {
-        V[h] = digits63(bv[h], er, cs[k0 + h]);
+        V[h] = digits63(bv[h], er, cs[k0 + h]) + kBalance;
         sg[h] = (bv[h] >> 63) ? -1.0f : 1.0f;
       }
 #pragma unroll
@@ -437,25 +450,25 @@ __global__ void __launch_bounds__(kGmThreads, TiledCfg<NT>::ctas) ozgemm_tiled_k
 
     long long hi[8], lo[8];
     {
-      float c[5][2][4];
-      gm_orders<2, 6, 5>(c, aY, kStrY, bA, bB, bAB, kStrT, kStrT, kStrT, kA, kB, needB);
+      float c[4][2][4];
+      gm_orders<2, 5, 4>(c, aY, kStrY, bA, bB, bAB, kStrT, kStrT, kStrT, kA, kB, needB);
 #pragma unroll
       for (int o = 0; o < 8; ++o) {
         const int tl = o >> 2, r = o & 3;
-        const int t2 = f2i(c[0][tl][r]), t3 = f2i(c[1][tl][r]), t4 = f2i(c[2][tl][r]);
-        const int t5 = f2i(c[3][tl][r]), t6 = f2i(c[4][tl][r]);
-        hi[o] = ((long long)t2 << 28) + ((long long)(t3 * 128 + t4) << 14) + (long long)(t5 * 128 + t6);
+        const int t0 = f2i(c[0][tl][r]), t1 = f2i(c[1][tl][r]), t2 = f2i(c[2][tl][r]);
+        const int t3 = f2i(c[3][tl][r]);
+        hi[o] = ((long long)(t0 * 256 + t1) << 16) + (long long)(t2 * 256 + t3);
       }
     }
     {
       float c[4][2][4];
-      gm_orders<7, 10, 9>(c, aY, kStrY, bA, bB, bAB, kStrT, kStrT, kStrT, kA, kB, needB);
+      gm_orders<6, 9, 8>(c, aY, kStrY, bA, bB, bAB, kStrT, kStrT, kStrT, kA, kB, needB);
 #pragma unroll
       for (int o = 0; o < 8; ++o) {
         const int tl = o >> 2, r = o & 3;
-        const int t7 = f2i(c[0][tl][r]), t8 = f2i(c[1][tl][r]), t9 = f2i(c[2][tl][r]);
-        const int t10 = f2i(c[3][tl][r]);
-        lo[o] = ((long long)(t7 * 128 + t8) << 14) + (long long)(t9 * 128 + t10);
+        const int t4 = f2i(c[0][tl][r]), t5 = f2i(c[1][tl][r]), t6 = f2i(c[2][tl][r]);
+        const int t7 = f2i(c[3][tl][r]);
+        lo[o] = ((long long)(t4 * 256 + t5) << 16) + (long long)(t6 * 256 + t7);
       }
     }
 #pragma unroll
@@ -466,7 +479,7 @@ __global__ void __launch_bounds__(kGmThreads, TiledCfg<NT>::ctas) ozgemm_tiled_k
       const int col = 8 * (tl ? tB : tA) + 2 * (lane & 3) + (r & 1);
       if (row >= nr || col >= n) continue;
       const double v = bad[row] ? __longlong_as_double(0x7FF8000000000000ll)
-                                : fixed_to_double(hi[o], lo[o], 28, erow[row] + fcol[col] - 2114);
+                                : fixed_to_double(hi[o], lo[o], 32, erow[row] + fcol[col] - 2114);
       a.Yout[(r0 + row) + (int64_t)col * a.ldyout] = v;
     }
   }
@@ -500,7 +513,7 @@ int ozgemm_grid(int64_t m, int n) {
 
 double ozgemm_tc_flops_per_row(int n) {
   int pairs = 0;
-  for (int d = 2; d <= 10; ++d) pairs += std::min(d - 1, kGmDigits) - std::max(1, d - kGmDigits) + 1;
+  for (int o = 0; o < kGmDigits; ++o) pairs += o + 1;  // orders 0..7, o + 1 pairs each
   // m16n8k16 products per row: 8-column tiles times their k extent
   double kcols = 0.0;
   if (n > kGmNT || n <= 32) {
