@@ -138,12 +138,12 @@ __host__ __device__ __forceinline__ double fixed_to_double(long long hi, long lo
   return out;
 }
 
-// Rescales an accumulator pair (value = hi * 2^28 u + lo * u) to a unit 2^D
+// Rescales an accumulator pair (value = hi * 2^hs u + lo * u) to a unit 2^D
 // times larger when a column's running exponent grows by D: the bits that
 // leave hi move into lo before lo is shifted, so only bits below the new
 // lo unit are dropped.  For D >= 62 the old value lies below 2^-62 of the
 // entry's new magnitude and is dropped.
-__device__ __forceinline__ void shift_pair(long long &hi, long long &lo, int D) {
+__device__ __forceinline__ void shift_pair(long long &hi, long long &lo, int D, int hs = 28) {
   if (D <= 0) return;
   if (D >= 62) {
     hi = 0;
@@ -152,8 +152,8 @@ __device__ __forceinline__ void shift_pair(long long &hi, long long &lo, int D) 
   }
   const long long q = hi >> D;
   const long long rm = hi - (q << D);  // 0 <= rm < 2^D
-  if (D <= 34) lo = (lo + (rm << 28)) >> D;
-  else lo = (lo >> D) + (rm >> (D - 28));
+  if (D + hs <= 62) lo = (lo + (rm << hs)) >> D;
+  else lo = (lo >> D) + (rm >> (D - hs));
   hi = q;
 }
 

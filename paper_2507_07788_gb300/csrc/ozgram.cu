@@ -11,23 +11,27 @@
 // Representation (per 64-row tile, per column j):
 //   E_j = running maximum of the biased exponent of column j over the rows
 //   this CTA has seen; every element is written as
-//     x = sign * V * 2^(E_j - 1078),   V = sum_{t=1..8} d_t 2^(56 - 7 t),
-//   with 8 digits d_t in [0, 127] (56 bits relative to the column maximum,
-//   truncated).  A digit with its sign is an integer of magnitude <= 127,
-//   exact in bf16.
-// Products: x_i x_j = 2^(E_i + E_j - 2156) sum_{s,t} d_s(i) d_t(j) 2^(112 - 7(s+t)).
-//   Orders s + t <= 9 are kept (the rest lies below 2^-53 of the leading
+//     x = sign * V * 2^(E_j - 1078),   V < 2^56 (56 bits relative to the
+//     column maximum, truncated),
+//   V in 7 balanced base-256 digits, V = sum_{i=0..6} D_i 2^(8 (6 - i)),
+//   D_0 in [0, 256], D_i in [-128, 127] for i >= 1 (128 added to each of
+//   the six low bytes, bytes read back minus 128); a digit with its sign,
+//   and twice it, is an integer exact in bf16.
+// Products: x_i x_j = 2^(E_i + E_j - 2156) sum_{s,t} D_s(i) D_t(j) 2^(8 (12 - s - t)).
+//   Orders o = s + t <= 6 are kept (the rest lies below 2^-53 of the leading
 //   term).  Using P_st^T = P_ts, only s <= t is formed; the CTA stores
-//   P = sum_d (B_d + C_d / 2) w_d with B_d = sum_{s<t, s+t=d} P_st and
-//   C_d = P_{d/2,d/2}, and the reduction returns X = P + P^T.
-// Exactness: each order d has one FP32 mma.sync accumulator holding
-//   T_d = 2 B_d + C_d over a 64-row tile (the off-diagonal pairs enter with
-//   their A digits doubled, exact in bf16); |T_d| <= 8 * 64 * 127^2 < 2^23,
+//   P = sum_o (B_o + C_o / 2) w_o with B_o = sum_{s<t, s+t=o} P_st and
+//   C_o = P_{o/2,o/2}, and the reduction returns X = P + P^T.
+// Exactness: each order o has one FP32 mma.sync accumulator holding
+//   T_o = 2 B_o + C_o over a 64-row tile (the off-diagonal pairs enter with
+//   their A digits doubled, exact in bf16); |T_o| <= 9 * 2^20 < 2^24 (the
+//   top digit pairs with at most 2^8 * 2^7 per term, the others with 2^14),
 //   so the FP32 sums are exact and the FP32 -> int conversion is exact.
-//   Adjacent orders are combined exactly in int32 (T_d 2^7 + T_{d+1} < 2^31)
-//   and added into two int64 words per entry (orders 2..5 and 6..9), summed
-//   over the CTA's tiles (rescaled by right shifts when a column's running
-//   exponent grows), and rounded to FP64 once per CTA.
+//   Orders (0, 1), (2, 3), (4, 5) are combined exactly in int32
+//   (T_o 2^8 + T_o+1 < 2^31) and added into two int64 words per entry
+//   (orders 0..3 and 4..6), summed over the CTA's tiles (rescaled by right
+//   shifts when a column's running exponent grows), and rounded to FP64
+//   once per CTA.
 // Non-finite inputs make every partial of the CTA NaN (the control kernel
 // then reports a breakdown, as the FP64 path does).
 #include <algorithm>
@@ -54,12 +58,25 @@ struct OzCfg {
   static constexpr int warps = threads / 32;
   static constexpr int ctas = (NT > 64) ? 1 : 2;     // CTAs per SM
 };
-constexpr int kOzDigits = 8;
+constexpr int kOzDigits = 7;   // balanced base-256 digits of 56 bits
 
-// Orders 2..9 split into `groups` groups, balanced by the number of digit
-// pairs they contain (5 each for four groups): does group grp own order d?
-__device__ __forceinline__ bool order_in_group(int groups, int grp, int d) {
-  return groups == 1 || d == 2 + grp || d == 9 - grp;
+// Orders 0..6 split into `groups` groups ({0, 6}, {1, 5}, {2, 4}, {3} for
+// four groups): does group grp own order o?
+__device__ __forceinline__ bool order_in_group(int groups, int grp, int o) {
+  return groups == 1 || o == grp || o == 6 - grp;
+}
+constexpr int kOzMaxOrder = 6;
+constexpr unsigned long long kOzBalance = 0x0000808080808080ull;
+// Balanced digit i (0..6) of W = V + kOzBalance with sign s: byte 6 - i of W
+// minus 128 for i >= 1, placed in an FP32 2^23 + x by one byte permute and
+// signed in one FMA (exact); digit 0 is W >> 48 (up to 256: the carry out
+// of the six low bytes can reach bit 56).
+__device__ __forceinline__ float oz_digit(unsigned long long W, int i, float s) {
+  if (i == 0) return fmaf(__int_as_float(0x4B000000 | (int)(W >> 48)), s, -s * 8388608.0f);
+  const int b = 6 - i;
+  const uint32_t word = (b >= 4) ? (uint32_t)(W >> 32) : (uint32_t)W;
+  const float x = __int_as_float((int)__byte_perm(word, 0x4B000000u, 0x7440u | (uint32_t)(b & 3)));
+  return fmaf(x, s, -s * 8388736.0f);
 }
 
 }  // namespace
@@ -173,7 +190,7 @@ __global__ void __launch_bounds__(OzCfg<NT>::threads, OzCfg<NT>::ctas) ozgram_ke
       }
     }
     __syncthreads();
-    // ---- slice into 8 digit planes (two rows per thread step)
+    // ---- slice into 7 digit planes (two rows per thread step)
     for (int e = t; e < (kOzTR / 2) * NT; e += kOzThreads) {
       const int i = 2 * (e % (kOzTR / 2)), j = e / (kOzTR / 2);
       const int Ej = Erun[j];
@@ -187,18 +204,13 @@ __global__ void __launch_bounds__(OzCfg<NT>::threads, OzCfg<NT>::ctas) ozgram_ke
         if (ef) M |= 0x10000000000000ull;
         if (ef == 0x7FF) M = 0;
         const int sh = Ej - (ef ? ef : 1);
-        V[h] = (sh >= 56) ? 0ull : ((M << 3) >> sh);
+        V[h] = ((sh >= 56) ? 0ull : ((M << 3) >> sh)) + kOzBalance;
         sg[h] = (b >> 63) ? -1.0f : 1.0f;
       }
 #pragma unroll
       for (int d = 0; d < kOzDigits; ++d) {
-        // two signed digits -> exact FP32 (s (2^23 + x) - s 2^23 = s x in one
-        // FMA) -> one packed bf16x2
-        const float f0 = fmaf(__int_as_float(0x4B000000 | (int)((V[0] >> (49 - 7 * d)) & 127u)), sg[0],
-                              -8388608.0f * sg[0]);
-        const float f1 = fmaf(__int_as_float(0x4B000000 | (int)((V[1] >> (49 - 7 * d)) & 127u)), sg[1],
-                              -8388608.0f * sg[1]);
-        const __nv_bfloat162 pr = __floats2bfloat162_rn(f0, f1);
+        // two signed digits -> exact FP32 -> one packed bf16x2
+        const __nv_bfloat162 pr = __floats2bfloat162_rn(oz_digit(V[0], d, sg[0]), oz_digit(V[1], d, sg[1]));
         *(uint32_t *)(planes + ((size_t)d * NT + j) * kOzLDK + i) = *(const uint32_t *)&pr;
       }
     }
@@ -219,25 +231,25 @@ __global__ void __launch_bounds__(OzCfg<NT>::threads, OzCfg<NT>::ctas) ozgram_ke
           const int gi = i0 + (lane >> 2) + ((r >> 1) << 3);
           const int gj = j0 + nt * 8 + 2 * (lane & 3) + (r & 1);
           const int k = slot_base + nt * 4 + r;
-          shift_pair(acc_hi[k], acc_lo[k], Edel[gi] + Edel[gj]);
+          shift_pair(acc_hi[k], acc_lo[k], Edel[gi] + Edel[gj], 24);
         }
-      // order d: T_d = sum over pairs s <= t, s + t = d of (2 if s < t else 1)
-      // D_s^T D_t; adjacent orders (2k, 2k+1) combined in int32, then added
-      // to the int64 word of their order group with its weight
+      // order o: T_o = sum over pairs s <= t, s + t = o of (2 if s < t else 1)
+      // D_s^T D_t; orders (0, 1), (2, 3), (4, 5) combined in int32, then
+      // added to the int64 word of their order group with its weight
       int pend = 0;  // T of the even order of the current pair of orders, per slot
       int tv[NTILE][4];
 #pragma unroll
-      for (int d = 2; d <= 9; ++d) {
+      for (int d = 0; d <= kOzMaxOrder; ++d) {
         if (!order_in_group(gg.groups, grp, d)) continue;
         float c[NTILE][4];
 #pragma unroll
         for (int nt = 0; nt < NTILE; ++nt) c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.0f;
 #pragma unroll 1
-        for (int s = (d > kOzDigits + 1) ? d - kOzDigits : 1; 2 * s <= d; ++s) {
+        for (int s = 0; 2 * s <= d; ++s) {
           const int tt = d - s;
           const bool diag = (s == tt);
-          const uint16_t *As = planes + ((size_t)(s - 1) * NT + i0) * kOzLDK;
-          const uint16_t *Bt = planes + ((size_t)(tt - 1) * NT + j0) * kOzLDK;
+          const uint16_t *As = planes + ((size_t)s * NT + i0) * kOzLDK;
+          const uint16_t *Bt = planes + ((size_t)tt * NT + j0) * kOzLDK;
 #pragma unroll 2
           for (int ks = 0; ks < kOzTR; ks += 16) {
             uint32_t a0, a1, a2, a3;
@@ -263,23 +275,24 @@ __global__ void __launch_bounds__(OzCfg<NT>::threads, OzCfg<NT>::ctas) ozgram_ke
             }
           }
         }
-        // drain: with one group every order pair (2k, 2k+1) is combined as
-        // T_2k 2^7 + T_2k+1 in int32; with four groups each order alone
-        const bool hi = d <= 5;
-        if (gg.groups == 1 && (d & 1) == 0) {
+        // drain: with one group the order pairs (2k, 2k+1) are combined as
+        // T_2k 2^8 + T_2k+1 in int32 (order 6 alone); with four groups each
+        // order alone.  hi holds orders 0..3 (unit: order 3), lo 4..6.
+        const bool hi = d <= 3;
+        if (gg.groups == 1 && (d & 1) == 0 && d < kOzMaxOrder) {
 #pragma unroll
           for (int nt = 0; nt < NTILE; ++nt)
 #pragma unroll
             for (int r = 0; r < 4; ++r) tv[nt][r] = f2i(c[nt][r]);
           pend = 1;
         } else {
-          const int shl = hi ? 7 * (5 - d) : 7 * (9 - d);
+          const int shl = hi ? 8 * (3 - d) : 8 * (kOzMaxOrder - d);
 #pragma unroll
           for (int nt = 0; nt < NTILE; ++nt)
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
               const int v = f2i(c[nt][r]);
-              const long long w = pend ? (long long)(tv[nt][r] * 128 + v) : (long long)v;
+              const long long w = pend ? (long long)(tv[nt][r] * 256 + v) : (long long)v;
               const int k = slot_base + nt * 4 + r;
               if (hi) acc_hi[k] += w << shl;
               else acc_lo[k] += w << shl;
@@ -293,8 +306,12 @@ __global__ void __launch_bounds__(OzCfg<NT>::threads, OzCfg<NT>::ctas) ozgram_ke
   }
 
   // ---- combine the order groups exactly, round to FP64 once per entry
-  long long *ohi = (long long *)planes;  // PR x NT, reuses the plane storage
-  long long *olo = ohi + PR * NT;        // PR x NT
+  // (ohi, olo reuse the tile and plane storage, which lie back to back)
+  static_assert(sizeof(double) * NT * kOzTR + sizeof(uint16_t) * kOzDigits * NT * kOzLDK >=
+                    2 * sizeof(long long) * PR * NT,
+                "the group combine must fit in the tile and plane storage");
+  long long *ohi = (long long *)smem;  // PR x NT
+  long long *olo = ohi + PR * NT;      // PR x NT
   for (int e = t; e < PR * NT; e += kOzThreads) {
     ohi[e] = 0;
     olo[e] = 0;
@@ -327,9 +344,9 @@ __global__ void __launch_bounds__(OzCfg<NT>::threads, OzCfg<NT>::ctas) ozgram_ke
   for (int e = t; e < PR * n; e += kOzThreads) {
     const int li = e % PR, j = e / PR, i = half * PR + li;
     if (i >= n) continue;
-    // P_ij = (hi 2^28 + lo) 2^(Erun_i + Erun_j - 2108)
+    // P_ij = (hi 2^24 + lo) 2^(Erun_i + Erun_j - 2109)
     const double v = bad ? __longlong_as_double(0x7FF8000000000000ll)
-                         : fixed_to_double(ohi[li + j * PR], olo[li + j * PR], 28, Erun[i] + Erun[j] - 2108);
+                         : fixed_to_double(ohi[li + j * PR], olo[li + j * PR], 24, Erun[i] + Erun[j] - 2109);
     const int64_t pe = i + (int64_t)j * n;
     P[pe] = a.accumulate ? P[pe] + v : v;
   }
