@@ -162,16 +162,15 @@ cqr_status cholqr_gram(const cqr_opts *opts, int64_t m, int64_t n, const double 
                        double *X, int64_t ldx, void *stream);
 
 /*
- * cholqr_factor_host -- the same factorisation on HOST buffers, with the
- * copies overlapped with the passes where the tensor-core path runs
- * (n <= 128, CQR_PREC_FP64, emulation CQR_EMU_AUTO): A goes to the device in
- * row chunks while the first Gramian consumes the chunks that have landed,
- * and when Q is page-locked (cudaHostAlloc / cudaHostRegister) each pass
- * writes its Q chunks straight into it as they are solved, so only the last
- * chunk's copy trails the last pass.  Otherwise A is copied whole first and
- * Q copied whole after.  The first Gramian sums its partials by row chunk,
- * so Q and R agree with cholqr_factor on the same data to rounding, not bit
- * for bit.
+ * cholqr_factor_host -- the same factorisation on HOST buffers: A is copied
+ * to the device and factored exactly as cholqr_factor factors it (Q and R
+ * agree bit for bit).  Where the tensor-core path runs (n <= 128,
+ * CQR_PREC_FP64, emulation CQR_EMU_AUTO) and Q is page-locked
+ * (cudaHostAlloc / cudaHostRegister), the pass expected to be the last
+ * (its input has ||Q^T Q - I||_F < 1/2) writes each solved row chunk of Q
+ * straight into the host Q while the next chunks run, and only chunks that
+ * missed the final pass are copied after the stop.  Otherwise Q is copied
+ * whole after the stop.
  *   A, lda    host, m x n, lda >= m (read only; pinned for full bandwidth).
  *   Q, ldq    host, m x n output, ldq >= m; must not overlap A.  Its contents
  *             are undefined while the call runs and after an error.

@@ -89,13 +89,12 @@ AuxCtx *aux_ctx(int nchunks) {
 }
 
 // Copy stream of the host-staged factorisation, per host thread and device,
-// with an event per row chunk for its host->device copy (h) and for the
-// device->host copy of Q after a pass (c), and a page-locked record of the
-// pass whose Q each chunk last received.
+// with an event per row chunk for the device->host copy of Q after a pass,
+// and a page-locked record of the pass whose Q each chunk last received.
 struct CopyCtx {
   cudaStream_t st = nullptr;
   cudaEvent_t start = nullptr;
-  std::vector<cudaEvent_t> h, c;
+  std::vector<cudaEvent_t> c;
   int *copied = nullptr;    // host view
   int *copied_d = nullptr;  // device view
 };
@@ -103,13 +102,13 @@ struct CopyCtx {
 constexpr int kCopyGrid = 16, kCopyThreads = 1024;
 
 // Q chunk -> host after pass k's solve of that chunk, speculatively: pass k
-// is taken to be the last when its input was already orthonormal to
-// ||Q^T Q - I||_F < kCopyAheadOrth (one Cholesky QR pass of such a Q lands
-// on the roundoff floor).  It copies iff pass k ran (the control step sets
+// is taken to be the last when its input has ||Q^T Q - I||_F < kCopyAheadOrth
+// (then cond(Q^T Q) <= (1 + 1/2) / (1 - 1/2) = 3, and one Cholesky QR pass of
+// such a Q lands on the roundoff floor).  It copies iff pass k ran (the control step sets
 // iters to the index of the pass it admits; iters never decreases) and that
 // test holds; the control step after pass k waits for these copies, so the
 // state it reads is the one before pass k.  `copied` records the pass.
-constexpr double kCopyAheadOrth = 1e-2;
+constexpr double kCopyAheadOrth = 0.5;
 
 __global__ void __launch_bounds__(kCopyThreads) copy_out_kernel(const double *src, int64_t lds, int64_t rows,
                                                                 int cols, double *dst, int64_t ldd, int k,
@@ -137,18 +136,12 @@ CopyCtx *copy_ctx(int nchunks) {
       return nullptr;
     }
   }
-  while ((int)x.h.size() < nchunks) {
-    cudaEvent_t a, b;
-    if (cudaEventCreateWithFlags(&a, cudaEventDisableTiming) != cudaSuccess) {
-      (void)cudaGetLastError();
-      return nullptr;
-    }
+  while ((int)x.c.size() < nchunks) {
+    cudaEvent_t b;
     if (cudaEventCreateWithFlags(&b, cudaEventDisableTiming) != cudaSuccess) {
       (void)cudaGetLastError();
-      cudaEventDestroy(a);
       return nullptr;
     }
-    x.h.push_back(a);
     x.c.push_back(b);
   }
   return &x;
@@ -273,10 +266,9 @@ struct Problem {
   int min_iter;
   cqr_opts o;
   // Host staging (cholqr_factor_host): Y0 == Y is the device copy of hA,
-  // filled by row chunks on a copy stream while the first Gramian runs; hQ
-  // (host memory the device can write, or null) receives Q chunk by chunk as
-  // each pass's solve finishes, and *hq_written tells the caller whether it
-  // holds the final Q.
+  // copied ahead of the first Gramian; hQ (host memory the device can write,
+  // or null) receives Q chunk by chunk as the pass expected to be the last
+  // solves it, and *hq_written tells the caller whether it holds the final Q.
   const double *hA = nullptr;
   int64_t ldha = 0;
   double *hQ = nullptr;
@@ -524,31 +516,6 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
       if (mk != nullptr) cudaEventRecord(mk->b, str);
       return e;
     }
-    if (stage && !trsm) {
-      // first Gramian by row chunks, each as soon as its copy has landed
-      for (int c = 0; c < nchunks && e == cudaSuccess; ++c) {
-        const int64_t r0 = (int64_t)c * chunk_rows;
-        const int64_t rc = std::min(chunk_rows, P.m - r0);
-        if (rc <= 0) break;
-        e = cudaStreamWaitEvent(str, cx->h[c], 0);
-        RowSweep z = a;
-        z.m = rc;
-        z.Yin = a.Yin + r0;
-        z.do_trsm = 0;
-        z.accumulate = (c > 0) ? 1 : 0;
-        z.rows_per_cta = chunk_rpc;
-        z.E = (int64_t)p * p;
-        SweepMark *mg = kmark(MARK_GRAM, 0, (double)rc * p * (p + 1.0), 8.0 * (double)rc * p);
-        if (mg && e == cudaSuccess) cudaEventRecord(mg->a, str);
-        if (e == cudaSuccess) e = launch_ozgram(z, Gc, str);
-        if (mg && e == cudaSuccess) cudaEventRecord(mg->b, str);
-        g_launches++;
-      }
-      last_oz = true;
-      last_oz_G = Gc;
-      if (mk != nullptr) cudaEventRecord(mk->b, str);
-      return e;
-    }
     if (oz && !(first && !trsm && mixed)) {
       RowSweep z = a;
       z.rows_per_cta = oz_rows_per_cta;
@@ -643,24 +610,17 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
   };
 
   cudaError_t e = cudaSuccess;
-  if (P.hA != nullptr && !stage) {
-    // host input without the pipeline: one copy before everything
+  if (P.hA != nullptr) {
+    // host input: one copy ahead of everything, so the first Gramian (and
+    // with it the whole factorisation) is formed exactly as from device data
     e = cudaMemcpy2DAsync(const_cast<double *>(P.Y0), sizeof(double) * P.ldy0, P.hA,
                           sizeof(double) * P.ldha, sizeof(double) * P.m, p, cudaMemcpyHostToDevice, str);
-  } else if (stage) {
+  }
+  if (stage) {
     for (int c = 0; c < nchunks; ++c) cx->copied[c] = -1;
-    // row chunk c of A on the copy stream, after the caller's stream has
-    // reached this point (the device buffer is allocated there)
-    e = cudaEventRecord(cx->start, str);
+    // the copy stream starts after the caller's stream has reached this point
+    if (e == cudaSuccess) e = cudaEventRecord(cx->start, str);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cx->st, cx->start, 0);
-    for (int c = 0; c < nchunks && e == cudaSuccess; ++c) {
-      const int64_t r0 = (int64_t)c * chunk_rows;
-      const int64_t rc = std::min(chunk_rows, P.m - r0);
-      if (rc <= 0) break;
-      e = cudaMemcpy2DAsync(const_cast<double *>(P.Y0) + r0, sizeof(double) * P.ldy0, P.hA + r0,
-                            sizeof(double) * P.ldha, sizeof(double) * rc, p, cudaMemcpyHostToDevice, cx->st);
-      if (e == cudaSuccess) e = cudaEventRecord(cx->h[c], cx->st);
-    }
   }
   if (e == cudaSuccess) e = launch_init(P.R, P.ldr, p, P.B, P.ldb, q, s.st, str);
   g_launches++;
