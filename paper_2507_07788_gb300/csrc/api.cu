@@ -299,11 +299,17 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
                           (double)p * (p + 1.0) * kU64);
   }
 
-  // Tensor-core Gramian (Ozaki digits) for factorisations with n <= 128.
-  // Wide appends to tall bases (m >= kOzUpdMinRows, 32 <= p <= 64) form
-  // their cross Gramian [Q_in Y]^T Y on the tensor cores too (xoz) and keep
-  // the FP64 projection + solve; the others keep the fused FP64 sweep.
-  const bool xoz = (P.mode == MODE_UPDATE) && (P.o.emulation == CQR_EMU_AUTO) &&
+  // Tensor-core pass pipeline (digit Gramian, digit or FP64 solve) for
+  // factorisations with n <= 128, and for appends to an empty basis above
+  // the serving runtime's batched-append rows (q = 0: the row work of Alg. 2
+  // is the same solve and Gramian; the control step keeps Alg. 2's shifts
+  // and minimum iterations).  Wide appends to tall non-empty bases
+  // (m >= kOzUpdMinRows, 32 <= p <= 64) form their cross Gramian
+  // [Q_in Y]^T Y on the tensor cores (xoz) and keep the FP64 projection +
+  // solve; the others keep the fused FP64 sweep.
+  const bool ozu = (P.mode == MODE_UPDATE) && (q == 0) && (P.o.emulation == CQR_EMU_AUTO) &&
+                   (P.m > kOzUpdMinRows) && (p <= kOzMaxN);
+  const bool xoz = (P.mode == MODE_UPDATE) && (P.o.emulation == CQR_EMU_AUTO) && !ozu &&
                    (P.m >= kOzUpdMinRows) && (p >= kOzUpdMinP) && (p <= 64);
   int Gx = 0;
   int64_t x_rows_per_cta = 0;
@@ -313,7 +319,7 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
     const int64_t tiles = (P.m + tr - 1) / tr;
     x_rows_per_cta = ((tiles + Gx - 1) / Gx) * tr;
   }
-  const bool oz = (P.mode == MODE_FACTOR) && (p <= kOzMaxN) && (P.o.emulation == CQR_EMU_AUTO);
+  const bool oz = ((P.mode == MODE_FACTOR) || ozu) && (p <= kOzMaxN) && (P.o.emulation == CQR_EMU_AUTO);
   const int Goz = oz ? ozgram_grid(P.m, p) : 0;
   int64_t oz_rows_per_cta = 0;
   if (oz) {
@@ -328,7 +334,7 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
   const int nchunks = oz ? (int)std::max<int64_t>(1, std::min<int64_t>(kMaxChunks, P.m / min_chunk)) : 1;
   const bool pipe = oz;
   // the solve of the pipelined passes: Q = Y T on the tensor cores (T = R~^{-1}
-  // formed by the control kernel) for 33 <= n <= 64, FP64 substitution
+  // formed after the control kernel) for 17 <= n <= 128, FP64 substitution
   // otherwise
   const bool gemm = pipe && p >= kOzGemmMinN && p <= kOzGemmMaxN;
   int64_t chunk_rows = 0, chunk_rpc = 0;
@@ -588,7 +594,7 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
     c.B = P.B;
     c.ldb = P.ldb;
     c.st = s.st;
-    c.r_external = (P.mode == MODE_FACTOR) ? 1 : 0;
+    c.r_external = (P.mode == MODE_FACTOR || q == 0) ? 1 : 0;
     g_launches++;
     cudaError_t e = launch_ctrl(c, str);
     if (e == cudaSuccess && c.r_external) {

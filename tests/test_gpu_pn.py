@@ -106,3 +106,21 @@ def test_pn_nan_panel_breaks_down_and_stops(cq, orc):
     res = cq.pn(cq.to_colmajor(A), 4, check=False)
     Qo, Ro, sto, info_o = orc.pncholqr(A, 4)
     assert res.status == sto == cq.ERR_BREAKDOWN
+
+
+@pytest.mark.parametrize("r", [1, 3])
+def test_pn_tall_matches_oracle(cq, orc, r):
+    # m above the batched-append rows: the first panel (an append to an empty
+    # basis) runs the tensor-core pass pipeline, later panels the update path
+    m, n = 300007, 48
+    A = synth.test_matrix(m, n, 1e10, rep=36)
+    dA = cq.to_colmajor(A)
+    res = cq.pn(dA, r, check=False)
+    torch.cuda.synchronize()
+    Q, R = res.Q.cpu().numpy(), res.R.cpu().numpy()
+    Qo, Ro, sto, info_o = orc.pncholqr(A, r)
+    assert res.status == sto == cq.OK, (res.status, sto)
+    assert np.linalg.norm(Q.T @ Q - np.eye(n)) <= 1e-13
+    assert orc.rrr(A, Q, R) <= 1e-13
+    assert np.max(np.abs(R - Ro)) <= r_tol(1e10, n, Ro)
+    assert np.max(np.abs(Q - Qo)) <= q_tol(1e10, m, n)
