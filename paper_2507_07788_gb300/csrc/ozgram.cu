@@ -169,24 +169,18 @@ __global__ void __launch_bounds__(OzCfg<NT>::threads, OzCfg<NT>::ctas) ozgram_ke
     }
     // ---- column exponents: running maximum, growth since the last tile
     for (int j = warp; j < NT; j += kOzWarps) {
-      int mx = 1, bad = 0;
-      for (int i = lane; i < kOzTR; i += 32) {
-        const unsigned long long b = (unsigned long long)__double_as_longlong(tile[j * kOzTR + i]);
-        const int ef = (int)((b >> 52) & 0x7FF);
-        bad |= (ef == 0x7FF);
-        mx = max(mx, align_exp(b));
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
-      }
+      // biased exponents from the high words; 0x7FF (NaN / Inf) is the
+      // largest, so it also flags a non-finite entry
+      const uint32_t *hw = (const uint32_t *)(tile + j * kOzTR) + 1;
+      int mx = 1;
+      for (int i = lane; i < kOzTR; i += 32) mx = max(mx, (int)((hw[2 * i] >> 20) & 0x7FF));
+      mx = __reduce_max_sync(0xffffffffu, mx);
       if (lane == 0) {
         const int old = Erun[j];
         const int nw = max(old, mx);
         Edel[j] = nw - old;
         Erun[j] = nw;
-        if (bad) *flag = 1;
+        if (mx == 0x7FF) *flag = 1;
       }
     }
     __syncthreads();

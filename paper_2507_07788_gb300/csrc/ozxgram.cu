@@ -132,23 +132,18 @@ __global__ void __launch_bounds__(kXThreads, 1) ozxgram_kernel(RowSweep a, int n
     // ---- column exponents: running maximum, growth since the last tile
     for (int c = warp; c < NC; c += kXWarps) {
       if (!live(c)) continue;
-      int mx = 1, bad = 0;
-      for (int i = lane; i < kXTR; i += 32) {
-        const unsigned long long b = (unsigned long long)__double_as_longlong(tile[c * kXTR + i]);
-        bad |= (((b >> 52) & 0x7FF) == 0x7FF);
-        mx = max(mx, align_exp(b));
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
-      }
+      // biased exponents from the high words; 0x7FF (NaN / Inf) is the
+      // largest, so it also flags a non-finite entry
+      const uint32_t *hw = (const uint32_t *)(tile + c * kXTR) + 1;
+      int mx = 1;
+      for (int i = lane; i < kXTR; i += 32) mx = max(mx, (int)((hw[2 * i] >> 20) & 0x7FF));
+      mx = __reduce_max_sync(0xffffffffu, mx);
       if (lane == 0) {
         const int old = Erun[c];
         const int nw = max(old, mx);
         Edel[c] = nw - old;
         Erun[c] = nw;
-        if (bad) *flag = 1;
+        if (mx == 0x7FF) *flag = 1;
       }
     }
     __syncthreads();
