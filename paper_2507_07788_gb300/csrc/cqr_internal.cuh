@@ -190,8 +190,9 @@ constexpr int kOzUpdMinP = 32;
 constexpr int kOzGemmMinN = 17;
 int ozgram_tile_rows();
 constexpr int kOzMaxN = 128;
-// FP64 row solve Q = Y R~^{-1} alone (one thread per row, registers); shares
-// SMs with ozgram_kernel when the two run on different streams.
+// FP64 row solve Q = Y R~^{-1} alone for n <= 16 (one thread per row,
+// registers); shares SMs with ozgram_kernel when the two run on different
+// streams.
 cudaError_t launch_trsm_rows(const RowSweep &a, int grid, cudaStream_t s);
 int trsm_rows_grid(int64_t m);
 
