@@ -262,6 +262,22 @@ cqr_status basis_create(int64_t m, int64_t n_max, const cqr_opts *opts, void *st
 cqr_status basis_append(cqr_basis *b, int64_t p, const double *A_in, int64_t lda,
                         cqr_info *info, void *stream);
 
+/*
+ * basis_enable_digit_cache -- keep a digit copy of the basis columns on the
+ * device (7 bf16 digits per entry, 14 bytes: 1.75x the size of Q) so that
+ * later appends of p <= 16 columns to a basis of more than 262144 rows form
+ * their cross Gramian [Q_in A_in]^T A_in (Alg. 2 lines 2-4, 15-16) on the
+ * tensor cores from the cached digits instead of FP64 products.  Each column
+ * is written as sign * V * 2^(E_k - 1078) with E_k its largest biased
+ * exponent and V < 2^56 in 7 balanced base-256 digits; the cache fills for
+ * the present columns now and for new ones at each successful append.  The
+ * result follows the same tolerances as without the cache (the Gramian's
+ * digit products are exact; each entry is rounded once).
+ *   Returns CQR_OK (also if the cache exists), CQR_ERR_OOM (the basis is
+ *   unchanged and appends keep the FP64 path), or CQR_ERR_CUDA.
+ */
+cqr_status basis_enable_digit_cache(cqr_basis *b, void *stream);
+
 /* basis_free -- release the handle and its device storage (NULL is a no-op).
  * The caller must make sure no queued work still uses the basis. */
 cqr_status basis_free(cqr_basis *b);

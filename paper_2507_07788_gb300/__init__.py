@@ -106,6 +106,7 @@ _SIGNATURES = {
     "basis_create": (C.c_int, [_I64, _I64, C.POINTER(Opts), _VP, C.POINTER(_VP)]),
     "basis_append": (C.c_int, [_VP, _I64, _P, _I64, C.POINTER(Info), _VP]),
     "basis_free": (C.c_int, [_VP]),
+    "basis_enable_digit_cache": (C.c_int, [_VP, _VP]),
     "basis_cols": (_I64, [_VP]),
     "basis_rows": (_I64, [_VP]),
     "basis_capacity": (_I64, [_VP]),
@@ -359,6 +360,14 @@ class Basis:
         if check and st < 0:
             raise CholQRError(st, "basis_append")
         return st, info.as_dict()
+
+    def enable_digit_cache(self, stream=None):
+        """basis_enable_digit_cache: keep the digits of the basis columns on the
+        device so narrow appends to a tall basis form their cross Gramian on
+        the tensor cores."""
+        st = lib().basis_enable_digit_cache(self._h, _stream_ptr(stream if stream is not None else self._stream))
+        if st != OK:
+            raise CholQRError(st, "basis_enable_digit_cache")
 
     @property
     def cols(self) -> int:

@@ -214,6 +214,8 @@ struct Scratch {
   DevState *st;
   double *C, *Rt, *Rdinv, *Bt, *Tinv, *partials;
   int *Tscale;
+  uint16_t *Bd;  // digits of the scaled B~ (cached-digit projection)
+  int *fexp;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -227,7 +229,8 @@ cudaError_t scratch_alloc(Scratch &s, int q, int p, int G, int64_t E, cudaStream
   const size_t b_P = align256(sizeof(double) * (size_t)G * (size_t)E);
   keep_pool_memory();
   const size_t b_Ts = align256(sizeof(int) * (size_t)p);
-  cudaError_t e = cudaMallocAsync((void **)&s.base, b_st + b_C + 2 * b_Rt + b_Rd + b_Bt + b_Ts + b_P, str);
+  const size_t b_Bd = align256(ozcproj_scratch_bytes());
+  cudaError_t e = cudaMallocAsync((void **)&s.base, b_st + b_C + 2 * b_Rt + b_Rd + b_Bt + b_Ts + b_Bd + b_P, str);
   if (e != cudaSuccess) return e;
   char *p0 = s.base;
   s.st = (DevState *)p0;
@@ -244,6 +247,9 @@ cudaError_t scratch_alloc(Scratch &s, int q, int p, int G, int64_t E, cudaStream
   p0 += b_Rt;
   s.Tscale = (int *)p0;
   p0 += b_Ts;
+  s.Bd = (uint16_t *)p0;
+  s.fexp = (int *)(p0 + sizeof(uint16_t) * 7 * 16 * (256 + 8));
+  p0 += b_Bd;
   s.partials = (double *)p0;
   return cudaSuccess;
 }
@@ -269,6 +275,10 @@ struct Problem {
   // copied ahead of the first Gramian; hQ (host memory the device can write,
   // or null) receives Q chunk by chunk as the pass expected to be the last
   // solves it, and *hq_written tells the caller whether it holds the final Q.
+  // Digit cache of Q_in (appends to a basis that keeps one), or null.
+  const uint16_t *Qd = nullptr;
+  const int *Qe = nullptr;
+  int64_t ldc = 0, cplane = 0;
   const double *hA = nullptr;
   int64_t ldha = 0;
   double *hQ = nullptr;
@@ -309,13 +319,18 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
   // solve; the others keep the fused FP64 sweep.
   const bool ozu = (P.mode == MODE_UPDATE) && (q == 0) && (P.o.emulation == CQR_EMU_AUTO) &&
                    (P.m > kOzUpdMinRows) && (p <= kOzMaxN);
-  const bool xoz = (P.mode == MODE_UPDATE) && (P.o.emulation == CQR_EMU_AUTO) && !ozu &&
+  // Narrow appends (p <= 16) to a basis with a digit cache form the cross
+  // Gramian from the cached digits of Q_in instead (cxg), with the same
+  // FP64 projection + solve.
+  const bool cxg = (P.mode == MODE_UPDATE) && (P.o.emulation == CQR_EMU_AUTO) && !ozu && q > 0 &&
+                   P.Qd != nullptr && (P.m > kOzUpdMinRows) && (p <= kOzCacheMaxP);
+  const bool xoz = (P.mode == MODE_UPDATE) && (P.o.emulation == CQR_EMU_AUTO) && !ozu && !cxg &&
                    (P.m >= kOzUpdMinRows) && (p >= kOzUpdMinP) && (p <= 64);
   int Gx = 0;
   int64_t x_rows_per_cta = 0;
-  if (xoz) {
-    Gx = ozxgram_grid(P.m, q, p);
-    const int64_t tr = ozxgram_tile_rows();
+  if (xoz || cxg) {
+    Gx = xoz ? ozxgram_grid(P.m, q, p) : ozcgram_grid(P.m, q, p);
+    const int64_t tr = xoz ? ozxgram_tile_rows() : ozcgram_tile_rows();
     const int64_t tiles = (P.m + tr - 1) / tr;
     x_rows_per_cta = ((tiles + Gx - 1) / Gx) * tr;
   }
@@ -352,7 +367,7 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
   const bool stage = cx != nullptr;
   if (P.hq_written != nullptr) *P.hq_written = false;
   const int64_t oz_parts = oz ? std::max<int64_t>((int64_t)Goz, (int64_t)Gc) * p * p : 0;
-  const int64_t x_parts = xoz ? (int64_t)Gx * (q + p) * p : 0;
+  const int64_t x_parts = (xoz || cxg) ? (int64_t)Gx * (q + p) * p : 0;
   const int64_t part_elems = std::max<int64_t>(E, (std::max(oz_parts, x_parts) + G - 1) / G);
   bool last_x = false;   // the last sweep left dense cross-Gramian partials
   bool last_oz = false;  // which reduction the last sweep needs
@@ -430,14 +445,24 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
     cudaError_t e = cudaSuccess;
     last_oz = false;
     last_x = false;
-    if (xoz) {
+    if (xoz || cxg) {
       // projection + solve on the FP64 sweep (transform only), then the
       // cross Gramian of the new block on the tensor cores
       if (trsm) {
-        RowSweep tf = a;
-        tf.E = 0;
-        e = launch_rowsweep(tf, G, str);
-        g_launches++;
+        if (cxg && q <= kOzCacheProjMaxQ) {
+          // P = Q_in B~ from the cached digits, then the FP64 row solve
+          RowSweep tf = a;
+          const int Gp = ozcproj_grid(P.m);
+          const int64_t tr = ozcgram_tile_rows();
+          tf.rows_per_cta = (((P.m + tr - 1) / tr + Gp - 1) / Gp) * tr;
+          e = launch_ozcproj(tf, P.Qd, P.ldc, P.cplane, P.Qe, s.Bd, s.fexp, Gp, str);
+          g_launches += 2;
+        } else {
+          RowSweep tf = a;
+          tf.E = 0;
+          e = launch_rowsweep(tf, G, str);
+          g_launches++;
+        }
       }
       RowSweep x = a;
       x.Yin = trsm ? P.Y : a.Yin;
@@ -446,7 +471,8 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
       x.rows_per_cta = x_rows_per_cta;
       SweepMark *mg = kmark(MARK_GRAM, npass, 2.0 * m_d * (q + p) * p, 8.0 * m_d * (q + p));
       if (mg && e == cudaSuccess) cudaEventRecord(mg->a, str);
-      if (e == cudaSuccess) e = launch_ozxgram(x, Gx, str);
+      if (e == cudaSuccess)
+        e = xoz ? launch_ozxgram(x, Gx, str) : launch_ozcgram(x, P.Qd, P.ldc, P.cplane, P.Qe, Gx, str);
       if (mg && e == cudaSuccess) cudaEventRecord(mg->b, str);
       g_launches++;
       last_x = true;
@@ -1001,9 +1027,50 @@ cqr_status basis_append(cqr_basis *b, int64_t p, const double *A_in, int64_t lda
   P.mode = MODE_UPDATE;
   P.min_iter = b->opts.update_min_iter;
   P.o = b->opts;
+  if (b->Qd != nullptr) {
+    P.Qd = b->Qd;
+    P.Qe = b->Qe;
+    P.ldc = b->ldc;
+    P.cplane = b->ldc * b->n_max;
+  }
   cqr_status st = run(P, info, (cudaStream_t)stream);
-  if (st == CQR_OK || st == CQR_NOT_CONVERGED) b->q = q + p;
+  if (st == CQR_OK || st == CQR_NOT_CONVERGED) {
+    if (b->Qd != nullptr) {
+      // the new columns join the digit cache before anything can read them
+      cudaError_t e = launch_cache_fill(b->Q, b->ldq, b->m, (int)q, (int)p, b->Qe, b->Qd, b->ldc,
+                                        b->ldc * b->n_max, (cudaStream_t)stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+      if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return cuda_status(e);  // the basis keeps its previous q columns
+      }
+    }
+    b->q = q + p;
+  }
   return st;
+}
+
+cqr_status basis_enable_digit_cache(cqr_basis *b, void *stream) {
+  if (b == nullptr) return CQR_ERR_INVALID;
+  if (b->Qd != nullptr) return CQR_OK;
+  const int64_t ldc = (b->m + 63) & ~(int64_t)63;
+  uint16_t *Qd = nullptr;
+  int *Qe = nullptr;
+  cudaError_t e = cudaMalloc((void **)&Qd, sizeof(uint16_t) * 7 * (size_t)ldc * b->n_max);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&Qe, sizeof(int) * (size_t)b->n_max);
+  if (e == cudaSuccess && b->q > 0)
+    e = launch_cache_fill(b->Q, b->ldq, b->m, 0, (int)b->q, Qe, Qd, ldc, ldc * b->n_max, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    if (Qd) cudaFree(Qd);
+    if (Qe) cudaFree(Qe);
+    return cuda_status(e);
+  }
+  b->Qd = Qd;
+  b->Qe = Qe;
+  b->ldc = ldc;
+  return CQR_OK;
 }
 
 cqr_status cholqr_pn(const cqr_opts *opts, int64_t m, int64_t n, int64_t r, const double *A,
@@ -1075,6 +1142,8 @@ cqr_status cholqr_pn(const cqr_opts *opts, int64_t m, int64_t n, int64_t r, cons
 
 cqr_status basis_free(cqr_basis *b) {
   if (b == nullptr) return CQR_OK;
+  if (b->Qd != nullptr) cudaFree(b->Qd);
+  if (b->Qe != nullptr) cudaFree(b->Qe);
   cudaError_t e1 = cudaFree(b->Q);
   cudaError_t e2 = cudaFree(b->R);
   free(b);

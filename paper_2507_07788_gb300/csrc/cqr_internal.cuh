@@ -14,6 +14,11 @@ struct cqr_basis {
   double *Q;
   double *R;
   cqr_opts opts;
+  // digit cache of Q's columns (basis_enable_digit_cache): 7 bf16 planes of
+  // n_max x ldc (ldc = m rounded up to 64) and one exponent per column
+  uint16_t *Qd;
+  int *Qe;
+  int64_t ldc;
 };
 
 namespace cqr {
@@ -167,6 +172,23 @@ int ozgram_grid(int64_t m, int n);
 cudaError_t launch_ozgemm(const RowSweep &a, int grid, cudaStream_t s);
 int ozgemm_grid(int64_t m, int n);
 int ozgemm_tile_rows(int n);
+// Digit cache of a basis (csrc/ozcache.cu): fill columns k0 .. k0 + p - 1,
+// and the cross Gramian [Q_in Y]^T Y of appends of p <= 16 columns that
+// reads it (partials (q + p) x p per row group, for launch_reduce_dense).
+cudaError_t launch_cache_fill(const double *Q, int64_t ldq, int64_t m, int k0, int p, int *Qe, uint16_t *Qd,
+                              int64_t ldc, int64_t plane, cudaStream_t s);
+cudaError_t launch_ozcgram(const RowSweep &a, const uint16_t *Qd, int64_t ldc, int64_t plane, const int *Qe,
+                           int groups, cudaStream_t s);
+int ozcgram_grid(int64_t m, int q, int p);
+int ozcgram_tile_rows();
+// Projection and solve of such appends from the same cache (q <= 256):
+// P = Q_in B~ exactly on the tensor cores, then y <- (y - P) R~^{-1} in FP64.
+cudaError_t launch_ozcproj(const RowSweep &a, const uint16_t *Qd, int64_t ldc, int64_t plane, const int *Qe,
+                           uint16_t *Bd, int *fexp, int grid, cudaStream_t s);
+size_t ozcproj_scratch_bytes();
+int ozcproj_grid(int64_t m);
+constexpr int kOzCacheProjMaxQ = 256;
+constexpr int kOzCacheMaxP = 16;
 // bf16 FLOPs the tensor-core solve issues per row at width n (digit pairs x
 // the k-blocks its upper-triangular T does not skip).
 double ozgemm_tc_flops_per_row(int n);

@@ -188,3 +188,57 @@ def test_tall_basis_nan_breaks_down(cq):
     st, info = b.append(cq.to_colmajor(bad), check=False)
     assert st == cq.ERR_BREAKDOWN and b.cols == 8
     b.close()
+
+
+@pytest.mark.parametrize("widths", [(8, 8, 16, 4, 8), (64, 8, 1)])
+def test_tall_basis_digit_cache(cq, orc, widths):
+    # a basis that keeps the digits of its columns: appends of <= 16 columns
+    # form their cross Gramian from the cached digits of Q_in on the tensor
+    # cores (the first append, to the empty basis, takes the factorisation's
+    # pipeline; wide ones the split cross Gramian); all follow the oracle
+    m = 300007
+    b = cq.Basis(m, sum(widths))
+    b.enable_digit_cache()
+    Qo = np.zeros((m, 0))
+    Ro = np.zeros((0, 0))
+    blocks = []
+    rng = np.random.default_rng(91)
+    for k, p in enumerate(widths):
+        if k == 0:
+            blk = synth.gaussian(m, p, seed=90 + k)
+        else:
+            blk = Qo @ rng.standard_normal((Qo.shape[1], p)) * 0.1 + synth.gaussian(m, p, seed=90 + k) * 1e-6
+        blocks.append(blk)
+        st, info = b.append(cq.to_colmajor(blk))
+        Qg, Rg = b.Q().cpu().numpy(), b.R().cpu().numpy()
+        Qo, Ro, dR, dQ, scale, sto, info_o = _check_append(orc, Qo, Ro, blk, Qg, Rg, m, info, k)
+        assert st == sto and st >= 0, (k, st, info, info_o)
+        Afull = np.hstack(blocks)
+        assert orc.rrr(Afull, Qg, Rg) <= 1e-13, k
+        sv = np.linalg.svd(Afull, compute_uv=False)
+        kap = sv[0] / sv[-1]
+        q = Qg.shape[1] - p
+        print(f"append {k} p={p}: iters={info['iters']}/{info_o.iters} dR={dR:.2e} dQ={dQ:.2e} kappa={kap:.1e}")
+        assert dR <= 200 * kap * U * math.sqrt(q + p) * scale + 1e-15
+        assert dQ <= max(1e-12, 200 * kap * U * math.sqrt(p) / math.sqrt(m))
+    b.close()
+
+
+def test_digit_cache_enabled_late_and_nan(cq, orc):
+    # the cache filled for columns already in the basis, then a NaN append
+    # breaks down and leaves basis and cache in use for the next append
+    m = 300007
+    b = cq.Basis(m, 24, opts=cq.default_opts(max_escalations=0))
+    b.append(cq.to_colmajor(synth.gaussian(m, 8, seed=95)))
+    b.enable_digit_cache()
+    b.enable_digit_cache()  # a second call is a no-op
+    bad = synth.gaussian(m, 8, seed=96)
+    bad[123456, 3] = np.nan
+    st, info = b.append(cq.to_colmajor(bad), check=False)
+    assert st == cq.ERR_BREAKDOWN and b.cols == 8
+    nxt = synth.gaussian(m, 8, seed=97)
+    st, info = b.append(cq.to_colmajor(nxt))
+    assert st == cq.OK and b.cols == 16
+    Qg = b.Q().cpu().numpy()
+    assert np.linalg.norm(Qg.T @ Qg - np.eye(16)) <= 1e-13
+    b.close()
