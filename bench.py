@@ -321,18 +321,22 @@ def roofline_from(tm, m, n, hbm_peak, hbm_src, tc_peak, tc_src):
             "peak_source": fp64_src}
 
 
-def leg_update(cq, torch, m, p=8, count=32, seed=0):
+def leg_update(cq, torch, m, p=8, count=32, seed=0, cache=True):
     """Basis growth (Alg. 2): 32 appends of 8 columns up to n = 256 at m rows.
     block_k = Q_prev G 0.1 + N eta (eta log-uniform in [1e-12, 1]); the first
     block is N.  Inputs are drawn on the device from a seeded generator; the
     orthogonality of every new block against the whole basis is checked
-    right after its append."""
+    right after its append.  With `cache` the basis keeps the digits of its
+    columns (basis_enable_digit_cache), so the appends' cross Gramian and
+    projection run on the tensor cores."""
     import numpy as np
     from paper_2507_07788_gb300.synth import seed_for
     gen = torch.Generator(device="cuda")
     gen.manual_seed(seed_for(m, p, count, seed) & 0x7FFFFFFFFFFFFFFF)
     rng = np.random.default_rng(seed_for(m, p, count, seed, 1))
     b = cq.Basis(m, p * count)
+    if cache:
+        b.enable_digit_cache()
     blk = cq.colmajor(m, p)
     times, worst, iters, shifts, statuses = [], 0.0, [], [], []
     torch.cuda.synchronize()
@@ -361,7 +365,8 @@ def leg_update(cq, torch, m, p=8, count=32, seed=0):
     b.close()
     bytes_alg = 0.0
     tot = sum(times)
-    return {"workload": f"basis growth m={m}: {count} appends of p={p} to n={q_end}, blocks Q_prev G 0.1 + N eta",
+    return {"workload": f"basis growth m={m}: {count} appends of p={p} to n={q_end}, blocks Q_prev G 0.1 + N eta"
+                        + (", basis digit cache" if cache else ", FP64 projection and cross Gramian"),
             "appends_per_s": count / tot, "ms_per_append_mean": 1e3 * tot / count,
             "ms_per_append_last": 1e3 * times[-1], "rows_cols_per_s": m * q_end / tot,
             "max_block_orth_frob": worst, "iters": iters, "shifts": shifts,
@@ -547,6 +552,9 @@ def run_ours(args):
 
     if rank == 0 and not args.no_update:
         line["update"] = leg_update(cq, torch, args.update_m)
+        fp64 = leg_update(cq, torch, args.update_m, cache=False)
+        line["update"]["without_cache"] = {k: fp64[k] for k in ("ms_per_append_mean", "ms_per_append_last",
+                                                                 "rows_cols_per_s", "max_block_orth_frob")}
 
     if rank == 0 and not args.no_mixed:
         line["mixed"] = leg_mixed(cq, torch, synth, args.mixed_m)

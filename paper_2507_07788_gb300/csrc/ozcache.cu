@@ -45,6 +45,20 @@ using namespace oz;
 
 namespace {
 
+// Four 8x8 b16 matrices, each stored with its rows as the fragment's
+// columns (the transposing form).
+__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2,
+                                          uint32_t &r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+
+// Asynchronous 16-byte global -> shared copy (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src));
+}
+
 constexpr int kCD = 7;                                // digits
 constexpr unsigned long long kCBal = 0x0000808080808080ull;
 constexpr int kCTR = 64;                              // tile rows
