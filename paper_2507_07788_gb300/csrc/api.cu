@@ -1096,6 +1096,22 @@ cqr_status cholqr_pn(const cqr_opts *opts, int64_t m, int64_t n, int64_t r, cons
     (void)cudaGetLastError();
     return cuda_status(e);
   }
+  // Panels of <= 16 columns on a tall block keep a transient digit cache of
+  // the columns already factored (as a basis with basis_enable_digit_cache):
+  // their cross Gramian and projection then run on the tensor cores.
+  const int64_t pmax = (n + r - 1) / r;
+  uint16_t *Qd = nullptr;
+  int *Qe = nullptr;
+  const int64_t ldc = (m + 63) & ~(int64_t)63;
+  if (r > 1 && pmax <= kOzCacheMaxP && m > kOzUpdMinRows && o.emulation == CQR_EMU_AUTO) {
+    if (cudaMallocAsync((void **)&Qd, sizeof(uint16_t) * 7 * (size_t)ldc * n, str) != cudaSuccess ||
+        cudaMallocAsync((void **)&Qe, sizeof(int) * (size_t)n, str) != cudaSuccess) {
+      (void)cudaGetLastError();  // no cache: the panels keep the FP64 path
+      if (Qd) cudaFreeAsync(Qd, str);
+      Qd = nullptr;
+      Qe = nullptr;
+    }
+  }
   cqr_info tot{};
   cqr_status status = CQR_OK;
   int64_t q = 0;
@@ -1119,6 +1135,12 @@ cqr_status cholqr_pn(const cqr_opts *opts, int64_t m, int64_t n, int64_t r, cons
     P.mode = MODE_UPDATE;
     P.min_iter = o.update_min_iter;
     P.o = o;
+    if (Qd != nullptr) {
+      P.Qd = Qd;
+      P.Qe = Qe;
+      P.ldc = ldc;
+      P.cplane = ldc * n;
+    }
     cqr_info pi{};
     const cqr_status st = run(P, &pi, str);
     tot.iters += pi.iters;
@@ -1134,7 +1156,22 @@ cqr_status cholqr_pn(const cqr_opts *opts, int64_t m, int64_t n, int64_t r, cons
       break;
     }
     if (st == CQR_NOT_CONVERGED) status = CQR_NOT_CONVERGED;
+    if (Qd != nullptr && k + 1 < r) {
+      // the panel's columns join the cache before the next panel reads it
+      cudaError_t e = launch_cache_fill(Q, ldq, m, (int)q, (int)p, Qe, Qd, ldc, ldc * n, str);
+      if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        status = cuda_status(e);
+        break;
+      }
+    }
     q += p;
+  }
+  if (Qd != nullptr) {
+    cudaFreeAsync(Qd, str);
+    cudaFreeAsync(Qe, str);
+    if (cudaStreamSynchronize(str) != cudaSuccess && status >= 0) status = CQR_ERR_CUDA;
+    (void)cudaGetLastError();
   }
   if (info != nullptr) *info = tot;
   return status;
