@@ -277,40 +277,41 @@ __global__ void __launch_bounds__(kCThreads, 2) ozcgram_kernel(RowSweep a, const
       shift_pair(acc_hi[r], acc_lo[r], Edz[zi] + Edy[yj], 24);
     }
     const int mi = lane >> 3, rr = lane & 7;
-    int tv[4];
+    // every order at once: per k-step the warp loads each Y digit and each
+    // Z digit once
+    float c[kCMaxOrder + 1][4];
 #pragma unroll
-    for (int o = 0; o <= kCMaxOrder; ++o) {
-      float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int o = 0; o <= kCMaxOrder; ++o) c[o][0] = c[o][1] = c[o][2] = c[o][3] = 0.0f;
 #pragma unroll 1
-      for (int s = 0; s <= o; ++s) {
-        const int tt = o - s;
-        const uint16_t *As = zpl + ((size_t)s * kCZ + i0) * kCLD;
-        const uint16_t *Bt = ypl + ((size_t)tt * kCY + j0) * kCLD;
+    for (int ks = 0; ks < kCTR; ks += 16) {
+      uint32_t bf[kCD][2];
 #pragma unroll
-        for (int ks = 0; ks < kCTR; ks += 16) {
-          uint32_t a0, a1, a2, a3, b0, b1;
-          ldsm_x4(smem_u32(As + ((mi & 1) * 8 + rr) * kCLD + ks + (mi >> 1) * 8), a0, a1, a2, a3);
-          ldsm_x2(smem_u32(Bt + rr * kCLD + ks + (mi & 1) * 8), b0, b1);
-          mma_bf16(c, a0, a1, a2, a3, b0, b1);
-        }
-      }
-      // drain: orders (0,1), (2,3), (4,5) paired in int32, order 6 alone;
-      // hi holds orders 0..3 (unit: order 3), lo orders 4..6
-      if ((o & 1) == 0 && o < kCMaxOrder) {
+      for (int tt = 0; tt < kCD; ++tt)
+        ldsm_x2(smem_u32(ypl + ((size_t)tt * kCY + j0 + rr) * kCLD + ks + (mi & 1) * 8), bf[tt][0], bf[tt][1]);
 #pragma unroll
-        for (int r = 0; r < 4; ++r) tv[r] = f2i(c[r]);
-      } else {
-        const bool hi = o <= 3;
-        const int shl = hi ? 8 * (3 - o) : 8 * (kCMaxOrder - o);
+      for (int sd = 0; sd < kCD; ++sd) {
+        uint32_t a0, a1, a2, a3;
+        ldsm_x4(smem_u32(zpl + ((size_t)sd * kCZ + i0 + (mi & 1) * 8 + rr) * kCLD + ks + (mi >> 1) * 8), a0,
+                a1, a2, a3);
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          const int v = f2i(c[r]);
-          const long long w = (o < kCMaxOrder) ? (long long)(tv[r] * 256 + v) : (long long)v;
-          if (hi) acc_hi[r] += w << shl;
-          else acc_lo[r] += w << shl;
-        }
+        for (int tt = 0; tt + sd <= kCMaxOrder; ++tt) mma_bf16(c[sd + tt], a0, a1, a2, a3, bf[tt][0], bf[tt][1]);
       }
     }
+    // drain: orders (0,1), (2,3), (4,5) paired in int32, order 6 alone; hi
+    // holds orders 0..3 (unit: order 3), lo orders 4..6
+#pragma unroll
+    for (int o = 1; o <= kCMaxOrder; o += 2) {
+      const bool hi = o <= 3;
+      const int shl = hi ? 8 * (3 - o) : 8 * (kCMaxOrder - o);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const long long w = (long long)(f2i(c[o - 1][r]) * 256 + f2i(c[o][r]));
+        if (hi) acc_hi[r] += w << shl;
+        else acc_lo[r] += w << shl;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) acc_lo[r] += (long long)f2i(c[kCMaxOrder][r]);
     __syncthreads();  // the next tile restages the planes
   }
 
@@ -457,40 +458,40 @@ __global__ void __launch_bounds__(kCThreads, 1) ozcproj_kernel(RowSweep a, const
     __syncthreads();
     const uint16_t *zp = zbuf + (size_t)(step & 1) * kCD * kCZ * kCLD;
     const int k0 = (int)(step % nch) * kCZ;
-    int tv[4];
+    // every order at once: per k-step each Q digit and each B' digit once
+    float c[kCMaxOrder + 1][4];
 #pragma unroll
-    for (int o = 0; o <= kCMaxOrder; ++o) {
-      float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int o = 0; o <= kCMaxOrder; ++o) c[o][0] = c[o][1] = c[o][2] = c[o][3] = 0.0f;
 #pragma unroll 1
-      for (int sd = 0; sd <= o; ++sd) {
-        const int td = o - sd;
-        const uint16_t *As = zp + (size_t)sd * kCZ * kCLD;  // [k][row]: A = rows x k, transposed loads
-        const uint16_t *Bs = bpl + ((size_t)td * kCY + j0) * kCPK + k0;
+    for (int ks = 0; ks < kCZ; ks += 16) {
+      uint32_t bf[kCD][2];
 #pragma unroll
-        for (int ks = 0; ks < kCZ; ks += 16) {
-          uint32_t a0, a1, a2, a3, b0, b1;
-          // block (mi & 1): rows +8; (mi >> 1): k +8
-          ldsm_x4_t(smem_u32(As + (size_t)(ks + (mi >> 1) * 8 + rr) * kCLD + i0 + (mi & 1) * 8), a0, a1, a2,
-                    a3);
-          ldsm_x2(smem_u32(Bs + (size_t)rr * kCPK + ks + (mi & 1) * 8), b0, b1);
-          mma_bf16(c, a0, a1, a2, a3, b0, b1);
-        }
-      }
-      if ((o & 1) == 0 && o < kCMaxOrder) {
+      for (int td = 0; td < kCD; ++td)
+        ldsm_x2(smem_u32(bpl + ((size_t)td * kCY + j0 + rr) * kCPK + k0 + ks + (mi & 1) * 8), bf[td][0],
+                bf[td][1]);
 #pragma unroll
-        for (int r = 0; r < 4; ++r) tv[r] = f2i(c[r]);
-      } else {
-        const bool hi = o <= 3;
-        const int shl = hi ? 8 * (3 - o) : 8 * (kCMaxOrder - o);
+      for (int sd = 0; sd < kCD; ++sd) {
+        uint32_t a0, a1, a2, a3;
+        // [k][row] storage, transposed loads: block (mi & 1) rows +8, (mi >> 1) k +8
+        ldsm_x4_t(smem_u32(zp + ((size_t)sd * kCZ + ks + (mi >> 1) * 8 + rr) * kCLD + i0 + (mi & 1) * 8), a0,
+                  a1, a2, a3);
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          const int v = f2i(c[r]);
-          const long long w = (o < kCMaxOrder) ? (long long)(tv[r] * 256 + v) : (long long)v;
-          if (hi) acc_hi[r] += w << shl;
-          else acc_lo[r] += w << shl;
-        }
+        for (int td = 0; td + sd <= kCMaxOrder; ++td) mma_bf16(c[sd + td], a0, a1, a2, a3, bf[td][0], bf[td][1]);
       }
     }
+#pragma unroll
+    for (int o = 1; o <= kCMaxOrder; o += 2) {
+      const bool hi = o <= 3;
+      const int shl = hi ? 8 * (3 - o) : 8 * (kCMaxOrder - o);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const long long w = (long long)(f2i(c[o - 1][r]) * 256 + f2i(c[o][r]));
+        if (hi) acc_hi[r] += w << shl;
+        else acc_lo[r] += w << shl;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) acc_lo[r] += (long long)f2i(c[kCMaxOrder][r]);
     if (step % nch == nch - 1) {
       // ---- the tile's P, rounded once, then the FP64 row solve
       const int64_t r0 = row0 + (step / nch) * kCTR;
