@@ -95,11 +95,16 @@ typedef struct cqr_opts {
   int32_t emulation;       /* CQR_EMU_*                          (AUTO) */
 } cqr_opts;
 
-/* How FP64 Gramians are formed.  CQR_EMU_AUTO: on the tensor cores with the
- * Ozaki splitting scheme (exact digit products, FP64-class accuracy) where
- * the kernels support it (cholqr_factor and cholqr_gram with n <= 64), FP64
- * CUDA cores elsewhere (basis_append always).  CQR_EMU_OFF: FP64 CUDA cores
- * everywhere. */
+/* How the FP64 products of a pass are formed.  CQR_EMU_AUTO: on the tensor
+ * cores with the Ozaki splitting scheme (exact digit products, each entry
+ * rounded to FP64 once) where the kernels support it: the Gramians of
+ * cholqr_factor and cholqr_gram for n <= 128 and the factorisation's
+ * triangular solve for 17 <= n <= 128; for basis_append and cholqr_pn on
+ * more than 262144 rows, an append to an empty basis (the factorisation's
+ * pipeline), the cross Gramian of appends of 32..64 columns, and the cross
+ * Gramian and projection of appends of <= 16 columns to a basis with a digit
+ * cache (basis_enable_digit_cache; q <= 256 for the projection); FP64 CUDA
+ * cores elsewhere.  CQR_EMU_OFF: FP64 CUDA cores everywhere. */
 enum { CQR_EMU_AUTO = 0, CQR_EMU_OFF = 1 };
 
 /* Per-call report.  orth_frob is ||X - I||_F of the last Gramian formed
