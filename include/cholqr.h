@@ -103,8 +103,9 @@ typedef struct cqr_opts {
  * more than 262144 rows, an append to an empty basis (the factorisation's
  * pipeline), the cross Gramian of appends of 32..64 columns, and the cross
  * Gramian and projection of appends of <= 16 columns to a basis with a digit
- * cache (basis_enable_digit_cache; q <= 256 for the projection); FP64 CUDA
- * cores elsewhere.  CQR_EMU_OFF: FP64 CUDA cores everywhere. */
+ * cache (basis_enable_digit_cache; cholqr_pn keeps one for panels of <= 16
+ * columns; q <= 256 for the projection); FP64 CUDA cores elsewhere.
+ * CQR_EMU_OFF: FP64 CUDA cores everywhere. */
 enum { CQR_EMU_AUTO = 0, CQR_EMU_OFF = 1 };
 
 /* Per-call report.  orth_frob is ||X - I||_F of the last Gramian formed
@@ -230,6 +231,11 @@ cqr_status cholqr_factor_noalloc(const cqr_opts *opts, int64_t m, int64_t n, con
  *             escalations summed over the panels; sigma_first = the first
  *             nonzero shift, sigma_last = the last; orth_frob and proj_frob of
  *             the last panel.
+ * With r > 1 panels of at most 16 columns on more than 262144 rows (and
+ * CQR_EMU_AUTO), the call keeps a stream-ordered digit cache of the columns
+ * already factored (14 bytes per entry of Q, freed before return), as a
+ * basis with basis_enable_digit_cache does; without room for it the panels
+ * take the FP64 path.
  * Returns the first error of a panel (later panels are not run), else
  * CQR_NOT_CONVERGED if any panel did not converge, else CQR_OK.
  */
