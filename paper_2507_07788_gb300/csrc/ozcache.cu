@@ -37,6 +37,7 @@
 #include <algorithm>
 
 #include "cqr_internal.cuh"
+#include "ozbalanced.cuh"
 #include "ozdigits.cuh"
 
 namespace cqr {
@@ -60,7 +61,6 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
 }
 
 constexpr int kCD = 7;                                // digits
-constexpr unsigned long long kCBal = 0x0000808080808080ull;
 constexpr int kCTR = 64;                              // tile rows
 constexpr int kCLD = kCTR + 8;                        // bf16 stride of a plane column
 constexpr int kCZ = 64;                               // Z columns per CTA
@@ -72,27 +72,6 @@ constexpr size_t kCSmem = sizeof(double) * (size_t)kCY * kCTR          // FP64 t
                           + sizeof(uint16_t) * (size_t)kCD * kCZ * kCLD  // Z digit planes
                           + sizeof(uint16_t) * (size_t)kCD * kCY * kCLD  // Y digit planes
                           + sizeof(int) * (size_t)(2 * kCZ + 2 * kCY + 4);
-
-// Digit i of W = V + kCBal with sign s: W >> 48 for i = 0 (the carry out of
-// the six low bytes can reach bit 56), else byte 6 - i minus 128; placed in
-// an FP32 2^23 + x by a shift or a byte permute, signed in one FMA (exact).
-__device__ __forceinline__ float cdigit(unsigned long long W, int i, float s) {
-  if (i == 0) return fmaf(__int_as_float(0x4B000000 | (int)(W >> 48)), s, -s * 8388608.0f);
-  const int b = 6 - i;
-  const uint32_t word = (b >= 4) ? (uint32_t)(W >> 32) : (uint32_t)W;
-  const float x = __int_as_float((int)__byte_perm(word, 0x4B000000u, 0x7440u | (uint32_t)(b & 3)));
-  return fmaf(x, s, -s * 8388736.0f);
-}
-
-// W = V + kCBal of element bits b against the reference exponent E.
-__device__ __forceinline__ unsigned long long cwords(unsigned long long b, int E) {
-  const int ef = (int)((b >> 52) & 0x7FF);
-  unsigned long long M = b & 0xFFFFFFFFFFFFFull;
-  if (ef) M |= 0x10000000000000ull;
-  if (ef == 0x7FF) M = 0;
-  const int sh = E - (ef ? ef : 1);
-  return ((sh >= 56 || sh < 0) ? 0ull : ((M << 3) >> sh)) + kCBal;
-}
 
 }  // namespace
 
