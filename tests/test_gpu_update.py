@@ -242,3 +242,27 @@ def test_digit_cache_enabled_late_and_nan(cq, orc):
     Qg = b.Q().cpu().numpy()
     assert np.linalg.norm(Qg.T @ Qg - np.eye(16)) <= 1e-13
     b.close()
+
+
+def test_digit_cache_beyond_projection_width(cq, orc):
+    # q > 256: the narrow append keeps the FP64 projection and solve, its cross
+    # Gramian still reads the cached digits (five 64-column Z blocks)
+    m = 300007
+    widths = (128, 128, 8, 8)
+    b = cq.Basis(m, sum(widths))
+    b.enable_digit_cache()
+    Qo = np.zeros((m, 0))
+    Ro = np.zeros((0, 0))
+    rng = np.random.default_rng(93)
+    for k, p in enumerate(widths):
+        if k == 0:
+            blk = synth.gaussian(m, p, seed=100 + k)
+        else:
+            blk = Qo @ rng.standard_normal((Qo.shape[1], p)) * 0.1 + synth.gaussian(m, p, seed=100 + k) * 1e-3
+        st, info = b.append(cq.to_colmajor(blk))
+        Qg, Rg = b.Q().cpu().numpy(), b.R().cpu().numpy()
+        Qo, Ro, dR, dQ, scale, sto, info_o = _check_append(orc, Qo, Ro, blk, Qg, Rg, m, info, k)
+        assert st == sto and st >= 0, (k, st, info, info_o)
+    Qg = b.Q().cpu().numpy()
+    assert np.linalg.norm(Qg.T @ Qg - np.eye(Qg.shape[1])) <= 1e-12
+    b.close()
