@@ -178,8 +178,9 @@ cqr_status cholqr_gram(const cqr_opts *opts, int64_t m, int64_t n, const double 
  * missed the final pass are copied after the stop.  Otherwise Q is copied
  * whole after the stop.
  *   A, lda    host, m x n, lda >= m (read only; pinned for full bandwidth).
- *   Q, ldq    host, m x n output, ldq >= m; must not overlap A.  Its contents
- *             are undefined while the call runs and after an error.
+ *   Q, ldq    host, m x n output, ldq >= m; must not overlap A (else
+ *             CQR_ERR_INVALID).  Its contents are undefined while the
+ *             call runs and after an error.
  *   R, ldr    host, n x n output, ldr >= n.
  * The device copies are stream-ordered scratch freed before return; the call
  * returns after the stream has drained.  Status as cholqr_factor.

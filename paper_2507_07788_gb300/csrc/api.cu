@@ -271,14 +271,14 @@ struct Problem {
   int mode;
   int min_iter;
   cqr_opts o;
-  // Host staging (cholqr_factor_host): Y0 == Y is the device copy of hA,
-  // copied ahead of the first Gramian; hQ (host memory the device can write,
-  // or null) receives Q chunk by chunk as the pass expected to be the last
-  // solves it, and *hq_written tells the caller whether it holds the final Q.
   // Digit cache of Q_in (appends to a basis that keeps one), or null.
   const uint16_t *Qd = nullptr;
   const int *Qe = nullptr;
   int64_t ldc = 0, cplane = 0;
+  // Host staging (cholqr_factor_host): Y0 == Y is the device copy of hA,
+  // copied ahead of the first Gramian; hQ (host memory the device can write,
+  // or null) receives Q chunk by chunk as the pass expected to be the last
+  // solves it, and *hq_written tells the caller whether it holds the final Q.
   const double *hA = nullptr;
   int64_t ldha = 0;
   double *hQ = nullptr;
@@ -362,6 +362,7 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
     chunk_rpc = ((tiles + Gc - 1) / Gc) * tr;
   }
   AuxCtx *ax = pipe ? aux_ctx(nchunks) : nullptr;
+  if (pipe && ax == nullptr) return CQR_ERR_CUDA;  // no auxiliary stream or events
   // host staging pipelined with the passes (the tensor-core pipeline only)
   CopyCtx *cx = (P.hA != nullptr && pipe && !mixed && ax != nullptr) ? copy_ctx(nchunks) : nullptr;
   const bool stage = cx != nullptr;
@@ -901,6 +902,12 @@ cqr_status cholqr_factor_host(const cqr_opts *opts, int64_t m, int64_t n, const 
   if (!opts_valid(o)) return CQR_ERR_INVALID;
   if (n < 1 || n > CQR_MAX_N || m < n || lda < m || ldq < m || ldr < n) return CQR_ERR_INVALID;
   if (A == nullptr || Q == nullptr || R == nullptr) return CQR_ERR_INVALID;
+  {
+    // Q is written while A may still be read (the copy-out of the last pass)
+    const char *a0 = (const char *)A, *a1 = (const char *)(A + lda * (n - 1) + m);
+    const char *q0 = (const char *)Q, *q1 = (const char *)(Q + ldq * (n - 1) + m);
+    if (a0 < q1 && q0 < a1) return CQR_ERR_INVALID;
+  }
   if (host_state() == nullptr) return CQR_ERR_CUDA;
   cudaStream_t str = (cudaStream_t)stream;
   keep_pool_memory();

@@ -90,6 +90,15 @@ def test_factor_rejects_partial_overlap(cq):
     assert st == cq.ERR_INVALID
 
 
+def test_factor_host_rejects_overlap_without_gpu(cq):
+    # the host entry point writes Q while its input copy may still read A
+    base = 0x100000
+    for qoff, ldq in ((0, 100), (8 * 50, 100)):
+        st = cq.cholqr_factor_host(None, 100, 4, C.c_void_p(base), 100, C.c_void_p(base + qoff), ldq,
+                                   C.c_void_p(0x900000), 4, None, None)
+        assert st == cq.ERR_INVALID
+
+
 @pytest.mark.parametrize("m,n,r,lda,ldq,ldr", [
     (100, 8, 0, 100, 100, 8),       # r = 0
     (100, 8, 9, 100, 100, 8),       # r > n
