@@ -1,0 +1,95 @@
+"""The roofline arithmetic of bench.py on CPU, from synthetic per-launch
+timings: the dominant kernel is the one with the larger total time, its
+achieved rate is the algorithmic work of one launch over the mean launch
+time, and its DRAM traffic is the committed ncu capture scaled by rows."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+bench = pytest.importorskip("bench")
+
+KEYS = ("sweep", "fused", "solve", "gram", "tsolve")
+
+
+def _timing(**kw):
+    tm = {}
+    for k in KEYS:
+        tm[f"{k}_launches"] = 0
+        for f in ("ms", "flops", "bytes"):
+            tm[f"{k}_{f}"] = 0.0
+    tm["tsolve_tc_flops"] = 0.0
+    tm.update(kw)
+    return tm
+
+
+def _capture(name):
+    d = {}
+    for line in open(os.path.join(ROOT, "profiles", f"traffic_{name}.txt")):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            d[k.strip()] = v.strip()
+    return float(d["capture_bytes_per_launch"]), float(d["capture_rows"])
+
+
+def test_tensor_pipeline_dominant_kernel():
+    # 24 launches each of the digit Gramian and the digit solve on row chunks
+    # of 125000 rows at n = 64; the Gramian takes longer in total
+    n, rows, L = 64, 125000, 24
+    g_ms, s_ms = 0.20, 0.18
+    tc_solve_per_launch = 3.0e10
+    tm = _timing(gram_launches=L, gram_ms=L * g_ms, gram_flops=L * rows * n * (n + 1.0),
+                 gram_bytes=L * 8.0 * rows * n,
+                 tsolve_launches=L, tsolve_ms=L * s_ms, tsolve_flops=L * rows * n * n,
+                 tsolve_bytes=L * 16.0 * rows * n, tsolve_tc_flops=L * tc_solve_per_launch)
+    r = bench.roofline_from(tm, 1_000_000, n, 6686.8, "measured", 1730.8, "measured")
+    assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
+    assert r["kernel"].startswith("ozgram_kernel") and "solve" in r
+    # 16 symmetric digit pairs, each a 64 x 64 block per row, in 0.2 ms
+    want = rows * 2 * 16 * 64 * 64 / (g_ms * 1e-3) / 1e12
+    assert r["achieved"] == pytest.approx(want, rel=1e-12)
+    assert r["frac"] == pytest.approx(want / 1730.8, rel=1e-12)
+    assert r["hbm"]["achieved_gbs"] == pytest.approx(8.0 * rows * n / (g_ms * 1e-3) / 1e9, rel=1e-12)
+    b, cr = _capture("ozgram")
+    assert r["traffic"] == pytest.approx(b * rows / cr, rel=1e-12)
+    s = r["solve"]
+    assert s["achieved"] == pytest.approx(tc_solve_per_launch / (s_ms * 1e-3) / 1e12, rel=1e-12)
+    b, cr = _capture("ozgemm")
+    assert s["traffic"] == pytest.approx(b * rows / cr, rel=1e-12)
+
+
+def test_solve_dominates_when_it_takes_longer():
+    n, rows, L = 128, 62500, 16
+    tm = _timing(gram_launches=L, gram_ms=L * 0.1, gram_flops=L * rows * n * (n + 1.0),
+                 gram_bytes=L * 8.0 * rows * n,
+                 tsolve_launches=L, tsolve_ms=L * 0.3, tsolve_flops=L * rows * n * n,
+                 tsolve_bytes=L * 16.0 * rows * n, tsolve_tc_flops=L * 5.0e10)
+    r = bench.roofline_from(tm, 1_000_000, n, 6686.8, "measured", 1730.8, "measured")
+    assert r["kernel"].startswith("ozgemm_kernel") and "gram" in r
+    assert r["achieved"] == pytest.approx(5.0e10 / 0.3e-3 / 1e12, rel=1e-12)
+    # the Gramian at n = 128: 16 pairs of 128 x 128 blocks per row
+    assert r["gram"]["achieved"] == pytest.approx(rows * 2 * 16 * 128 * 128 / 0.1e-3 / 1e12, rel=1e-12)
+
+
+def test_narrow_blocks_report_the_fp64_solve():
+    n, rows, L = 16, 125000, 8
+    tm = _timing(gram_launches=L, gram_ms=L * 0.05, gram_flops=L * rows * n * (n + 1.0),
+                 gram_bytes=L * 8.0 * rows * n,
+                 solve_launches=L, solve_ms=L * 0.04, solve_flops=L * rows * n * n,
+                 solve_bytes=L * 16.0 * rows * n)
+    r = bench.roofline_from(tm, 1_000_000, n, 6686.8, "measured", 1730.8, "measured")
+    assert r["bound"] == "alu" and r["kernel"].startswith("trsm_rows_kernel")
+    assert r["achieved"] == pytest.approx(rows * n * n / 0.04e-3 / 1e12, rel=1e-12)
+    assert r["frac"] == pytest.approx(r["achieved"] * 1e12 / bench.FP64_PEAK_FLOPS, rel=1e-12)
+    assert "gram" in r
+
+
+def test_fp64_sweep_without_tensor_kernels():
+    n, m = 64, 200000
+    tm = _timing(fused_launches=3, fused_ms=3 * 2.0, fused_flops=3 * 4.0 * m * n * n,
+                 fused_bytes=3 * 16.0 * m * n)
+    r = bench.roofline_from(tm, m, n, 6686.8, "measured", 1730.8, "measured")
+    assert r["bound"] == "alu" and r["kernel"].startswith("rowsweep_kernel")
+    assert r["achieved"] == pytest.approx(4.0 * m * n * n / 2.0e-3 / 1e12, rel=1e-12)
