@@ -313,8 +313,11 @@ cqr_status basis_r(const cqr_basis *b, const double **R, int64_t *ldr);
  *     requests on one basis run in submission order;
  *   - factor requests and large appends run on `slots` worker streams
  *     concurrently; appends of at most 32 columns to bases of at most
- *     `small_rows` rows are batched: one persistent launch per step covers
- *     every append of the batch, replayed from captured CUDA graphs;
+ *     `small_rows` rows that keep no digit cache are batched: one
+ *     persistent launch per step covers every append of the batch, replayed
+ *     from captured CUDA graphs;
+ *   - a factor request replaces its basis's columns (and refills the
+ *     basis's digit cache, if it keeps one);
  *   - each result is bitwise the same alone and in the mix (a batched problem
  *     uses the same per-CTA work and reduction order as alone).
  * Timestamps are seconds on the server's steady clock (cqr_server_now).

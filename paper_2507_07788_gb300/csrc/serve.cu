@@ -125,8 +125,9 @@ bool is_small_append(const cqr_server *s, const Request &r) {
   if (r.kind != 1) return false;
   const int64_t q = r.b->q, p = r.w;
   const int64_t E = q * p + p * (p + 1) / 2;
+  // a basis with a digit cache takes basis_append, which keeps the cache
   return p <= kSmallMaxP && E <= (int64_t)kThreads * kBatchEPT && r.b->m <= s->o.small_rows &&
-         s->ws.cap > 0;
+         s->ws.cap > 0 && r.b->Qd == nullptr;
 }
 
 void finish_locked(cqr_server *s, Request *r) {
@@ -202,6 +203,9 @@ void execute_single(cqr_server *s, Request *r, cudaStream_t str) {
     if (e == cudaSuccess)
       e = cudaMemcpy2DAsync(b->R, sizeof(double) * b->ldr, Rs, sizeof(double) * n, sizeof(double) * n,
                             n, cudaMemcpyDeviceToDevice, str);
+    // the basis's digit cache (if it keeps one) follows its new columns
+    if (e == cudaSuccess && b->Qd != nullptr)
+      e = launch_cache_fill(b->Q, b->ldq, m, 0, (int)n, b->Qe, b->Qd, b->ldc, b->ldc * b->n_max, str);
     if (e == cudaSuccess) e = cudaStreamSynchronize(str);
     if (e == cudaSuccess) b->q = n;
     else st = CQR_ERR_CUDA;

@@ -107,3 +107,36 @@ def test_hbm_budget_limits_concurrency(cq):
     assert all(r.result["status"] == cq.OK for r in wl.reqs)
     for b in bases:
         b.close()
+
+
+def test_cached_basis_through_the_server(cq, orc):
+    # a basis with a digit cache: the factor request refills the cache for
+    # its new columns, and small appends go to basis_append (which keeps the
+    # cache) instead of the batched launch; the cached cross Gramian and
+    # projection then see the factor's columns, not the ones it replaced
+    from paper_2507_07788_gb300 import synth
+    m, n, p = 300007, 16, 8
+    b = cq.Basis(m, 48)
+    b.enable_digit_cache()
+    b.append(cq.to_colmajor(synth.gaussian(m, 20, seed=11)))
+    A = synth.test_matrix(m, n, 1e8, rep=2)
+    srv = cq.Server(slots=2, batch_max=8, small_rows=400_000)
+    r = srv.wait(srv.submit_factor(b, cq.to_colmajor(A)))
+    assert r["status"] == cq.OK and b.cols == n
+    Qf = b.Q().cpu().numpy()[:, :n]
+    rng = np.random.default_rng(12)
+    blocks = [A]
+    for k in range(2):
+        blk = Qf @ rng.standard_normal((n, p)) * 0.1 + synth.gaussian(m, p, seed=20 + k) * 1e-3
+        blocks.append(blk)
+        r = srv.wait(srv.submit_append(b, cq.to_colmajor(blk)))
+        assert r["status"] >= 0 and r["batched"] == 0, r
+    srv.close()
+    q = n + 2 * p
+    assert b.cols == q
+    Q = b.Q().cpu().numpy()[:, :q]
+    R = b.R().cpu().numpy()[:q, :q]
+    X = np.hstack(blocks)
+    assert orc.loo_frob(Q) <= 1e-12
+    assert np.linalg.norm(X - Q @ R) / np.linalg.norm(X) <= 1e-13
+    b.close()
