@@ -278,13 +278,16 @@ cqr_status basis_append(cqr_basis *b, int64_t p, const double *A_in, int64_t lda
  * basis_enable_digit_cache -- keep a digit copy of the basis columns on the
  * device (7 bf16 digits per entry, 14 bytes: 1.75x the size of Q) so that
  * later appends of p <= 16 columns to a basis of more than 262144 rows form
- * their cross Gramian [Q_in A_in]^T A_in (Alg. 2 lines 2-4, 15-16) on the
- * tensor cores from the cached digits instead of FP64 products.  Each column
- * is written as sign * V * 2^(E_k - 1078) with E_k its largest biased
- * exponent and V < 2^56 in 7 balanced base-256 digits; the cache fills for
- * the present columns now and for new ones at each successful append.  The
- * result follows the same tolerances as without the cache (the Gramian's
- * digit products are exact; each entry is rounded once).
+ * their cross Gramian [Q_in A_in]^T A_in (Alg. 2 lines 2-4, 15-16) and, while
+ * the basis has at most 256 columns, the projection Q_in B~ of the solve
+ * (Alg. 2 line 12) on the tensor cores from the cached digits instead of
+ * FP64 products.  Each column is written as sign * V * 2^(E_k - 1078) with
+ * E_k its largest biased exponent and V < 2^56 in 7 balanced base-256
+ * digits; the cache fills for the present columns now and for new ones at
+ * each successful append (and, in the serving runtime, when a factor
+ * request replaces the columns).  The result follows the same tolerances as
+ * without the cache (the digit products are exact; each entry is rounded
+ * once).
  *   Returns CQR_OK (also if the cache exists), CQR_ERR_OOM (the basis is
  *   unchanged and appends keep the FP64 path), or CQR_ERR_CUDA.
  */
