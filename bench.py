@@ -7,10 +7,14 @@ m = 1,000,000, n = 64, kappa = 1e12.  Metric: rows*cols/s = m n / t_step,
 summed over ranks (each rank factors its own matrix: replicas, weak scaling).
 
 Prints ONE JSON line (rank 0) with the contract keys plus:
-  roofline      dominant kernel (the FP64 row solve of the pass pipeline; the
-                fused solve + Gramian row sweep where the tensor-core Gramian
-                is off), its achieved rate from CUDA events on its launch
-                stream, against the FP64 peak, with the digit Gramian beside it;
+  roofline      dominant kernel by total time in the timed region: at
+                17 <= n <= 128 the tensor-core digit Gramian or digit solve
+                (bf16 digit FLOP against the sustained bf16 peak, with the
+                FP64-equivalent rate and HBM rate beside it, and the other
+                kernel nested); at n <= 16 the FP64 row solve, and without
+                the tensor-core path the fused FP64 row sweep (against the
+                FP64 peak); achieved rates from CUDA events on each launch's
+                stream, DRAM traffic from the committed ncu capture;
   cpu_baseline  the CPU oracle on a bounded sample of the same matrix;
   e2e           the same metric through cholqr_factor_host (host buffers,
                 copies inside the timed region);
