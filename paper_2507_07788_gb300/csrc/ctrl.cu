@@ -66,13 +66,14 @@ __device__ __forceinline__ float d2f_trunc(double x) {
 // starting from the all-ones vector).  Power iteration in FP32 from the
 // all-ones vector, stopped when the Rayleigh quotient changes by < 1e-3
 // relative (at most 100 steps); the result is never below max_i |X_ii|.
+// X enters the FP32 iteration scaled by 2^-e, e the exponent of max_i |X_ii|
+// (exact, so the iteration is the same as on X itself wherever X fits FP32),
+// which keeps Gramians of norm beyond the FP32 range (||A|| > 2^64) or
+// below its normal range finite and accurate.
 __device__ double norm_estimate(const double *X, int p, float *Xf, float *v, float *w,
                                 float *fred, double *red) {
   const int t = threadIdx.x, NT = blockDim.x;
   __syncthreads();  // Xf may alias storage read just before the call
-  for (int e = t; e < p * p; e += NT) Xf[e] = d2f_trunc(X[e]);
-  double dmax;
-  __syncthreads();
   if (t < 32) {
     double mv = 0.0;
     for (int i = t; i < p; i += 32) mv = fmax(mv, fabs(X[i + i * p]));
@@ -81,7 +82,13 @@ __device__ double norm_estimate(const double *X, int p, float *Xf, float *v, flo
     if (t == 0) red[31] = mv;
   }
   __syncthreads();
-  dmax = red[31];
+  const double dmax = red[31];
+  // 2^-e and 2^e for a finite, non-zero diagonal maximum (else 1)
+  int ex = 0;
+  if (dmax > 0.0 && dmax <= 1.7976931348623157e308)
+    ex = (int)((__double_as_longlong(dmax) >> 52) & 0x7FF) - 1023;
+  const double down = ldexp(1.0, -ex), up = ldexp(1.0, ex);
+  for (int e = t; e < p * p; e += NT) Xf[e] = d2f_trunc(X[e] * down);
   __syncthreads();
   const float inv = rsqrtf((float)p);
   for (int i = t; i < p; i += NT) v[i] = inv;
@@ -105,7 +112,7 @@ __device__ double norm_estimate(const double *X, int p, float *Xf, float *v, flo
     if (it > 0 && fabsf(lam - lam_prev) <= 1e-3f * fabsf(lam)) break;
     lam_prev = lam;
   }
-  double l = (double)lam;
+  double l = (double)lam * up;
   if (!(l == l)) l = INFINITY;
   return fmax(l, dmax);
 }

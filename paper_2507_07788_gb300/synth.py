@@ -6,8 +6,14 @@ their inputs from here.
 
 Test matrices (Sec. 4.1 of the paper): A = U diag(s) V^T with U (m x n) and
 V (n x n) random orthonormal factors of seeded Gaussian matrices and
-singular values s_i log-spaced from 1 down to 1/kappa.  The paper varies the
-seed with the dimensions and the condition number; here the seed is a
+singular values s_i log-spaced between 1 and kappa.  The paper prints them
+from 1 up to kappa (||A||_2 = kappa); by default they run from 1 down to
+1/kappa (||A||_2 = 1), the same matrix divided by kappa up to rounding.
+The methods are invariant under that scaling (their shifts scale with the
+Gramian they factor) except isCholQR, which reuses the shift of the first
+Gramian, of norm ||A||^2, on later Gramians of norm about 1: the Fig. 1
+reproduction takes the paper's scale (paper_scale=True).  The paper varies
+the seed with the dimensions and the condition number; here the seed is a
 splitmix64 hash of (m, n, round(log10 kappa), rep, salt).
 
 Update blocks (basis growth): block_k = Q_prev G 0.1 + N eta with G (q x p)
@@ -48,18 +54,23 @@ def _orthonormal(rng: np.random.Generator, rows: int, cols: int) -> np.ndarray:
 
 
 def singular_values(n: int, kappa: float) -> np.ndarray:
-    """log-spaced 1 -> 1/kappa (Sec. 4.1)."""
+    """log-spaced 1 -> 1/kappa (Sec. 4.1 up to the factor kappa)."""
     if n == 1:
         return np.ones(1)
     return np.logspace(0.0, -math.log10(kappa), n)
 
 
-def test_matrix(m: int, n: int, kappa: float, rep: int = 0, salt: int = 0) -> np.ndarray:
-    """A = U diag(s) V^T, column-major float64 (m x n)."""
+def test_matrix(m: int, n: int, kappa: float, rep: int = 0, salt: int = 0,
+                paper_scale: bool = False) -> np.ndarray:
+    """A = U diag(s) V^T, column-major float64 (m x n); with paper_scale the
+    singular values run from 1 up to kappa (Sec. 4.1), else from 1 down to
+    1/kappa."""
     rng = np.random.default_rng(seed_for(m, n, round(math.log10(max(kappa, 1.0))), rep, salt))
     U = _orthonormal(rng, m, n)
     V = _orthonormal(rng, n, n)
     s = singular_values(n, kappa)
+    if paper_scale:
+        s = s * kappa
     return np.asfortranarray((U * s) @ V.T)
 
 

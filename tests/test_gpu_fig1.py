@@ -118,3 +118,36 @@ def test_ischolqr_reuses_one_shift(cq, orc):
     assert info["shifts"] >= 2
     assert info["sigma_last"] == info["sigma_first"] or info["escalations"] > 0
     assert info["sigma_first"] == pytest.approx(info_o.sigma_first, rel=1e-2)
+
+
+def test_fig1_on_the_papers_scale(cq, orc):
+    # Sec. 4.1 builds A with singular values from 1 up to kappa (||A|| = kappa,
+    # Gramians up to 1e40 at kappa = 1e20).  The shifts of rsCholQR and the
+    # default scale with each pass's Gramian, so they hold to 1e20 as on the
+    # unit scale.  isCholQR reapplies the first breakdown's shift, sized from
+    # ||A||^2, to later Gramians of norm about 1 (Sec. 2.1): it holds to 1e15,
+    # where a later pass does not break down, and fails at 1e20, where the
+    # reused shift only rescales Q at every pass.
+    m, n = GOLD["fig1_shape"]["m"], GOLD["fig1_shape"]["n"]
+    red = GOLD["loo_red_line"]["value"]
+    tol = GOLD["stop_tol_frob"]["value"]
+    mi = GOLD["max_iter"]["value"]
+    band = band_fail = 0
+    for e in range(0, 21):
+        kappa = 10.0 ** e
+        for rep in range(3):
+            A = synth.test_matrix(m, n, kappa, rep=rep, salt=1, paper_scale=True)
+            for pol in (cq.SHIFT_ON_BREAKDOWN, cq.SHIFT_SCHOLQR3):
+                Q, R, st, info = _run(cq, A, shift_policy=pol, tol=tol, max_iter=mi)
+                assert st == cq.OK, (kappa, rep, pol, info)
+                assert orc.loo(Q) < red and orc.rrr(A, Q, R) < 1e-13, (kappa, rep, pol)
+            Qi, Ri, sti, infoi = _run(cq, A, shift_policy=cq.SHIFT_ISCHOLQR, tol=tol, max_iter=mi)
+            failed = sti != cq.OK or orc.loo(Qi) >= red
+            if kappa < GOLD["ischolqr_unreliable_from_kappa"]["value"]:
+                assert not failed and orc.rrr(A, Qi, Ri) < 1e-13, (kappa, rep, infoi)
+            else:
+                band += 1
+                band_fail += failed
+                if kappa >= 1e20:
+                    assert failed, (kappa, rep, infoi)
+    assert band_fail >= 3, (band_fail, band)

@@ -245,14 +245,17 @@ def _fig1_cases():
 
 
 def test_fig1_robustness_claims(orc):
-    """Sec. 4.2 / Fig. 1 at 300 x 10: CholQR2 breaks down above ~1e8, sCholQR3
-    holds to 1e15, rsCholQR stays below the red line up to 1e20."""
+    """Sec. 4.2 / Fig. 1 at 300 x 10, singular values from 1 up to kappa as
+    Sec. 4.1 builds them: CholQR2 breaks down above ~1e8, sCholQR3 and
+    isCholQR hold to 1e15 and become unreliable from 1e16, rsCholQR stays
+    below the red line up to 1e20."""
     m, n = GOLD["fig1_shape"]["m"], GOLD["fig1_shape"]["n"]
     red = GOLD["loo_red_line"]["value"]
     tol = GOLD["stop_tol_frob"]["value"]
     c2_fail_high = c2_high = s3_fail_high = s3_high = 0
+    is_fail_high = is_high = 0
     for kappa, rep in _fig1_cases():
-        A = synth.test_matrix(m, n, kappa, rep=rep, salt=1)
+        A = synth.test_matrix(m, n, kappa, rep=rep, salt=1, paper_scale=True)
         # CholQR2: two unshifted passes
         Q2, _, st2, _ = orc.cholqr(A, shift_policy=orc.SHIFT_NONE, max_iter=2, min_iter=2, tol=tol)
         if kappa <= 1e6:
@@ -270,6 +273,21 @@ def test_fig1_robustness_claims(orc):
         if kappa >= 1e16:
             s3_high += 1
             s3_fail_high += st3 == orc.ERR_BREAKDOWN or orc.loo(Q3) >= red
+        # isCholQR: the shift of the first breakdown, sized from ||A||^2,
+        # reapplied at every later breakdown (Sec. 2.1)
+        Qi, Ri, sti, _ = orc.cholqr(A, shift_policy=orc.SHIFT_ISCHOLQR, tol=tol,
+                                    max_iter=GOLD["max_iter"]["value"])
+        failed_i = sti != orc.OK or orc.loo(Qi) >= red
+        if kappa < GOLD["ischolqr_unreliable_from_kappa"]["value"]:
+            assert not failed_i and orc.rrr(A, Qi, Ri) < 1e-13, (kappa, rep)
+        else:
+            # unreliable, depending on the seed; at 1e20 the reused shift,
+            # 11 (mn + n(n+1)) u ||A||^2 ~ 4e28, exceeds the norm of the
+            # later Gramians (about 1) so far that every case fails
+            is_high += 1
+            is_fail_high += failed_i
+            if kappa >= 1e20:
+                assert failed_i, (kappa, rep)
         # rsCholQR (Alg. 1) and the default sCholQR3-with-recomputation
         for pol in (orc.SHIFT_ON_BREAKDOWN, orc.SHIFT_SCHOLQR3):
             Q, R, st, info = orc.cholqr(A, shift_policy=pol, tol=tol,
@@ -279,6 +297,7 @@ def test_fig1_robustness_claims(orc):
             assert orc.rrr(A, Q, R) < 1e-13
     assert c2_fail_high >= 0.9 * c2_high
     assert s3_fail_high >= 0.9 * s3_high
+    assert 3 * is_fail_high >= is_high, (is_fail_high, is_high)
 
 
 # ---------------------------------------------------------------- Alg. 2 / Proposition 2.1
