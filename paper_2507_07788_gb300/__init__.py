@@ -420,7 +420,9 @@ def _device_view(ptr: int, rows: int, cols: int, ld: int):
 class Server:
     """Continuous-batching request server over device-resident bases
     (cqr_server_*).  Submissions return tickets; wait() returns the result
-    with its timestamps on the server clock."""
+    with its timestamps on the server clock.  The server reads a request's
+    input until the request completes, so the binding holds the input tensor
+    (and its basis) until wait(), drain() or close()."""
 
     def __init__(self, slots=4, batch_max=16, hbm_budget_bytes=8 << 30, small_rows=262144):
         o = ServerOpts(slots, batch_max, hbm_budget_bytes, small_rows)
@@ -429,6 +431,7 @@ class Server:
         if st != OK:
             raise CholQRError(st, "cqr_server_create")
         self._h = h
+        self._held = {}
 
     def now(self) -> float:
         return lib().cqr_server_now(self._h)
@@ -440,6 +443,7 @@ class Server:
                                             C.byref(opts) if opts is not None else None, C.byref(t))
         if st != OK:
             raise CholQRError(st, "cqr_server_submit_factor")
+        self._held[t.value] = (A, basis)
         return t.value
 
     def submit_append(self, basis: "Basis", A_in) -> int:
@@ -449,6 +453,7 @@ class Server:
                                             C.byref(t))
         if st != OK:
             raise CholQRError(st, "cqr_server_submit_append")
+        self._held[t.value] = (A_in, basis)
         return t.value
 
     def wait(self, ticket: int) -> dict:
@@ -456,15 +461,18 @@ class Server:
         st = lib().cqr_server_wait(self._h, ticket, C.byref(r))
         if st != OK:
             raise CholQRError(st, "cqr_server_wait")
+        self._held.pop(ticket, None)
         return r.as_dict()
 
     def drain(self) -> None:
         lib().cqr_server_drain(self._h)
+        self._held.clear()
 
     def close(self) -> None:
         if getattr(self, "_h", None):
             lib().cqr_server_destroy(self._h)
             self._h = None
+        self._held = {}
 
     def __del__(self):
         try:
