@@ -158,7 +158,7 @@ cqr_status cholqr_factor(const cqr_opts *opts, int64_t m, int64_t n, const doubl
 /*
  * cholqr_gram -- the Gramian X = A^T A of Alg. 1 line 3, formed by the same
  * row sweep and fixed-order reduction as the factorisation's first pass
- * (tensor-core digit arithmetic for n <= 64 unless opts->emulation is
+ * (tensor-core digit arithmetic for n <= 128 unless opts->emulation is
  * CQR_EMU_OFF; FP64 CUDA cores otherwise).
  *   A, lda    device, m x n, lda >= m (read only).
  *   X, ldx    device, n x n output (both triangles), ldx >= n.

@@ -10,7 +10,7 @@
 //   repeat: sweep (solve+Gram), reduce, ctrl
 // The row sweeps and reductions return immediately once the control kernel
 // has marked the call done, so launching a few passes ahead is harmless.  The
-// host reads the 64-byte device state once after `kPrelaunch` passes and
+// host reads the 72-byte device state once after `kPrelaunch` passes and
 // only launches further passes (one at a time) when the tolerance has not
 // been met yet.
 #include <stdio.h>
@@ -48,7 +48,7 @@ struct SweepMark {
 };
 
 // Per host thread: an auxiliary stream and events for the chunked pass
-// pipeline (FP64 row solve of chunk c+1 on the caller's stream overlapping
+// pipeline (the row solve of chunk c+1 on the caller's stream overlapping
 // the tensor-core Gramian of chunk c on the auxiliary stream).
 struct AuxCtx {
   cudaStream_t aux = nullptr;
@@ -103,11 +103,12 @@ constexpr int kCopyGrid = 16, kCopyThreads = 1024;
 
 // Q chunk -> host after pass k's solve of that chunk, speculatively: pass k
 // is taken to be the last when its input has ||Q^T Q - I||_F < kCopyAheadOrth
-// (then cond(Q^T Q) <= (1 + 1/2) / (1 - 1/2) = 3, and one Cholesky QR pass of
-// such a Q lands on the roundoff floor).  It copies iff pass k ran (the control step sets
-// iters to the index of the pass it admits; iters never decreases) and that
-// test holds; the control step after pass k waits for these copies, so the
-// state it reads is the one before pass k.  `copied` records the pass.
+// (then cond(Q^T Q) <= (1 + 1/2) / (1 - 1/2) = 3, and one Cholesky QR pass
+// of such a Q lands on the roundoff floor).  It copies iff pass k ran (the
+// control step sets iters to the index of the pass it admits; iters never
+// decreases) and that test holds; the control step after pass k waits for
+// these copies, so the state it reads is the one before pass k.  `copied`
+// records the pass.
 constexpr double kCopyAheadOrth = 0.5;
 
 __global__ void __launch_bounds__(kCopyThreads) copy_out_kernel(const double *src, int64_t lds, int64_t rows,
