@@ -11,7 +11,17 @@ Matrices are FP64 and column-major: a CUDA tensor of shape (m, n) with
 
 Low-level functions carry the C names (``cholqr_factor``, ``basis_create``,
 ``basis_append``, ``basis_free``...) and take raw pointers; :func:`factor`
-and :class:`Basis` wrap them for tensors.
+and :class:`Basis` wrap them for tensors::
+
+    import paper_2507_07788_gb300 as cq
+    A = cq.to_colmajor(a)               # numpy (m, n) float64 -> CUDA tensor
+    res = cq.factor(A)                  # sCholQR3: res.Q, res.R, res.status
+    b = cq.Basis(m, n_max)              # growing basis (Alg. 2)
+    b.enable_digit_cache()              # optional: tensor-core narrow appends
+    st, info = b.append(cq.to_colmajor(block))
+    Q, R = b.Q(), b.R()                 # device views of the basis
+    res = cq.pn(A, r=4)                 # pnCholQR (Alg. 3)
+    res = cq.factor_host(a)             # host buffers in, host Q and R out
 """
 from __future__ import annotations
 
