@@ -191,6 +191,29 @@ def test_kappa_1e20_rscholqr(cq, orc):
     assert orc.rrr(A, Q, R) <= 1e-13
 
 
+@pytest.mark.parametrize("n", [20, 64, 128])
+@pytest.mark.parametrize("kappa", [1e8, 1e15, 1e20])
+def test_factor_on_the_papers_scale(cq, orc, n, kappa):
+    # singular values from 1 up to kappa, as Sec. 4.1 builds them: Gramians
+    # of norm up to 1e40, beyond the FP32 range of the norm estimate's power
+    # iteration (which runs on X scaled by a power of two); the digit
+    # Gramian and solve track FP64 exponents and need no scaling
+    m = 20037
+    A = synth.test_matrix(m, n, kappa, rep=5, paper_scale=True)
+    Q, R, st, info = run_gpu(cq, A)
+    assert st == cq.OK, info
+    assert orc.loo(Q) < 3.16e-13 and orc.loo_frob(Q) <= 1e-13
+    assert orc.rrr(A, Q, R) <= 1e-13
+    assert np.all(np.tril(R, -1) == 0) and np.all(np.diag(R) > 0)
+    X = orc.gram(A)
+    assert info["sigma_first"] == pytest.approx(orc.shift(m, n, orc.sym_norm2(X)), rel=1e-2)
+    if kappa <= 1e15:
+        Qo, Ro, sto, info_o = orc.cholqr(A)
+        assert sto == cq.OK and abs(info["iters"] - info_o.iters) <= 1
+        assert np.max(np.abs(R - Ro)) <= r_tol(kappa, n, Ro)
+        assert np.max(np.abs(Q - Qo)) <= q_tol(kappa, m, n)
+
+
 def test_deterministic(cq):
     A = synth.test_matrix(50000, 32, 1e10, rep=8)
     Q1, R1, _, _ = run_gpu(cq, A)
