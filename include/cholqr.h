@@ -355,7 +355,9 @@ cqr_status cqr_server_create(const cqr_server_opts *opts, cqr_server **out);
 cqr_status cqr_server_submit_factor(cqr_server *s, cqr_basis *b, int64_t n, const double *A,
                                     int64_t lda, const cqr_opts *opts, uint64_t *ticket);
 /* Append request (M2): basis_append(b, p, A_in) when admitted.  A_in stays
- * caller-owned and unchanged until completion. */
+ * caller-owned and unchanged until completion; it must not overlap the
+ * basis storage (else CQR_ERR_INVALID at submission).  An append past the
+ * basis capacity completes with CQR_ERR_CAPACITY. */
 cqr_status cqr_server_submit_append(cqr_server *s, cqr_basis *b, int64_t p, const double *A_in,
                                     int64_t lda, uint64_t *ticket);
 /* Blocks until the request completes and copies its result (out may be NULL). */

@@ -125,9 +125,11 @@ bool is_small_append(const cqr_server *s, const Request &r) {
   if (r.kind != 1) return false;
   const int64_t q = r.b->q, p = r.w;
   const int64_t E = q * p + p * (p + 1) / 2;
-  // a basis with a digit cache takes basis_append, which keeps the cache
+  // a basis with a digit cache takes basis_append, which keeps the cache;
+  // so does an append past the capacity, which basis_append rejects (the
+  // batched launch writes the new columns without that check)
   return p <= kSmallMaxP && E <= (int64_t)kThreads * kBatchEPT && r.b->m <= s->o.small_rows &&
-         s->ws.cap > 0 && r.b->Qd == nullptr;
+         s->ws.cap > 0 && r.b->Qd == nullptr && q + p <= r.b->n_max;
 }
 
 void finish_locked(cqr_server *s, Request *r) {
@@ -585,6 +587,12 @@ cqr_status cqr_server_submit_append(cqr_server *s, cqr_basis *b, int64_t p, cons
                                     int64_t lda, uint64_t *ticket) {
   if (s == nullptr || b == nullptr || A_in == nullptr) return CQR_ERR_INVALID;
   if (p < 1 || p > CQR_MAX_N || lda < b->m) return CQR_ERR_INVALID;
+  {
+    // as basis_append: the block must not overlap the basis storage
+    const char *a0 = (const char *)A_in, *a1 = (const char *)(A_in + lda * (p - 1) + b->m);
+    const char *q0 = (const char *)b->Q, *q1 = (const char *)(b->Q + b->ldq * b->n_max);
+    if (a0 < q1 && q0 < a1) return CQR_ERR_INVALID;
+  }
   Request *r = new (std::nothrow) Request();
   if (r == nullptr) return CQR_ERR_OOM;
   r->kind = 1;
