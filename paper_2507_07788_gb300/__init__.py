@@ -309,11 +309,13 @@ def pn(A, r: int, Q=None, R=None, opts: Opts | None = None, stream=None, check=T
 
 def gram(A, opts: Opts | None = None, stream=None):
     """X = A^T A of a column-major CUDA tensor through cholqr_gram."""
+    torch = _torch()
     lda = _check_colmajor(A, "A")
     m, n = A.shape
     X = colmajor(n, n, device=A.device)
-    st = lib().cholqr_gram(C.byref(opts) if opts is not None else None, m, n, A.data_ptr(), lda,
-                           X.data_ptr(), n, _stream_ptr(stream))
+    with torch.cuda.device(A.device):
+        st = lib().cholqr_gram(C.byref(opts) if opts is not None else None, m, n, A.data_ptr(), lda,
+                               X.data_ptr(), n, _stream_ptr(stream))
     if st != OK:
         raise CholQRError(st, "cholqr_gram")
     return X
