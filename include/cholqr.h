@@ -61,7 +61,10 @@ typedef enum cqr_status {
  *                           that Fig. 1 compares against).
  *   CQR_SHIFT_ISCHOLQR      no first shift; the shift is computed once, from
  *                           the Gramian of the first breakdown, and reused at
- *                           every later breakdown (isCholQR, Fig. 1).
+ *                           every later breakdown (isCholQR, Fig. 1).  Sized
+ *                           from ||A||^2, that shift is too large for later
+ *                           Gramians when ||A|| >> 1 (Sec. 2.1): from
+ *                           kappa ~ 1e16 the policy fails for such A.
  * The last two are comparison policies for Fig. 1; the factorisation's
  * other rules (stop test, x10 escalation of a failing shift) are shared. */
 enum {
