@@ -227,7 +227,7 @@ def test_deterministic(cq):
     (200003, 16, 1.0, "pinned"),     # converges before the pre-launched passes end
     (200003, 48, 1e4, "pageable"),   # Q not device-addressable: one copy at the end
     (170001, 40, 1e10, "strided"),   # ldq > m, lda > m
-    (200003, 100, 1e12, "pinned"),   # n > 64: FP64 substitution, half-height chunks
+    (200003, 100, 1e12, "pinned"),   # n > 64: the 128-wide digit solve, half-height chunks
 ])
 def test_host_entry_point(cq, orc, m, n, kappa, q_kind):
     # cholqr_factor_host copies A in, factors it exactly as cholqr_factor

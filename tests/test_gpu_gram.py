@@ -1,6 +1,7 @@
 """The Gramian X = A^T A (Alg. 1 line 3) as the library forms it
-(cholqr_gram): tensor-core digit arithmetic (Ozaki splitting) for n <= 64 and
-FP64 CUDA cores otherwise, against the oracle's FP64 triple loop.
+(cholqr_gram): tensor-core digit arithmetic (Ozaki splitting) for n <= 128
+(emulation AUTO) and FP64 CUDA cores with emulation OFF, against the oracle's
+FP64 triple loop.
 
 Tolerance: both sides are within the FP64 dot-product bound, so
 |X_gpu - X_oracle|_ij <= 2 * gamma_m * (|A|^T |A|)_ij with gamma_m = m u / (1 - m u).
