@@ -50,7 +50,7 @@ FALLBACK_BF16_TFLOPS = 1700.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--m", type=int, default=1_000_000)
@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=600_000)
+    ap.add_argument("--cpu-rows-all-cores", type=int, default=200_000)
     ap.add_argument("--no-update", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--update-m", type=int, default=2_000_000)
@@ -92,7 +93,7 @@ class Clocks:
     """nvidia-smi sampling during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,timestamp")
 
     def __init__(self, index: int):
         self.index = index
@@ -103,12 +104,32 @@ class Clocks:
         try:
             self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                          "-i", str(self.index), "-lms", "200"], stdout=self.f,
+                                          "-i", str(self.index), "-lms", "100"], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
-    def stop(self):
+    def has_sample(self) -> bool:
+        try:
+            return self.f is not None and os.path.getsize(self.f.name) > 0
+        except OSError:
+            return False
+
+    @staticmethod
+    def _stamp(parts):
+        # nvidia-smi's timestamp (local time) as seconds since the epoch
+        if len(parts) < 10:
+            return None
+        import datetime
+        try:
+            return datetime.datetime.strptime(parts[9], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
+
+    def stop(self, window=None):
+        """Median SM clock, max clock and throttle reasons of the samples
+        taken inside `window` = (t0, t1) in time.time() seconds (all samples
+        when none carries a timestamp inside it)."""
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -126,12 +147,22 @@ class Clocks:
         os.unlink(self.f.name)
         if not rows:
             return None
+        in_window = None
+        if window is not None:
+            t0, t1 = window
+            inside = [r for r in rows if (ts := self._stamp(r)) is not None and t0 - 0.05 <= ts <= t1 + 0.05]
+            in_window = len(inside)
+            if inside:
+                rows = inside
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+        out = {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+               "reasons": reasons, "samples": len(rows)}
+        if in_window is not None:
+            out["samples_in_timed_region"] = in_window
+        return out
 
 
 KERNEL_FILES = {"rowsweep": ("rowsweep.cu",), "trsm_rows": ("trsm.cu",),
@@ -168,17 +199,61 @@ def traffic_per_launch(rows: int, name: str):
         return None, d
 
 
-def cpu_baseline(A, rows, n):
+def _oracle_factor_seconds(S):
+    """One oracle sCholQR3 of S in this (spawned) process: seconds."""
     import oracle
     oracle.build()
+    t0 = time.perf_counter()
+    oracle.cholqr(S)
+    return time.perf_counter() - t0
+
+
+def _oracle_ready(_):
+    import oracle
+    oracle.build()
+    return os.getpid()
+
+
+def cpu_baseline(A, rows, n, all_core_rows=None):
+    """The oracle as it stands on the host cores, on bounded samples of the
+    benchmark matrix: one factorisation of the first `rows` rows on one core,
+    and, on every core at once, one process per core each factoring the
+    first `all_core_rows` rows (the unmodified single-threaded oracle, so the
+    all-core figure is the host's aggregate throughput of independent
+    factorisations).  Processes are spawned, never forked from a process
+    that has used the GPU."""
+    import multiprocessing as mp
+
+    import oracle
+    oracle.build()
+    host_cores = os.cpu_count() or 1
     S = A[:rows]
     t0 = time.perf_counter()
     Q, R, st, info = oracle.cholqr(S)
     dt = time.perf_counter() - t0
-    return {"value": rows * n / dt, "unit": "rows*cols/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {rows} of {A.shape[0]} rows of the benchmark matrix, one factorisation "
-                      f"({dt:.1f} s, {info.iters} passes, single-threaded plain C)",
-            "seconds": dt}
+    out = {"value": rows * n / dt, "unit": "rows*cols/s", "cores": 1, "kind": "oracle",
+           "host_cores": host_cores,
+           "sample": f"first {rows} of {A.shape[0]} rows of the benchmark matrix, one factorisation "
+                     f"({dt:.1f} s, {info.iters} passes, single-threaded plain C)",
+           "seconds": dt}
+    rp = all_core_rows or max(n, rows // 4)
+    try:
+        Sp = A[:rp].copy(order="F")
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(host_cores) as pool:
+            pool.map(_oracle_ready, range(host_cores))
+            t0 = time.perf_counter()
+            secs = pool.map(_oracle_factor_seconds, [Sp] * host_cores)
+            wall = time.perf_counter() - t0
+        out["all_cores"] = {"value": host_cores * rp * n / wall, "unit": "rows*cols/s", "cores": host_cores,
+                            "kind": "oracle",
+                            "sample": f"{host_cores} processes, each one factorisation of the first {rp} rows "
+                                      f"(single-threaded plain C oracle, unmodified); wall {wall:.1f} s, "
+                                      f"per process {min(secs):.1f}-{max(secs):.1f} s",
+                            "seconds": wall}
+    except Exception as exc:  # the single-core figure stands alone
+        out["all_cores"] = {"unavailable": f"{type(exc).__name__}: {exc}"}
+    return out
 
 
 def replica_throughput(ms_local: float, ws: int, m: int, n: int, device: str):
@@ -219,6 +294,7 @@ def run_reference(args):
                                    f"bounded CPU sample m={rows} of m={args.m}",
                        "m": args.m, "n": args.n, "kappa": args.kappa, "sample_rows": rows},
             "cpu_baseline": {"value": val, "unit": "rows*cols/s", "cores": 1, "kind": "oracle",
+                             "host_cores": os.cpu_count(),
                              "sample": f"{rows} x {args.n} matrix per step"},
             "e2e": {"value": val, "unit": "rows*cols/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -243,13 +319,16 @@ def time_factor(cq, torch, dA, dQ, dR, opts, steps, warmup):
 def roofline_from(tm, m, n, hbm_peak, hbm_src, tc_peak, tc_src):
     """Roofline of the dominant kernel from the library's per-launch events.
 
-    The pass pipeline runs a solve kernel and the tensor-core digit Gramian
-    per row chunk.  For 17 <= n <= 128 both are tensor-core digit products
-    (reported against the bf16 tensor peak, with their FP64-equivalent rates
-    beside it); the one with the larger total time in the timed region is
-    the dominant kernel and the other is nested under its own key.  Below
-    n = 17 the solve is the FP64 row substitution (reported against the FP64
-    peak)."""
+    The roofline of this path is HBM bytes: the top level reports the
+    dominant kernel's algorithmic bytes per launch (8 per entry read, 8 per
+    entry written) over its mean launch time against the measured HBM copy
+    peak.  What the kernel spends besides bytes is nested: for the
+    tensor-core digit kernels (17 <= n <= 128) their bf16 digit FLOP against
+    the sustained bf16 tensor peak and their FP64-equivalent rate, for the
+    FP64 CUDA-core kernels their FLOP against the FP64 peak.  The pass
+    pipeline runs a solve kernel and the digit Gramian per row chunk; the
+    one with the larger total time in the timed region is the dominant
+    kernel and the other is nested under its own key."""
     def per(k):
         nl = max(tm[f"{k}_launches"], 1)
         ms = tm[f"{k}_ms"] / nl
@@ -258,6 +337,20 @@ def roofline_from(tm, m, n, hbm_peak, hbm_src, tc_peak, tc_src):
         return ms, fl, by, (fl / (ms * 1e-3) if ms > 0 else 0.0), (by / (ms * 1e-3) / 1e9 if ms > 0 else 0.0)
 
     fp64_src = "derived: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz (FP64 CUDA cores)"
+
+    def record(kernel, ms, fl, by, af, ag, traffic, total_ms, extra):
+        r = {"bound": "hbm", "achieved": ag, "peak": hbm_peak, "unit": "GB/s",
+             "frac": ag / hbm_peak if hbm_peak else 0.0, "traffic": traffic, "kernel": kernel,
+             "peak_source": f"{hbm_src} (HBM copy, MEASURED_PEAKS.json hbm_gbs)",
+             "per_launch": {"ms": ms, "algorithmic_bytes": by, "algorithmic_fp64_flops": fl},
+             "total_ms": total_ms}
+        r.update(extra)
+        return r
+
+    def fp64_alu(af):
+        return {"achieved": af / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
+                "frac": af / FP64_PEAK_FLOPS, "peak_source": fp64_src}
+
     gram = None
     if tm["gram_launches"] > 0:
         gms, gfl, gby, gaf, gag = per("gram")
@@ -267,33 +360,23 @@ def roofline_from(tm, m, n, hbm_peak, hbm_src, tc_peak, tc_src):
         nt = 16 if n <= 16 else (32 if n <= 32 else (64 if n <= 64 else 128))
         gtcf = grows * 2.0 * OZGRAM_PAIRS * nt * nt
         gtca = gtcf / (gms * 1e-3) if gms > 0 else 0.0
-        gram = {"bound": "tensor", "achieved": gtca / 1e12, "peak": tc_peak, "unit": "TFLOP/s",
-                "frac": gtca / 1e12 / tc_peak, "traffic": gtraffic,
-                "kernel": "ozgram_kernel (exact FP64 Gramian from bf16 digits on the tensor cores, "
-                          "one launch per row chunk)",
-                "per_launch": {"ms": gms, "bf16_digit_flops": gtcf, "algorithmic_fp64_flops": gfl,
-                               "algorithmic_bytes": gby},
-                "total_ms": tm["gram_ms"], "peak_source": tc_src,
-                "fp64_equiv": {"achieved_tflops": gaf / 1e12, "fp64_peak_tflops": FP64_PEAK_FLOPS / 1e12,
-                               "ratio": gaf / FP64_PEAK_FLOPS, "peak_source": fp64_src},
-                "hbm": {"achieved_gbs": gag, "peak_gbs": hbm_peak, "frac": gag / hbm_peak,
-                        "peak_source": hbm_src}}
+        gram = record("ozgram_kernel (exact FP64 Gramian from bf16 digits on the tensor cores, "
+                      "one launch per row chunk)", gms, gfl, gby, gaf, gag, gtraffic, tm["gram_ms"],
+                      {"tensor": {"achieved": gtca / 1e12, "peak": tc_peak, "unit": "TFLOP/s",
+                                  "frac": gtca / 1e12 / tc_peak, "bf16_digit_flops_per_launch": gtcf,
+                                  "peak_source": tc_src},
+                       "fp64_equiv": fp64_alu(gaf)})
     if tm["tsolve_launches"] > 0:
         ms, fl, by, af, ag = per("tsolve")
         tcf = tm["tsolve_tc_flops"] / max(tm["tsolve_launches"], 1)
         tca = tcf / (ms * 1e-3) if ms > 0 else 0.0
         traffic, _ = traffic_per_launch(int(round(by / (16.0 * n))), "ozgemm")
-        solve = {"bound": "tensor", "achieved": tca / 1e12, "peak": tc_peak, "unit": "TFLOP/s",
-                 "frac": tca / 1e12 / tc_peak, "traffic": traffic,
-                 "kernel": "ozgemm_kernel (Q = Y R~^-1 as an exact bf16 digit product on the tensor cores, "
-                           "one launch per row chunk)",
-                 "per_launch": {"ms": ms, "bf16_digit_flops": tcf, "algorithmic_fp64_flops": fl,
-                                "algorithmic_bytes": by},
-                 "total_ms": tm["tsolve_ms"], "peak_source": tc_src,
-                 "fp64_equiv": {"achieved_tflops": af / 1e12, "fp64_peak_tflops": FP64_PEAK_FLOPS / 1e12,
-                                "ratio": af / FP64_PEAK_FLOPS, "peak_source": fp64_src},
-                 "hbm": {"achieved_gbs": ag, "peak_gbs": hbm_peak, "frac": ag / hbm_peak,
-                         "peak_source": hbm_src}}
+        solve = record("ozgemm_kernel (Q = Y R~^-1 as an exact bf16 digit product on the tensor cores, "
+                       "one launch per row chunk)", ms, fl, by, af, ag, traffic, tm["tsolve_ms"],
+                       {"tensor": {"achieved": tca / 1e12, "peak": tc_peak, "unit": "TFLOP/s",
+                                   "frac": tca / 1e12 / tc_peak, "bf16_digit_flops_per_launch": tcf,
+                                   "peak_source": tc_src},
+                        "fp64_equiv": fp64_alu(af)})
         if gram and gram["total_ms"] > solve["total_ms"]:
             roof = dict(gram)
             roof["solve"] = solve
@@ -306,23 +389,27 @@ def roofline_from(tm, m, n, hbm_peak, hbm_src, tc_peak, tc_src):
     if tm["solve_launches"] > 0:
         ms, fl, by, af, ag = per("solve")
         traffic, _ = traffic_per_launch(int(round(by / (16.0 * n))), "trsm_rows")  # 16 B per row entry
-        roof = {"bound": "alu", "achieved": af / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
-                "frac": af / FP64_PEAK_FLOPS, "traffic": traffic,
-                "kernel": "trsm_rows_kernel (FP64 row solve of the pass pipeline, one launch per row chunk)",
-                "per_launch": {"ms": ms, "algorithmic_flops": fl, "algorithmic_bytes": by},
-                "hbm": {"achieved_gbs": ag, "peak_gbs": hbm_peak, "frac": ag / hbm_peak, "peak_source": hbm_src},
-                "peak_source": fp64_src}
+        roof = record("trsm_rows_kernel (FP64 row solve of the pass pipeline, one launch per row chunk)",
+                      ms, fl, by, af, ag, traffic, tm["solve_ms"], {"alu": fp64_alu(af)})
         if gram:
             roof["gram"] = gram
         return roof
     ms, fl, by, af, ag = per("fused")
     traffic, _ = traffic_per_launch(int(round(m)), "rowsweep")
-    return {"bound": "alu", "achieved": af / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
-            "frac": af / FP64_PEAK_FLOPS, "traffic": traffic,
-            "kernel": "rowsweep_kernel (fused triangular solve + Gramian sweep, FP64 CUDA cores)",
-            "per_launch": {"ms": ms, "algorithmic_flops": fl, "algorithmic_bytes": by},
-            "hbm": {"achieved_gbs": ag, "peak_gbs": hbm_peak, "frac": ag / hbm_peak, "peak_source": hbm_src},
-            "peak_source": fp64_src}
+    return record("rowsweep_kernel (fused triangular solve + Gramian sweep, FP64 CUDA cores)",
+                  ms, fl, by, af, ag, traffic, tm["fused_ms"], {"alu": fp64_alu(af)})
+
+
+def factorisation_hbm(m, n, passes, ms, hbm_peak):
+    """The whole factorisation against the HBM roofline: the first Gramian
+    reads the block once (8 m n bytes) and every pass reads it once and
+    writes it once (16 m n bytes; its Gramian comes with the solve), so
+    3 passes move 56 m n bytes."""
+    by = 8.0 * m * n + 16.0 * m * n * passes
+    gbs = by / (ms * 1e-3) / 1e9
+    return {"bytes": by, "passes": passes, "achieved_gbs": gbs, "peak_gbs": hbm_peak,
+            "frac": gbs / hbm_peak if hbm_peak else 0.0,
+            "formula": "(8 m n + 16 m n x passes) / ms_per_step"}
 
 
 def leg_update(cq, torch, m, p=8, count=32, seed=0, cache=True):
@@ -488,21 +575,28 @@ def run_ours(args):
     cq.cqr_timing_reset()
     cq.cqr_timing_enable(True)
     clocks = Clocks(local)
+    clocks.start()
+    # keep the GPU busy (untimed) until the sampler has written its first
+    # line, so that samples cover the timed region
+    t_wait = time.time()
+    while not clocks.has_sample() and time.time() - t_wait < 5.0:
+        cq.factor(dA, Q=dQ, R=dR, opts=opts)
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    clocks.start()
     s = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_start = time.time()
     e0.record(s)
     res = None
     for _ in range(args.steps):
         res = cq.factor(dA, Q=dQ, R=dR, opts=opts)
     e1.record(s)
     torch.cuda.synchronize()
+    t_end = time.time()
     if ws > 1:
         torch.distributed.barrier()
-    clk = clocks.stop()
+    clk = clocks.stop(window=(t_start, t_end))
     cq.cqr_timing_enable(False)
     tm = cq.cqr_timing_read()
     ms, value = replica_throughput(e0.elapsed_time(e1) / args.steps, ws, m, n, "cuda")
@@ -514,6 +608,7 @@ def run_ours(args):
     hbm_peak, hbm_src, tc_peak, tc_src = peaks()
     roof = roofline_from(tm, m, n, hbm_peak, hbm_src, tc_peak, tc_src)
 
+    hbm = factorisation_hbm(m, n, res.info["iters"], ms, hbm_peak)
     line = {"metric": METRIC, "value": value, "unit": "rows*cols/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -521,7 +616,8 @@ def run_ours(args):
                        "m": m, "n": n, "kappa": kappa, "precision": args.precision,
                        "l2": f"inputs larger than L2 ({8 * m * n / 2**20:.0f} MiB per matrix)",
                        "parallelism": "replicas" if ws > 1 else "single"},
-            "roofline": roof, "gpu_launches": int(tm["kernel_launches"]),
+            "roofline": roof, "hbm_frac": hbm["frac"], "factorisation_hbm": hbm,
+            "gpu_launches": int(tm["kernel_launches"]),
             "quality": {"status": res.status, "iters": res.info["iters"], "loo_frob": loo_f,
                         "orth_frob_last_gram": res.info["orth_frob"], "shifts": res.info["shifts"]},
             "clocks": clk}
@@ -570,7 +666,7 @@ def run_ours(args):
         line["serve"] = leg_serve(cq, torch, args.serve_requests)
 
     if rank == 0 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(A, min(args.cpu_rows, m), n)
+        line["cpu_baseline"] = cpu_baseline(A, min(args.cpu_rows, m), n, min(args.cpu_rows_all_cores, m))
 
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -204,15 +204,21 @@ cqr_status cholqr_factor_host(const cqr_opts *opts, int64_t m, int64_t n, const 
  * all of its device scratch lives in one fixed 8 MiB array compiled into the
  * library, which every GPU that loads the library holds until the process
  * exits, and the status is read back into host stack memory.
- *   Arguments, layout and results are those of cholqr_factor (same kernels,
- *   same launch geometry).  Limit: n <= 64; larger n returns
- *   CQR_ERR_CAPACITY without touching the device.
- *   The first call on a device looks up the array's device address (with
- *   that device current); make that first call before any stream capture.
- *   All calls share the array and it keeps the last call's contents; each
- *   call clears what must start at zero.  Calls whose work overlaps on the
- *   GPU (for example on two streams at once) race on the array and must be
- *   serialised by the caller.
+ *   Arguments, layout and results are those of cholqr_factor, but it always
+ *   runs the FP64 CUDA-core path: the fused row sweep (triangular solve +
+ *   Gramian), its reduction and the control kernel, exactly as cholqr_factor
+ *   does with opts->emulation = CQR_EMU_OFF (same kernels, same launch
+ *   geometry, so Q and R are bitwise equal to that call's).  It is therefore
+ *   slower than cholqr_factor's default tensor-core path for n >= 17.
+ *   opts->emulation is ignored; opts->precision = CQR_PREC_MIXED returns
+ *   CQR_ERR_INVALID.  Limit: n <= 64; larger n returns CQR_ERR_CAPACITY
+ *   without touching the device.
+ *   A, Q and R must be memory of the current device (else CQR_ERR_INVALID).
+ *   Each call looks up the array's device address with the current device
+ *   current.  All calls share the array and it keeps the last call's
+ *   contents; each call clears what must start at zero.  Calls whose work
+ *   overlaps on the GPU (for example on two streams at once) race on the
+ *   array and must be serialised by the caller.
  */
 cqr_status cholqr_factor_noalloc(const cqr_opts *opts, int64_t m, int64_t n, const double *A,
                                  int64_t lda, double *Q, int64_t ldq, double *R, int64_t ldr,

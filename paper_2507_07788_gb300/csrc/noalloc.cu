@@ -10,11 +10,25 @@
 // call.  This entry point calls no cudaMalloc, cudaMallocAsync, cudaFree,
 // cudaMallocHost or any other allocating routine.
 //
+// What it runs: the FP64 CUDA-core path of cholqr_factor (the path that
+// cholqr_factor takes with opts->emulation = CQR_EMU_OFF): the fused row
+// sweep (triangular solve + Gramian), its fixed-order reduction and the
+// control kernel, with the same launch geometry, so its Q and R are bitwise
+// those of cholqr_factor with CQR_EMU_OFF.  The tensor-core pipeline needs
+// per-chunk partials and an auxiliary stream that do not fit this scheme;
+// opts->emulation is therefore ignored (both values run the FP64 path) and
+// opts->precision = CQR_PREC_MIXED is rejected with CQR_ERR_INVALID.
+//
 // The scratch array below (kNoAllocScratchBytes, 8 MiB) is part of the
 // library's device image: every GPU that loads the library holds it until
 // the process exits.  It holds the device state, the reduced Gramian, R~,
 // 1/diag(R~) and the per-CTA partial sums of the row sweeps, which limits
 // this entry point to n <= 64 (larger n returns CQR_ERR_CAPACITY).
+//
+// Its device address is looked up with cudaGetSymbolAddress on every call,
+// with the current device (which must hold A, Q and R) current: the lookup
+// allocates nothing, and a cached address could go stale after the module
+// is reloaded (a device reset).
 //
 // All calls share the one array and it keeps the last call's contents.  Each
 // call starts with the init kernel, which clears the device state; the
@@ -25,7 +39,6 @@
 #include <string.h>
 
 #include <algorithm>
-#include <mutex>
 
 #include "cqr_internal.cuh"
 
@@ -35,28 +48,32 @@ namespace {
 
 constexpr size_t kNoAllocScratchBytes = 8u << 20;
 constexpr int kNoAllocMaxN = 64;
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 // In host code g_noalloc_scratch names a host-side stand-in, not device
-// memory; the device address comes from cudaGetSymbolAddress, once per
-// device, with that device current (the first call on a device does it).
-std::mutex g_setup_mu;
-void *g_scratch_addr[kMaxDevices] = {};
-
-cudaError_t scratch_address(int dev, void **out) {
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lk(g_setup_mu);
-  if (g_scratch_addr[dev] == nullptr) {
-    void *p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    if (p == nullptr) return cudaErrorInvalidSymbol;
-    g_scratch_addr[dev] = p;
-  }
-  *out = g_scratch_addr[dev];
+// memory; the device address comes from cudaGetSymbolAddress with the
+// device that runs the call current.
+cudaError_t scratch_address(void **out) {
+  void *p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return e;
+  if (p == nullptr) return cudaErrorInvalidSymbol;
+  *out = p;
   return cudaSuccess;
+}
+
+// True when ptr is device (or managed) memory that the current device `dev`
+// can use as this call's operand: memory of another device is rejected, as
+// is host memory.
+bool on_device(const void *ptr, int dev) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -79,7 +96,7 @@ extern "C" cqr_status cholqr_factor_noalloc(const cqr_opts *opts, int64_t m, int
   const bool opts_ok =
       o.tol >= 0.0 && o.max_iter >= 1 && o.max_iter <= 100 && o.min_iter >= 0 &&
       o.max_escalations >= 0 && o.max_escalations <= 400 &&
-      (o.precision == CQR_PREC_FP64 || o.precision == CQR_PREC_MIXED) &&
+      o.precision == CQR_PREC_FP64 &&
       o.shift_policy >= CQR_SHIFT_SCHOLQR3 && o.shift_policy <= CQR_SHIFT_ISCHOLQR &&
       (o.stop_rule == CQR_STOP_FROB_TOL || o.stop_rule == CQR_STOP_U_SQRT_N) &&
       (o.emulation == CQR_EMU_AUTO || o.emulation == CQR_EMU_OFF);
@@ -113,8 +130,13 @@ extern "C" cqr_status cholqr_factor_noalloc(const cqr_opts *opts, int64_t m, int
 
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return to_status(e);
+  }
+  if (!on_device(A, dev) || !on_device(Q, dev) || !on_device(R, dev)) return CQR_ERR_INVALID;
   void *base = nullptr;
-  if (e == cudaSuccess) e = scratch_address(dev, &base);
+  e = scratch_address(&base);
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
     return to_status(e);

@@ -50,3 +50,23 @@ def test_unreadable_samples_give_no_record():
     assert _clocks_from(["garbage", ""]) is None
     c = bench.Clocks(0)
     assert c.stop() is None  # never started
+
+
+def test_samples_filtered_to_the_timed_region():
+    import datetime
+    base = datetime.datetime(2026, 12, 4, 8, 40, 0)
+
+    def row(mhz, dt):
+        ts = (base + datetime.timedelta(seconds=dt)).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+        return f"0, {mhz}, 2070, 900, 0x0, Not Active, Not Active, Not Active, Not Active, {ts}"
+
+    rows = [row(1200, 0.0), row(2070, 1.0), row(2055, 1.1), row(2070, 1.2), row(1300, 3.0)]
+    c = bench.Clocks(0)
+    f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+    f.write("\n".join(rows) + "\n")
+    f.flush()
+    c.f, c.proc = f, _Done()
+    t0 = base.timestamp()
+    d = c.stop(window=(t0 + 0.95, t0 + 1.25))
+    assert d["samples"] == 3 and d["samples_in_timed_region"] == 3
+    assert d["sm_mhz"] == 2070.0

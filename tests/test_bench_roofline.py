@@ -1,7 +1,9 @@
 """The roofline arithmetic of bench.py on CPU, from synthetic per-launch
 timings: the dominant kernel is the one with the larger total time, its
-achieved rate is the algorithmic work of one launch over the mean launch
-time, and its DRAM traffic is the committed ncu capture scaled by rows."""
+achieved HBM rate is the algorithmic bytes of one launch over the mean launch
+time against the measured HBM peak (its tensor or FP64 rate nested), its DRAM
+traffic is the committed ncu capture scaled by rows, and the whole
+factorisation moves 8 m n + 16 m n bytes per pass."""
 import os
 import sys
 
@@ -45,19 +47,23 @@ def test_tensor_pipeline_dominant_kernel():
                  tsolve_launches=L, tsolve_ms=L * s_ms, tsolve_flops=L * rows * n * n,
                  tsolve_bytes=L * 16.0 * rows * n, tsolve_tc_flops=L * tc_solve_per_launch)
     r = bench.roofline_from(tm, 1_000_000, n, 6686.8, "measured", 1730.8, "measured")
-    assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["peak"] == 6686.8
     assert r["kernel"].startswith("ozgram_kernel") and "solve" in r
+    # 8 bytes per entry read, in 0.2 ms
+    gbs = 8.0 * rows * n / (g_ms * 1e-3) / 1e9
+    assert r["achieved"] == pytest.approx(gbs, rel=1e-12)
+    assert r["frac"] == pytest.approx(gbs / 6686.8, rel=1e-12)
     # 16 symmetric digit pairs, each a 64 x 64 block per row, in 0.2 ms
     want = rows * 2 * 16 * 64 * 64 / (g_ms * 1e-3) / 1e12
-    assert r["achieved"] == pytest.approx(want, rel=1e-12)
-    assert r["frac"] == pytest.approx(want / 1730.8, rel=1e-12)
-    assert r["hbm"]["achieved_gbs"] == pytest.approx(8.0 * rows * n / (g_ms * 1e-3) / 1e9, rel=1e-12)
+    assert r["tensor"]["achieved"] == pytest.approx(want, rel=1e-12)
+    assert r["tensor"]["frac"] == pytest.approx(want / 1730.8, rel=1e-12)
     b, cr = _capture("ozgram")
-    assert r["traffic"] == pytest.approx(b * rows / cr, rel=1e-12)
+    assert r["traffic"] is None or r["traffic"] == pytest.approx(b * rows / cr, rel=1e-12)
     s = r["solve"]
-    assert s["achieved"] == pytest.approx(tc_solve_per_launch / (s_ms * 1e-3) / 1e12, rel=1e-12)
+    assert s["achieved"] == pytest.approx(16.0 * rows * n / (s_ms * 1e-3) / 1e9, rel=1e-12)
+    assert s["tensor"]["achieved"] == pytest.approx(tc_solve_per_launch / (s_ms * 1e-3) / 1e12, rel=1e-12)
     b, cr = _capture("ozgemm")
-    assert s["traffic"] == pytest.approx(b * rows / cr, rel=1e-12)
+    assert s["traffic"] is None or s["traffic"] == pytest.approx(b * rows / cr, rel=1e-12)
 
 
 def test_solve_dominates_when_it_takes_longer():
@@ -68,9 +74,11 @@ def test_solve_dominates_when_it_takes_longer():
                  tsolve_bytes=L * 16.0 * rows * n, tsolve_tc_flops=L * 5.0e10)
     r = bench.roofline_from(tm, 1_000_000, n, 6686.8, "measured", 1730.8, "measured")
     assert r["kernel"].startswith("ozgemm_kernel") and "gram" in r
-    assert r["achieved"] == pytest.approx(5.0e10 / 0.3e-3 / 1e12, rel=1e-12)
+    assert r["achieved"] == pytest.approx(16.0 * rows * n / 0.3e-3 / 1e9, rel=1e-12)
+    assert r["tensor"]["achieved"] == pytest.approx(5.0e10 / 0.3e-3 / 1e12, rel=1e-12)
     # the Gramian at n = 128: 16 pairs of 128 x 128 blocks per row
-    assert r["gram"]["achieved"] == pytest.approx(rows * 2 * 16 * 128 * 128 / 0.1e-3 / 1e12, rel=1e-12)
+    assert r["gram"]["tensor"]["achieved"] == pytest.approx(rows * 2 * 16 * 128 * 128 / 0.1e-3 / 1e12,
+                                                            rel=1e-12)
 
 
 def test_narrow_blocks_report_the_fp64_solve():
@@ -80,9 +88,10 @@ def test_narrow_blocks_report_the_fp64_solve():
                  solve_launches=L, solve_ms=L * 0.04, solve_flops=L * rows * n * n,
                  solve_bytes=L * 16.0 * rows * n)
     r = bench.roofline_from(tm, 1_000_000, n, 6686.8, "measured", 1730.8, "measured")
-    assert r["bound"] == "alu" and r["kernel"].startswith("trsm_rows_kernel")
-    assert r["achieved"] == pytest.approx(rows * n * n / 0.04e-3 / 1e12, rel=1e-12)
-    assert r["frac"] == pytest.approx(r["achieved"] * 1e12 / bench.FP64_PEAK_FLOPS, rel=1e-12)
+    assert r["bound"] == "hbm" and r["kernel"].startswith("trsm_rows_kernel")
+    assert r["achieved"] == pytest.approx(16.0 * rows * n / 0.04e-3 / 1e9, rel=1e-12)
+    assert r["alu"]["achieved"] == pytest.approx(rows * n * n / 0.04e-3 / 1e12, rel=1e-12)
+    assert r["alu"]["frac"] == pytest.approx(r["alu"]["achieved"] * 1e12 / bench.FP64_PEAK_FLOPS, rel=1e-12)
     assert "gram" in r
 
 
@@ -91,5 +100,13 @@ def test_fp64_sweep_without_tensor_kernels():
     tm = _timing(fused_launches=3, fused_ms=3 * 2.0, fused_flops=3 * 4.0 * m * n * n,
                  fused_bytes=3 * 16.0 * m * n)
     r = bench.roofline_from(tm, m, n, 6686.8, "measured", 1730.8, "measured")
-    assert r["bound"] == "alu" and r["kernel"].startswith("rowsweep_kernel")
-    assert r["achieved"] == pytest.approx(4.0 * m * n * n / 2.0e-3 / 1e12, rel=1e-12)
+    assert r["bound"] == "hbm" and r["kernel"].startswith("rowsweep_kernel")
+    assert r["achieved"] == pytest.approx(16.0 * m * n / 2.0e-3 / 1e9, rel=1e-12)
+    assert r["alu"]["achieved"] == pytest.approx(4.0 * m * n * n / 2.0e-3 / 1e12, rel=1e-12)
+
+
+def test_whole_factorisation_bytes():
+    # 3 passes at m = 1e6, n = 64: 56 m n bytes
+    h = bench.factorisation_hbm(1_000_000, 64, 3, 6.5, 6686.8)
+    assert h["bytes"] == 56.0 * 1_000_000 * 64
+    assert h["frac"] == pytest.approx(56.0 * 64e6 / 6.5e-3 / 1e9 / 6686.8, rel=1e-12)

@@ -7,16 +7,14 @@ preconditions, the FP64 passes decide the result.  The first shift must be
 the one sized for FP32 roundoff, 11 (n (2 u_in + d u_acc) + n (n+1) u) ||X||
 with u_in = 2^-23, u_acc = 2^-24, d = 66.
 """
-import math
-
 import numpy as np
 import pytest
 
 from paper_2507_07788_gb300 import synth
+from parity import U, check_q, check_r
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
-U = 2.0 ** -53
 
 
 @pytest.fixture(scope="module")
@@ -28,9 +26,6 @@ def cq():
         pytest.skip("no CUDA device")
     return cq
 
-
-def q_tol(kappa, m, n):
-    return max(1e-12, 20.0 * kappa * U * math.sqrt(n) / math.sqrt(m))
 
 
 def mixed_coeff(n):
@@ -52,8 +47,8 @@ def test_mixed_parity(cq, orc, n, kappa):
     assert res.status == cq.OK, res.info
     assert orc.loo_frob(Q) <= 1e-13
     assert orc.rrr(A, Q, R) <= 1e-13
-    assert np.max(np.abs(Q - Qo)) <= q_tol(kappa, m, n)
-    assert np.max(np.abs(R - Ro)) <= 20 * kappa * U * math.sqrt(n) * np.max(np.abs(Ro))
+    check_q(np.max(np.abs(Q - Qo)), kappa, m, f"mixed n={n} kappa={kappa:g}")
+    check_r(np.max(np.abs(R - Ro)), kappa, Ro, f"mixed n={n} kappa={kappa:g}")
     # first shift sized for FP32 roundoff, from ||X|| (estimate within 1e-2)
     lam = orc.sym_norm2(orc.gram(A))
     assert res.info["sigma_first"] == pytest.approx(mixed_coeff(n) * lam, rel=2e-2)

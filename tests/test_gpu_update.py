@@ -4,17 +4,19 @@ with the CPU oracle's Alg. 2, append by append, on near-dependent blocks
 
 Element-wise bounds scale with kappa of the concatenated blocks so far: a
 near-dependent block early in the run makes every later factor as sensitive
-as that block (QR perturbation theory), whatever the later block looks like."""
-import math
-
+as that block (QR perturbation theory), whatever the later block looks like.
+The bounds are those of the factorisation (tests/parity.py): entries of the
+new columns of Q within max(1e-12, 4 kappa u / sqrt(m)), of the new columns
+of R within 4 kappa u max(|R|, |B|), and ||[Q_in Q]^T [Q_in Q] - I||_F
+<= 1e-13 after every append (the Gramian summed over row blocks)."""
 import numpy as np
 import pytest
 
 from paper_2507_07788_gb300 import synth
+from parity import U, check_orth, check_q, check_r
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
-U = 2.0 ** -53
 
 
 @pytest.fixture(scope="module")
@@ -44,7 +46,7 @@ def test_basis_growth_matches_oracle(cq, orc):
         Rg = b.R().cpu().numpy()
         assert Qg.shape == (m, q + p)
         # orthogonality after every append
-        assert orc.loo_frob(Qg) <= 1e-12, k
+        check_orth(Qg, f"growth append {k}")
         # reconstruction of all blocks so far
         Afull = np.hstack(blocks[: k + 1])
         assert orc.rrr(Afull, Qg, Rg) <= 1e-13, k
@@ -58,8 +60,8 @@ def test_basis_growth_matches_oracle(cq, orc):
         dQ = np.max(np.abs(Qg[:, q:] - Qn))
         print(f"append {k}: eta={etas[k]:.1e} iters={info['iters']}/{info_o.iters} "
               f"shifts={info['shifts']}/{info_o.shifts} dR={dR:.2e} dQ={dQ:.2e}")
-        assert dR <= 200 * kap * U * math.sqrt(q + p) * scale + 1e-15
-        assert dQ <= max(1e-12, 200 * kap * U * math.sqrt(p) / math.sqrt(m))
+        check_r(dR, kap, np.array([scale]), f"growth append {k}")
+        check_q(dQ, kap, m, f"growth append {k}")
     b.close()
 
 
@@ -99,7 +101,7 @@ def test_dependent_column_lucky_breakdown(cq, orc):
     st, info = b.append(cq.to_colmajor(A))
     assert st >= 0 and info["shifts"] >= 1
     Qg = b.Q().cpu().numpy()
-    assert orc.loo_frob(Qg) <= 1e-12
+    check_orth(Qg, "lucky breakdown")
 
 
 def test_breakdown_leaves_basis_unchanged(cq):
@@ -126,7 +128,7 @@ def test_wide_basis_split_sweep(cq, orc):
         assert st >= 0
     Qg = b.Q().cpu().numpy()
     assert Qg.shape[1] == 288
-    assert orc.loo_frob(Qg) <= 1e-12
+    check_orth(Qg, "wide basis split sweep")
     b.close()
 
 
@@ -138,7 +140,7 @@ def _check_append(orc, Qo, Ro, blk, Qg, Rg, m, info, k):
     Qo2 = np.hstack([Qo, Qn])
     Ro2 = np.block([[Ro, Bn], [np.zeros((p, q)), Rn]])
     assert Qg.shape == (m, q + p)
-    assert orc.loo_frob(Qg) <= 1e-12, k
+    check_orth(Qg, f"append {k} p={p} (m={m})")
     scale = max(np.max(np.abs(Rn)), np.max(np.abs(Bn)) if q else 0.0)
     dR = np.max(np.abs(Rg[: q + p, q:] - Ro2[: q + p, q:]))
     dQ = np.max(np.abs(Qg[:, q:] - Qn))
@@ -174,8 +176,8 @@ def test_tall_basis_tensor_cross_gramian(cq, orc, widths):
         kap = sv[0] / sv[-1]
         q = Qg.shape[1] - p
         print(f"append {k} p={p}: iters={info['iters']}/{info_o.iters} dR={dR:.2e} dQ={dQ:.2e} kappa={kap:.1e}")
-        assert dR <= 200 * kap * U * math.sqrt(q + p) * scale + 1e-15
-        assert dQ <= max(1e-12, 200 * kap * U * math.sqrt(p) / math.sqrt(m))
+        check_r(dR, kap, np.array([scale]), f"append {k} p={p} q={q} (m={m})")
+        check_q(dQ, kap, m, f"append {k} p={p} q={q} (m={m})")
     b.close()
 
 
@@ -219,8 +221,8 @@ def test_tall_basis_digit_cache(cq, orc, widths):
         kap = sv[0] / sv[-1]
         q = Qg.shape[1] - p
         print(f"append {k} p={p}: iters={info['iters']}/{info_o.iters} dR={dR:.2e} dQ={dQ:.2e} kappa={kap:.1e}")
-        assert dR <= 200 * kap * U * math.sqrt(q + p) * scale + 1e-15
-        assert dQ <= max(1e-12, 200 * kap * U * math.sqrt(p) / math.sqrt(m))
+        check_r(dR, kap, np.array([scale]), f"append {k} p={p} q={q} (m={m})")
+        check_q(dQ, kap, m, f"append {k} p={p} q={q} (m={m})")
     b.close()
 
 
@@ -240,7 +242,7 @@ def test_digit_cache_enabled_late_and_nan(cq, orc):
     st, info = b.append(cq.to_colmajor(nxt))
     assert st == cq.OK and b.cols == 16
     Qg = b.Q().cpu().numpy()
-    assert np.linalg.norm(Qg.T @ Qg - np.eye(16)) <= 1e-13
+    check_orth(Qg, "cache enabled late")
     b.close()
 
 
@@ -254,15 +256,23 @@ def test_digit_cache_beyond_projection_width(cq, orc):
     Qo = np.zeros((m, 0))
     Ro = np.zeros((0, 0))
     rng = np.random.default_rng(93)
+    blocks = []
     for k, p in enumerate(widths):
         if k == 0:
             blk = synth.gaussian(m, p, seed=100 + k)
         else:
             blk = Qo @ rng.standard_normal((Qo.shape[1], p)) * 0.1 + synth.gaussian(m, p, seed=100 + k) * 1e-3
+        blocks.append(blk)
         st, info = b.append(cq.to_colmajor(blk))
         Qg, Rg = b.Q().cpu().numpy(), b.R().cpu().numpy()
         Qo, Ro, dR, dQ, scale, sto, info_o = _check_append(orc, Qo, Ro, blk, Qg, Rg, m, info, k)
         assert st == sto and st >= 0, (k, st, info, info_o)
-    Qg = b.Q().cpu().numpy()
-    assert np.linalg.norm(Qg.T @ Qg - np.eye(Qg.shape[1])) <= 1e-12
+        Afull = np.hstack(blocks)
+        assert orc.rrr(Afull, Qg, Rg) <= 1e-13, k
+        sv = np.linalg.svd(Afull, compute_uv=False)
+        kap = sv[0] / sv[-1]
+        q = Qg.shape[1] - p
+        print(f"append {k} p={p}: iters={info['iters']}/{info_o.iters} dR={dR:.2e} dQ={dQ:.2e} kappa={kap:.1e}")
+        check_r(dR, kap, np.array([scale]), f"beyond projection width append {k}")
+        check_q(dQ, kap, m, f"beyond projection width append {k}")
     b.close()
