@@ -74,7 +74,7 @@ def test_factor_parity_config1(cq, orc, kappa, rep):
     dr = np.max(np.abs(R - Ro))
     print(f"kappa={kappa:.0e} rep={rep} iters={info['iters']} maxdQ={dq:.2e} maxdR={dr:.2e} "
           f"loo={orc.loo_frob(Q):.2e}")
-    check_r(dr, kappa, Ro, f"config1 kappa={kappa:g} rep={rep}")
+    check_r(dr, kappa, Ro, m, f"config1 kappa={kappa:g} rep={rep}")
     check_q(dq, kappa, m, f"config1 kappa={kappa:g} rep={rep}")
 
 
@@ -86,7 +86,7 @@ def test_factor_shapes(cq, orc, m, n):
     Qo, Ro, sto, info_o = orc.cholqr(A)
     assert st == sto and st >= 0
     assert info["iters"] == info_o.iters
-    check_r(np.max(np.abs(R - Ro)), 1e3, Ro, f"shape {m}x{n}")
+    check_r(np.max(np.abs(R - Ro)), 1e3, Ro, m, f"shape {m}x{n}")
     check_q(np.max(np.abs(Q - Qo)), 1e3, m, f"shape {m}x{n}")
 
 
@@ -200,7 +200,7 @@ def test_factor_on_the_papers_scale(cq, orc, n, kappa):
     if kappa <= 1e15:
         Qo, Ro, sto, info_o = orc.cholqr(A)
         assert sto == cq.OK and abs(info["iters"] - info_o.iters) <= 1
-        check_r(np.max(np.abs(R - Ro)), kappa, Ro, f"paper scale n={n} kappa={kappa:g}")
+        check_r(np.max(np.abs(R - Ro)), kappa, Ro, m, f"paper scale n={n} kappa={kappa:g}")
         check_q(np.max(np.abs(Q - Qo)), kappa, m, f"paper scale n={n} kappa={kappa:g}")
 
 
@@ -298,7 +298,7 @@ def test_emulated_and_native_gramian_agree(cq, orc, kappa, n):
     for name, Q, R in (("digit", Qe, Re), ("fp64", Qn, Rn)):
         assert orc.loo_frob(Q) <= 1e-13
         assert orc.rrr(A, Q, R) <= 1e-13
-        check_r(np.max(np.abs(R - Ro)), kappa, Ro, f"{name} n={n} kappa={kappa:g}")
+        check_r(np.max(np.abs(R - Ro)), kappa, Ro, m, f"{name} n={n} kappa={kappa:g}")
         check_q(np.max(np.abs(Q - Qo)), kappa, m, f"{name} n={n} kappa={kappa:g}")
 
 
@@ -317,7 +317,7 @@ def test_chunked_pipeline_parity(cq, orc, n):
     assert abs(info["iters"] - info_o.iters) <= 1
     assert orc.loo_frob(Q) <= 1e-13
     assert orc.rrr(A, Q, R) <= 1e-13
-    check_r(np.max(np.abs(R - Ro)), 1e10, Ro, f"chunked n={n}")
+    check_r(np.max(np.abs(R - Ro)), 1e10, Ro, m, f"chunked n={n}")
     check_q(np.max(np.abs(Q - Qo)), 1e10, m, f"chunked n={n}")
 
 

@@ -48,7 +48,7 @@ def test_mixed_parity(cq, orc, n, kappa):
     assert orc.loo_frob(Q) <= 1e-13
     assert orc.rrr(A, Q, R) <= 1e-13
     check_q(np.max(np.abs(Q - Qo)), kappa, m, f"mixed n={n} kappa={kappa:g}")
-    check_r(np.max(np.abs(R - Ro)), kappa, Ro, f"mixed n={n} kappa={kappa:g}")
+    check_r(np.max(np.abs(R - Ro)), kappa, Ro, m, f"mixed n={n} kappa={kappa:g}")
     # first shift sized for FP32 roundoff, from ||X|| (estimate within 1e-2)
     lam = orc.sym_norm2(orc.gram(A))
     assert res.info["sigma_first"] == pytest.approx(mixed_coeff(n) * lam, rel=2e-2)

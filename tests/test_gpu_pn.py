@@ -40,7 +40,7 @@ def test_pn_matches_oracle(cq, orc, kappa, r):
     assert orc.loo_frob(Q) <= 1e-13
     assert orc.rrr(A, Q, R) <= 1e-13
     assert np.all(np.tril(R, -1) == 0) and np.all(np.diag(R) > 0)
-    check_r(np.max(np.abs(R - Ro)), kappa, Ro, f"pn r={r} kappa={kappa:g}")
+    check_r(np.max(np.abs(R - Ro)), kappa, Ro, m, f"pn r={r} kappa={kappa:g}")
     check_q(np.max(np.abs(Q - Qo)), kappa, m, f"pn r={r} kappa={kappa:g}")
     # a panel sitting at a breakdown or stop threshold may take one pass
     # more or fewer on one side
@@ -71,7 +71,7 @@ def test_pn_and_factor_give_the_same_qr(cq, orc):
     rf = cq.factor(dA)
     torch.cuda.synchronize()
     Rp, Rf = rp.R.cpu().numpy(), rf.R.cpu().numpy()
-    check_r(np.max(np.abs(Rp - Rf)), 1e6, Rf, "pn vs factor")
+    check_r(np.max(np.abs(Rp - Rf)), 1e6, Rf, m, "pn vs factor")
     check_q(np.max(np.abs(rp.Q.cpu().numpy() - rf.Q.cpu().numpy())), 1e6, m, "pn vs factor")
 
 
@@ -114,5 +114,5 @@ def test_pn_tall_matches_oracle(cq, orc, r):
     assert res.status == sto == cq.OK, (res.status, sto)
     assert np.linalg.norm(Q.T @ Q - np.eye(n)) <= 1e-13
     assert orc.rrr(A, Q, R) <= 1e-13
-    check_r(np.max(np.abs(R - Ro)), 1e10, Ro, f"pn tall n={n}")
+    check_r(np.max(np.abs(R - Ro)), 1e10, Ro, m, f"pn tall n={n}")
     check_q(np.max(np.abs(Q - Qo)), 1e10, m, f"pn tall n={n}")

@@ -67,7 +67,7 @@ def test_same_alone_and_in_the_mix(cq, orc):
         sv = np.linalg.svd(Ro, compute_uv=False)
         kap = sv[0] / sv[-1]
         check_q(float(np.max(np.abs(Qa - Qo))), kap, Qa.shape[0], f"served basis {bi}")
-        check_r(float(np.max(np.abs(np.triu(Ra[:q, :q]) - Ro))), kap, Ro, f"served basis {bi}")
+        check_r(float(np.max(np.abs(np.triu(Ra[:q, :q]) - Ro))), kap, Ro, Qa.shape[0], f"served basis {bi}")
     for b in b1 + b2:
         b.close()
 

@@ -60,7 +60,7 @@ def test_basis_growth_matches_oracle(cq, orc):
         dQ = np.max(np.abs(Qg[:, q:] - Qn))
         print(f"append {k}: eta={etas[k]:.1e} iters={info['iters']}/{info_o.iters} "
               f"shifts={info['shifts']}/{info_o.shifts} dR={dR:.2e} dQ={dQ:.2e}")
-        check_r(dR, kap, np.array([scale]), f"growth append {k}")
+        check_r(dR, kap, np.array([scale]), m, f"growth append {k}")
         check_q(dQ, kap, m, f"growth append {k}")
     b.close()
 
@@ -176,7 +176,7 @@ def test_tall_basis_tensor_cross_gramian(cq, orc, widths):
         kap = sv[0] / sv[-1]
         q = Qg.shape[1] - p
         print(f"append {k} p={p}: iters={info['iters']}/{info_o.iters} dR={dR:.2e} dQ={dQ:.2e} kappa={kap:.1e}")
-        check_r(dR, kap, np.array([scale]), f"append {k} p={p} q={q} (m={m})")
+        check_r(dR, kap, np.array([scale]), m, f"append {k} p={p} q={q} (m={m})")
         check_q(dQ, kap, m, f"append {k} p={p} q={q} (m={m})")
     b.close()
 
@@ -221,7 +221,7 @@ def test_tall_basis_digit_cache(cq, orc, widths):
         kap = sv[0] / sv[-1]
         q = Qg.shape[1] - p
         print(f"append {k} p={p}: iters={info['iters']}/{info_o.iters} dR={dR:.2e} dQ={dQ:.2e} kappa={kap:.1e}")
-        check_r(dR, kap, np.array([scale]), f"append {k} p={p} q={q} (m={m})")
+        check_r(dR, kap, np.array([scale]), m, f"append {k} p={p} q={q} (m={m})")
         check_q(dQ, kap, m, f"append {k} p={p} q={q} (m={m})")
     b.close()
 
@@ -273,6 +273,6 @@ def test_digit_cache_beyond_projection_width(cq, orc):
         kap = sv[0] / sv[-1]
         q = Qg.shape[1] - p
         print(f"append {k} p={p}: iters={info['iters']}/{info_o.iters} dR={dR:.2e} dQ={dQ:.2e} kappa={kap:.1e}")
-        check_r(dR, kap, np.array([scale]), f"beyond projection width append {k}")
+        check_r(dR, kap, np.array([scale]), m, f"beyond projection width append {k}")
         check_q(dQ, kap, m, f"beyond projection width append {k}")
     b.close()

@@ -47,7 +47,7 @@ def test_benchmark_size_factorisation(cq, orc):
     Qo, Ro, sto, info_o = orc.cholqr(A)
     assert sto == cq.OK
     check_q(float(np.max(np.abs(Q - Qo))), kappa, m, "benchmark size 1e6x64")
-    check_r(float(np.max(np.abs(R - Ro))), kappa, Ro, "benchmark size 1e6x64")
+    check_r(float(np.max(np.abs(R - Ro))), kappa, Ro, m, "benchmark size 1e6x64")
     del Qo
 
     # the oracle's Gramian of A against the library's, every entry within

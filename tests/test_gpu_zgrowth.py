@@ -77,7 +77,7 @@ def test_growth_32_appends_of_8_digit_cache(cq, orc):
         print(f"append {k}: q={q} eta={eta:.1e} iters={info['iters']}/{info_o.iters} "
               f"shifts={info['shifts']}/{info_o.shifts} orth={orth:.1e} dQ={dQ:.1e} dR={dR:.1e} "
               f"kappa={kap:.1e}")
-        check_r(dR, kap, np.array([scale]), f"growth m={m} append {k}")
+        check_r(dR, kap, np.array([scale]), m, f"growth m={m} append {k}")
         check_q(dQ, kap, m, f"growth m={m} append {k}")
     assert b.cols == p * count
     print(f"largest ||Q^T Q - I||_F over the run: {worst:.2e}")

@@ -60,9 +60,9 @@ def test_noalloc_two_calls_in_a_row(cq, orc):
         assert np.array_equal(Qn, Qe) and np.array_equal(Rn, Re)
         assert infon == infoe
         # and within the parity bounds of the default path and of the oracle
-        check_r(np.max(np.abs(Rn - Rf)), kappa, Rf, f"noalloc vs factor {m}x{n}")
+        check_r(np.max(np.abs(Rn - Rf)), kappa, Rf, m, f"noalloc vs factor {m}x{n}")
         check_q(np.max(np.abs(Qn - Qf)), kappa, m, f"noalloc vs factor {m}x{n}")
-        check_r(np.max(np.abs(Rn - Ro)), kappa, Ro, f"noalloc vs oracle {m}x{n}")
+        check_r(np.max(np.abs(Rn - Ro)), kappa, Ro, m, f"noalloc vs oracle {m}x{n}")
         check_q(np.max(np.abs(Qn - Qo)), kappa, m, f"noalloc vs oracle {m}x{n}")
         assert orc.loo_frob(Qn) <= 1e-13 and orc.rrr(A, Qn, Rn) <= 1e-13
 
@@ -76,7 +76,7 @@ def test_noalloc_in_place(cq, orc):
     assert sti == ste == sto == cq.OK
     assert np.array_equal(Qi, Qe) and np.array_equal(Ri, Re)
     check_q(np.max(np.abs(Qi - Qo)), kappa, m, "noalloc in place")
-    check_r(np.max(np.abs(Ri - Ro)), kappa, Ro, "noalloc in place")
+    check_r(np.max(np.abs(Ri - Ro)), kappa, Ro, m, "noalloc in place")
 
 
 def test_noalloc_options_follow_the_fp64_path(cq):
