@@ -45,7 +45,8 @@ typedef enum cqr_status {
   CQR_ERR_OOM = -3,       /* device allocation failed */
   CQR_ERR_CAPACITY = -4,  /* basis_append: q + p > n_max */
   CQR_ERR_CUDA = -5,      /* a CUDA runtime call or launch failed */
-  CQR_ERR_TIMEOUT = -6    /* reserved for waits that give up */
+  CQR_ERR_TIMEOUT = -6,   /* reserved for waits that give up */
+  CQR_ERR_REDUCE = -7     /* cholqr_factor_sharded: the reducer reported a failure */
 } cqr_status;
 
 /* Shift policy of the factorisation (Alg. 1, Sec. 2.1, and Sec. 4.1 item 2):
@@ -223,6 +224,61 @@ cqr_status cholqr_factor_host(const cqr_opts *opts, int64_t m, int64_t n, const 
 cqr_status cholqr_factor_noalloc(const cqr_opts *opts, int64_t m, int64_t n, const double *A,
                                  int64_t lda, double *Q, int64_t ldq, double *R, int64_t ldr,
                                  cqr_info *info, void *stream);
+
+/*
+ * Row-sharded factorisation (communication-avoiding Cholesky QR, Sec. 1):
+ * the m rows of A are split into contiguous blocks, one per rank (one GPU or
+ * one process each).  Each rank forms the partial Gramian of its own rows;
+ * the partials are exchanged through the caller's reducer and summed in
+ * rank order 0, 1, ..., world-1 by a library kernel, so every rank holds the
+ * bitwise same Gramian and takes the same shift, breakdown and stop
+ * decisions; the triangular solves are row-local.  One exchange of n x n
+ * doubles per pass (and one for the first Gramian).
+ *
+ * cqr_reducer: caller-owned exchange buffers and callback.
+ *   world, rank   number of ranks and this rank (0 <= rank < world).
+ *   send          device, at least `capacity` doubles: the library writes its
+ *                 local block (count doubles) there before each call.
+ *   recv          device, at least world * capacity doubles: on return of
+ *                 allgather (or, for work queued on `stream`, when that work
+ *                 completes) recv[r * count .. (r + 1) * count) must hold rank
+ *                 r's block, on every rank.
+ *   capacity      doubles available in send (n * n is enough).
+ *   allgather     called by the library on every rank the same number of
+ *                 times, in the same order; its work must be ordered on
+ *                 `stream` (queued there, or complete before it returns).
+ *                 Returns 0 on success; any other value makes the call stop
+ *                 and return CQR_ERR_REDUCE.
+ *   ctx           passed through to allgather.
+ */
+typedef struct cqr_reducer {
+  int32_t world;
+  int32_t rank;
+  double *send;
+  double *recv;
+  int64_t capacity;
+  int (*allgather)(void *ctx, int64_t count, void *stream);
+  void *ctx;
+} cqr_reducer;
+
+/*
+ * cholqr_factor_sharded -- cholqr_factor (Alg. 1 with the sCholQR3 first
+ * shift, Sec. 2.1 and 4.1) on this rank's row block of a matrix with m_total
+ * rows.  The shift uses m_total (Alg. 1 line 6).  Every rank must call it
+ * with the same opts, n and m_total; the results are this rank's rows of Q
+ * and the full R (the same on every rank).
+ *   m_local   rows of this rank's block, 1 <= m_local <= m_total, m_total >= n.
+ *   A, Q      device, m_local x n blocks (lda, ldq >= m_local), as in
+ *             cholqr_factor (Q may be A).
+ *   R         device, n x n (ldr >= n).
+ *   red       reducer (see above), not NULL; capacity >= n * n.
+ * Returns the status of cholqr_factor, or CQR_ERR_REDUCE if a reducer call
+ * failed (outputs unspecified; every rank's later reducer calls are skipped,
+ * so peers must detect the failure through their own reducer).
+ */
+cqr_status cholqr_factor_sharded(const cqr_opts *opts, int64_t m_local, int64_t m_total, int64_t n,
+                                 const double *A, int64_t lda, double *Q, int64_t ldq, double *R,
+                                 int64_t ldr, const cqr_reducer *red, cqr_info *info, void *stream);
 
 /*
  * cholqr_pn -- pnCholQR, Alg. 3 (Sec. 2.3): QR of A (m x n) by r column

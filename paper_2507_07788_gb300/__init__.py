@@ -35,6 +35,7 @@ LIB_PATH = os.path.join(_HERE, "libcholqr.so")
 # status codes (cqr_status)
 OK, NOT_CONVERGED = 0, 1
 ERR_INVALID, ERR_BREAKDOWN, ERR_OOM, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT = -1, -2, -3, -4, -5, -6
+ERR_REDUCE = -7
 SHIFT_SCHOLQR3, SHIFT_ON_BREAKDOWN, SHIFT_NONE, SHIFT_SCHOLQR3_STRICT, SHIFT_ISCHOLQR = 0, 1, 2, 3, 4
 STOP_FROB_TOL, STOP_U_SQRT_N = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
@@ -91,6 +92,15 @@ class RequestResult(C.Structure):
         return d
 
 
+ALLGATHER_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int64, C.c_void_p)
+
+
+class Reducer(C.Structure):
+    """cqr_reducer: exchange buffers and callback of a row-sharded factorisation."""
+    _fields_ = [("world", C.c_int32), ("rank", C.c_int32), ("send", C.c_void_p), ("recv", C.c_void_p),
+                ("capacity", C.c_int64), ("allgather", ALLGATHER_FN), ("ctx", C.c_void_p)]
+
+
 class CholQRError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         self.status = status
@@ -109,6 +119,8 @@ _SIGNATURES = {
     "cholqr_factor_host": (C.c_int, [C.POINTER(Opts), _I64, _I64, _P, _I64, _P, _I64, _P, _I64,
                                      C.POINTER(Info), _VP]),
     "cholqr_gram": (C.c_int, [C.POINTER(Opts), _I64, _I64, _P, _I64, _P, _I64, _VP]),
+    "cholqr_factor_sharded": (C.c_int, [C.POINTER(Opts), _I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64,
+                                        C.POINTER(Reducer), C.POINTER(Info), _VP]),
     "cholqr_pn": (C.c_int, [C.POINTER(Opts), _I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64,
                             C.POINTER(Info), _VP]),
     "cholqr_factor_noalloc": (C.c_int, [C.POINTER(Opts), _I64, _I64, _P, _I64, _P, _I64, _P,
@@ -185,6 +197,13 @@ def cholqr_factor_noalloc(opts, m, n, A, lda, Q, ldq, R, ldr, info, stream) -> i
     """cholqr_factor with all scratch in the library's fixed device array (no
     allocation; n <= 64); for callers that cannot allocate device memory."""
     return lib().cholqr_factor_noalloc(opts, m, n, A, lda, Q, ldq, R, ldr, info, stream)
+
+
+def cholqr_factor_sharded(opts, m_local, m_total, n, A, lda, Q, ldq, R, ldr, reducer, info, stream) -> int:
+    """Row-sharded sCholQR3 on this rank's rows (reducer: a Reducer structure);
+    see paper_2507_07788_gb300.sharded for reducers and a tensor wrapper."""
+    return lib().cholqr_factor_sharded(opts, m_local, m_total, n, A, lda, Q, ldq, R, ldr, reducer, info,
+                                       stream)
 
 
 def basis_create(m, n_max, opts, stream):

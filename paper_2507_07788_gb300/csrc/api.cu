@@ -285,6 +285,11 @@ struct Problem {
   double *hQ = nullptr;
   int64_t ldhq = 0;
   bool *hq_written = nullptr;
+  // Row-sharded factorisation (cholqr_factor_sharded): this rank's rows are
+  // P.m of m_total; each reduced Gramian is exchanged through the reducer and
+  // summed in rank order before the control step.
+  const cqr_reducer *red = nullptr;
+  int64_t m_total = 0;
 };
 
 cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
@@ -593,16 +598,31 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
     if (mk != nullptr) cudaEventRecord(mk->b, str);
     return e;
   };
-  auto reduce = [&]() -> cudaError_t {
+  bool red_failed = false;  // a reducer call of a sharded factorisation failed
+  auto reduce_local = [&]() -> cudaError_t {
     g_launches++;
     if (last_x) return launch_reduce_dense(s.partials, Gx, (int64_t)(q + p) * p, s.C, s.st, str);
     if (last_oz) return launch_reduce_oz(s.partials, last_oz_G, p, s.C, s.st, str);
     Reduce r{s.partials, G, E, q, p, s.C, s.st};
     return launch_reduce(r, str);
   };
+  auto reduce = [&]() -> cudaError_t {
+    cudaError_t e = reduce_local();
+    if (e != cudaSuccess || P.red == nullptr) return e;
+    // this rank's Gramian -> send; gather all ranks' blocks; sum in rank order
+    const int64_t count = (int64_t)(q + p) * p;
+    e = cudaMemcpyAsync(P.red->send, s.C, sizeof(double) * count, cudaMemcpyDeviceToDevice, str);
+    if (e != cudaSuccess) return e;
+    if (P.red->allgather(P.red->ctx, count, (void *)str) != 0) {
+      red_failed = true;
+      return cudaErrorUnknown;
+    }
+    g_launches++;
+    return launch_sum_ranks(P.red->recv, P.red->world, count, s.C, str);
+  };
   auto ctrl = [&]() -> cudaError_t {
     Ctrl c{};
-    c.m = P.m;
+    c.m = (P.red != nullptr) ? P.m_total : P.m;
     c.q = q;
     c.p = p;
     c.mode = P.mode;
@@ -675,6 +695,12 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
     (void)cudaGetLastError();
     if (stage) (void)cudaStreamSynchronize(cx->st);
     cudaFreeAsync(s.base, str);
+    if (red_failed) {
+      // queued work may still read the reducer's buffers: drain it first
+      (void)cudaStreamSynchronize(str);
+      (void)cudaGetLastError();
+      return CQR_ERR_REDUCE;
+    }
     return cuda_status(e);
   }
   if (!hs->done) {
@@ -796,6 +822,7 @@ const char *cqr_status_string(int status) {
     case CQR_ERR_CAPACITY: return "basis capacity exceeded";
     case CQR_ERR_CUDA: return "CUDA error";
     case CQR_ERR_TIMEOUT: return "timeout";
+    case CQR_ERR_REDUCE: return "reducer failure (sharded factorisation)";
     default: return "unknown status";
   }
 }
@@ -833,6 +860,49 @@ cqr_status cholqr_factor(const cqr_opts *opts, int64_t m, int64_t n, const doubl
   P.mode = MODE_FACTOR;
   P.min_iter = o.min_iter;
   P.o = o;
+  return run(P, info, (cudaStream_t)stream);
+}
+
+cqr_status cholqr_factor_sharded(const cqr_opts *opts, int64_t m_local, int64_t m_total, int64_t n,
+                                 const double *A, int64_t lda, double *Q, int64_t ldq, double *R,
+                                 int64_t ldr, const cqr_reducer *red, cqr_info *info, void *stream) {
+  cqr_opts o;
+  cqr_default_opts(&o);
+  if (opts != nullptr) o = *opts;
+  if (!opts_valid(o)) return CQR_ERR_INVALID;
+  if (red == nullptr || red->world < 1 || red->rank < 0 || red->rank >= red->world ||
+      red->allgather == nullptr || red->send == nullptr || red->recv == nullptr)
+    return CQR_ERR_INVALID;
+  if (n < 1 || n > CQR_MAX_N || m_local < 1 || m_total < n || m_local > m_total || lda < m_local ||
+      ldq < m_local || ldr < n || red->capacity < n * n)
+    return CQR_ERR_INVALID;
+  if (A == nullptr || Q == nullptr || R == nullptr) return CQR_ERR_INVALID;
+  if (A == Q && lda != ldq) return CQR_ERR_INVALID;
+  if (A != Q) {
+    const char *a0 = (const char *)A, *a1 = (const char *)(A + lda * (n - 1) + m_local);
+    const char *q0 = (const char *)Q, *q1 = (const char *)(Q + ldq * (n - 1) + m_local);
+    if (a0 < q1 && q0 < a1) return CQR_ERR_INVALID;
+  }
+  if (host_state() == nullptr) return CQR_ERR_CUDA;
+  Problem P{};
+  P.m = m_local;
+  P.q = 0;
+  P.p = (int)n;
+  P.Qin = nullptr;
+  P.ldqin = 1;
+  P.Y0 = A;
+  P.ldy0 = lda;
+  P.Y = Q;
+  P.ldy = ldq;
+  P.R = R;
+  P.ldr = ldr;
+  P.B = nullptr;
+  P.ldb = 1;
+  P.mode = MODE_FACTOR;
+  P.min_iter = o.min_iter;
+  P.o = o;
+  P.red = red;
+  P.m_total = m_total;
   return run(P, info, (cudaStream_t)stream);
 }
 

@@ -218,6 +218,10 @@ constexpr int kOzMaxN = 128;
 cudaError_t launch_trsm_rows(const RowSweep &a, int grid, cudaStream_t s);
 int trsm_rows_grid(int64_t m);
 
+// Row-sharded factorisation: C[e] = sum over ranks r = 0, 1, ... (in that
+// order) of recv[r * count + e].
+cudaError_t launch_sum_ranks(const double *recv, int world, int64_t count, double *C, cudaStream_t s);
+
 // Geometry of a row sweep for the given widths: tile rows, shared stride and
 // bytes of dynamic shared memory.
 void rowsweep_geometry(int q, int p, int *tile_rows, int *lds, size_t *smem);

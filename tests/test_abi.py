@@ -13,7 +13,9 @@ HEADER = os.path.join(ROOT, "include", "cholqr.h")
 def header_functions(path=HEADER):
     text = open(path).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w]*\s*\**\s*([A-Za-z_]\w*)\s*\(", text, flags=re.M)
+    # a declaration: type, then whitespace or '*', then the name and '(' (a
+    # function-pointer member such as "int (*f)(...)" is not one)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_]\w*(?:\s+|\s*\*+\s*)([A-Za-z_]\w*)\s*\(", text, flags=re.M)
     return [n for n in names if n not in ("if", "while", "defined")]
 
 
