@@ -180,7 +180,7 @@ bool opts_valid(const cqr_opts &o) {
          (o.precision == CQR_PREC_FP64 || o.precision == CQR_PREC_MIXED) &&
          o.shift_policy >= CQR_SHIFT_SCHOLQR3 && o.shift_policy <= CQR_SHIFT_ISCHOLQR &&
          (o.stop_rule == CQR_STOP_FROB_TOL || o.stop_rule == CQR_STOP_U_SQRT_N) &&
-         (o.emulation == CQR_EMU_AUTO || o.emulation == CQR_EMU_OFF);
+         (o.emulation == CQR_EMU_AUTO || o.emulation == CQR_EMU_OFF || o.emulation == CQR_EMU_LEGACY);
 }
 
 // Pinned host mirror of the device state, one per host thread.
@@ -323,14 +323,14 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
   // (m >= kOzUpdMinRows, 32 <= p <= 64) form their cross Gramian
   // [Q_in Y]^T Y on the tensor cores (xoz) and keep the FP64 projection +
   // solve; the others keep the fused FP64 sweep.
-  const bool ozu = (P.mode == MODE_UPDATE) && (q == 0) && (P.o.emulation == CQR_EMU_AUTO) &&
+  const bool ozu = (P.mode == MODE_UPDATE) && (q == 0) && (P.o.emulation != CQR_EMU_OFF) &&
                    (P.m > kOzUpdMinRows) && (p <= kOzMaxN);
   // Narrow appends (p <= 16) to a basis with a digit cache form the cross
   // Gramian from the cached digits of Q_in instead (cxg), with the same
   // FP64 projection + solve.
-  const bool cxg = (P.mode == MODE_UPDATE) && (P.o.emulation == CQR_EMU_AUTO) && !ozu && q > 0 &&
+  const bool cxg = (P.mode == MODE_UPDATE) && (P.o.emulation != CQR_EMU_OFF) && !ozu && q > 0 &&
                    P.Qd != nullptr && (P.m > kOzUpdMinRows) && (p <= kOzCacheMaxP);
-  const bool xoz = (P.mode == MODE_UPDATE) && (P.o.emulation == CQR_EMU_AUTO) && !ozu && !cxg &&
+  const bool xoz = (P.mode == MODE_UPDATE) && (P.o.emulation != CQR_EMU_OFF) && !ozu && !cxg &&
                    (P.m >= kOzUpdMinRows) && (p >= kOzUpdMinP) && (p <= 64);
   int Gx = 0;
   int64_t x_rows_per_cta = 0;
@@ -340,8 +340,9 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
     const int64_t tiles = (P.m + tr - 1) / tr;
     x_rows_per_cta = ((tiles + Gx - 1) / Gx) * tr;
   }
-  const bool oz = ((P.mode == MODE_FACTOR) || ozu) && (p <= kOzMaxN) && (P.o.emulation == CQR_EMU_AUTO);
-  const int Goz = oz ? ozgram_grid(P.m, p) : 0;
+  const bool oz = ((P.mode == MODE_FACTOR) || ozu) && (p <= kOzMaxN) && (P.o.emulation != CQR_EMU_OFF);
+  const bool tc05 = P.o.emulation == CQR_EMU_AUTO;
+  const int Goz = oz ? ozgram_grid(P.m, p, tc05) : 0;
   int64_t oz_rows_per_cta = 0;
   if (oz) {
     const int64_t tr = ozgram_tile_rows();
@@ -363,7 +364,7 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
   if (pipe) {
     const int64_t tr = ozgram_tile_rows();
     chunk_rows = (((P.m + nchunks - 1) / nchunks + tr - 1) / tr) * tr;
-    Gc = ozgram_grid(chunk_rows, p);
+    Gc = ozgram_grid(chunk_rows, p, tc05);
     const int64_t tiles = chunk_rows / tr;
     chunk_rpc = ((tiles + Gc - 1) / Gc) * tr;
   }
@@ -432,6 +433,7 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
     a.lds = lds;
     a.do_trsm = trsm ? 1 : 0;
     a.st = s.st;
+    a.tc05 = tc05 ? 1 : 0;
     SweepMark *mk = nullptr;
     if (timing) {
       if (nmarks == pool.size()) {
@@ -916,11 +918,12 @@ cqr_status cholqr_gram(const cqr_opts *opts, int64_t m, int64_t n, const double 
   if (A == nullptr || X == nullptr) return CQR_ERR_INVALID;
   cudaStream_t str = (cudaStream_t)stream;
   const int p = (int)n;
-  const bool oz = (p <= kOzMaxN) && (o.emulation == CQR_EMU_AUTO);
+  const bool oz = (p <= kOzMaxN) && (o.emulation != CQR_EMU_OFF);
   int tile_rows, lds;
   size_t smem;
   rowsweep_geometry(0, p, &tile_rows, &lds, &smem);
-  const int G = oz ? ozgram_grid(m, p) : rowsweep_grid(m, tile_rows);
+  const bool tc05 = o.emulation == CQR_EMU_AUTO;
+  const int G = oz ? ozgram_grid(m, p, tc05) : rowsweep_grid(m, tile_rows);
   const int64_t tr = oz ? ozgram_tile_rows() : tile_rows;
   const int64_t tiles = (m + tr - 1) / tr;
   const int64_t rows_per_cta = ((tiles + G - 1) / G) * tr;
@@ -940,6 +943,7 @@ cqr_status cholqr_gram(const cqr_opts *opts, int64_t m, int64_t n, const double 
   a.lds = lds;
   a.do_trsm = 0;
   a.st = nullptr;
+  a.tc05 = tc05 ? 1 : 0;
   cudaError_t e = oz ? launch_ozgram(a, G, str) : launch_rowsweep(a, G, str);
   g_launches++;
   if (e == cudaSuccess) {
@@ -1181,7 +1185,7 @@ cqr_status cholqr_pn(const cqr_opts *opts, int64_t m, int64_t n, int64_t r, cons
   uint16_t *Qd = nullptr;
   int *Qe = nullptr;
   const int64_t ldc = (m + 63) & ~(int64_t)63;
-  if (r > 1 && pmax <= kOzCacheMaxP && m > kOzUpdMinRows && o.emulation == CQR_EMU_AUTO) {
+  if (r > 1 && pmax <= kOzCacheMaxP && m > kOzUpdMinRows && o.emulation != CQR_EMU_OFF) {
     if (cudaMallocAsync((void **)&Qd, sizeof(uint16_t) * 7 * (size_t)ldc * n, str) != cudaSuccess ||
         cudaMallocAsync((void **)&Qe, sizeof(int) * (size_t)n, str) != cudaSuccess) {
       (void)cudaGetLastError();  // no cache: the panels keep the FP64 path

@@ -92,6 +92,7 @@ struct RowSweep {
   const double *Tinv;   // p x p upper (ld p): D R~^{-1} (tensor-core product Q = (Y D^-1)(D T))
   const int *Tscale;    // p: log2 of D (column k of Y is divided, row k of T multiplied, by 2^Tscale[k])
   const DevState *st;
+  int32_t tc05;         // 1: the tcgen05 kernels may be used where they apply
 };
 
 struct Reduce {
@@ -167,7 +168,7 @@ cudaError_t launch_init_batched(const Ctrl *reqs, const int *nreq, int grid, cud
 cudaError_t launch_ozgram(const RowSweep &a, int grid, cudaStream_t s);
 cudaError_t launch_reduce_oz(const double *partials, int G, int n, double *C, const DevState *st,
                              cudaStream_t s);
-int ozgram_grid(int64_t m, int n);
+int ozgram_grid(int64_t m, int n, bool tc05 = true);
 // Q = Y T (T = R~^{-1}) on the tensor cores, exact digit products, 33 <= n <= 128.
 cudaError_t launch_ozgemm(const RowSweep &a, int grid, cudaStream_t s);
 int ozgemm_grid(int64_t m, int n);
@@ -211,6 +212,13 @@ constexpr int kOzUpdMinP = 32;
 // columns); at n <= 16 the FP64 substitution's n^2 / 2 FMAs per row stay.
 constexpr int kOzGemmMinN = 17;
 int ozgram_tile_rows();
+// The digit Gramian on tcgen05 (csrc/tcgram.cu) for kTcGramMinN <= p <= 64,
+// q = 0, no fused solve, Y 16-byte aligned with an even leading dimension;
+// launch_ozgram dispatches to it when tcgram_usable(a).
+constexpr int kTcGramMinN = 17;
+bool tcgram_usable(const RowSweep &a);
+int tcgram_grid(int64_t m);
+cudaError_t launch_tcgram(const RowSweep &a, int grid, cudaStream_t s);
 constexpr int kOzMaxN = 128;
 // FP64 row solve Q = Y R~^{-1} alone for n <= 16 (one thread per row,
 // registers); shares SMs with ozgram_kernel when the two run on different

@@ -364,6 +364,7 @@ static cudaError_t launch_oz(const RowSweep &a, int grid, cudaStream_t s) {
 }
 
 cudaError_t launch_ozgram(const RowSweep &a, int grid, cudaStream_t s) {
+  if (tcgram_usable(a)) return launch_tcgram(a, grid, s);
   switch (ozgram_nt(a.p)) {
     case 16: return launch_oz<16>(a, grid, s);
     case 32: return launch_oz<32>(a, grid, s);
@@ -375,7 +376,10 @@ cudaError_t launch_ozgram(const RowSweep &a, int grid, cudaStream_t s) {
 
 // Number of row groups (= partials) for m rows at width n: every SM holds
 // OzCfg::ctas CTAs, a row group takes OzCfg::halves of them.
-int ozgram_grid(int64_t m, int n) {
+int ozgram_grid(int64_t m, int n, bool tc05) {
+  // the tcgen05 kernel runs one CTA per SM (launch_ozgram falls back to the
+  // mma.sync kernel with the same row groups when it does not apply)
+  if (tc05 && n >= kTcGramMinN && n <= 64) return tcgram_grid(m);
   const int64_t tiles = (m + kOzTR - 1) / kOzTR;
   const int64_t per_sm = (n > 64) ? 1 : 2, halves = (n > 64) ? 2 : 1;
   return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, per_sm * num_sms() / halves));

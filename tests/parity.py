@@ -9,8 +9,9 @@ about 1/sqrt(m), so entries differ by about kappa u / sqrt(m).  The bounds
   |R_gpu - R_oracle|_max <= C_R (kappa + sqrt(m)) u max|R|
 use constants fixed from the largest ratio measured over the test matrices
 (printed at the end of every run by the terminal summary of conftest.py):
-C_Q = C_R = 4, a few times the largest measured ratio and far below the 20
-sqrt(n) of the first version of these tests.  The sqrt(m) term of the R
+C_Q = 4 and C_R = 3, about ten times the largest measured ratio and far
+below the 20 sqrt(n) of the first version of these tests.  A Q difference
+below the 1e-12 floor is recorded against the floor.  The sqrt(m) term of the R
 bound is the oracle's own Gramian: it sums m products in sequence, with a
 rounding error that grows like sqrt(m) u relative to the Gramian, and R
 inherits it even at kappa = 1 (measured on GB300: max|dR| = 0.3 sqrt(m) u
@@ -30,7 +31,7 @@ import numpy as np
 
 U = 2.0 ** -53
 C_Q = 4.0
-C_R = 4.0
+C_R = 3.0
 ORTH_GATE = 1e-13
 RESID_GATE = 1e-13
 
@@ -65,7 +66,7 @@ def r_tol(kappa: float, n, R, m: int = 1) -> float:
 
 
 def check_q(dq: float, kappa: float, m: int, where: str = "") -> None:
-    record("Q  (max|dQ| / (kappa u / sqrt m))", dq, q_unit(kappa, m), where)
+    record("Q  (max|dQ| / max(kappa u / sqrt m, 1e-12 / C_Q))", dq, q_tol(kappa, m) / C_Q, where)
     assert dq <= q_tol(kappa, m), (where, dq, q_tol(kappa, m))
 
 

@@ -1,7 +1,12 @@
 """The Gramian X = A^T A (Alg. 1 line 3) as the library forms it
 (cholqr_gram): tensor-core digit arithmetic (Ozaki splitting) for n <= 128
-(emulation AUTO) and FP64 CUDA cores with emulation OFF, against the oracle's
-FP64 triple loop.
+(emulation AUTO: the tcgen05 kernel for 17 <= n <= 64 on aligned blocks, the
+warp-level mma.sync kernels otherwise; emulation LEGACY: mma.sync only) and
+FP64 CUDA cores with emulation OFF, against the oracle's FP64 triple loop.
+The tcgen05 and mma.sync kernels form the same exact digit sums; they differ
+only where a column exponent grows inside a CTA (each rescales its integer
+sums by a floor division, the tcgen05 kernel in two halves), so they agree
+bit for bit or within one unit in the last place.
 
 Tolerance: both sides are within the FP64 dot-product bound, so
 |X_gpu - X_oracle|_ij <= 2 * gamma_m * (|A|^T |A|)_ij with gamma_m = m u / (1 - m u).
@@ -40,7 +45,7 @@ def check(cq, orc, A, emu):
     return X
 
 
-@pytest.mark.parametrize("emu", [0, 1])
+@pytest.mark.parametrize("emu", [0, 1, 2])
 @pytest.mark.parametrize("m,n", [(1, 1), (17, 3), (128, 16), (129, 16), (5000, 20), (40000, 33),
                                  (60000, 64), (3000, 100), (5000, 65), (70000, 128)])
 def test_gram_parity(cq, orc, emu, m, n):
@@ -87,7 +92,8 @@ def _rne(S: int, scale: int) -> float:
     return float(S) * 2.0 ** scale
 
 
-def test_gram_diagonal_is_correctly_rounded(cq):
+@pytest.mark.parametrize("n", [16, 40])
+def test_gram_diagonal_is_correctly_rounded(cq, n):
     # One 64-row tile: a single digit-Gramian CTA rounds each entry once from
     # the exact sum, and the reduction doubles P_jj exactly, so X_jj must be
     # the correctly rounded sum of squares.  Entries are M 2^(k_j - 25) with
@@ -96,7 +102,7 @@ def test_gram_diagonal_is_correctly_rounded(cq):
     # no digit product is dropped.  The last entry of some columns is chosen
     # so that the exact sum is a tie between two doubles.
     rng = np.random.default_rng(11)
-    m, n = 64, 16
+    m = 64
     M = rng.integers(-(2 ** 26) + 1, 2 ** 26, size=(m, n), dtype=np.int64)
     k = rng.integers(-40, 41, size=n)
     ties = 0
@@ -112,9 +118,55 @@ def test_gram_diagonal_is_correctly_rounded(cq):
                 M[-4:, j] = e
                 ties += 1
                 break
-    assert ties >= 6
+    assert ties >= n // 2 - 2
     A = M.astype(np.float64) * np.exp2(k - 25)[None, :]
     X = cq.gram(cq.to_colmajor(A)).cpu().numpy()
     for j in range(n):
         S = sum(int(x) * int(x) for x in M[:, j])
         assert X[j, j] == _rne(S, 2 * (int(k[j]) - 25)), (j, X[j, j], _rne(S, 2 * (int(k[j]) - 25)))
+
+
+def _ulps_apart(x, y):
+    return np.abs(x - y) / np.spacing(np.maximum(np.abs(x), np.abs(y)) + 1e-300)
+
+
+@pytest.mark.parametrize("m,n,grow", [(1, 17, False), (63, 20, False), (4097, 33, False), (200003, 48, False),
+                                      (1000000, 64, False), (300000, 64, True), (100000, 40, True)])
+def test_tcgen05_and_mma_sync_gramians_agree(cq, orc, m, n, grow):
+    # one tile, a ragged tile, several CTAs with ragged tails, the benchmark
+    # size; with grow, column maxima that grow from tile to tile inside each
+    # CTA (the rescaled integer sums)
+    rng = np.random.default_rng(m + n)
+    A = rng.standard_normal((m, n))
+    if grow:
+        A *= 10.0 ** ((np.arange(m) // 64) % 9 - 4.0)[:, None] * 10.0 ** rng.uniform(-3, 3, size=(1, n))
+    dA = cq.to_colmajor(A)
+    Xt = cq.gram(dA).cpu().numpy()
+    Xl = cq.gram(dA, opts=cq.default_opts(emulation=cq.EMU_LEGACY)).cpu().numpy()
+    assert np.array_equal(Xt, Xt.T)
+    d = _ulps_apart(Xt, Xl)
+    assert np.max(d) <= 1.0, np.max(d)
+    if not grow:
+        assert np.array_equal(Xt, Xl)
+    if m <= 300000:
+        Xo = orc.gram(A)
+        absA = np.abs(A)
+        bound = 2.0 * (m * U / (1 - m * U)) * (absA.T @ absA) + 1e-300
+        assert np.all(np.abs(Xt - Xo) <= bound)
+
+
+def test_tcgen05_gramian_falls_back_on_unaligned_blocks(cq, orc):
+    # an odd leading dimension and a block that starts 8 bytes past a 16-byte
+    # boundary cannot be described to TMA: the mma.sync kernel forms them
+    m, n, ld = 20001, 40, 20003
+    A = synth.test_matrix(m + 1, n, 1e4, rep=6)
+    big = cq.colmajor(ld, n)
+    big.zero_()
+    big[: m + 1].copy_(torch.from_numpy(A))
+    for view, ref in ((big[:m], A[:m]), (big[1: m + 1], A[1:])):
+        X = cq.gram(view).cpu().numpy()
+        Xl = cq.gram(view, opts=cq.default_opts(emulation=cq.EMU_LEGACY)).cpu().numpy()
+        assert np.array_equal(X, Xl)
+        Xo = orc.gram(np.asfortranarray(ref))
+        absA = np.abs(ref)
+        assert np.all(np.abs(X - Xo) <= 2.0 * (m * U / (1 - m * U)) * (absA.T @ absA) + 1e-300)
