@@ -501,11 +501,11 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
         tr.Yout = a.Yout + r0;
         const double rcd = (double)rc;
         SweepMark *ms = kmark(gemm ? MARK_TSOLVE : MARK_SOLVE, npass, rcd * p * p, 16.0 * rcd * p);
-        if (ms) ms->tc_flops = gemm ? rcd * ozgemm_tc_flops_per_row(p) : 0.0;
+        if (ms) ms->tc_flops = gemm ? rcd * ozgemm_tc_flops_per_row(p, tc05) : 0.0;
         if (ms) cudaEventRecord(ms->a, str);
         if (gemm) {
-          const int Gg = ozgemm_grid(rc, p);
-          const int64_t tg = ozgemm_tile_rows(p);
+          const int Gg = ozgemm_grid(rc, p, tc05);
+          const int64_t tg = ozgemm_tile_rows(p, tc05);
           tr.rows_per_cta = (((rc + tg - 1) / tg + Gg - 1) / Gg) * tg;
           tr.Tinv = s.Tinv;
           tr.Tscale = s.Tscale;

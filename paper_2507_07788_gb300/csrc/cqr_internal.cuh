@@ -171,8 +171,8 @@ cudaError_t launch_reduce_oz(const double *partials, int G, int n, double *C, co
 int ozgram_grid(int64_t m, int n, bool tc05 = true);
 // Q = Y T (T = R~^{-1}) on the tensor cores, exact digit products, 33 <= n <= 128.
 cudaError_t launch_ozgemm(const RowSweep &a, int grid, cudaStream_t s);
-int ozgemm_grid(int64_t m, int n);
-int ozgemm_tile_rows(int n);
+int ozgemm_grid(int64_t m, int n, bool tc05 = true);
+int ozgemm_tile_rows(int n, bool tc05 = true);
 // Digit cache of a basis (csrc/ozcache.cu): fill columns k0 .. k0 + p - 1,
 // and the cross Gramian [Q_in Y]^T Y of appends of p <= 16 columns that
 // reads it (partials (q + p) x p per row group, for launch_reduce_dense).
@@ -192,7 +192,7 @@ constexpr int kOzCacheProjMaxQ = 256;
 constexpr int kOzCacheMaxP = 16;
 // bf16 FLOPs the tensor-core solve issues per row at width n (digit pairs x
 // the k-blocks its upper-triangular T does not skip).
-double ozgemm_tc_flops_per_row(int n);
+double ozgemm_tc_flops_per_row(int n, bool tc05 = true);
 constexpr int kOzGemmMaxN = 128;
 // Cross Gramian of the update, C = [Q_in Y]^T Y, on the tensor cores (exact
 // digit products, p <= 64): partials of `groups` row groups, each (q + p) x p.
@@ -219,6 +219,15 @@ constexpr int kTcGramMinN = 17;
 bool tcgram_usable(const RowSweep &a);
 int tcgram_grid(int64_t m);
 cudaError_t launch_tcgram(const RowSweep &a, int grid, cudaStream_t s);
+// The digit solve Q = Y T on tcgen05 (csrc/tcgemm.cu) for kTcGemmMinN <= p
+// <= 64 in 128-row tiles; launch_ozgemm dispatches to it when
+// tcgemm_usable(a).
+constexpr int kTcGemmMinN = 17;
+bool tcgemm_usable(const RowSweep &a);
+int tcgemm_tile_rows();
+int tcgemm_grid(int64_t m);
+double tcgemm_tc_flops_per_row();
+cudaError_t launch_tcgemm(const RowSweep &a, int grid, cudaStream_t s);
 constexpr int kOzMaxN = 128;
 // FP64 row solve Q = Y R~^{-1} alone for n <= 16 (one thread per row,
 // registers); shares SMs with ozgram_kernel when the two run on different

@@ -500,18 +500,22 @@ static cudaError_t launch_gm_tiled(const RowSweep &a, int grid, cudaStream_t s) 
   return cudaGetLastError();
 }
 
-int ozgemm_tile_rows(int n) {
+int ozgemm_tile_rows(int n, bool tc05) {
+  if (tc05 && n >= kTcGemmMinN && n <= kGmNT) return tcgemm_tile_rows();
   return n > kGmNT ? TiledCfg<128>::tr : (n > 32 ? kGmTR : TiledCfg<32>::tr);
 }
 
-int ozgemm_grid(int64_t m, int n) {
-  const int64_t tr = ozgemm_tile_rows(n);
+int ozgemm_grid(int64_t m, int n, bool tc05) {
+  // the tcgen05 solve runs one CTA per SM
+  if (tc05 && n >= kTcGemmMinN && n <= kGmNT) return tcgemm_grid(m);
+  const int64_t tr = ozgemm_tile_rows(n, false);
   const int64_t tiles = (m + tr - 1) / tr;
   const int64_t per_sm = n > kGmNT ? TiledCfg<128>::ctas : 2;
   return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, per_sm * (int64_t)num_sms()));
 }
 
-double ozgemm_tc_flops_per_row(int n) {
+double ozgemm_tc_flops_per_row(int n, bool tc05) {
+  if (tc05 && n >= kTcGemmMinN && n <= kGmNT) return tcgemm_tc_flops_per_row();
   int pairs = 0;
   for (int o = 0; o < kGmDigits; ++o) pairs += o + 1;  // orders 0..7, o + 1 pairs each
   // m16n8k16 products per row: 8-column tiles times their k extent
@@ -531,6 +535,7 @@ double ozgemm_tc_flops_per_row(int n) {
 cudaError_t launch_ozgemm(const RowSweep &a, int grid, cudaStream_t s) {
   if (a.Tinv == nullptr || a.Tscale == nullptr) return cudaErrorInvalidValue;
   if (a.p < kOzGemmMinN || a.p > 128) return cudaErrorInvalidValue;
+  if (tcgemm_usable(a)) return launch_tcgemm(a, grid, s);
   if (a.p <= 32) return launch_gm_tiled<32>(a, grid, s);
   if (a.p <= kGmNT) return launch_gm(a, grid, s);
   return launch_gm_tiled<128>(a, grid, s);
