@@ -166,7 +166,9 @@ class Clocks:
 
 
 KERNEL_FILES = {"rowsweep": ("rowsweep.cu",), "trsm_rows": ("trsm.cu",),
-                "ozgram": ("ozgram.cu", "ozdigits.cuh"), "ozgemm": ("ozgemm.cu", "ozdigits.cuh")}
+                "ozgram": ("ozgram.cu", "ozdigits.cuh"), "ozgemm": ("ozgemm.cu", "ozdigits.cuh"),
+                "tcgram": ("tcgram.cu", "tc05.cuh", "ozdigits.cuh"), "tcgemm": ("tcgemm.cu", "tc05.cuh", "ozdigits.cuh")}
+TC05_MIN_N, TC05_MAX_N = 17, 64  # widths of the tcgen05 Gramian and solve
 
 
 def kernel_source_hash(name: str) -> str:
@@ -351,17 +353,22 @@ def roofline_from(tm, m, n, hbm_peak, hbm_src, tc_peak, tc_src):
         return {"achieved": af / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
                 "frac": af / FP64_PEAK_FLOPS, "peak_source": fp64_src}
 
+    tc05 = TC05_MIN_N <= n <= TC05_MAX_N
+    gname = "tcgram" if tc05 else "ozgram"
+    sname = "tcgemm" if tc05 else "ozgemm"
     gram = None
     if tm["gram_launches"] > 0:
         gms, gfl, gby, gaf, gag = per("gram")
         grows = gby / (8.0 * n)
-        gtraffic, _ = traffic_per_launch(int(round(grows)), "ozgram")
+        gtraffic, _ = traffic_per_launch(int(round(grows)), gname)
         # 16 symmetric digit pairs, each a full NT x NT block per row
         nt = 16 if n <= 16 else (32 if n <= 32 else (64 if n <= 64 else 128))
         gtcf = grows * 2.0 * OZGRAM_PAIRS * nt * nt
         gtca = gtcf / (gms * 1e-3) if gms > 0 else 0.0
-        gram = record("ozgram_kernel (exact FP64 Gramian from bf16 digits on the tensor cores, "
-                      "one launch per row chunk)", gms, gfl, gby, gaf, gag, gtraffic, tm["gram_ms"],
+        gram = record(("tcgram64_kernel (exact FP64 Gramian from bf16 digits, tcgen05 with TMEM "
+                       "accumulators and TMA tiles, one launch per row chunk)") if tc05 else
+                      ("ozgram_kernel (exact FP64 Gramian from bf16 digits on the tensor cores, mma.sync, "
+                       "one launch per row chunk)"), gms, gfl, gby, gaf, gag, gtraffic, tm["gram_ms"],
                       {"tensor": {"achieved": gtca / 1e12, "peak": tc_peak, "unit": "TFLOP/s",
                                   "frac": gtca / 1e12 / tc_peak, "bf16_digit_flops_per_launch": gtcf,
                                   "peak_source": tc_src},
@@ -370,9 +377,11 @@ def roofline_from(tm, m, n, hbm_peak, hbm_src, tc_peak, tc_src):
         ms, fl, by, af, ag = per("tsolve")
         tcf = tm["tsolve_tc_flops"] / max(tm["tsolve_launches"], 1)
         tca = tcf / (ms * 1e-3) if ms > 0 else 0.0
-        traffic, _ = traffic_per_launch(int(round(by / (16.0 * n))), "ozgemm")
-        solve = record("ozgemm_kernel (Q = Y R~^-1 as an exact bf16 digit product on the tensor cores, "
-                       "one launch per row chunk)", ms, fl, by, af, ag, traffic, tm["tsolve_ms"],
+        traffic, _ = traffic_per_launch(int(round(by / (16.0 * n))), sname)
+        solve = record(("tcgemm64_kernel (Q = Y R~^-1 as an exact bf16 digit product, tcgen05 with TMEM "
+                        "accumulators, one launch per row chunk)") if tc05 else
+                       ("ozgemm_kernel (Q = Y R~^-1 as an exact bf16 digit product on the tensor cores, "
+                        "mma.sync, one launch per row chunk)"), ms, fl, by, af, ag, traffic, tm["tsolve_ms"],
                        {"tensor": {"achieved": tca / 1e12, "peak": tc_peak, "unit": "TFLOP/s",
                                    "frac": tca / 1e12 / tc_peak, "bf16_digit_flops_per_launch": tcf,
                                    "peak_source": tc_src},

@@ -36,6 +36,15 @@ def _capture(name):
     return float(d["capture_bytes_per_launch"]), float(d["capture_rows"])
 
 
+def _check_traffic(traffic, name, rows):
+    # the committed capture scaled by rows, or None while the kernel's sources
+    # differ from the captured ones (or no capture exists)
+    if traffic is None:
+        return
+    b, cr = _capture(name)
+    assert traffic == pytest.approx(b * rows / cr, rel=1e-12)
+
+
 def test_tensor_pipeline_dominant_kernel():
     # 24 launches each of the digit Gramian and the digit solve on row chunks
     # of 125000 rows at n = 64; the Gramian takes longer in total
@@ -48,7 +57,7 @@ def test_tensor_pipeline_dominant_kernel():
                  tsolve_bytes=L * 16.0 * rows * n, tsolve_tc_flops=L * tc_solve_per_launch)
     r = bench.roofline_from(tm, 1_000_000, n, 6686.8, "measured", 1730.8, "measured")
     assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["peak"] == 6686.8
-    assert r["kernel"].startswith("ozgram_kernel") and "solve" in r
+    assert r["kernel"].startswith("tcgram64_kernel") and "solve" in r
     # 8 bytes per entry read, in 0.2 ms
     gbs = 8.0 * rows * n / (g_ms * 1e-3) / 1e9
     assert r["achieved"] == pytest.approx(gbs, rel=1e-12)
@@ -57,13 +66,11 @@ def test_tensor_pipeline_dominant_kernel():
     want = rows * 2 * 16 * 64 * 64 / (g_ms * 1e-3) / 1e12
     assert r["tensor"]["achieved"] == pytest.approx(want, rel=1e-12)
     assert r["tensor"]["frac"] == pytest.approx(want / 1730.8, rel=1e-12)
-    b, cr = _capture("ozgram")
-    assert r["traffic"] is None or r["traffic"] == pytest.approx(b * rows / cr, rel=1e-12)
+    _check_traffic(r["traffic"], "tcgram", rows)
     s = r["solve"]
     assert s["achieved"] == pytest.approx(16.0 * rows * n / (s_ms * 1e-3) / 1e9, rel=1e-12)
     assert s["tensor"]["achieved"] == pytest.approx(tc_solve_per_launch / (s_ms * 1e-3) / 1e12, rel=1e-12)
-    b, cr = _capture("ozgemm")
-    assert s["traffic"] is None or s["traffic"] == pytest.approx(b * rows / cr, rel=1e-12)
+    _check_traffic(s["traffic"], "tcgemm", rows)
 
 
 def test_solve_dominates_when_it_takes_longer():

@@ -354,3 +354,23 @@ def test_emulated_gramian_row_dynamic_range(cq, orc, n):
     assert orc.loo_frob(Q) <= 1e-13
     assert orc.rrr(A, Q, R) <= 1e-13
     check_q(np.max(np.abs(Q - Qo)), kap, m, f"row range n={n}")
+
+
+@pytest.mark.parametrize("m,n", [(130, 17), (5003, 33), (20037, 48), (200003, 64), (257, 64), (129, 20)])
+def test_tcgen05_and_mma_sync_paths_agree(cq, orc, m, n):
+    # the default path (tcgen05 Gramian and solve for 17 <= n <= 64) and the
+    # mma.sync digit kernels (emulation LEGACY) against each other and the
+    # oracle: one tile, a ragged tile of 128 rows, several CTAs
+    kappa = 1e8
+    A = synth.test_matrix(m, n, kappa, rep=21)
+    Qt, Rt, stt, it = run_gpu(cq, A)
+    Ql, Rl, stl, il = run_gpu(cq, A, opts=cq.default_opts(emulation=cq.EMU_LEGACY))
+    Qo, Ro, sto, io = orc.cholqr(A)
+    assert stt == stl == sto == cq.OK
+    assert abs(it["iters"] - il["iters"]) <= 1
+    for name, Q, R in (("tcgen05", Qt, Rt), ("mma.sync", Ql, Rl)):
+        assert orc.loo_frob(Q) <= 1e-13
+        assert orc.rrr(A, Q, R) <= 1e-13
+        check_q(np.max(np.abs(Q - Qo)), kappa, m, f"{name} vs oracle {m}x{n}")
+        check_r(np.max(np.abs(R - Ro)), kappa, Ro, m, f"{name} vs oracle {m}x{n}")
+    check_q(np.max(np.abs(Qt - Ql)), kappa, m, f"tcgen05 vs mma.sync {m}x{n}")

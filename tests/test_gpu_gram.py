@@ -155,6 +155,8 @@ def test_tcgen05_and_mma_sync_gramians_agree(cq, orc, m, n, grow):
 def test_tcgen05_gramian_falls_back_on_unaligned_blocks(cq, orc):
     # an odd leading dimension and a block that starts 8 bytes past a 16-byte
     # boundary cannot be described to TMA: the mma.sync kernel forms them
+    # (over the tcgen05 kernel's row groups, so the partials differ from the
+    # LEGACY run's and the results agree within their rounding)
     m, n, ld = 20001, 40, 20003
     A = synth.test_matrix(m + 1, n, 1e4, rep=6)
     big = cq.colmajor(ld, n)
@@ -163,7 +165,8 @@ def test_tcgen05_gramian_falls_back_on_unaligned_blocks(cq, orc):
     for view, ref in ((big[:m], A[:m]), (big[1: m + 1], A[1:])):
         X = cq.gram(view).cpu().numpy()
         Xl = cq.gram(view, opts=cq.default_opts(emulation=cq.EMU_LEGACY)).cpu().numpy()
-        assert np.array_equal(X, Xl)
-        Xo = orc.gram(np.asfortranarray(ref))
         absA = np.abs(ref)
-        assert np.all(np.abs(X - Xo) <= 2.0 * (m * U / (1 - m * U)) * (absA.T @ absA) + 1e-300)
+        AtA = absA.T @ absA
+        assert np.all(np.abs(X - Xl) <= 4.0 * (1 + 2 * 152) * U * AtA + 1e-300)
+        Xo = orc.gram(np.asfortranarray(ref))
+        assert np.all(np.abs(X - Xo) <= 2.0 * (m * U / (1 - m * U)) * AtA + 1e-300)
