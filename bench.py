@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--n", type=int, default=64)
     ap.add_argument("--kappa", type=float, default=1e12)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--emulation", default="auto", choices=["auto", "tcgen05", "off"],
+                    help="digit kernels: auto = warp-level mma.sync, tcgen05 = the tcgen05 Gramian and solve "
+                         "for 17 <= n <= 64, off = FP64 CUDA cores")
+    ap.add_argument("--no-tcgen05-leg", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -318,7 +322,7 @@ def time_factor(cq, torch, dA, dQ, dR, opts, steps, warmup):
     return e0.elapsed_time(e1) / steps, res
 
 
-def roofline_from(tm, m, n, hbm_peak, hbm_src, tc_peak, tc_src):
+def roofline_from(tm, m, n, hbm_peak, hbm_src, tc_peak, tc_src, tcgen05=False):
     """Roofline of the dominant kernel from the library's per-launch events.
 
     The roofline of this path is HBM bytes: the top level reports the
@@ -353,7 +357,7 @@ def roofline_from(tm, m, n, hbm_peak, hbm_src, tc_peak, tc_src):
         return {"achieved": af / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
                 "frac": af / FP64_PEAK_FLOPS, "peak_source": fp64_src}
 
-    tc05 = TC05_MIN_N <= n <= TC05_MAX_N
+    tc05 = tcgen05 and TC05_MIN_N <= n <= TC05_MAX_N
     gname = "tcgram" if tc05 else "ozgram"
     sname = "tcgemm" if tc05 else "ozgemm"
     gram = None
@@ -572,7 +576,9 @@ def run_ours(args):
     torch.cuda.set_device(local)
     _build.build()
     m, n, kappa = args.m, args.n, args.kappa
-    opts = cq.default_opts(precision=cq.PREC_MIXED if args.precision == "mixed" else cq.PREC_FP64)
+    emu = {"auto": cq.EMU_AUTO, "tcgen05": cq.EMU_TCGEN05, "off": cq.EMU_OFF}[args.emulation]
+    opts = cq.default_opts(precision=cq.PREC_MIXED if args.precision == "mixed" else cq.PREC_FP64,
+                           emulation=emu)
 
     A = synth.test_matrix(m, n, kappa, rep=rank)
     dA = cq.to_colmajor(A)
@@ -615,7 +621,7 @@ def run_ours(args):
     loo_f = float(torch.linalg.norm(G - torch.eye(n, dtype=G.dtype, device=G.device)))
 
     hbm_peak, hbm_src, tc_peak, tc_src = peaks()
-    roof = roofline_from(tm, m, n, hbm_peak, hbm_src, tc_peak, tc_src)
+    roof = roofline_from(tm, m, n, hbm_peak, hbm_src, tc_peak, tc_src, tcgen05=(args.emulation == "tcgen05"))
 
     hbm = factorisation_hbm(m, n, res.info["iters"], ms, hbm_peak)
     line = {"metric": METRIC, "value": value, "unit": "rows*cols/s", "n_gpus": ws, "steps": args.steps,
@@ -623,6 +629,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"sCholQR3 FP64 m={m} n={n} kappa={kappa:g} (A=U diag(s) V^T, Sec. 4.1)",
                        "m": m, "n": n, "kappa": kappa, "precision": args.precision,
+                       "emulation": args.emulation,
                        "l2": f"inputs larger than L2 ({8 * m * n / 2**20:.0f} MiB per matrix)",
                        "parallelism": "replicas" if ws > 1 else "single"},
             "roofline": roof, "hbm_frac": hbm["frac"], "factorisation_hbm": hbm,
@@ -645,6 +652,15 @@ def run_ours(args):
         line["e2e"] = {"value": m * n / dt, "unit": "rows*cols/s", "h2d_bytes_per_step": 8 * m * n,
                        "d2h_bytes_per_step": 8 * (m * n + n * n), "ms_per_step": dt * 1e3,
                        "api": "cholqr_factor_host (pinned host A, Q, R allocated once; H2D + factor + D2H in the timed region)"}
+
+    if rank == 0 and not args.no_tcgen05_leg and args.emulation != "tcgen05":
+        # the same factorisation with the tcgen05 Gramian and solve
+        o5 = cq.default_opts(precision=opts.precision, emulation=cq.EMU_TCGEN05)
+        t5, r5 = time_factor(cq, torch, dA, dQ, dR, o5, 10, 3)
+        line["tcgen05_leg"] = {"workload": f"the headline factorisation with emulation TCGEN05 (tcgen05 Gramian "
+                                           f"and solve for 17 <= n <= 64)", "ms": t5,
+                               "rows_cols_per_s": m * n / (t5 * 1e-3), "iters": r5.info["iters"],
+                               "status": r5.status, "vs_default": ms / t5}
 
     if rank == 0 and not args.no_sweep:
         sweep = []

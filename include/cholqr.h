@@ -102,19 +102,20 @@ typedef struct cqr_opts {
 /* How the FP64 products of a pass are formed.  CQR_EMU_AUTO: on the tensor
  * cores with the Ozaki splitting scheme (exact digit products, each entry
  * rounded to FP64 once) where the kernels support it: the Gramians of
- * cholqr_factor and cholqr_gram for n <= 128 (for 17 <= n <= 64 with the
- * tcgen05 kernel, TMEM accumulators and TMA-loaded tiles, when the block is
- * 16-byte aligned with an even leading dimension) and the factorisation's
+ * cholqr_factor and cholqr_gram for n <= 128 and the factorisation's
  * triangular solve for 17 <= n <= 128; for basis_append and cholqr_pn on
  * more than 262144 rows, an append to an empty basis (the factorisation's
  * pipeline), the cross Gramian of appends of 32..64 columns, and the cross
  * Gramian and projection of appends of <= 16 columns to a basis with a digit
  * cache (basis_enable_digit_cache; cholqr_pn keeps one for panels of <= 16
- * columns; q <= 256 for the projection); FP64 CUDA cores elsewhere.
- * CQR_EMU_OFF: FP64 CUDA cores everywhere.  CQR_EMU_LEGACY: as AUTO, but the
- * digit kernels are all the warp-level mma.sync ones (the tcgen05 Gramian is
- * not used); the same exact products, for comparison. */
-enum { CQR_EMU_AUTO = 0, CQR_EMU_OFF = 1, CQR_EMU_LEGACY = 2 };
+ * columns; q <= 256 for the projection); FP64 CUDA cores elsewhere.  These
+ * kernels issue warp-level mma.sync.  CQR_EMU_OFF: FP64 CUDA cores
+ * everywhere.  CQR_EMU_TCGEN05: as AUTO, but for 17 <= n <= 64 the Gramian
+ * and the solve of cholqr_factor (and the Gramian of cholqr_gram) run on
+ * tcgen05 kernels with TMEM accumulators (the Gramian's tiles TMA-loaded when
+ * the block is 16-byte aligned with an even leading dimension); the same
+ * exact digit products. */
+enum { CQR_EMU_AUTO = 0, CQR_EMU_OFF = 1, CQR_EMU_TCGEN05 = 2 };
 
 /* Per-call report.  orth_frob is ||X - I||_F of the last Gramian formed
  * (for basis_append: of the projected Gramian Q^T Q - B~^T B~), proj_frob is

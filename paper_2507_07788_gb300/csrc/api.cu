@@ -180,7 +180,7 @@ bool opts_valid(const cqr_opts &o) {
          (o.precision == CQR_PREC_FP64 || o.precision == CQR_PREC_MIXED) &&
          o.shift_policy >= CQR_SHIFT_SCHOLQR3 && o.shift_policy <= CQR_SHIFT_ISCHOLQR &&
          (o.stop_rule == CQR_STOP_FROB_TOL || o.stop_rule == CQR_STOP_U_SQRT_N) &&
-         (o.emulation == CQR_EMU_AUTO || o.emulation == CQR_EMU_OFF || o.emulation == CQR_EMU_LEGACY);
+         (o.emulation == CQR_EMU_AUTO || o.emulation == CQR_EMU_OFF || o.emulation == CQR_EMU_TCGEN05);
 }
 
 // Pinned host mirror of the device state, one per host thread.
@@ -341,7 +341,7 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
     x_rows_per_cta = ((tiles + Gx - 1) / Gx) * tr;
   }
   const bool oz = ((P.mode == MODE_FACTOR) || ozu) && (p <= kOzMaxN) && (P.o.emulation != CQR_EMU_OFF);
-  const bool tc05 = P.o.emulation == CQR_EMU_AUTO;
+  const bool tc05 = P.o.emulation == CQR_EMU_TCGEN05;
   const int Goz = oz ? ozgram_grid(P.m, p, tc05) : 0;
   int64_t oz_rows_per_cta = 0;
   if (oz) {
@@ -353,7 +353,12 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
   // solve and the Gramian always run as separate kernels (one chunk for small
   // m), with chunks half as tall since each row is twice as wide.
   const int64_t min_chunk = (p > 64) ? kMinChunkRows / 2 : kMinChunkRows;
-  const int nchunks = oz ? (int)std::max<int64_t>(1, std::min<int64_t>(kMaxChunks, P.m / min_chunk)) : 1;
+  // The tcgen05 Gramian and solve (17 <= n <= 64) each occupy whole SMs, so
+  // chunks on two streams would only queue behind each other: one chunk.
+  const bool tc05_pass = (P.o.emulation == CQR_EMU_TCGEN05) && p >= kTcGramMinN && p <= 64;
+  const int nchunks = (oz && !tc05_pass)
+                          ? (int)std::max<int64_t>(1, std::min<int64_t>(kMaxChunks, P.m / min_chunk))
+                          : 1;
   const bool pipe = oz;
   // the solve of the pipelined passes: Q = Y T on the tensor cores (T = R~^{-1}
   // formed after the control kernel) for 17 <= n <= 128, FP64 substitution
@@ -922,7 +927,7 @@ cqr_status cholqr_gram(const cqr_opts *opts, int64_t m, int64_t n, const double 
   int tile_rows, lds;
   size_t smem;
   rowsweep_geometry(0, p, &tile_rows, &lds, &smem);
-  const bool tc05 = o.emulation == CQR_EMU_AUTO;
+  const bool tc05 = o.emulation == CQR_EMU_TCGEN05;
   const int G = oz ? ozgram_grid(m, p, tc05) : rowsweep_grid(m, tile_rows);
   const int64_t tr = oz ? ozgram_tile_rows() : tile_rows;
   const int64_t tiles = (m + tr - 1) / tr;

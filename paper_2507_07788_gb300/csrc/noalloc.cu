@@ -99,7 +99,7 @@ extern "C" cqr_status cholqr_factor_noalloc(const cqr_opts *opts, int64_t m, int
       o.precision == CQR_PREC_FP64 &&
       o.shift_policy >= CQR_SHIFT_SCHOLQR3 && o.shift_policy <= CQR_SHIFT_ISCHOLQR &&
       (o.stop_rule == CQR_STOP_FROB_TOL || o.stop_rule == CQR_STOP_U_SQRT_N) &&
-      (o.emulation == CQR_EMU_AUTO || o.emulation == CQR_EMU_OFF || o.emulation == CQR_EMU_LEGACY);
+      (o.emulation == CQR_EMU_AUTO || o.emulation == CQR_EMU_OFF || o.emulation == CQR_EMU_TCGEN05);
   if (!opts_ok) return CQR_ERR_INVALID;
   if (n < 1 || m < n || lda < m || ldq < m || ldr < n) return CQR_ERR_INVALID;
   if (A == nullptr || Q == nullptr || R == nullptr) return CQR_ERR_INVALID;

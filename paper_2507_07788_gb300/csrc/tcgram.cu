@@ -35,20 +35,21 @@
 // 64 x 64 x 64.  Two region sets (512 TMEM columns) alternate between tiles,
 // so the products of one tile overlap the drain of the previous one.
 //
-// Roles (384 threads, one CTA per SM; 12 warps of up to 168 registers fit
-// the four 16K-register sub-partitions of an SM):
-//   warps 0-3   split: wait for the TMA tile, hold their 16 columns (two rows
+// Roles (512 threads, one CTA per SM; 16 warps of up to 128 registers, four
+// per 16K-register sub-partition of the SM, so that each scheduler has two
+// splitting warps to hide the latency of the digit arithmetic):
+//   warps 0-7   split: wait for the TMA tile, hold their 8 columns (two rows
 //               per lane) in registers, release the tile, update E_j, write
 //               the 11 planes; one mbarrier phase per tile and plane stage.
 //               Lane 0 of warp 0 also issues the TMA loads of the 64 x 64
-//               FP64 tiles of Y: the next one as soon as all four split warps
-//               have taken the current one into registers.  Lane 0 of warp 1
-//               issues the tile's 40 tcgen05.mma once all four split warps
-//               have written their planes; warp 1 also allocates and frees
-//               the 512 TMEM columns.
-//   warps 4-11  drain: lane L of warp w reads TMEM lane L = 32 (w % 4) + lane
+//               FP64 tiles of Y: the next one as soon as every split warp
+//               has taken the current one into registers.  Lane 0 of warp 1
+//               issues the tile's 40 tcgen05.mma once every split warp has
+//               written its planes; warp 1 also allocates and frees the 512
+//               TMEM columns.
+//   warps 8-15  drain: lane L of warp w reads TMEM lane L = 32 (w % 4) + lane
 //               (entry row L mod 64; orders T0, T2, T4, T6 for L < 64 and T1,
-//               T3, T5 for L >= 64) for 32 columns (half (w - 4) / 4), converts
+//               T3, T5 for L >= 64) for 32 columns (half (w - 8) / 4), converts
 //               the exact FP32 sums to integers and adds them into a 96-bit
 //               integer per entry (int64 high part, uint32 low part).  At the
 //               end the two halves of each entry are added and rounded.
@@ -76,9 +77,10 @@ constexpr int kPlanes = 11;
 constexpr int kPlaneBytes = kNT * kTR * 2;            // 8 KB
 constexpr int kStageBytes = kPlanes * kPlaneBytes;    // 88 KB
 constexpr int kRawBytes = kTR * kNT * 8;              // 32 KB
-constexpr int kSplitWarps = 4, kDrainWarps = 8;
+constexpr int kSplitWarps = 8, kDrainWarps = 8;
+constexpr int kColsPerSplit = kNT / kSplitWarps;      // 8 columns per split warp
 constexpr int kMmaWarp = 1;                           // a split warp: lane 0 issues the MMAs
-constexpr int kTcThreads = (kSplitWarps + kDrainWarps) * 32;  // 384: 3 warps per SM sub-partition
+constexpr int kTcThreads = (kSplitWarps + kDrainWarps) * 32;  // 512: 4 warps of <= 128 registers per sub-partition
 // exponent-growth records in flight: a split warp starts tile k only after
 // the drain of tile k - 5 is done, so 8 slots are never overwritten early
 constexpr int kRing = 8;
@@ -173,7 +175,7 @@ __device__ __forceinline__ void shift96(long long &hi, uint32_t &lo, int D) {
 
 // One CTA: rows [g rows_per_cta, ...) of row group g (rows_per_cta a multiple
 // of 64), in 64-row tiles; writes P (n x n, ld n) to partials[g n n].
-__global__ void __maxnreg__(168) tcgram64_kernel(const __grid_constant__ CUtensorMap tmap, RowSweep a) {
+__global__ void __maxnreg__(128) tcgram64_kernel(const __grid_constant__ CUtensorMap tmap, RowSweep a) {
   if (a.st != nullptr && a.st->done) return;
   extern __shared__ unsigned char smem_dyn[];
   unsigned char *base = (unsigned char *)(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
@@ -217,10 +219,10 @@ __global__ void __maxnreg__(168) tcgram64_kernel(const __grid_constant__ CUtenso
     tma_load_2d(sbase + kOffRaw, &tmap, (int)row0, 0, bar_raw_full);
   }
   if (warp < kSplitWarps) {
-    // ---- split: columns warp * 16 .. + 15, rows 2 lane, 2 lane + 1 of each tile
-    int erun[16];
+    // ---- split: columns warp * 8 .. + 7, rows 2 lane, 2 lane + 1 of each tile
+    int erun[kColsPerSplit];
 #pragma unroll
-    for (int c = 0; c < 16; ++c) erun[c] = 1;
+    for (int c = 0; c < kColsPerSplit; ++c) erun[c] = 1;
     const double *raw = (const double *)(base + kOffRaw);
     constexpr uint32_t idesc = idesc_bf16_f32(128, kNT);
     int issued = 0;  // MMA tiles issued (warp 1, lane 0)
@@ -230,9 +232,9 @@ __global__ void __maxnreg__(168) tcgram64_kernel(const __grid_constant__ CUtenso
         cs->timeout = 1;
         break;
       }
-      double2 v[16];
+      double2 v[kColsPerSplit];
 #pragma unroll
-      for (int c = 0; c < 16; ++c) v[c] = *(const double2 *)(raw + (warp * 16 + c) * kTR + 2 * lane);
+      for (int c = 0; c < kColsPerSplit; ++c) v[c] = *(const double2 *)(raw + (warp * kColsPerSplit + c) * kTR + 2 * lane);
       __syncwarp();
       if (lane == 0) mbar_arrive(bar_raw_empty);
       if (warp == 0 && lane == 0 && k + 1 < ntiles) {
@@ -247,7 +249,7 @@ __global__ void __maxnreg__(168) tcgram64_kernel(const __grid_constant__ CUtenso
       // column exponents: running maximum and its growth in this tile
       int grew = 0, nonfinite = 0;
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
+      for (int c = 0; c < kColsPerSplit; ++c) {
         const int e0 = (int)((__double2hiint(v[c].x) >> 20) & 0x7FF);
         const int e1 = (int)((__double2hiint(v[c].y) >> 20) & 0x7FF);
         const int mx = __reduce_max_sync(0xffffffffu, max(1, max(e0, e1)));
@@ -256,7 +258,7 @@ __global__ void __maxnreg__(168) tcgram64_kernel(const __grid_constant__ CUtenso
         erun[c] = nw;
         grew |= del;
         nonfinite |= (mx == 0x7FF);
-        if (lane == 0) cs->edel[slot][warp * 16 + c] = del;
+        if (lane == 0) cs->edel[slot][warp * kColsPerSplit + c] = del;
       }
       if (lane == 0) {
         cs->grew[slot][warp] = grew;
@@ -271,8 +273,8 @@ __global__ void __maxnreg__(168) tcgram64_kernel(const __grid_constant__ CUtenso
       }
       unsigned char *stage = base + kOffPlanes + s * kStageBytes;
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        const int j = warp * 16 + c;
+      for (int c = 0; c < kColsPerSplit; ++c) {
+        const int j = warp * kColsPerSplit + c;
         const int Ej = erun[c];
         unsigned long long W[2];
         float sg[2];
@@ -344,7 +346,7 @@ __global__ void __maxnreg__(168) tcgram64_kernel(const __grid_constant__ CUtenso
       cs->timeout = 1;  // every issued product completes before TMEM is freed
     if (lane == 0) {
 #pragma unroll
-      for (int c = 0; c < 16; ++c) cs->erun[warp * 16 + c] = erun[c];
+      for (int c = 0; c < kColsPerSplit; ++c) cs->erun[warp * kColsPerSplit + c] = erun[c];
     }
     // the final exponents are published to the drain warps
     named_bar_arrive(kBarErun, (kSplitWarps + kDrainWarps) * 32);
@@ -367,7 +369,10 @@ __global__ void __maxnreg__(168) tcgram64_kernel(const __grid_constant__ CUtenso
         break;
       }
       fence_after_sync();
-      if ((cs->grew[slot][0] | cs->grew[slot][1] | cs->grew[slot][2] | cs->grew[slot][3]) != 0) {
+      int anygrew = 0;
+#pragma unroll
+      for (int w = 0; w < kSplitWarps; ++w) anygrew |= cs->grew[slot][w];
+      if (anygrew != 0) {
         const int ei = cs->edel[slot][ent_i];
         const int4 *ej = (const int4 *)&cs->edel[slot][half * 32];
 #pragma unroll

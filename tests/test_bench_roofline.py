@@ -55,9 +55,11 @@ def test_tensor_pipeline_dominant_kernel():
                  gram_bytes=L * 8.0 * rows * n,
                  tsolve_launches=L, tsolve_ms=L * s_ms, tsolve_flops=L * rows * n * n,
                  tsolve_bytes=L * 16.0 * rows * n, tsolve_tc_flops=L * tc_solve_per_launch)
-    r = bench.roofline_from(tm, 1_000_000, n, 6686.8, "measured", 1730.8, "measured")
+    r = bench.roofline_from(tm, 1_000_000, n, 6686.8, "measured", 1730.8, "measured", tcgen05=True)
     assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["peak"] == 6686.8
     assert r["kernel"].startswith("tcgram64_kernel") and "solve" in r
+    r0 = bench.roofline_from(tm, 1_000_000, n, 6686.8, "measured", 1730.8, "measured")
+    assert r0["kernel"].startswith("ozgram_kernel") and r0["solve"]["kernel"].startswith("ozgemm_kernel")
     # 8 bytes per entry read, in 0.2 ms
     gbs = 8.0 * rows * n / (g_ms * 1e-3) / 1e9
     assert r["achieved"] == pytest.approx(gbs, rel=1e-12)

@@ -358,13 +358,13 @@ def test_emulated_gramian_row_dynamic_range(cq, orc, n):
 
 @pytest.mark.parametrize("m,n", [(130, 17), (5003, 33), (20037, 48), (200003, 64), (257, 64), (129, 20)])
 def test_tcgen05_and_mma_sync_paths_agree(cq, orc, m, n):
-    # the default path (tcgen05 Gramian and solve for 17 <= n <= 64) and the
-    # mma.sync digit kernels (emulation LEGACY) against each other and the
-    # oracle: one tile, a ragged tile of 128 rows, several CTAs
+    # the tcgen05 Gramian and solve (emulation TCGEN05, 17 <= n <= 64) and the
+    # default mma.sync digit kernels against each other and the oracle: one
+    # tile, a ragged tile of 128 rows, several CTAs
     kappa = 1e8
     A = synth.test_matrix(m, n, kappa, rep=21)
-    Qt, Rt, stt, it = run_gpu(cq, A)
-    Ql, Rl, stl, il = run_gpu(cq, A, opts=cq.default_opts(emulation=cq.EMU_LEGACY))
+    Qt, Rt, stt, it = run_gpu(cq, A, opts=cq.default_opts(emulation=cq.EMU_TCGEN05))
+    Ql, Rl, stl, il = run_gpu(cq, A)
     Qo, Ro, sto, io = orc.cholqr(A)
     assert stt == stl == sto == cq.OK
     assert abs(it["iters"] - il["iters"]) <= 1

@@ -1,7 +1,7 @@
 """The Gramian X = A^T A (Alg. 1 line 3) as the library forms it
 (cholqr_gram): tensor-core digit arithmetic (Ozaki splitting) for n <= 128
-(emulation AUTO: the tcgen05 kernel for 17 <= n <= 64 on aligned blocks, the
-warp-level mma.sync kernels otherwise; emulation LEGACY: mma.sync only) and
+(emulation AUTO: the warp-level mma.sync kernels; emulation TCGEN05: the
+tcgen05 kernel for 17 <= n <= 64 on aligned blocks, mma.sync otherwise) and
 FP64 CUDA cores with emulation OFF, against the oracle's FP64 triple loop.
 The tcgen05 and mma.sync kernels form the same exact digit products, but
 each CTA splits X between its partial P and P^T differently (the tcgen05
@@ -94,8 +94,9 @@ def _rne(S: int, scale: int) -> float:
     return float(S) * 2.0 ** scale
 
 
+@pytest.mark.parametrize("emu", [0, 2])
 @pytest.mark.parametrize("n", [16, 40])
-def test_gram_diagonal_is_correctly_rounded(cq, n):
+def test_gram_diagonal_is_correctly_rounded(cq, n, emu):
     # One 64-row tile: a single digit-Gramian CTA rounds each entry once from
     # the exact sum, and the reduction doubles P_jj exactly, so X_jj must be
     # the correctly rounded sum of squares.  Entries are M 2^(k_j - 25) with
@@ -122,7 +123,7 @@ def test_gram_diagonal_is_correctly_rounded(cq, n):
                 break
     assert ties >= n // 2 - 2
     A = M.astype(np.float64) * np.exp2(k - 25)[None, :]
-    X = cq.gram(cq.to_colmajor(A)).cpu().numpy()
+    X = cq.gram(cq.to_colmajor(A), opts=cq.default_opts(emulation=emu)).cpu().numpy()
     for j in range(n):
         S = sum(int(x) * int(x) for x in M[:, j])
         assert X[j, j] == _rne(S, 2 * (int(k[j]) - 25)), (j, X[j, j], _rne(S, 2 * (int(k[j]) - 25)))
@@ -139,8 +140,8 @@ def test_tcgen05_and_mma_sync_gramians_agree(cq, orc, m, n, grow):
     if grow:
         A *= 10.0 ** ((np.arange(m) // 64) % 9 - 4.0)[:, None] * 10.0 ** rng.uniform(-3, 3, size=(1, n))
     dA = cq.to_colmajor(A)
-    Xt = cq.gram(dA).cpu().numpy()
-    Xl = cq.gram(dA, opts=cq.default_opts(emulation=cq.EMU_LEGACY)).cpu().numpy()
+    Xt = cq.gram(dA, opts=cq.default_opts(emulation=cq.EMU_TCGEN05)).cpu().numpy()
+    Xl = cq.gram(dA).cpu().numpy()
     assert np.array_equal(Xt, Xt.T)
     absA = np.abs(A)
     AtA = absA.T @ absA
@@ -156,15 +157,15 @@ def test_tcgen05_gramian_falls_back_on_unaligned_blocks(cq, orc):
     # an odd leading dimension and a block that starts 8 bytes past a 16-byte
     # boundary cannot be described to TMA: the mma.sync kernel forms them
     # (over the tcgen05 kernel's row groups, so the partials differ from the
-    # LEGACY run's and the results agree within their rounding)
+    # default run's and the results agree within their rounding)
     m, n, ld = 20001, 40, 20003
     A = synth.test_matrix(m + 1, n, 1e4, rep=6)
     big = cq.colmajor(ld, n)
     big.zero_()
     big[: m + 1].copy_(torch.from_numpy(A))
     for view, ref in ((big[:m], A[:m]), (big[1: m + 1], A[1:])):
-        X = cq.gram(view).cpu().numpy()
-        Xl = cq.gram(view, opts=cq.default_opts(emulation=cq.EMU_LEGACY)).cpu().numpy()
+        X = cq.gram(view, opts=cq.default_opts(emulation=cq.EMU_TCGEN05)).cpu().numpy()
+        Xl = cq.gram(view).cpu().numpy()
         absA = np.abs(ref)
         AtA = absA.T @ absA
         assert np.all(np.abs(X - Xl) <= 4.0 * (1 + 2 * 152) * U * AtA + 1e-300)
