@@ -59,7 +59,7 @@ constexpr int kOffA = 0;
 constexpr int kOffB = kQDig * kAPlane;            // 128 KB
 constexpr int kOffC = kOffB + kQDig * kBPlane;    // 192 KB
 constexpr int kQSplitW = 8, kQDrainW = 8;
-constexpr int kQThreads = (kQSplitW + kQDrainW) * 32;  // 512
+constexpr int kQThreads = (kQSplitW + kQDrainW) * 32;  // 512, 128 registers each
 constexpr int kQRing = 4;
 constexpr uint64_t kQWaitNs = 2000000000ull;
 constexpr int kNoExpQ = -(1 << 28);               // scaled exponent of a zero
@@ -132,7 +132,7 @@ __device__ __forceinline__ int f2i_q(uint32_t bits) {
 
 // One CTA: rows [g rows_per_cta, ...) of Y (rows_per_cta a multiple of 128)
 // in 128-row tiles; Q = (Y D^-1)(D T) into a.Yout.
-__global__ void __maxnreg__(128) tcgemm64_kernel(RowSweep a) {
+__global__ void __launch_bounds__(kQThreads, 1) tcgemm64_kernel(RowSweep a) {
   if (a.st != nullptr && a.st->done) return;
   const int64_t row0 = (int64_t)blockIdx.x * a.rows_per_cta;
   const int64_t row1 = min(a.m, row0 + a.rows_per_cta);
@@ -265,12 +265,14 @@ __global__ void __maxnreg__(128) tcgemm64_kernel(RowSweep a) {
                (k < 1 || mbar_wait(smem_addr(&cs->r1_empty), (k - 1) & 1, kQWaitNs));
           if (ok) {
             fence_after_sync();
+            // K step by K step, alternating the orders' accumulators (the
+            // first pair of each order, at K step 0, overwrites it)
 #pragma unroll
-            for (int o = 0; o < 4; ++o)
+            for (int ks = 0; ks < 4; ++ks)
 #pragma unroll
-              for (int i = 0; i <= o; ++i)
+              for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int ks = 0; ks < 4; ++ks)
+                for (int o = i; o < 4; ++o)
                   mma_ss(tmem + (uint32_t)(o * kQN), sdesc_sw128(sbase + kOffA + i * kAPlane + ks * 32),
                          sdesc_sw128(sbase + kOffB + (o - i) * kBPlane + ks * 32), idesc,
                          (i == 0 && ks == 0) ? 0u : 1u);
@@ -280,14 +282,15 @@ __global__ void __maxnreg__(128) tcgemm64_kernel(RowSweep a) {
           if (ok) {
             fence_after_sync();
 #pragma unroll
-            for (int o = 4; o < 8; ++o)
+            for (int ks = 0; ks < 4; ++ks)
 #pragma unroll
-              for (int i = 0; i <= o; ++i)
+              for (int i = 0; i < 8; ++i)
 #pragma unroll
-                for (int ks = 0; ks < 4; ++ks)
-                  mma_ss(tmem + (uint32_t)(256 + (o - 4) * kQN), sdesc_sw128(sbase + kOffA + i * kAPlane + ks * 32),
-                         sdesc_sw128(sbase + kOffB + (o - i) * kBPlane + ks * 32), idesc,
-                         (i == 0 && ks == 0) ? 0u : 1u);
+                for (int o = 4; o < 8; ++o)
+                  if (i <= o)
+                    mma_ss(tmem + (uint32_t)(256 + (o - 4) * kQN), sdesc_sw128(sbase + kOffA + i * kAPlane + ks * 32),
+                           sdesc_sw128(sbase + kOffB + (o - i) * kBPlane + ks * 32), idesc,
+                           (i == 0 && ks == 0) ? 0u : 1u);
             mma_commit(smem_addr(&cs->r2_full));
             mma_commit(smem_addr(&cs->planes_empty));
             ++issued;
@@ -320,12 +323,12 @@ __global__ void __maxnreg__(128) tcgemm64_kernel(RowSweep a) {
 #pragma unroll
       for (int o = 0; o < 4; ++o)
 #pragma unroll
-        for (int c8 = 0; c8 < 32; c8 += 8) {
-          uint32_t x[8];
-          tmem_ld8(tl + (uint32_t)(o * kQN + c8), x);
+        for (int c16 = 0; c16 < 32; c16 += 16) {
+          uint32_t x[16];
+          tmem_ld16(tl + (uint32_t)(o * kQN + c16), x);
           tmem_wait_ld();
 #pragma unroll
-          for (int e = 0; e < 8; ++e) hi[c8 + e] += (long long)f2i_q(x[e]) << (8 * (3 - o));
+          for (int e = 0; e < 16; ++e) hi[c16 + e] += (long long)f2i_q(x[e]) << (8 * (3 - o));
         }
       fence_before_sync();
       __syncwarp();
@@ -338,27 +341,27 @@ __global__ void __maxnreg__(128) tcgemm64_kernel(RowSweep a) {
       const int er = cs->erow[slot][row];
       const bool bad = cs->rbad[slot][row] != 0 || cs->timeout != 0;
       const int64_t rr = row0 + (int64_t)k * kQR + row;
-      // round 2: lo = T4 2^24 + T5 2^16 + T6 2^8 + T7, eight columns at a time;
-      // Q_rj = (hi 2^32 + lo) 2^(e_r + f_j - 2114), rounded once
+      // round 2: lo = T4 2^24 + T5 2^16 + T6 2^8 + T7, sixteen columns at a
+      // time; Q_rj = (hi 2^32 + lo) 2^(e_r + f_j - 2114), rounded once
 #pragma unroll
-      for (int c8 = 0; c8 < 32; c8 += 8) {
-        long long lo[8];
+      for (int c16 = 0; c16 < 32; c16 += 16) {
+        long long lo[16];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) lo[e] = 0;
+        for (int e = 0; e < 16; ++e) lo[e] = 0;
 #pragma unroll
         for (int o = 4; o < 8; ++o) {
-          uint32_t x[8];
-          tmem_ld8(tl + (uint32_t)(256 + (o - 4) * kQN + c8), x);
+          uint32_t x[16];
+          tmem_ld16(tl + (uint32_t)(256 + (o - 4) * kQN + c16), x);
           tmem_wait_ld();
 #pragma unroll
-          for (int e = 0; e < 8; ++e) lo[e] += (long long)f2i_q(x[e]) << (8 * (7 - o));
+          for (int e = 0; e < 16; ++e) lo[e] += (long long)f2i_q(x[e]) << (8 * (7 - o));
         }
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int j = half * 32 + c8 + e;
+        for (int e = 0; e < 16; ++e) {
+          const int j = half * 32 + c16 + e;
           if (rr < row1 && j < n) {
             const double v = bad ? __longlong_as_double(0x7FF8000000000000ll)
-                                 : oz::fixed_to_double(hi[c8 + e], lo[e], 32, er + cs->fcol[j] - 2114);
+                                 : oz::fixed_to_double(hi[c16 + e], lo[e], 32, er + cs->fcol[j] - 2114);
             a.Yout[rr + (int64_t)j * a.ldyout] = v;
           }
         }

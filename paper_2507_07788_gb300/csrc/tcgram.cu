@@ -80,7 +80,12 @@ constexpr int kRawBytes = kTR * kNT * 8;              // 32 KB
 constexpr int kSplitWarps = 8, kDrainWarps = 8;
 constexpr int kColsPerSplit = kNT / kSplitWarps;      // 8 columns per split warp
 constexpr int kMmaWarp = 1;                           // a split warp: lane 0 issues the MMAs
-constexpr int kTcThreads = (kSplitWarps + kDrainWarps) * 32;  // 512: 4 warps of <= 128 registers per sub-partition
+constexpr int kTcThreads = (kSplitWarps + kDrainWarps) * 32;  // 512, launched with 128 registers each
+// setmaxnreg: the split warpgroups give registers to the drain warpgroups
+// (8 x 32 x 80 + 8 x 32 x 176 = 512 x 128)
+constexpr int kSplitRegs = 80, kDrainRegs = 176;
+static_assert(kSplitWarps * kSplitRegs + kDrainWarps * kDrainRegs == (kSplitWarps + kDrainWarps) * 128,
+              "register reallocation must add up to the launch's registers");
 // exponent-growth records in flight: a split warp starts tile k only after
 // the drain of tile k - 5 is done, so 8 slots are never overwritten early
 constexpr int kRing = 8;
@@ -109,14 +114,25 @@ static_assert(kSmemBytes <= 227 * 1024, "shared memory of the tcgen05 Gramian");
 static_assert(kStageBytes % 1024 == 0 && kOffRaw % 1024 == 0, "1024-byte aligned operands");
 static_assert(kDrainWarps * 32 * 12 <= 2 * kStageBytes, "the final combine fits in the plane stages");
 
-// (A plane, B plane, region) of the 10 MMAs of a tile; the first MMA of each
-// region overwrites it
+// (A plane, B plane, region, overwrites) of the 10 MMAs of a tile, in the
+// order they are issued within a K step: regions 0, 1, 2, 3, 1, 2, 3, 2, 3, 3,
+// so that consecutive MMAs rarely wait for each other's accumulator; the first
+// MMA into each region overwrites it
 struct MmaUnit {
-  int a, b, r;
+  int a, b, r, first;
 };
-__constant__ MmaUnit kUnits[10] = {{1, 1, 0}, {4, 1, 1}, {3, 3, 1}, {6, 1, 2}, {5, 3, 2},
-                                   {9, 9, 2}, {8, 1, 3}, {7, 3, 3}, {6, 9, 3}, {0, 0, 3}};
-__host__ __device__ constexpr bool first_of_region(int u) { return u == 0 || u == 1 || u == 3 || u == 6; }
+__host__ __device__ constexpr MmaUnit mma_unit(int q) {
+  return q == 0   ? MmaUnit{1, 1, 0, 1}
+         : q == 1 ? MmaUnit{4, 1, 1, 1}
+         : q == 2 ? MmaUnit{6, 1, 2, 1}
+         : q == 3 ? MmaUnit{8, 1, 3, 1}
+         : q == 4 ? MmaUnit{3, 3, 1, 0}
+         : q == 5 ? MmaUnit{5, 3, 2, 0}
+         : q == 6 ? MmaUnit{7, 3, 3, 0}
+         : q == 7 ? MmaUnit{9, 9, 2, 0}
+         : q == 8 ? MmaUnit{6, 9, 3, 0}
+                  : MmaUnit{0, 0, 3, 0};
+}
 
 // named barriers (0 is __syncthreads)
 constexpr int kBarErun = 1;   // split warps publish the final exponents to the drain warps
@@ -175,7 +191,7 @@ __device__ __forceinline__ void shift96(long long &hi, uint32_t &lo, int D) {
 
 // One CTA: rows [g rows_per_cta, ...) of row group g (rows_per_cta a multiple
 // of 64), in 64-row tiles; writes P (n x n, ld n) to partials[g n n].
-__global__ void __maxnreg__(128) tcgram64_kernel(const __grid_constant__ CUtensorMap tmap, RowSweep a) {
+__global__ void __launch_bounds__(kTcThreads, 1) tcgram64_kernel(const __grid_constant__ CUtensorMap tmap, RowSweep a) {
   if (a.st != nullptr && a.st->done) return;
   extern __shared__ unsigned char smem_dyn[];
   unsigned char *base = (unsigned char *)(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
@@ -219,6 +235,7 @@ __global__ void __maxnreg__(128) tcgram64_kernel(const __grid_constant__ CUtenso
     tma_load_2d(sbase + kOffRaw, &tmap, (int)row0, 0, bar_raw_full);
   }
   if (warp < kSplitWarps) {
+    regs_dec<kSplitRegs>();
     // ---- split: columns warp * 8 .. + 7, rows 2 lane, 2 lane + 1 of each tile
     int erun[kColsPerSplit];
 #pragma unroll
@@ -320,16 +337,17 @@ __global__ void __maxnreg__(128) tcgram64_kernel(const __grid_constant__ CUtenso
             fence_after_sync();
             const uint32_t stage = sbase + kOffPlanes + s * kStageBytes;
             const uint32_t dbase = tmem + (uint32_t)(s * 4 * kNT);
+            // K step by K step; the first MMA into each region (its first
+            // unit, K step 0) overwrites it
 #pragma unroll
-            for (int u = 0; u < 10; ++u) {
-              const MmaUnit U = kUnits[u];
+            for (int ks = 0; ks < 4; ++ks)
 #pragma unroll
-              for (int ks = 0; ks < 4; ++ks) {
+              for (int q = 0; q < 10; ++q) {
+                const MmaUnit U = mma_unit(q);
                 const uint64_t ad = sdesc_sw128(stage + U.a * kPlaneBytes + ks * 32);
                 const uint64_t bd = sdesc_sw128(stage + U.b * kPlaneBytes + ks * 32);
-                mma_ss(dbase + (uint32_t)(U.r * kNT), ad, bd, idesc, (first_of_region(u) && ks == 0) ? 0u : 1u);
+                mma_ss(dbase + (uint32_t)(U.r * kNT), ad, bd, idesc, (U.first && ks == 0) ? 0u : 1u);
               }
-            }
             mma_commit(smem_addr(&cs->planes_empty[s]));
             mma_commit(smem_addr(&cs->acc_full[s]));
             ++issued;
@@ -351,6 +369,7 @@ __global__ void __maxnreg__(128) tcgram64_kernel(const __grid_constant__ CUtenso
     // the final exponents are published to the drain warps
     named_bar_arrive(kBarErun, (kSplitWarps + kDrainWarps) * 32);
   } else {
+    regs_inc<kDrainRegs>();
     // ---- drain: TMEM lane lrow, columns half * 32 .. + 31; entry
     // (ent_i, half * 32 + c) of this thread's side in hi[c] 2^32 + lo[c]
     long long hi[32];
@@ -392,21 +411,19 @@ __global__ void __maxnreg__(128) tcgram64_kernel(const __grid_constant__ CUtenso
         if (side == 1 && r == 3) break;  // the bottom half of R3 is unused
         const int o = 2 * r + side;
         const int w = 8 * (6 - o);       // 48, 32, 16, 0 (top) / 40, 24, 8 (bottom)
+        // the region's 32 columns in one load and one wait
+        uint32_t x[32];
+        tmem_ld32(tb + (uint32_t)(r * kNT), x);
+        tmem_wait_ld();
 #pragma unroll
-        for (int c8 = 0; c8 < 32; c8 += 8) {
-          uint32_t x[8];
-          tmem_ld8(tb + (uint32_t)(r * kNT + c8), x);
-          tmem_wait_ld();
-#pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            const long long tv = (long long)f2i_exact(x[e]);
-            if (w >= 32) {
-              hi[c8 + e] += tv << (w - 32);
-            } else {
-              const long long sum = (long long)lo[c8 + e] + (tv << w);
-              lo[c8 + e] = (uint32_t)sum;
-              hi[c8 + e] += sum >> 32;
-            }
+        for (int e = 0; e < 32; ++e) {
+          const long long tv = (long long)f2i_exact(x[e]);
+          if (w >= 32) {
+            hi[e] += tv << (w - 32);
+          } else {
+            const long long sum = (long long)lo[e] + (tv << w);
+            lo[e] = (uint32_t)sum;
+            hi[e] += sum >> 32;
           }
         }
       }
