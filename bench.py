@@ -478,7 +478,10 @@ def leg_update(cq, torch, m, p=8, count=32, seed=0, cache=True):
 
 
 def leg_mixed(cq, torch, synth, m, n=128, kappas=(1e6, 1e10, 1e14), steps=3):
-    """Mixed precision vs plain FP64 at m x 128 on the same matrices."""
+    """Mixed precision vs plain FP64 at m x 128 on the same matrices; beside
+    each factorisation, its first-pass Gramian alone (cholqr_gram with the
+    same options: the exact digit Gramian for FP64, the reduced-digit one for
+    mixed)."""
     out = []
     for kap in kappas:
         A = synth.test_matrix(m, n, kap, rep=21)
@@ -492,9 +495,18 @@ def leg_mixed(cq, torch, synth, m, n=128, kappas=(1e6, 1e10, 1e14), steps=3):
             Gm = dQ.t() @ dQ
             loo = float(torch.linalg.norm(Gm - torch.eye(n, dtype=Gm.dtype, device=Gm.device)))
             rrr = float(torch.linalg.norm(dA - dQ @ torch.triu(dR)) / torch.linalg.norm(dA))
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            cq.gram(dA, opts=o)
+            torch.cuda.synchronize()
+            g0.record()
+            for _ in range(steps):
+                cq.gram(dA, opts=o)
+            g1.record()
+            torch.cuda.synchronize()
             row[name] = {"ms": ms, "rows_cols_per_s": m * n / (ms * 1e-3), "iters": res.info["iters"],
                          "status": res.status, "loo_frob": loo, "rrr_frob": rrr,
-                         "sigma_first": res.info["sigma_first"]}
+                         "sigma_first": res.info["sigma_first"],
+                         "first_gram_ms": g0.elapsed_time(g1) / steps}
         row["speedup_mixed_vs_fp64"] = row["fp64"]["ms"] / row["mixed"]["ms"]
         out.append(row)
         del dA, dQ, dR
@@ -533,24 +545,48 @@ def leg_pn(cq, torch, synth, m, n=64, kappa=1e12, rs=(1, 2, 4, 8), steps=2):
             "scholqr3_ms": ms_f, "scholqr3_iters": rf.info["iters"], "rows": rows}
 
 
-def leg_serve(cq, torch, n_requests=512):
-    """Serving: Poisson arrivals (mean 2 ms, seed 0) of factor / append requests
-    over 64 device-resident bases (m log-uniform in [1e4, 2e6], capacity 256);
+def leg_serve(cq, torch, n_requests=512, utilization=0.7):
+    """Serving: Poisson arrivals (seed 0) of factor / append requests over 64
+    device-resident bases (m log-uniform in [1e4, 2e6], capacity 256);
     factors n in [8, 128], kappa log-uniform in [1e2, 1e14]; appends of 4..32
-    columns; 50/50 mix.  Latency = completion - arrival."""
+    columns; 50/50 mix.  The requests are first served one at a time (each
+    submitted when the previous completed) to measure their mean service
+    time S; the arrival process is then scaled to mean gap S / utilization
+    and replayed in real time on fresh bases.  Latency = completion -
+    submission."""
+    import numpy as np
     from paper_2507_07788_gb300 import serve_driver as sd
     t0 = time.perf_counter()
-    wl = sd.make_workload(n_bases=64, n_requests=n_requests, mean_gap_s=2e-3, seed=0)
+    wl = sd.make_workload(n_bases=64, n_requests=n_requests, mean_gap_s=1.0, seed=0)
     sd.make_payloads(wl, seed=0)
-    bases = sd.make_bases(cq, wl)
     gen_s = time.perf_counter() - t0
-    srv = cq.Server(slots=4, batch_max=16, hbm_budget_bytes=16 << 30, small_rows=262144)
+
+    def server():
+        return cq.Server(slots=4, batch_max=16, hbm_budget_bytes=16 << 30, small_rows=262144)
+
+    bases = sd.make_bases(cq, wl)
+    srv = server()
+    sd.run_alone(cq, srv, bases, wl)
+    srv.close()
+    for b in bases:
+        b.close()
+    alone = sd.service_times(wl)
+    s_mean = float(alone.mean())
+    gap = s_mean / utilization
+    sd.scale_arrivals(wl, gap)
+    bases = sd.make_bases(cq, wl)
+    srv = server()
     info = sd.replay(cq, srv, bases, wl, realtime=True)
     srv.close()
     st = sd.latency_stats(wl)
     st.update(info)
-    st["workload"] = (f"{n_requests} requests, Poisson mean 2 ms, 64 bases m log-uniform [1e4, 2e6], "
-                      "factor n U[8,128] kappa logU[1e2,1e14] / append p U[4,32], 50/50, FP64")
+    st["utilization"] = utilization
+    st["alone"] = {"mean_ms": s_mean * 1e3, "p50_ms": float(np.percentile(alone, 50) * 1e3),
+                   "p99_ms": float(np.percentile(alone, 99) * 1e3)}
+    st["mean_gap_ms"] = gap * 1e3
+    st["workload"] = (f"{n_requests} requests, Poisson arrivals at mean gap = mean service time alone / "
+                      f"{utilization}, 64 bases m log-uniform [1e4, 2e6], factor n U[8,128] kappa "
+                      "logU[1e2,1e14] / append p U[4,32], 50/50, FP64")
     st["arrival_span_s"] = wl.reqs[-1].arrival
     st["setup_s"] = gen_s
     st["factors"] = sum(1 for r in wl.reqs if r.kind == "factor")

@@ -81,9 +81,19 @@ enum {
 enum { CQR_STOP_FROB_TOL = 0, CQR_STOP_U_SQRT_N = 1 };
 
 /* Arithmetic of the row-sweeping kernels.  CQR_PREC_FP64: every step in FP64.
- * CQR_PREC_MIXED: the Gramian of the first (shifted) pass is formed from
- * inputs rounded to FP32 with FP32 products, the shift is sized for that
- * roundoff; everything else stays FP64. */
+ * CQR_PREC_MIXED (cholqr_factor only): the Gramian of the first (shifted)
+ * pass is formed at reduced precision and the first shift is sized for its
+ * error bound, in the form of Alg. 1 line 6; the norm estimate, Cholesky,
+ * solves and all later passes stay FP64.  With the digit kernels (n <= 128,
+ * emulation not CQR_EMU_OFF, no reducer) that Gramian keeps 5 balanced
+ * base-256 digits (40 bits relative to each column's largest binary
+ * exponent E_j) and the digit orders <= 4 on the tensor cores, and
+ *   sigma = 11 (m e sum_j 4^(E_j - 1022) + n (n + 1 + G + 9) u ||X||),
+ * e = 2.0324e-12 (a row's error bound in units of 2^(E_i + E_j - 2044)),
+ * G = the kernel's partial count, u = 2^-53.  Otherwise (emulation off, wider
+ * n, or cholqr_factor_sharded, whose shift must not depend on the rank's
+ * rows) it is formed from inputs truncated to FP32 with FP32 products and
+ *   sigma = 11 (n (2 2^-23 + 66 2^-24) + n (n + 1) u) ||X||. */
 enum { CQR_PREC_FP64 = 0, CQR_PREC_MIXED = 1 };
 
 typedef struct cqr_opts {
@@ -168,7 +178,9 @@ cqr_status cholqr_factor(const cqr_opts *opts, int64_t m, int64_t n, const doubl
  * cholqr_gram -- the Gramian X = A^T A of Alg. 1 line 3, formed by the same
  * row sweep and fixed-order reduction as the factorisation's first pass
  * (tensor-core digit arithmetic for n <= 128 unless opts->emulation is
- * CQR_EMU_OFF; FP64 CUDA cores otherwise).
+ * CQR_EMU_OFF; FP64 CUDA cores otherwise).  With opts->precision =
+ * CQR_PREC_MIXED it is the first-pass Gramian of the mixed factorisation
+ * (5-digit on the tensor cores, or FP32 with CQR_EMU_OFF; see CQR_PREC_MIXED).
  *   A, lda    device, m x n, lda >= m (read only).
  *   X, ldx    device, n x n output (both triangles), ldx >= n.
  *   1 <= n <= CQR_MAX_N, m >= 1.

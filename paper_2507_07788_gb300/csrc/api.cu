@@ -217,6 +217,7 @@ struct Scratch {
   int *Tscale;
   uint16_t *Bd;  // digits of the scaled B~ (cached-digit projection)
   int *fexp;
+  int *emax;     // column exponents of the reduced-digit first Gramian
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -231,7 +232,8 @@ cudaError_t scratch_alloc(Scratch &s, int q, int p, int G, int64_t E, cudaStream
   keep_pool_memory();
   const size_t b_Ts = align256(sizeof(int) * (size_t)p);
   const size_t b_Bd = align256(ozcproj_scratch_bytes());
-  cudaError_t e = cudaMallocAsync((void **)&s.base, b_st + b_C + 2 * b_Rt + b_Rd + b_Bt + b_Ts + b_Bd + b_P, str);
+  cudaError_t e =
+      cudaMallocAsync((void **)&s.base, b_st + b_C + 2 * b_Rt + b_Rd + b_Bt + 2 * b_Ts + b_Bd + b_P, str);
   if (e != cudaSuccess) return e;
   char *p0 = s.base;
   s.st = (DevState *)p0;
@@ -247,6 +249,8 @@ cudaError_t scratch_alloc(Scratch &s, int q, int p, int G, int64_t E, cudaStream
   s.Tinv = (double *)p0;
   p0 += b_Rt;
   s.Tscale = (int *)p0;
+  p0 += b_Ts;
+  s.emax = (int *)p0;
   p0 += b_Ts;
   s.Bd = (uint16_t *)p0;
   s.fexp = (int *)(p0 + sizeof(uint16_t) * 7 * 16 * (256 + 8));
@@ -308,8 +312,22 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
   // u_in = 2^-23 (truncation to FP32), u_acc = 2^-24, d = FP32 summation
   // depth of one partial, u = 2^-53 for the FP64 Cholesky.
   const bool mixed = (P.mode == MODE_FACTOR) && (P.o.precision == CQR_PREC_MIXED);
-  double mixed_coeff = 0.0;
-  if (mixed) {
+  // With the digit kernels (n <= 128, emulation on, one process) the first
+  // Gramian is the reduced-digit one (kOzMixedDigits digits) and its shift
+  //   sigma = 11 (m e_row sum_j Ubar_j^2 + n (n + 1 + G + 9) u ||X||)
+  // covers its truncation (m rows of at most e_row Ubar_i Ubar_j each, a
+  // rank-one bound of norm e_row sum_j Ubar_j^2), the single rounding of the
+  // G partials and their fixed-order sum (at most (G + 9) u ||X|| per entry)
+  // and the FP64 Cholesky (n (n + 1) u ||X||), in the form of Alg. 1 line 6.
+  // Otherwise it is the FP32 sweep.  A sharded factorisation keeps the FP32
+  // sweep: its shift does not depend on the rank's rows.
+  const bool mixed_oz = mixed && (p <= kOzMaxN) && (P.o.emulation != CQR_EMU_OFF) && (P.red == nullptr);
+  double mixed_coeff = 0.0, mixed_emax_coeff = 0.0;
+  const int Gmix = mixed_oz ? ozgram_grid(P.m, p, false) : 0;  // partials of that Gramian
+  if (mixed_oz) {
+    mixed_coeff = 11.0 * (double)p * ((double)p + 1.0 + (double)Gmix + 9.0) * kU64;
+    mixed_emax_coeff = 11.0 * (double)P.m * kOzMixedRowErr;
+  } else if (mixed) {
     const double u_in = 1.1920928955078125e-07, u_acc = 5.9604644775390625e-08;
     mixed_coeff = 11.0 * ((double)p * (2.0 * u_in + kGram32Depth * u_acc) +
                           (double)p * (p + 1.0) * kU64);
@@ -379,7 +397,8 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
   CopyCtx *cx = (P.hA != nullptr && pipe && !mixed && ax != nullptr) ? copy_ctx(nchunks) : nullptr;
   const bool stage = cx != nullptr;
   if (P.hq_written != nullptr) *P.hq_written = false;
-  const int64_t oz_parts = oz ? std::max<int64_t>((int64_t)Goz, (int64_t)Gc) * p * p : 0;
+  const int64_t oz_parts =
+      oz ? std::max<int64_t>(std::max<int64_t>((int64_t)Goz, (int64_t)Gc), (int64_t)Gmix) * p * p : 0;
   const int64_t x_parts = (xoz || cxg) ? (int64_t)Gx * (q + p) * p : 0;
   const int64_t part_elems = std::max<int64_t>(E, (std::max(oz_parts, x_parts) + G - 1) / G);
   bool last_x = false;   // the last sweep left dense cross-Gramian partials
@@ -562,10 +581,26 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
       if (mk != nullptr) cudaEventRecord(mk->b, str);
       return e;
     }
-    if (oz && !(first && !trsm && mixed)) {
+    if (oz && !(first && !trsm && mixed && !mixed_oz)) {
       RowSweep z = a;
       z.rows_per_cta = oz_rows_per_cta;
       z.E = (int64_t)p * p;
+      if (first && !trsm && mixed_oz) {
+        // the reduced-digit Gramian on the mma.sync kernel, which records
+        // the column exponents for the shift
+        const int64_t tiles = (P.m + ozgram_tile_rows() - 1) / ozgram_tile_rows();
+        z.rows_per_cta = ((tiles + Gmix - 1) / Gmix) * ozgram_tile_rows();
+        z.digits = kOzMixedDigits;
+        z.emax = s.emax;
+        z.tc05 = 0;
+        e = cudaMemsetAsync(s.emax, 0, sizeof(int) * p, str);
+        if (e == cudaSuccess) e = launch_ozgram(z, Gmix, str);
+        g_launches++;
+        last_oz = true;
+        last_oz_G = Gmix;
+        if (mk != nullptr) cudaEventRecord(mk->b, str);
+        return e;
+      }
       SweepMark *mg = trsm ? nullptr : kmark(MARK_GRAM, 0, m_d * p * (p + 1.0), 8.0 * m_d * p);
       if (mg) cudaEventRecord(mg->a, str);
       e = launch_ozgram(z, Goz, str);
@@ -640,6 +675,8 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
     c.stop_rule = P.o.stop_rule;
     c.tol = P.o.tol;
     c.first_shift_coeff = mixed_coeff;
+    c.emax = mixed_oz ? s.emax : nullptr;
+    c.emax_coeff = mixed_emax_coeff;
     c.C = s.C;
     c.Rt = s.Rt;
     c.Rdinv = s.Rdinv;
@@ -927,7 +964,10 @@ cqr_status cholqr_gram(const cqr_opts *opts, int64_t m, int64_t n, const double 
   int tile_rows, lds;
   size_t smem;
   rowsweep_geometry(0, p, &tile_rows, &lds, &smem);
-  const bool tc05 = o.emulation == CQR_EMU_TCGEN05;
+  // CQR_PREC_MIXED: the Gramian of the mixed factorisation's first pass
+  // (reduced-digit on the tensor cores, or FP32 with emulation off)
+  const bool mixed = o.precision == CQR_PREC_MIXED;
+  const bool tc05 = (o.emulation == CQR_EMU_TCGEN05) && !mixed;
   const int G = oz ? ozgram_grid(m, p, tc05) : rowsweep_grid(m, tile_rows);
   const int64_t tr = oz ? ozgram_tile_rows() : tile_rows;
   const int64_t tiles = (m + tr - 1) / tr;
@@ -949,7 +989,21 @@ cqr_status cholqr_gram(const cqr_opts *opts, int64_t m, int64_t n, const double 
   a.do_trsm = 0;
   a.st = nullptr;
   a.tc05 = tc05 ? 1 : 0;
-  cudaError_t e = oz ? launch_ozgram(a, G, str) : launch_rowsweep(a, G, str);
+  cudaError_t e = cudaSuccess;
+  if (oz) {
+    if (mixed) {
+      a.digits = kOzMixedDigits;
+      a.emax = s.emax;
+      e = cudaMemsetAsync(s.emax, 0, sizeof(int) * p, str);
+    }
+    if (e == cudaSuccess) e = launch_ozgram(a, G, str);
+  } else if (mixed) {
+    size_t smem32;
+    gram32_geometry(0, p, &a.tile_rows, &a.lds, &smem32);
+    e = launch_gram32(a, G, str);
+  } else {
+    e = launch_rowsweep(a, G, str);
+  }
   g_launches++;
   if (e == cudaSuccess) {
     if (oz) {

@@ -93,6 +93,8 @@ struct RowSweep {
   const int *Tscale;    // p: log2 of D (column k of Y is divided, row k of T multiplied, by 2^Tscale[k])
   const DevState *st;
   int32_t tc05;         // 1: the tcgen05 kernels may be used where they apply
+  int32_t digits;       // digit Gramian: 0 (= 7, exact FP64) or kOzMixedDigits
+  int *emax;            // digit Gramian: atomicMax of the final column exponents (or null)
 };
 
 struct Reduce {
@@ -113,8 +115,13 @@ struct Ctrl {
   int32_t shift_policy, max_iter, min_iter, max_escalations, stop_rule;
   double tol;
   // Mixed precision: when > 0 the first pass is always shifted by
-  // max(first_shift_coeff * ||X||, 2u) (the Gramian came from FP32 data).
+  // max(first_shift_coeff * ||X|| + emax_coeff * sum_j 4^(emax_j - 1022), 2u)
+  // (the Gramian came from FP32 data, emax null, or from the reduced-digit
+  // Gramian, whose error bound is per row emax_coeff / m Ubar_i Ubar_j with
+  // Ubar_j = 2^(emax_j - 1022)).
   double first_shift_coeff;
+  const int *emax;      // p column exponents of the first Gramian (or null)
+  double emax_coeff;
   int32_t r_external;  // 1: R <- R~ R is left to launch_rupdate (factor mode)
   const double *C;  // (q + p) x p, ld q + p
   double *Rt;       // p x p, ld p
@@ -169,6 +176,12 @@ cudaError_t launch_ozgram(const RowSweep &a, int grid, cudaStream_t s);
 cudaError_t launch_reduce_oz(const double *partials, int G, int n, double *C, const DevState *st,
                              cudaStream_t s);
 int ozgram_grid(int64_t m, int n, bool tc05 = true);
+// Reduced-digit Gramian of the mixed-precision first pass: 5 balanced
+// base-256 digits, orders <= 4; per row it adds less than
+// kOzMixedRowErr Ubar_i Ubar_j to X_ij (Ubar_j = 2^(E_j - 1022) for the
+// column's largest biased exponent E_j).
+constexpr int kOzMixedDigits = 5;
+constexpr double kOzMixedRowErr = 2.0324e-12;  // about 2^-38.84: 2^-38.99 plus the floor rescalings, with margin
 // Q = Y T (T = R~^{-1}) on the tensor cores, exact digit products, 33 <= n <= 128.
 cudaError_t launch_ozgemm(const RowSweep &a, int grid, cudaStream_t s);
 int ozgemm_grid(int64_t m, int n, bool tc05 = true);

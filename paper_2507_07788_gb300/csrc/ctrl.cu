@@ -252,7 +252,17 @@ __device__ void ctrl_body(const Ctrl &c, double *sm) {
     const double sigma_once = st->sigma_once;  // read before thread 0 may set it
     if (shifted_first) {
       const double lam = norm_estimate(X, p, (float *)Rk, v, w, fred, red);
-      sigma = mixed_first ? fmax(c.first_shift_coeff * lam, 2.0 * kU64) : shift_alg1(c.m, p, lam);
+      if (mixed_first) {
+        // the reduced-digit Gramian's bound: emax_coeff sum_j Ubar_j^2
+        // (largest eigenvalue of the rank-one bound Ubar Ubar^T), summed in
+        // column order
+        double ub = 0.0;
+        if (c.emax != nullptr)
+          for (int j = 0; j < p; ++j) ub += ldexp(1.0, 2 * (c.emax[j] - 1022));
+        sigma = fmax(c.first_shift_coeff * lam + c.emax_coeff * ub, 2.0 * kU64);
+      } else {
+        sigma = shift_alg1(c.m, p, lam);
+      }
       ++shifts;
       s_first = sigma;
     }

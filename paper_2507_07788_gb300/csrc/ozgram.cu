@@ -58,7 +58,7 @@ struct OzCfg {
   static constexpr int warps = threads / 32;
   static constexpr int ctas = (NT > 64) ? 1 : 2;     // CTAs per SM
 };
-constexpr int kOzDigits = 7;   // balanced base-256 digits of 56 bits
+constexpr int kOzDigits = 7;   // balanced base-256 digits of 56 bits (planes allocated for all 7)
 
 // Orders 0..6 split into `groups` groups ({0, 6}, {1, 5}, {2, 4}, {3} for
 // four groups): does group grp own order o?
@@ -99,8 +99,22 @@ __host__ __device__ constexpr OzGeom oz_geom(int NT, int PR) {
 // optional FP64 row solve (Alg. 1 line 9, n <= 64) before the Gramian of the
 // tile.  Writes rows [h PR, (h+1) PR) of the group's partial P (n x n, ld n)
 // to partials[g * n * n], h = the CTA's half.
-template <int NT>
+//
+// ND = 7 is the exact FP64 Gramian described above.  ND = 5 (the first pass
+// of the mixed-precision variant) keeps the leading 5 balanced digits of
+// each element and the orders o <= 4 (9 of the 16 symmetric digit pairs):
+// with U_j = 2^(E_j - 1078) and Ubar_j = 2^56 U_j (> |y_rj|), the dropped
+// digits are at most 128 (2^8 + 1) U_j < 2^15.006 U_j per element (plus
+// < U_j from the truncation to 56 bits) and the dropped orders 5..8 of a
+// row's product at most (4 2^70 + 3 2^62 + ...) U_i U_j < 2^72.005 U_i U_j,
+// so each row adds less than 2^73.01 U_i U_j = 2^-38.99 Ubar_i Ubar_j of
+// error to X_ij (the floor rescalings add < 2^-65 Ubar_i Ubar_j per tile).
+// With `emax` set the CTA records its final column exponents there
+// (atomicMax), for the shift that covers this error.
+template <int NT, int ND>
 __global__ void __launch_bounds__(OzCfg<NT>::threads, OzCfg<NT>::ctas) ozgram_kernel(RowSweep a) {
+  static_assert(ND == 7 || ND == 5, "digit counts of the Gramian");
+  constexpr int kMaxOrder = ND - 1;
   if (a.st != nullptr && a.st->done) return;
   constexpr int JB = (NT >= 32) ? 32 : 16;
   constexpr int NTILE = JB / 8;               // n8 tiles per unit
@@ -184,7 +198,7 @@ __global__ void __launch_bounds__(OzCfg<NT>::threads, OzCfg<NT>::ctas) ozgram_ke
       }
     }
     __syncthreads();
-    // ---- slice into 7 digit planes (two rows per thread step)
+    // ---- slice into ND digit planes (two rows per thread step)
     for (int e = t; e < (kOzTR / 2) * NT; e += kOzThreads) {
       const int i = 2 * (e % (kOzTR / 2)), j = e / (kOzTR / 2);
       const int Ej = Erun[j];
@@ -202,7 +216,7 @@ __global__ void __launch_bounds__(OzCfg<NT>::threads, OzCfg<NT>::ctas) ozgram_ke
         sg[h] = (b >> 63) ? -1.0f : 1.0f;
       }
 #pragma unroll
-      for (int d = 0; d < kOzDigits; ++d) {
+      for (int d = 0; d < ND; ++d) {
         // two signed digits -> exact FP32 -> one packed bf16x2
         const __nv_bfloat162 pr = __floats2bfloat162_rn(oz_digit(V[0], d, sg[0]), oz_digit(V[1], d, sg[1]));
         *(uint32_t *)(planes + ((size_t)d * NT + j) * kOzLDK + i) = *(const uint32_t *)&pr;
@@ -233,7 +247,7 @@ __global__ void __launch_bounds__(OzCfg<NT>::threads, OzCfg<NT>::ctas) ozgram_ke
       int pend = 0;  // T of the even order of the current pair of orders, per slot
       int tv[NTILE][4];
 #pragma unroll
-      for (int d = 0; d <= kOzMaxOrder; ++d) {
+      for (int d = 0; d <= kMaxOrder; ++d) {
         if (!order_in_group(gg.groups, grp, d)) continue;
         float c[NTILE][4];
 #pragma unroll
@@ -273,7 +287,7 @@ __global__ void __launch_bounds__(OzCfg<NT>::threads, OzCfg<NT>::ctas) ozgram_ke
         // T_2k 2^8 + T_2k+1 in int32 (order 6 alone); with four groups each
         // order alone.  hi holds orders 0..3 (unit: order 3), lo 4..6.
         const bool hi = d <= 3;
-        if (gg.groups == 1 && (d & 1) == 0 && d < kOzMaxOrder) {
+        if (gg.groups == 1 && (d & 1) == 0 && d < kMaxOrder) {
 #pragma unroll
           for (int nt = 0; nt < NTILE; ++nt)
 #pragma unroll
@@ -334,6 +348,8 @@ __global__ void __launch_bounds__(OzCfg<NT>::threads, OzCfg<NT>::ctas) ozgram_ke
     __syncthreads();
   }
   const bool bad = *flag != 0;
+  if (a.emax != nullptr && half == 0)
+    for (int j = t; j < n; j += kOzThreads) atomicMax(a.emax + j, Erun[j]);
   double *P = a.partials + grp_id * n * n;
   for (int e = t; e < PR * n; e += kOzThreads) {
     const int li = e % PR, j = e / PR, i = half * PR + li;
@@ -352,26 +368,33 @@ size_t ozgram_smem_bytes(int NT) {
 
 int ozgram_nt(int n) { return n <= 16 ? 16 : (n <= 32 ? 32 : (n <= 64 ? 64 : 128)); }
 
-template <int NT>
+template <int NT, int ND>
 static cudaError_t launch_oz(const RowSweep &a, int grid, cudaStream_t s) {
   static KernelAttr attr;
   const size_t smem = ozgram_smem_bytes(NT);
-  set_smem_attr(attr, ozgram_kernel<NT>, (int)smem, true);
+  set_smem_attr(attr, ozgram_kernel<NT, ND>, (int)smem, true);
   // the fused solve exists for n <= 64 only
   if (NT > 64 && a.do_trsm) return cudaErrorInvalidValue;
-  ozgram_kernel<NT><<<grid * OzCfg<NT>::halves, OzCfg<NT>::threads, smem, s>>>(a);
+  ozgram_kernel<NT, ND><<<grid * OzCfg<NT>::halves, OzCfg<NT>::threads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_ozgram(const RowSweep &a, int grid, cudaStream_t s) {
-  if (tcgram_usable(a)) return launch_tcgram(a, grid, s);
+template <int ND>
+static cudaError_t launch_oz_nd(const RowSweep &a, int grid, cudaStream_t s) {
   switch (ozgram_nt(a.p)) {
-    case 16: return launch_oz<16>(a, grid, s);
-    case 32: return launch_oz<32>(a, grid, s);
-    case 64: return launch_oz<64>(a, grid, s);
-    case 128: return launch_oz<128>(a, grid, s);
+    case 16: return launch_oz<16, ND>(a, grid, s);
+    case 32: return launch_oz<32, ND>(a, grid, s);
+    case 64: return launch_oz<64, ND>(a, grid, s);
+    case 128: return launch_oz<128, ND>(a, grid, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_ozgram(const RowSweep &a, int grid, cudaStream_t s) {
+  if (a.digits == kOzMixedDigits) return launch_oz_nd<kOzMixedDigits>(a, grid, s);
+  if (a.digits != 0 && a.digits != kOzDigits) return cudaErrorInvalidValue;
+  if (tcgram_usable(a)) return launch_tcgram(a, grid, s);
+  return launch_oz_nd<kOzDigits>(a, grid, s);
 }
 
 // Number of row groups (= partials) for m rows at width n: every SM holds

@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tcgram64_kernel(const __grid_co
             const uint32_t dbase = tmem + (uint32_t)(s * 4 * kNT);
             // K step by K step; the first MMA into each region (its first
             // unit, K step 0) overwrites it
-#pragma unroll
+#pragma unroll 1
             for (int ks = 0; ks < 4; ++ks)
 #pragma unroll
               for (int q = 0; q < 10; ++q) {
@@ -553,6 +553,7 @@ constexpr int64_t kTcGramMaxRowsPerCta = (int64_t)8192 * kTR;
 
 bool tcgram_usable(const RowSweep &a) {
   return a.tc05 && a.q == 0 && a.p >= kTcGramMinN && a.p <= kNT && !a.do_trsm && a.m >= 1 &&
+         a.digits == 0 && a.emax == nullptr &&
          (((uintptr_t)a.Yin) & 15) == 0 && (a.ldyin % 2) == 0 && a.rows_per_cta % kTR == 0 &&
          a.rows_per_cta <= kTcGramMaxRowsPerCta && a.m <= 0x7FFFFFFF && device_is_sm103() &&
          encode_tiled() != nullptr && kernel_launchable();

@@ -135,6 +135,19 @@ def run_alone(cq, server, bases, wl: Workload):
         r.result = server.wait(r.ticket)
 
 
+def scale_arrivals(wl: Workload, factor: float):
+    """Multiplies every arrival time by `factor`: a Poisson process of rate
+    lambda becomes one of rate lambda / factor with the same request order."""
+    for r in wl.reqs:
+        r.arrival *= factor
+    return wl
+
+
+def service_times(wl: Workload):
+    """Per-request service time (completion - submission) of a run_alone pass."""
+    return np.array([r.result["t_done"] - r.result["t_submit"] for r in wl.reqs])
+
+
 def latency_stats(wl: Workload):
     lat = np.array([r.result["t_done"] - r.result["t_submit"] for r in wl.reqs])
     ok = [r for r in wl.reqs if r.result["status"] >= 0]

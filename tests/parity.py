@@ -90,3 +90,27 @@ def check_orth(Q, where: str = "", gate: float = ORTH_GATE) -> float:
     record("orthogonality (||Q^T Q - I||_F / 1e-13)", v, ORTH_GATE, where)
     assert v <= gate, (where, v)
     return v
+
+
+# Reduced-digit Gramian of the mixed-precision first pass: a row adds at most
+# MIXED_ROW_ERR Ubar_i Ubar_j to X_ij, Ubar_j = 2^(E_j - 1022) for the largest
+# biased exponent E_j of column j (the constant the library's header states).
+MIXED_ROW_ERR = 2.0324e-12
+
+
+def ubar(A) -> np.ndarray:
+    """2^(E_j - 1022): the power of two just above column j's largest |entry|
+    (E_j >= 1, as the kernel starts its running exponents at 1)."""
+    cm = np.max(np.abs(A), axis=0)
+    e = np.frexp(cm)[1]  # cm = f 2^e with f in [0.5, 1): E_j = e + 1022
+    return np.ldexp(1.0, np.maximum(np.where(cm > 0, e, -1021), -1021))
+
+
+def mixed_shift_terms(A, lam: float, partials_max: int) -> tuple[float, float]:
+    """(lower, upper) of the first shift of the reduced-digit mixed path:
+    11 (m e sum_j Ubar_j^2 + n (n + 1 + G + 9) u ||X||) for G in [0, partials_max]."""
+    m, n = A.shape
+    base = 11.0 * m * MIXED_ROW_ERR * float(np.sum(ubar(A) ** 2))
+    lo = base + 11.0 * n * (n + 1.0 + 9.0) * U * lam
+    hi = base + 11.0 * n * (n + 1.0 + partials_max + 9.0) * U * lam
+    return lo, hi

@@ -5,7 +5,9 @@ pipeline.  Q and R are compared with the oracle's sCholQR3 of the same matrix
 entry by entry (about 15 s of oracle time) within the bounds of
 tests/parity.py; the oracle's Gramian of A is compared with the library's
 entry by entry, and the first shift with the one sized from it; the
-orthogonality, residual and shape of R are checked outright."""
+orthogonality, residual and shape of R are checked outright.  The
+mixed-precision variant (reduced-digit first Gramian) is compared with the
+same oracle factors."""
 import numpy as np
 import pytest
 
@@ -48,7 +50,19 @@ def test_benchmark_size_factorisation(cq, orc):
     assert sto == cq.OK
     check_q(float(np.max(np.abs(Q - Qo))), kappa, m, "benchmark size 1e6x64")
     check_r(float(np.max(np.abs(R - Ro))), kappa, Ro, m, "benchmark size 1e6x64")
-    del Qo
+
+    # the mixed-precision variant on the same matrix against the same oracle
+    # factors, with its first shift from the reduced-digit Gramian's bound
+    mx = cq.factor(dA, opts=cq.default_opts(precision=cq.PREC_MIXED), check=False)
+    torch.cuda.synchronize()
+    assert mx.status == cq.OK, mx.info
+    Qm, Rm = mx.Q.cpu().numpy(), mx.R.cpu().numpy()
+    check_orth(Qm, "mixed benchmark size")
+    assert orc.rrr(A, Qm, Rm) <= 1e-13
+    check_q(float(np.max(np.abs(Qm - Qo))), kappa, m, "mixed benchmark size 1e6x64")
+    check_r(float(np.max(np.abs(Rm - Ro))), kappa, Ro, m, "mixed benchmark size 1e6x64")
+    assert mx.info["iters"] <= res.info["iters"], (mx.info, res.info)
+    del Qo, Qm
 
     # the oracle's Gramian of A against the library's, every entry within
     # the FP64 dot-product bound, and the first shift from its norm

@@ -45,3 +45,14 @@ def test_stream_is_a_function_of_its_seed():
     key = lambda w: [(r.kind, r.basis, r.width, r.kappa, r.arrival) for r in w.reqs]
     assert a.m == b.m and key(a) == key(b)
     assert key(a) != key(c)
+
+
+def test_scaled_arrivals_keep_the_stream():
+    """Scaling the arrival process (the serving benchmark sets the mean gap
+    to the mean service time / utilization) changes only the times."""
+    a = sd.make_workload(n_bases=6, n_requests=40, mean_gap_s=1.0, seed=3)
+    b = sd.make_workload(n_bases=6, n_requests=40, mean_gap_s=2e-3, seed=3)
+    sd.scale_arrivals(a, 2e-3)
+    for ra, rb in zip(a.reqs, b.reqs):
+        assert (ra.kind, ra.basis, ra.width, ra.kappa) == (rb.kind, rb.basis, rb.width, rb.kappa)
+        assert math.isclose(ra.arrival, rb.arrival, rel_tol=1e-12)
