@@ -75,21 +75,34 @@ constexpr size_t kCSmem = sizeof(double) * (size_t)kCY * kCTR          // FP64 t
 
 }  // namespace
 
-// ---- cache fill: E_k of columns k0 .. k0 + p - 1 (one CTA per column)
+// ---- cache fill: E_k of columns k0 .. k0 + p - 1.  CTA (x, y) scans rows
+// [x rows_per_cta, ...) of column k0 + y with eight independent loads in
+// flight per thread and folds its maximum into Qe[k] (cleared to 0 before
+// the launch; every CTA contributes at least 1) with atomicMax.
 __global__ void __launch_bounds__(256) cache_exp_kernel(const double *Q, int64_t ldq, int64_t m, int k0,
-                                                        int *Qe) {
+                                                        int64_t rows_per_cta, int *Qe) {
   __shared__ int wm[8];
-  const int k = k0 + blockIdx.x;
-  const uint32_t *hw = (const uint32_t *)(Q + (int64_t)k * ldq) + 1;  // high words
+  const int k = k0 + (int)blockIdx.y;
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
+  const int64_t r1 = min(m, r0 + rows_per_cta);
+  const unsigned long long *col = (const unsigned long long *)(Q + (int64_t)k * ldq);
   int mx = 1;
-  for (int64_t r = threadIdx.x; r < m; r += blockDim.x) mx = max(mx, (int)((hw[2 * r] >> 20) & 0x7FF));
+  int64_t r = r0 + threadIdx.x;
+  for (; r + 7 * 256 < r1; r += 8 * 256) {
+    unsigned long long v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = __ldg(col + r + u * 256);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) mx = max(mx, (int)((v[u] >> 52) & 0x7FF));
+  }
+  for (; r < r1; r += 256) mx = max(mx, (int)((__ldg(col + r) >> 52) & 0x7FF));
   mx = __reduce_max_sync(0xffffffffu, mx);
   if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = mx;
   __syncthreads();
   if (threadIdx.x == 0) {
     int v = 1;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = max(v, wm[w]);
-    Qe[k] = v;
+    atomicMax(Qe + k, v);
   }
 }
 
@@ -123,8 +136,14 @@ __global__ void __launch_bounds__(256) cache_digits_kernel(const double *Q, int6
 cudaError_t launch_cache_fill(const double *Q, int64_t ldq, int64_t m, int k0, int p, int *Qe, uint16_t *Qd,
                               int64_t ldc, int64_t plane, cudaStream_t s) {
   if (p < 1 || (ldc & 63) != 0 || ldc < m) return cudaErrorInvalidValue;
-  cache_exp_kernel<<<p, 256, 0, s>>>(Q, ldq, m, k0, Qe);
-  cudaError_t e = cudaGetLastError();
+  // about four CTAs per SM over all columns, each slice at least 2048 rows
+  const int64_t slices = std::max<int64_t>(
+      1, std::min<int64_t>((m + 2047) / 2048, (4 * (int64_t)num_sms() + p - 1) / p));
+  const int64_t rpc = (m + slices - 1) / slices;
+  cudaError_t e = cudaMemsetAsync(Qe + k0, 0, sizeof(int) * (size_t)p, s);
+  if (e != cudaSuccess) return e;
+  cache_exp_kernel<<<dim3((unsigned)slices, (unsigned)p), 256, 0, s>>>(Q, ldq, m, k0, rpc, Qe);
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t items = (int64_t)p * (ldc / 2);
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((items + 255) / 256, 4 * (int64_t)num_sms()));

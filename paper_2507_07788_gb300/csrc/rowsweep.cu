@@ -52,6 +52,11 @@ __device__ __forceinline__ void rowsweep_body(const RowSweep &a, int bx, int by,
   uint32_t idx[EPT];
   double acc[EPT];
   const int64_t ebase = (int64_t)by * (kThreads * EPT);
+  // slots of this thread that hold entries (entry ebase + t + k kThreads,
+  // k < kact): the batched kernel is compiled for the largest E, and warps
+  // past the last entry skip the products
+  const int64_t left = a.E - ebase - t;
+  const int kact = left <= 0 ? 0 : (int)min((int64_t)EPT, (left + kThreads - 1) / kThreads);
 #pragma unroll
   for (int k = 0; k < EPT; ++k) {
     const int64_t e = ebase + t + (int64_t)k * kThreads;
@@ -101,7 +106,10 @@ __device__ __forceinline__ void rowsweep_body(const RowSweep &a, int bx, int by,
     for (int i = 0; i < nr; ++i) {
       const double *row = tile + i * lds;
 #pragma unroll
-      for (int k = 0; k < EPT; ++k) acc[k] = fma(row[idx[k] & 0xFFFFu], row[idx[k] >> 16], acc[k]);
+      for (int k = 0; k < EPT; ++k) {
+        if (k >= kact) break;
+        acc[k] = fma(row[idx[k] & 0xFFFFu], row[idx[k] >> 16], acc[k]);
+      }
     }
     __syncthreads();
   }

@@ -243,7 +243,9 @@ __global__ void __launch_bounds__(kQThreads, 1) tcgemm64_kernel(RowSweep a) {
           sg[h] = (b >> 63) ? -1.0f : 1.0f;
         }
         const uint32_t off = sw_off(r, k0 + 8 * c);
-#pragma unroll
+        // two digits per iteration: the fully unrolled split and drain
+        // overflowed the instruction cache (no-instruction stalls)
+#pragma unroll 2
         for (int d = 0; d < kQDig; ++d) {
           uint4 w;
           w.x = bf2(bdigit(W[0], d, sg[0]), bdigit(W[1], d, sg[1]));
@@ -267,7 +269,7 @@ __global__ void __launch_bounds__(kQThreads, 1) tcgemm64_kernel(RowSweep a) {
             fence_after_sync();
             // K step by K step, alternating the orders' accumulators (the
             // first pair of each order, at K step 0, overwrites it)
-#pragma unroll
+#pragma unroll 1
             for (int ks = 0; ks < 4; ++ks)
 #pragma unroll
               for (int i = 0; i < 4; ++i)
@@ -281,7 +283,7 @@ __global__ void __launch_bounds__(kQThreads, 1) tcgemm64_kernel(RowSweep a) {
           }
           if (ok) {
             fence_after_sync();
-#pragma unroll
+#pragma unroll 1
             for (int ks = 0; ks < 4; ++ks)
 #pragma unroll
               for (int i = 0; i < 8; ++i)
