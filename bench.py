@@ -58,8 +58,8 @@ def parse():
     ap.add_argument("--kappa", type=float, default=1e12)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--emulation", default="auto", choices=["auto", "tcgen05", "off"],
-                    help="digit kernels: auto = warp-level mma.sync, tcgen05 = the tcgen05 Gramian and solve "
-                         "for 17 <= n <= 64, off = FP64 CUDA cores")
+                    help="digit kernels: auto = the tcgen05 Gramian for 33 <= n <= 64 and mma.sync elsewhere, "
+                         "tcgen05 = the tcgen05 Gramian and solve for 17 <= n <= 64, off = FP64 CUDA cores")
     ap.add_argument("--no-tcgen05-leg", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -173,6 +173,17 @@ KERNEL_FILES = {"rowsweep": ("rowsweep.cu",), "trsm_rows": ("trsm.cu",),
                 "ozgram": ("ozgram.cu", "ozdigits.cuh"), "ozgemm": ("ozgemm.cu", "ozdigits.cuh"),
                 "tcgram": ("tcgram.cu", "tc05.cuh", "ozdigits.cuh"), "tcgemm": ("tcgemm.cu", "tc05.cuh", "ozdigits.cuh")}
 TC05_MIN_N, TC05_MAX_N = 17, 64  # widths of the tcgen05 Gramian and solve
+TC05_AUTO_GRAM_MIN_N = 33        # the Gramian runs on tcgen05 by default from this width
+
+
+def tc05_kernels(emulation: str, n: int):
+    """(Gramian, solve) on the tcgen05 kernels for this emulation mode and
+    width, the library's rule: the Gramian for 33 <= n <= 64 by default and
+    for 17 <= n <= 64 under tcgen05, the solve under tcgen05 only."""
+    gram = n <= TC05_MAX_N and ((emulation == "tcgen05" and n >= TC05_MIN_N) or
+                                (emulation == "auto" and n >= TC05_AUTO_GRAM_MIN_N))
+    solve = emulation == "tcgen05" and TC05_MIN_N <= n <= TC05_MAX_N
+    return gram, solve
 
 
 def kernel_source_hash(name: str) -> str:
@@ -322,7 +333,7 @@ def time_factor(cq, torch, dA, dQ, dR, opts, steps, warmup):
     return e0.elapsed_time(e1) / steps, res
 
 
-def roofline_from(tm, m, n, hbm_peak, hbm_src, tc_peak, tc_src, tcgen05=False):
+def roofline_from(tm, m, n, hbm_peak, hbm_src, tc_peak, tc_src, emulation="auto"):
     """Roofline of the dominant kernel from the library's per-launch events.
 
     The roofline of this path is HBM bytes: the top level reports the
@@ -357,9 +368,9 @@ def roofline_from(tm, m, n, hbm_peak, hbm_src, tc_peak, tc_src, tcgen05=False):
         return {"achieved": af / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
                 "frac": af / FP64_PEAK_FLOPS, "peak_source": fp64_src}
 
-    tc05 = tcgen05 and TC05_MIN_N <= n <= TC05_MAX_N
-    gname = "tcgram" if tc05 else "ozgram"
-    sname = "tcgemm" if tc05 else "ozgemm"
+    gram_tc05, solve_tc05 = tc05_kernels(emulation, n)
+    gname = "tcgram" if gram_tc05 else "ozgram"
+    sname = "tcgemm" if solve_tc05 else "ozgemm"
     gram = None
     if tm["gram_launches"] > 0:
         gms, gfl, gby, gaf, gag = per("gram")
@@ -370,7 +381,7 @@ def roofline_from(tm, m, n, hbm_peak, hbm_src, tc_peak, tc_src, tcgen05=False):
         gtcf = grows * 2.0 * OZGRAM_PAIRS * nt * nt
         gtca = gtcf / (gms * 1e-3) if gms > 0 else 0.0
         gram = record(("tcgram64_kernel (exact FP64 Gramian from bf16 digits, tcgen05 with TMEM "
-                       "accumulators and TMA tiles, one launch per row chunk)") if tc05 else
+                       "accumulators and TMA tiles, one launch per row chunk)") if gram_tc05 else
                       ("ozgram_kernel (exact FP64 Gramian from bf16 digits on the tensor cores, mma.sync, "
                        "one launch per row chunk)"), gms, gfl, gby, gaf, gag, gtraffic, tm["gram_ms"],
                       {"tensor": {"achieved": gtca / 1e12, "peak": tc_peak, "unit": "TFLOP/s",
@@ -383,7 +394,7 @@ def roofline_from(tm, m, n, hbm_peak, hbm_src, tc_peak, tc_src, tcgen05=False):
         tca = tcf / (ms * 1e-3) if ms > 0 else 0.0
         traffic, _ = traffic_per_launch(int(round(by / (16.0 * n))), sname)
         solve = record(("tcgemm64_kernel (Q = Y R~^-1 as an exact bf16 digit product, tcgen05 with TMEM "
-                        "accumulators, one launch per row chunk)") if tc05 else
+                        "accumulators, one launch per row chunk)") if solve_tc05 else
                        ("ozgemm_kernel (Q = Y R~^-1 as an exact bf16 digit product on the tensor cores, "
                         "mma.sync, one launch per row chunk)"), ms, fl, by, af, ag, traffic, tm["tsolve_ms"],
                        {"tensor": {"achieved": tca / 1e12, "peak": tc_peak, "unit": "TFLOP/s",
@@ -438,6 +449,17 @@ def leg_update(cq, torch, m, p=8, count=32, seed=0, cache=True):
     gen = torch.Generator(device="cuda")
     gen.manual_seed(seed_for(m, p, count, seed) & 0x7FFFFFFFFFFFFFFF)
     rng = np.random.default_rng(seed_for(m, p, count, seed, 1))
+    # warm-up: two appends to a throwaway basis of the same shape (first-use
+    # costs of the kernels and of the cache's memory stay out of the timing)
+    w = cq.Basis(m, 2 * p)
+    if cache:
+        w.enable_digit_cache()
+    wgen = torch.Generator(device="cuda")
+    wgen.manual_seed(seed_for(m, p, count, seed, 2) & 0x7FFFFFFFFFFFFFFF)
+    for _ in range(2):
+        w.append(cq.to_colmajor(torch.randn((m, p), generator=wgen, device="cuda", dtype=torch.float64)))
+    w.close()
+    torch.cuda.synchronize()
     b = cq.Basis(m, p * count)
     if cache:
         b.enable_digit_cache()
@@ -472,6 +494,7 @@ def leg_update(cq, torch, m, p=8, count=32, seed=0, cache=True):
     return {"workload": f"basis growth m={m}: {count} appends of p={p} to n={q_end}, blocks Q_prev G 0.1 + N eta"
                         + (", basis digit cache" if cache else ", FP64 projection and cross Gramian"),
             "appends_per_s": count / tot, "ms_per_append_mean": 1e3 * tot / count,
+            "ms_per_append_median": 1e3 * statistics.median(times), "ms_first_append": 1e3 * times[0],
             "ms_per_append_last": 1e3 * times[-1], "rows_cols_per_s": m * q_end / tot,
             "max_block_orth_frob": worst, "iters": iters, "shifts": shifts,
             "status": sorted(set(statuses))}
@@ -657,7 +680,7 @@ def run_ours(args):
     loo_f = float(torch.linalg.norm(G - torch.eye(n, dtype=G.dtype, device=G.device)))
 
     hbm_peak, hbm_src, tc_peak, tc_src = peaks()
-    roof = roofline_from(tm, m, n, hbm_peak, hbm_src, tc_peak, tc_src, tcgen05=(args.emulation == "tcgen05"))
+    roof = roofline_from(tm, m, n, hbm_peak, hbm_src, tc_peak, tc_src, emulation=args.emulation)
 
     hbm = factorisation_hbm(m, n, res.info["iters"], ms, hbm_peak)
     line = {"metric": METRIC, "value": value, "unit": "rows*cols/s", "n_gpus": ws, "steps": args.steps,

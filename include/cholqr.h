@@ -118,12 +118,14 @@ typedef struct cqr_opts {
  * pipeline), the cross Gramian of appends of 32..64 columns, and the cross
  * Gramian and projection of appends of <= 16 columns to a basis with a digit
  * cache (basis_enable_digit_cache; cholqr_pn keeps one for panels of <= 16
- * columns; q <= 256 for the projection); FP64 CUDA cores elsewhere.  These
- * kernels issue warp-level mma.sync.  CQR_EMU_OFF: FP64 CUDA cores
- * everywhere.  CQR_EMU_TCGEN05: as AUTO, but for 17 <= n <= 64 the Gramian
- * and the solve of cholqr_factor (and the Gramian of cholqr_gram) run on
- * tcgen05 kernels with TMEM accumulators (the Gramian's tiles TMA-loaded when
- * the block is 16-byte aligned with an even leading dimension); the same
+ * columns; q <= 256 for the projection); FP64 CUDA cores elsewhere.  For
+ * 33 <= n <= 64 the Gramian of cholqr_factor (and of an append to an empty
+ * basis) and of cholqr_gram runs on a tcgen05 kernel with TMEM accumulators
+ * and TMA-loaded tiles when the block is 16-byte aligned with an even
+ * leading dimension; the other kernels issue warp-level mma.sync.
+ * CQR_EMU_OFF: FP64 CUDA cores everywhere.  CQR_EMU_TCGEN05: as AUTO, with
+ * the tcgen05 Gramian from n = 17 and the factorisation's solve for
+ * 17 <= n <= 64 on a tcgen05 kernel too (one row chunk per pass); the same
  * exact digit products. */
 enum { CQR_EMU_AUTO = 0, CQR_EMU_OFF = 1, CQR_EMU_TCGEN05 = 2 };
 

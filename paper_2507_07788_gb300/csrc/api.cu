@@ -359,8 +359,11 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
     x_rows_per_cta = ((tiles + Gx - 1) / Gx) * tr;
   }
   const bool oz = ((P.mode == MODE_FACTOR) || ozu) && (p <= kOzMaxN) && (P.o.emulation != CQR_EMU_OFF);
+  // tcgen05 kernels: the Gramian under AUTO for 33 <= n <= 64 and under
+  // TCGEN05 for 17 <= n <= 64 (tc05_gram_mode); the solve under TCGEN05
   const bool tc05 = P.o.emulation == CQR_EMU_TCGEN05;
-  const int Goz = oz ? ozgram_grid(P.m, p, tc05) : 0;
+  const bool tcg = (P.mode == MODE_FACTOR || ozu) && tc05_gram_mode(P.o.emulation, p);
+  const int Goz = oz ? ozgram_grid(P.m, p, tcg) : 0;
   int64_t oz_rows_per_cta = 0;
   if (oz) {
     const int64_t tr = ozgram_tile_rows();
@@ -371,10 +374,14 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
   // solve and the Gramian always run as separate kernels (one chunk for small
   // m), with chunks half as tall since each row is twice as wide.
   const int64_t min_chunk = (p > 64) ? kMinChunkRows / 2 : kMinChunkRows;
-  // The tcgen05 Gramian and solve (17 <= n <= 64) each occupy whole SMs, so
-  // chunks on two streams would only queue behind each other: one chunk.
-  const bool tc05_pass = (P.o.emulation == CQR_EMU_TCGEN05) && p >= kTcGramMinN && p <= 64;
-  const int nchunks = (oz && !tc05_pass)
+  // The tcgen05 Gramian occupies whole SMs (216 KB of shared memory), so it
+  // cannot share SMs with the solve's chunks: it runs once per pass over all
+  // rows, after the solve (gram_whole).  The solve is then cut into chunks
+  // only when Q goes to the host, so that the copies overlap the later
+  // chunks; a row's result does not depend on its chunk.
+  const bool gram_whole = tcg;
+  const bool host_io = (P.hA != nullptr) && !mixed;
+  const int nchunks = (oz && (!gram_whole || host_io))
                           ? (int)std::max<int64_t>(1, std::min<int64_t>(kMaxChunks, P.m / min_chunk))
                           : 1;
   const bool pipe = oz;
@@ -387,14 +394,14 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
   if (pipe) {
     const int64_t tr = ozgram_tile_rows();
     chunk_rows = (((P.m + nchunks - 1) / nchunks + tr - 1) / tr) * tr;
-    Gc = ozgram_grid(chunk_rows, p, tc05);
+    Gc = ozgram_grid(chunk_rows, p, tcg);
     const int64_t tiles = chunk_rows / tr;
     chunk_rpc = ((tiles + Gc - 1) / Gc) * tr;
   }
   AuxCtx *ax = pipe ? aux_ctx(nchunks) : nullptr;
   if (pipe && ax == nullptr) return CQR_ERR_CUDA;  // no auxiliary stream or events
   // host staging pipelined with the passes (the tensor-core pipeline only)
-  CopyCtx *cx = (P.hA != nullptr && pipe && !mixed && ax != nullptr) ? copy_ctx(nchunks) : nullptr;
+  CopyCtx *cx = (host_io && pipe && ax != nullptr) ? copy_ctx(nchunks) : nullptr;
   const bool stage = cx != nullptr;
   if (P.hq_written != nullptr) *P.hq_written = false;
   const int64_t oz_parts =
@@ -457,7 +464,7 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
     a.lds = lds;
     a.do_trsm = trsm ? 1 : 0;
     a.st = s.st;
-    a.tc05 = tc05 ? 1 : 0;
+    a.tc05 = (tcg ? kTc05Gram : 0) | (tc05 ? kTc05Solve : 0);
     SweepMark *mk = nullptr;
     if (timing) {
       if (nmarks == pool.size()) {
@@ -553,6 +560,7 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
           if (e == cudaSuccess) e = cudaEventRecord(cx->c[c], cx->st);
           last_c = c;
         }
+        if (gram_whole) continue;  // the Gramian follows all chunks
         RowSweep z = a;
         z.m = rc;
         z.Yin = a.Yout + r0;
@@ -568,16 +576,32 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
         if (mg && e == cudaSuccess) cudaEventRecord(mg->b, ax->aux);
         g_launches++;
       }
-      // chunks past the end of m (none with the sizing above) would leave
-      // stale partials; all nchunks * Gc partials are written when rc > 0
-      if (e == cudaSuccess) e = cudaEventRecord(ax->done, ax->aux);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(str, ax->done, 0);
+      if (gram_whole) {
+        // one Gramian of the solved block over all rows, on this stream
+        RowSweep z = a;
+        z.Yin = a.Yout;
+        z.ldyin = a.ldyout;
+        z.do_trsm = 0;
+        z.accumulate = 0;
+        z.rows_per_cta = oz_rows_per_cta;
+        z.E = (int64_t)p * p;
+        SweepMark *mg = kmark(MARK_GRAM, npass, m_d * p * (p + 1.0), 8.0 * m_d * p);
+        if (mg && e == cudaSuccess) cudaEventRecord(mg->a, str);
+        if (e == cudaSuccess) e = launch_ozgram(z, Goz, str);
+        if (mg && e == cudaSuccess) cudaEventRecord(mg->b, str);
+        g_launches++;
+      } else {
+        // chunks past the end of m (none with the sizing above) would leave
+        // stale partials; all nchunks * Gc partials are written when rc > 0
+        if (e == cudaSuccess) e = cudaEventRecord(ax->done, ax->aux);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(str, ax->done, 0);
+      }
       // the control step reads the state the copies test, and the next pass
       // overwrites the chunks they read
       if (stage && P.hQ != nullptr && e == cudaSuccess && last_c >= 0)
         e = cudaStreamWaitEvent(str, cx->c[last_c], 0);
       last_oz = true;
-      last_oz_G = Gc;
+      last_oz_G = gram_whole ? Goz : Gc;
       if (mk != nullptr) cudaEventRecord(mk->b, str);
       return e;
     }
@@ -967,7 +991,7 @@ cqr_status cholqr_gram(const cqr_opts *opts, int64_t m, int64_t n, const double 
   // CQR_PREC_MIXED: the Gramian of the mixed factorisation's first pass
   // (reduced-digit on the tensor cores, or FP32 with emulation off)
   const bool mixed = o.precision == CQR_PREC_MIXED;
-  const bool tc05 = (o.emulation == CQR_EMU_TCGEN05) && !mixed;
+  const bool tc05 = tc05_gram_mode(o.emulation, p) && !mixed;
   const int G = oz ? ozgram_grid(m, p, tc05) : rowsweep_grid(m, tile_rows);
   const int64_t tr = oz ? ozgram_tile_rows() : tile_rows;
   const int64_t tiles = (m + tr - 1) / tr;
@@ -988,7 +1012,7 @@ cqr_status cholqr_gram(const cqr_opts *opts, int64_t m, int64_t n, const double 
   a.lds = lds;
   a.do_trsm = 0;
   a.st = nullptr;
-  a.tc05 = tc05 ? 1 : 0;
+  a.tc05 = tc05 ? kTc05Gram : 0;
   cudaError_t e = cudaSuccess;
   if (oz) {
     if (mixed) {

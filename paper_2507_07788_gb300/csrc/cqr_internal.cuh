@@ -92,7 +92,7 @@ struct RowSweep {
   const double *Tinv;   // p x p upper (ld p): D R~^{-1} (tensor-core product Q = (Y D^-1)(D T))
   const int *Tscale;    // p: log2 of D (column k of Y is divided, row k of T multiplied, by 2^Tscale[k])
   const DevState *st;
-  int32_t tc05;         // 1: the tcgen05 kernels may be used where they apply
+  int32_t tc05;         // kTc05Gram | kTc05Solve: the tcgen05 kernels that may be used where they apply
   int32_t digits;       // digit Gramian: 0 (= 7, exact FP64) or kOzMixedDigits
   int *emax;            // digit Gramian: atomicMax of the final column exponents (or null)
 };
@@ -229,6 +229,19 @@ int ozgram_tile_rows();
 // q = 0, no fused solve, Y 16-byte aligned with an even leading dimension;
 // launch_ozgram dispatches to it when tcgram_usable(a).
 constexpr int kTcGramMinN = 17;
+// RowSweep::tc05 bits
+constexpr int32_t kTc05Gram = 1, kTc05Solve = 2;
+// Widths whose Gramian runs on the tcgen05 kernel under CQR_EMU_AUTO (below
+// 33 columns the mma.sync kernel's narrower tile is faster than the tcgen05
+// kernel's 64 padded columns)
+constexpr int kTcGramAutoMinN = 33;
+// Does the factorisation's (and cholqr_gram's) Gramian use the tcgen05
+// kernel at this width and emulation mode?  The solve does under
+// CQR_EMU_TCGEN05 only.
+inline bool tc05_gram_mode(int emulation, int n) {
+  return n <= 64 && ((emulation == CQR_EMU_TCGEN05 && n >= kTcGramMinN) ||
+                     (emulation == CQR_EMU_AUTO && n >= kTcGramAutoMinN));
+}
 bool tcgram_usable(const RowSweep &a);
 int tcgram_grid(int64_t m);
 cudaError_t launch_tcgram(const RowSweep &a, int grid, cudaStream_t s);

@@ -89,6 +89,11 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const void *tmap, int 
       "l"(tmap), "r"(x), "r"(y), "r"(bar)
       : "memory");
 }
+// L2 prefetch of a 2-D tile (no shared memory written, no completion)
+__device__ __forceinline__ void tma_prefetch_l2_2d(const void *tmap, int x, int y) {
+  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(tmap), "r"(x), "r"(y)
+               : "memory");
+}
 __device__ __forceinline__ void prefetch_tmap(const void *tmap) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(tmap) : "memory");
 }

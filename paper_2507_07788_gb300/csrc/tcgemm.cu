@@ -411,7 +411,8 @@ bool sm103_q() {
 }  // namespace
 
 bool tcgemm_usable(const RowSweep &a) {
-  return a.tc05 && a.q == 0 && a.p >= kTcGemmMinN && a.p <= kQN && a.Tinv != nullptr && a.Tscale != nullptr &&
+  return (a.tc05 & kTc05Solve) && a.q == 0 && a.p >= kTcGemmMinN && a.p <= kQN && a.Tinv != nullptr &&
+         a.Tscale != nullptr &&
          a.rows_per_cta % kQR == 0 && sm103_q();
 }
 

@@ -90,6 +90,7 @@ static_assert(kSplitWarps * kSplitRegs + kDrainWarps * kDrainRegs == (kSplitWarp
 // the drain of tile k - 5 is done, so 8 slots are never overwritten early
 constexpr int kRing = 8;
 constexpr uint64_t kWaitNs = 2000000000ull;           // 2 s
+constexpr int kPrefetchAhead = 2;                     // tiles prefetched into L2 ahead of the TMA load
 constexpr unsigned long long kBalance = 0x0000808080808080ull;
 
 // shared-memory layout (offsets from a 1024-byte aligned base)
@@ -233,6 +234,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tcgram64_kernel(const __grid_co
     prefetch_tmap(&tmap);
     mbar_arrive_expect_tx(bar_raw_full, kRawBytes);
     tma_load_2d(sbase + kOffRaw, &tmap, (int)row0, 0, bar_raw_full);
+    for (int i = 1; i <= kPrefetchAhead; ++i)
+      if (row0 + (int64_t)i * kTR < row1) tma_prefetch_l2_2d(&tmap, (int)(row0 + (int64_t)i * kTR), 0);
   }
   if (warp < kSplitWarps) {
     regs_dec<kSplitRegs>();
@@ -243,10 +246,43 @@ __global__ void __launch_bounds__(kTcThreads, 1) tcgram64_kernel(const __grid_co
     const double *raw = (const double *)(base + kOffRaw);
     constexpr uint32_t idesc = idesc_bf16_f32(128, kNT);
     int issued = 0;  // MMA tiles issued (warp 1, lane 0)
+    // MMA issue of tile kk (warp kMmaWarp): every split warp has written its
+    // planes and the drain of tile kk - 2 has released the region set.
+    // Returns false (for the whole warp) when a wait gave up.
+    auto issue = [&](int kk) -> bool {
+      const int ss = kk & 1;
+      int ok = 1;
+      if (lane == 0) {
+        ok = mbar_wait(smem_addr(&cs->planes_full[ss]), (kk >> 1) & 1, kWaitNs) &&
+             (kk < 2 || mbar_wait(smem_addr(&cs->acc_empty[ss]), ((kk >> 1) - 1) & 1, kWaitNs));
+        if (ok) {
+          fence_after_sync();
+          const uint32_t stage = sbase + kOffPlanes + ss * kStageBytes;
+          const uint32_t dbase = tmem + (uint32_t)(ss * 4 * kNT);
+          // K step by K step; the first MMA into each region (its first
+          // unit, K step 0) overwrites it
+#pragma unroll 1
+          for (int ks = 0; ks < 4; ++ks)
+#pragma unroll
+            for (int q = 0; q < 10; ++q) {
+              const MmaUnit U = mma_unit(q);
+              const uint64_t ad = sdesc_sw128(stage + U.a * kPlaneBytes + ks * 32);
+              const uint64_t bd = sdesc_sw128(stage + U.b * kPlaneBytes + ks * 32);
+              mma_ss(dbase + (uint32_t)(U.r * kNT), ad, bd, idesc, (U.first && ks == 0) ? 0u : 1u);
+            }
+          mma_commit(smem_addr(&cs->planes_empty[ss]));
+          mma_commit(smem_addr(&cs->acc_full[ss]));
+          ++issued;
+        }
+      }
+      return __shfl_sync(0xffffffffu, ok, 0) != 0;
+    };
+    bool aborted = false;
     for (int k = 0; k < ntiles; ++k) {
       const int s = k & 1, slot = k % kRing;
       if (!__all_sync(0xffffffffu, mbar_wait(bar_raw_full, k & 1, kWaitNs))) {
         cs->timeout = 1;
+        aborted = true;
         break;
       }
       double2 v[kColsPerSplit];
@@ -261,7 +297,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) tcgram64_kernel(const __grid_co
         } else {
           mbar_arrive_expect_tx(bar_raw_full, kRawBytes);
           tma_load_2d(sbase + kOffRaw, &tmap, (int)(row0 + (int64_t)(k + 1) * kTR), 0, bar_raw_full);
+          // and bring the tile after it into L2, so that its load, issued
+          // one tile later, waits on L2 rather than HBM
+          if (row0 + (int64_t)(k + 1 + kPrefetchAhead) * kTR < row1)
+            tma_prefetch_l2_2d(&tmap, (int)(row0 + (int64_t)(k + 1 + kPrefetchAhead) * kTR), 0);
         }
+      }
+      // the products of the previous tile are issued only now, after this
+      // warp has released the staging tile, so that the next TMA load does
+      // not wait for the issue
+      if (warp == kMmaWarp && k >= 1 && !issue(k - 1)) {
+        cs->timeout = 1;
+        aborted = true;
+        break;
       }
       // column exponents: running maximum and its growth in this tile
       int grew = 0, nonfinite = 0;
@@ -286,6 +334,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tcgram64_kernel(const __grid_co
       // the plane stage is free once the MMAs of tile k - 2 have completed
       if (k >= 2 && !__all_sync(0xffffffffu, mbar_wait(smem_addr(&cs->planes_empty[s]), ((k >> 1) - 1) & 1, kWaitNs))) {
         cs->timeout = 1;
+        aborted = true;
         break;
       }
       unsigned char *stage = base + kOffPlanes + s * kStageBytes;
@@ -326,39 +375,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) tcgram64_kernel(const __grid_co
       fence_async_shared();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_addr(&cs->planes_full[s]));
-      if (warp == kMmaWarp) {
-        // ---- MMA issue: every split warp has written tile k's planes, and
-        // the drain of tile k - 2 has released this region set
-        int ok = 1;
-        if (lane == 0) {
-          ok = mbar_wait(smem_addr(&cs->planes_full[s]), (k >> 1) & 1, kWaitNs) &&
-               (k < 2 || mbar_wait(smem_addr(&cs->acc_empty[s]), ((k >> 1) - 1) & 1, kWaitNs));
-          if (ok) {
-            fence_after_sync();
-            const uint32_t stage = sbase + kOffPlanes + s * kStageBytes;
-            const uint32_t dbase = tmem + (uint32_t)(s * 4 * kNT);
-            // K step by K step; the first MMA into each region (its first
-            // unit, K step 0) overwrites it
-#pragma unroll 1
-            for (int ks = 0; ks < 4; ++ks)
-#pragma unroll
-              for (int q = 0; q < 10; ++q) {
-                const MmaUnit U = mma_unit(q);
-                const uint64_t ad = sdesc_sw128(stage + U.a * kPlaneBytes + ks * 32);
-                const uint64_t bd = sdesc_sw128(stage + U.b * kPlaneBytes + ks * 32);
-                mma_ss(dbase + (uint32_t)(U.r * kNT), ad, bd, idesc, (U.first && ks == 0) ? 0u : 1u);
-              }
-            mma_commit(smem_addr(&cs->planes_empty[s]));
-            mma_commit(smem_addr(&cs->acc_full[s]));
-            ++issued;
-          }
-        }
-        if (!__shfl_sync(0xffffffffu, ok, 0)) {
-          cs->timeout = 1;
-          break;
-        }
-      }
     }
+    // the products of the last tile
+    if (warp == kMmaWarp && !aborted && ntiles > 0 && !issue(ntiles - 1)) cs->timeout = 1;
     if (warp == kMmaWarp && lane == 0 && issued > 0 &&
         !mbar_wait(smem_addr(&cs->acc_full[(issued - 1) & 1]), ((issued - 1) >> 1) & 1, kWaitNs))
       cs->timeout = 1;  // every issued product completes before TMEM is freed
@@ -552,7 +571,7 @@ bool kernel_launchable() {
 constexpr int64_t kTcGramMaxRowsPerCta = (int64_t)8192 * kTR;
 
 bool tcgram_usable(const RowSweep &a) {
-  return a.tc05 && a.q == 0 && a.p >= kTcGramMinN && a.p <= kNT && !a.do_trsm && a.m >= 1 &&
+  return (a.tc05 & kTc05Gram) && a.q == 0 && a.p >= kTcGramMinN && a.p <= kNT && !a.do_trsm && a.m >= 1 &&
          a.digits == 0 && a.emax == nullptr &&
          (((uintptr_t)a.Yin) & 15) == 0 && (a.ldyin % 2) == 0 && a.rows_per_cta % kTR == 0 &&
          a.rows_per_cta <= kTcGramMaxRowsPerCta && a.m <= 0x7FFFFFFF && device_is_sm103() &&

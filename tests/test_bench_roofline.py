@@ -55,11 +55,17 @@ def test_tensor_pipeline_dominant_kernel():
                  gram_bytes=L * 8.0 * rows * n,
                  tsolve_launches=L, tsolve_ms=L * s_ms, tsolve_flops=L * rows * n * n,
                  tsolve_bytes=L * 16.0 * rows * n, tsolve_tc_flops=L * tc_solve_per_launch)
-    r = bench.roofline_from(tm, 1_000_000, n, 6686.8, "measured", 1730.8, "measured", tcgen05=True)
+    r = bench.roofline_from(tm, 1_000_000, n, 6686.8, "measured", 1730.8, "measured", emulation="tcgen05")
     assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["peak"] == 6686.8
-    assert r["kernel"].startswith("tcgram64_kernel") and "solve" in r
+    assert r["kernel"].startswith("tcgram64_kernel") and r["solve"]["kernel"].startswith("tcgemm64_kernel")
+    # by default the Gramian runs on tcgen05 from n = 33, the solve on mma.sync
     r0 = bench.roofline_from(tm, 1_000_000, n, 6686.8, "measured", 1730.8, "measured")
-    assert r0["kernel"].startswith("ozgram_kernel") and r0["solve"]["kernel"].startswith("ozgemm_kernel")
+    assert r0["kernel"].startswith("tcgram64_kernel") and r0["solve"]["kernel"].startswith("ozgemm_kernel")
+    r32 = bench.roofline_from(tm, 1_000_000, 32, 6686.8, "measured", 1730.8, "measured")
+    assert r32["kernel"].startswith("ozgram_kernel")
+    assert bench.tc05_kernels("auto", 33) == (True, False) and bench.tc05_kernels("auto", 32) == (False, False)
+    assert bench.tc05_kernels("tcgen05", 17) == (True, True) and bench.tc05_kernels("tcgen05", 65) == (False, False)
+    assert bench.tc05_kernels("off", 64) == (False, False)
     # 8 bytes per entry read, in 0.2 ms
     gbs = 8.0 * rows * n / (g_ms * 1e-3) / 1e9
     assert r["achieved"] == pytest.approx(gbs, rel=1e-12)

@@ -1,7 +1,9 @@
 """The Gramian X = A^T A (Alg. 1 line 3) as the library forms it
 (cholqr_gram): tensor-core digit arithmetic (Ozaki splitting) for n <= 128
-(emulation AUTO: the warp-level mma.sync kernels; emulation TCGEN05: the
-tcgen05 kernel for 17 <= n <= 64 on aligned blocks, mma.sync otherwise) and
+(emulation AUTO: the tcgen05 kernel for 33 <= n <= 64 and the warp-level
+mma.sync kernels elsewhere; emulation TCGEN05: the tcgen05 kernel for
+17 <= n <= 64; the tcgen05 kernel needs a 16-byte aligned block with an
+even leading dimension, the mma.sync kernel forms the others) and
 FP64 CUDA cores with emulation OFF, against the oracle's FP64 triple loop.
 The tcgen05 and mma.sync kernels form the same exact digit products, but
 each CTA splits X between its partial P and P^T differently (the tcgen05
@@ -141,7 +143,10 @@ def test_tcgen05_and_mma_sync_gramians_agree(cq, orc, m, n, grow):
         A *= 10.0 ** ((np.arange(m) // 64) % 9 - 4.0)[:, None] * 10.0 ** rng.uniform(-3, 3, size=(1, n))
     dA = cq.to_colmajor(A)
     Xt = cq.gram(dA, opts=cq.default_opts(emulation=cq.EMU_TCGEN05)).cpu().numpy()
-    Xl = cq.gram(dA).cpu().numpy()
+    # the same block 8 bytes past a 16-byte boundary: the mma.sync kernel
+    big = cq.colmajor(m + 1, n)
+    big[1:].copy_(dA)
+    Xl = cq.gram(big[1:]).cpu().numpy()
     assert np.array_equal(Xt, Xt.T)
     absA = np.abs(A)
     AtA = absA.T @ absA
