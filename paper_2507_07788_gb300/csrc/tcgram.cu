@@ -43,10 +43,13 @@
 //               the 11 planes; one mbarrier phase per tile and plane stage.
 //               Lane 0 of warp 0 also issues the TMA loads of the 64 x 64
 //               FP64 tiles of Y: the next one as soon as every split warp
-//               has taken the current one into registers.  Lane 0 of warp 1
-//               issues the tile's 40 tcgen05.mma once every split warp has
-//               written its planes; warp 1 also allocates and frees the 512
-//               TMEM columns.
+//               has taken the current one into registers (and prefetches
+//               the one after it into L2).  Lane 0 of warps 1, 2 and 3
+//               issues the 40 tcgen05.mma of a tile (16, 12 and 12, by
+//               accumulator region) once every split warp has written its
+//               planes, at the start of the next tile, after releasing the
+//               staging tile; warp 1 also allocates and frees the 512 TMEM
+//               columns.
 //   warps 8-15  drain: lane L of warp w reads TMEM lane L = 32 (w % 4) + lane
 //               (entry row L mod 64; orders T0, T2, T4, T6 for L < 64 and T1,
 //               T3, T5 for L >= 64) for 32 columns (half (w - 8) / 4), converts
@@ -79,7 +82,12 @@ constexpr int kStageBytes = kPlanes * kPlaneBytes;    // 88 KB
 constexpr int kRawBytes = kTR * kNT * 8;              // 32 KB
 constexpr int kSplitWarps = 8, kDrainWarps = 8;
 constexpr int kColsPerSplit = kNT / kSplitWarps;      // 8 columns per split warp
-constexpr int kMmaWarp = 1;                           // a split warp: lane 0 issues the MMAs
+constexpr int kMmaWarp = 1;                           // allocates and frees TMEM; the first MMA issuer
+// Lane 0 of split warps kMmaWarp .. kMmaWarp + kIssuers - 1 issues the MMAs
+// of a tile, each those of its own accumulator regions (R3; R2; R1 and R0:
+// 16, 12 and 12 MMAs), so that no warp spends the whole issue time
+constexpr int kIssuers = 3;
+__host__ __device__ constexpr int region_issuer(int r) { return r == 3 ? 0 : (r == 2 ? 1 : 2); }
 constexpr int kTcThreads = (kSplitWarps + kDrainWarps) * 32;  // 512, launched with 128 registers each
 // setmaxnreg: the split warpgroups give registers to the drain warpgroups
 // (8 x 32 x 80 + 8 x 32 x 176 = 512 x 128)
@@ -210,8 +218,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tcgram64_kernel(const __grid_co
     mbar_init(bar_raw_empty, kSplitWarps);
     for (int s = 0; s < 2; ++s) {
       mbar_init(smem_addr(&cs->planes_full[s]), kSplitWarps);
-      mbar_init(smem_addr(&cs->planes_empty[s]), 1);
-      mbar_init(smem_addr(&cs->acc_full[s]), 1);
+      mbar_init(smem_addr(&cs->planes_empty[s]), kIssuers);  // one commit per issuer
+      mbar_init(smem_addr(&cs->acc_full[s]), kIssuers);
       mbar_init(smem_addr(&cs->acc_empty[s]), kDrainWarps);
     }
     for (int r = 0; r < kRing; ++r) mbar_init(smem_addr(&cs->meta_full[r]), kSplitWarps);
@@ -245,10 +253,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) tcgram64_kernel(const __grid_co
     for (int c = 0; c < kColsPerSplit; ++c) erun[c] = 1;
     const double *raw = (const double *)(base + kOffRaw);
     constexpr uint32_t idesc = idesc_bf16_f32(128, kNT);
-    int issued = 0;  // MMA tiles issued (warp 1, lane 0)
-    // MMA issue of tile kk (warp kMmaWarp): every split warp has written its
-    // planes and the drain of tile kk - 2 has released the region set.
-    // Returns false (for the whole warp) when a wait gave up.
+    int issued = 0;  // MMA tiles issued (issuer warps, lane 0)
+    // MMA issue of tile kk by this issuer warp (its regions only): every
+    // split warp has written its planes and the drain of tile kk - 2 has
+    // released the region set.  Returns false (for the whole warp) when a
+    // wait gave up.
+    const int me = warp - kMmaWarp;  // issuer index, valid for 0 <= me < kIssuers
+    const bool issuer = me >= 0 && me < kIssuers;
     auto issue = [&](int kk) -> bool {
       const int ss = kk & 1;
       int ok = 1;
@@ -266,6 +277,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tcgram64_kernel(const __grid_co
 #pragma unroll
             for (int q = 0; q < 10; ++q) {
               const MmaUnit U = mma_unit(q);
+              if (region_issuer(U.r) != me) continue;
               const uint64_t ad = sdesc_sw128(stage + U.a * kPlaneBytes + ks * 32);
               const uint64_t bd = sdesc_sw128(stage + U.b * kPlaneBytes + ks * 32);
               mma_ss(dbase + (uint32_t)(U.r * kNT), ad, bd, idesc, (U.first && ks == 0) ? 0u : 1u);
@@ -306,7 +318,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tcgram64_kernel(const __grid_co
       // the products of the previous tile are issued only now, after this
       // warp has released the staging tile, so that the next TMA load does
       // not wait for the issue
-      if (warp == kMmaWarp && k >= 1 && !issue(k - 1)) {
+      if (issuer && k >= 1 && !issue(k - 1)) {
         cs->timeout = 1;
         aborted = true;
         break;
@@ -377,10 +389,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) tcgram64_kernel(const __grid_co
       if (lane == 0) mbar_arrive(smem_addr(&cs->planes_full[s]));
     }
     // the products of the last tile
-    if (warp == kMmaWarp && !aborted && ntiles > 0 && !issue(ntiles - 1)) cs->timeout = 1;
-    if (warp == kMmaWarp && lane == 0 && issued > 0 &&
+    if (issuer && !aborted && ntiles > 0 && !issue(ntiles - 1)) cs->timeout = 1;
+    // every issued product completes before TMEM is freed: each issuer waits
+    // for its last tile (whose barrier also counts the other issuers)
+    if (issuer && lane == 0 && issued > 0 &&
         !mbar_wait(smem_addr(&cs->acc_full[(issued - 1) & 1]), ((issued - 1) >> 1) & 1, kWaitNs))
-      cs->timeout = 1;  // every issued product completes before TMEM is freed
+      cs->timeout = 1;
     if (lane == 0) {
 #pragma unroll
       for (int c = 0; c < kColsPerSplit; ++c) cs->erun[warp * kColsPerSplit + c] = erun[c];
