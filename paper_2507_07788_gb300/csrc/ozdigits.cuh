@@ -138,6 +138,54 @@ __host__ __device__ __forceinline__ double fixed_to_double(long long hi, long lo
   return out;
 }
 
+// fixed_to_double out of line, for the rare results outside the normal range
+// (one copy of its code instead of one per inlined call site)
+__host__ __device__ __noinline__ inline double fixed_to_double_outlined(long long hi, long long lo, int hs, int e) {
+  return fixed_to_double(hi, lo, hs, e);
+}
+
+// The same rounding without data-dependent branches (for epilogues that
+// round many entries: independent entries overlap their dependency
+// chains).  The value v = hi 2^hs + lo is formed exactly as a 128-bit two's
+// complement integer T 2^64 + B, its magnitude taken with masks, the
+// leading one found with one count-leading-zeros, the 53-bit significand
+// rounded to nearest even with a sticky bit for the bits below it, and the
+// bits assembled; results outside the normal range take fixed_to_double.
+// Same arguments and result as fixed_to_double.
+__host__ __device__ __forceinline__ double fixed_to_double_bf(long long hi, long long lo, int hs, int e) {
+  // v = hi 2^hs + lo as (T, B): high and low 64-bit words, T signed
+  const unsigned long long hb = (unsigned long long)hi << hs;
+  const unsigned long long B0 = hb + (unsigned long long)lo;
+  const unsigned long long c0 = B0 < hb ? 1ull : 0ull;
+  const unsigned long long T0 = (unsigned long long)(hi >> (64 - hs)) + (unsigned long long)(lo >> 63) + c0;
+  // |v|: complement both words and add 1 when v < 0
+  const unsigned long long neg = (unsigned long long)((long long)T0 >> 63);  // all ones when v < 0
+  const unsigned long long B1 = (B0 ^ neg) + (neg & 1ull);
+  const unsigned long long T1 = (T0 ^ neg) + ((neg & 1ull) & (B1 == 0ull ? 1ull : 0ull));
+  // leading one at bit 127 - lz of the 128-bit magnitude
+  const int lzT = clz64(T1), lzB = clz64(B1);
+  const int lz = T1 != 0ull ? lzT : 64 + lzB;
+  const int sh = lz & 63;
+  const unsigned long long Bs = B1 << sh;
+  const unsigned long long cross = sh ? (B1 >> (64 - sh)) : 0ull;
+  const unsigned long long W = lz >= 64 ? Bs : ((T1 << sh) | cross);  // msb at bit 63
+  const unsigned long long rest = lz >= 64 ? 0ull : Bs;               // bits below W
+  unsigned long long mant = W >> 11;
+  const unsigned long long rb = W & 0x7FFull;
+  const bool up = (rb > 0x400ull) || (rb == 0x400ull && (rest != 0ull || (mant & 1ull)));
+  mant += up ? 1ull : 0ull;
+  const unsigned long long ov = mant >> 53;  // the significand rounded up to 2^53
+  mant >>= ov;
+  const int E = 127 - lz + (int)ov + e;
+  if ((T1 | B1) == 0ull) return 0.0;
+  if (E < -1022 || E > 1023) return fixed_to_double_outlined(hi, lo, hs, e);
+  const unsigned long long bits =
+      (neg & 0x8000000000000000ull) | ((unsigned long long)(E + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull);
+  double out;
+  memcpy(&out, &bits, sizeof(out));
+  return out;
+}
+
 // Rescales an accumulator pair (value = hi * 2^hs u + lo * u) to a unit 2^D
 // times larger when a column's running exponent grows by D: the bits that
 // leave hi move into lo before lo is shifted, so only bits below the new

@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(kQThreads, 1) tcgemm64_kernel(RowSweep a) {
           const int j = half * 32 + c16 + e;
           if (rr < row1 && j < n) {
             const double v = bad ? __longlong_as_double(0x7FF8000000000000ll)
-                                 : oz::fixed_to_double(hi[c16 + e], lo[e], 32, er + cs->fcol[j] - 2114);
+                                 : oz::fixed_to_double_bf(hi[c16 + e], lo[e], 32, er + cs->fcol[j] - 2114);
             a.Yout[rr + (int64_t)j * a.ldyout] = v;
           }
         }

@@ -1,5 +1,6 @@
 """The exact fixed-point -> FP64 rounding used by every tensor-core epilogue
-(fixed_to_double in csrc/ozdigits.cuh), compiled for the host and checked
+(fixed_to_double and its branch-free twin fixed_to_double_bf in
+csrc/ozdigits.cuh), compiled for the host and checked
 against exact rational arithmetic: (hi 2^hs + lo) 2^e must come back as the
 nearest FP64, ties to even, for every input in the normal range.  The cases
 cover both signs, carries between the two words, ties with and without
@@ -23,8 +24,9 @@ int main() {
   long long hi, lo; int hs, e;
   while (scanf("%lld %lld %d %d", &hi, &lo, &hs, &e) == 4) {
     double d = cqr::oz::fixed_to_double(hi, lo, hs, e);
-    unsigned long long b; memcpy(&b, &d, 8);
-    printf("%016llx\n", b);
+    double f = cqr::oz::fixed_to_double_bf(hi, lo, hs, e);
+    unsigned long long b, c; memcpy(&b, &d, 8); memcpy(&c, &f, 8);
+    printf("%016llx %016llx\n", b, c);
   }
   return 0;
 }
@@ -49,19 +51,18 @@ def exact(hi, lo, hs, e):
     return struct.unpack("<Q", struct.pack("<d", float(v)))[0]
 
 
-def cases():
-    rng = random.Random(20250710)
+def cases(hs=28):
+    rng = random.Random(20250710 + hs)
     out = []
-    hs = 28
     for _ in range(4000):
         bh, bl = rng.randint(0, 60), rng.randint(0, 60)
         hi = rng.randint(-(2 ** bh), 2 ** bh)
         lo = rng.randint(-(2 ** bl), 2 ** bl)
         out.append((hi, lo, hs, rng.randint(-900, 900)))
     # no high word; carries across the word boundary; a = -1 with r > 0
-    for lo in (1, -1, 2 ** 27, -(2 ** 27), 2 ** 28 - 1, -(2 ** 28) + 1, 2 ** 60, -(2 ** 60)):
+    for lo in (1, -1, 2 ** (hs - 1), -(2 ** (hs - 1)), 2 ** hs - 1, -(2 ** hs) + 1, 2 ** 60, -(2 ** 60)):
         out.append((0, lo, hs, 0))
-    for hi, lo in ((1, -1), (-1, 1), (-1, 2 ** 28 - 1), (2 ** 40, -(2 ** 28)), (-(2 ** 40), 2 ** 28)):
+    for hi, lo in ((1, -1), (-1, 1), (-1, 2 ** hs - 1), (2 ** 40, -(2 ** hs)), (-(2 ** 40), 2 ** hs)):
         out.append((hi, lo, hs, -3))
     # ties: the bit below the 53-bit significand set, with and without
     # sticky bits below it, on even and odd significands
@@ -80,12 +81,19 @@ def cases():
     return out
 
 
-def test_fixed_to_double_rounds_exactly(harness):
-    cs = cases()
+@pytest.mark.parametrize("hs", [24, 28, 32])
+def test_fixed_to_double_rounds_exactly(harness, hs):
+    """Both versions (fixed_to_double and the branch-free
+    fixed_to_double_bf) give the correctly rounded result, bit for bit the
+    same, for the word splits the epilogues use (2^24, 2^28, 2^32)."""
+    cs = cases(hs)
     inp = "".join(f"{h} {l} {s} {e}\n" for h, l, s, e in cs)
     res = subprocess.run([harness], input=inp, capture_output=True, text=True, check=True)
-    got = [int(x, 16) for x in res.stdout.split()]
+    pairs = [ln.split() for ln in res.stdout.splitlines()]
+    got = [int(a, 16) for a, _ in pairs]
+    fast = [int(b, 16) for _, b in pairs]
     assert len(got) == len(cs)
+    assert got == fast  # the branch-free version matches everywhere, the fallback range included
     checked = 0
     for (h, l, s, e), g in zip(cs, got):
         v = Fraction(h * 2 ** s + l) * Fraction(2) ** e
