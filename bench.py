@@ -196,10 +196,11 @@ def kernel_source_hash(name: str) -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_per_launch(rows: int, name: str):
+def traffic_per_launch(rows: int, name: str, cols: int = 0):
     """DRAM bytes per launch of a kernel from its committed ncu summary
-    (profiles/traffic_<name>.txt), scaled to `rows` rows per launch, or None
-    when the kernel sources changed since the counters were taken."""
+    (profiles/traffic_<name>.txt), scaled to `rows` rows (and `cols`
+    columns, when the capture names its width) per launch, or None when the
+    kernel sources changed since the counters were taken."""
     d = {}
     try:
         for line in open(os.path.join(ROOT, "profiles", f"traffic_{name}.txt")):
@@ -211,7 +212,10 @@ def traffic_per_launch(rows: int, name: str):
     if d.get("source_hash") != kernel_source_hash(name):
         return None, d
     try:
-        return float(d["capture_bytes_per_launch"]) * rows / float(d["capture_rows"]), d
+        scale = rows / float(d["capture_rows"])
+        if cols and "capture_cols" in d:
+            scale *= cols / float(d["capture_cols"])
+        return float(d["capture_bytes_per_launch"]) * scale, d
     except Exception:
         return None, d
 
@@ -375,7 +379,7 @@ def roofline_from(tm, m, n, hbm_peak, hbm_src, tc_peak, tc_src, emulation="auto"
     if tm["gram_launches"] > 0:
         gms, gfl, gby, gaf, gag = per("gram")
         grows = gby / (8.0 * n)
-        gtraffic, _ = traffic_per_launch(int(round(grows)), gname)
+        gtraffic, _ = traffic_per_launch(int(round(grows)), gname, n)
         # 16 symmetric digit pairs, each a full NT x NT block per row
         nt = 16 if n <= 16 else (32 if n <= 32 else (64 if n <= 64 else 128))
         gtcf = grows * 2.0 * OZGRAM_PAIRS * nt * nt
@@ -392,7 +396,7 @@ def roofline_from(tm, m, n, hbm_peak, hbm_src, tc_peak, tc_src, emulation="auto"
         ms, fl, by, af, ag = per("tsolve")
         tcf = tm["tsolve_tc_flops"] / max(tm["tsolve_launches"], 1)
         tca = tcf / (ms * 1e-3) if ms > 0 else 0.0
-        traffic, _ = traffic_per_launch(int(round(by / (16.0 * n))), sname)
+        traffic, _ = traffic_per_launch(int(round(by / (16.0 * n))), sname, n)
         solve = record(("tcgemm64_kernel (Q = Y R~^-1 as an exact bf16 digit product, tcgen05 with TMEM "
                         "accumulators, one launch per row chunk)") if solve_tc05 else
                        ("ozgemm_kernel (Q = Y R~^-1 as an exact bf16 digit product on the tensor cores, "
@@ -412,14 +416,14 @@ def roofline_from(tm, m, n, hbm_peak, hbm_src, tc_peak, tc_src, emulation="auto"
         return roof
     if tm["solve_launches"] > 0:
         ms, fl, by, af, ag = per("solve")
-        traffic, _ = traffic_per_launch(int(round(by / (16.0 * n))), "trsm_rows")  # 16 B per row entry
+        traffic, _ = traffic_per_launch(int(round(by / (16.0 * n))), "trsm_rows", n)  # 16 B per row entry
         roof = record("trsm_rows_kernel (FP64 row solve of the pass pipeline, one launch per row chunk)",
                       ms, fl, by, af, ag, traffic, tm["solve_ms"], {"alu": fp64_alu(af)})
         if gram:
             roof["gram"] = gram
         return roof
     ms, fl, by, af, ag = per("fused")
-    traffic, _ = traffic_per_launch(int(round(m)), "rowsweep")
+    traffic, _ = traffic_per_launch(int(round(m)), "rowsweep", n)
     return record("rowsweep_kernel (fused triangular solve + Gramian sweep, FP64 CUDA cores)",
                   ms, fl, by, af, ag, traffic, tm["fused_ms"], {"alu": fp64_alu(af)})
 

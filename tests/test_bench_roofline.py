@@ -33,16 +33,18 @@ def _capture(name):
         if ":" in line and not line.startswith("#"):
             k, v = line.split(":", 1)
             d[k.strip()] = v.strip()
-    return float(d["capture_bytes_per_launch"]), float(d["capture_rows"])
+    return float(d["capture_bytes_per_launch"]), float(d["capture_rows"]), float(d.get("capture_cols", 0))
 
 
-def _check_traffic(traffic, name, rows):
-    # the committed capture scaled by rows, or None while the kernel's sources
-    # differ from the captured ones (or no capture exists)
+def _check_traffic(traffic, name, rows, n=None):
+    # the committed capture scaled by rows (and columns, when the capture
+    # names its width), or None while the kernel's sources differ from the
+    # captured ones (or no capture exists)
     if traffic is None:
         return
-    b, cr = _capture(name)
-    assert traffic == pytest.approx(b * rows / cr, rel=1e-12)
+    b, cr, cc = _capture(name)
+    want = b * rows / cr * ((n / cc) if (n and cc) else 1.0)
+    assert traffic == pytest.approx(want, rel=1e-12)
 
 
 def test_tensor_pipeline_dominant_kernel():
@@ -74,11 +76,11 @@ def test_tensor_pipeline_dominant_kernel():
     want = rows * 2 * 16 * 64 * 64 / (g_ms * 1e-3) / 1e12
     assert r["tensor"]["achieved"] == pytest.approx(want, rel=1e-12)
     assert r["tensor"]["frac"] == pytest.approx(want / 1730.8, rel=1e-12)
-    _check_traffic(r["traffic"], "tcgram", rows)
+    _check_traffic(r["traffic"], "tcgram", rows, n)
     s = r["solve"]
     assert s["achieved"] == pytest.approx(16.0 * rows * n / (s_ms * 1e-3) / 1e9, rel=1e-12)
     assert s["tensor"]["achieved"] == pytest.approx(tc_solve_per_launch / (s_ms * 1e-3) / 1e12, rel=1e-12)
-    _check_traffic(s["traffic"], "tcgemm", rows)
+    _check_traffic(s["traffic"], "tcgemm", rows, n)
 
 
 def test_solve_dominates_when_it_takes_longer():
