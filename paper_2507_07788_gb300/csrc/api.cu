@@ -70,7 +70,14 @@ AuxCtx *aux_ctx(int nchunks) {
   thread_local AuxCtx per_device[kMaxDevices];
   AuxCtx &c = per_device[current_device()];
   if (c.aux == nullptr) {
-    if (cudaStreamCreateWithFlags(&c.aux, cudaStreamNonBlocking) != cudaSuccess ||
+    // the highest priority: a whole-pass Gramian launched here takes SMs
+    // ahead of the pending blocks of the host copies (default priority)
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+      (void)cudaGetLastError();
+      greatest = 0;
+    }
+    if (cudaStreamCreateWithPriority(&c.aux, cudaStreamNonBlocking, greatest) != cudaSuccess ||
         cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming) != cudaSuccess) {
       (void)cudaGetLastError();
       c.aux = nullptr;
@@ -577,7 +584,9 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
         g_launches++;
       }
       if (gram_whole) {
-        // one Gramian of the solved block over all rows, on this stream
+        // one Gramian of the solved block over all rows, after the last
+        // chunk, on the high-priority auxiliary stream (host copies of the
+        // chunks may still be running on the copy stream)
         RowSweep z = a;
         z.Yin = a.Yout;
         z.ldyin = a.ldyout;
@@ -585,11 +594,15 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
         z.accumulate = 0;
         z.rows_per_cta = oz_rows_per_cta;
         z.E = (int64_t)p * p;
+        if (e == cudaSuccess) e = cudaEventRecord(ax->ev[0], str);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ax->aux, ax->ev[0], 0);
         SweepMark *mg = kmark(MARK_GRAM, npass, m_d * p * (p + 1.0), 8.0 * m_d * p);
-        if (mg && e == cudaSuccess) cudaEventRecord(mg->a, str);
-        if (e == cudaSuccess) e = launch_ozgram(z, Goz, str);
-        if (mg && e == cudaSuccess) cudaEventRecord(mg->b, str);
+        if (mg && e == cudaSuccess) cudaEventRecord(mg->a, ax->aux);
+        if (e == cudaSuccess) e = launch_ozgram(z, Goz, ax->aux);
+        if (mg && e == cudaSuccess) cudaEventRecord(mg->b, ax->aux);
         g_launches++;
+        if (e == cudaSuccess) e = cudaEventRecord(ax->done, ax->aux);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(str, ax->done, 0);
       } else {
         // chunks past the end of m (none with the sizing above) would leave
         // stale partials; all nchunks * Gc partials are written when rc > 0
