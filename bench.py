@@ -580,7 +580,8 @@ def leg_serve(cq, torch, n_requests=512, utilization=0.7):
     submitted when the previous completed) to measure their mean service
     time S; the arrival process is then scaled to mean gap S / utilization
     and replayed in real time on fresh bases.  Latency = completion -
-    submission."""
+    submission.  Then the same stream is submitted all at once, for the
+    runtime's capacity (rows*cols/s at saturation)."""
     import numpy as np
     from paper_2507_07788_gb300 import serve_driver as sd
     t0 = time.perf_counter()
@@ -607,6 +608,16 @@ def leg_serve(cq, torch, n_requests=512, utilization=0.7):
     srv.close()
     st = sd.latency_stats(wl)
     st.update(info)
+    for b in bases:
+        b.close()
+    # capacity: the same stream submitted all at once (no arrival gaps)
+    bases = sd.make_bases(cq, wl)
+    srv = server()
+    sd.replay(cq, srv, bases, wl, realtime=False)
+    srv.close()
+    sat = sd.latency_stats(wl)
+    st["saturated"] = {"rows_cols_per_s": sat["rows_cols_per_s"], "makespan_s": sat["makespan_s"],
+                       "batched": sat["batched"], "max_batch": sat["max_batch"]}
     st["utilization"] = utilization
     st["alone"] = {"mean_ms": s_mean * 1e3, "p50_ms": float(np.percentile(alone, 50) * 1e3),
                    "p99_ms": float(np.percentile(alone, 99) * 1e3)}
