@@ -381,14 +381,16 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
   // solve and the Gramian always run as separate kernels (one chunk for small
   // m), with chunks half as tall since each row is twice as wide.
   const int64_t min_chunk = (p > 64) ? kMinChunkRows / 2 : kMinChunkRows;
-  // The tcgen05 Gramian occupies whole SMs (216 KB of shared memory), so it
-  // cannot share SMs with the solve's chunks: it runs once per pass over all
-  // rows, after the solve (gram_whole).  The solve is then cut into chunks
-  // only when Q goes to the host, so that the copies overlap the later
-  // chunks; a row's result does not depend on its chunk.
+  // The tcgen05 Gramian occupies whole SMs (216 KB of shared memory and the
+  // whole register file), so it cannot share SMs with the solve's chunks: it
+  // runs once per pass over all rows, after the solve (gram_whole), in one
+  // chunk.  Host staging of Q ahead of the end (host_io) then costs more
+  // than it saves: its copy kernels hold SMs the Gramian waits for (measured
+  // 10.71 ms with, 10.37 ms without, at 1e6 x 64), so it is kept for the
+  // chunked pipeline only.
   const bool gram_whole = tcg;
-  const bool host_io = (P.hA != nullptr) && !mixed;
-  const int nchunks = (oz && (!gram_whole || host_io))
+  const bool host_io = (P.hA != nullptr) && !mixed && !gram_whole;
+  const int nchunks = (oz && !gram_whole)
                           ? (int)std::max<int64_t>(1, std::min<int64_t>(kMaxChunks, P.m / min_chunk))
                           : 1;
   const bool pipe = oz;
