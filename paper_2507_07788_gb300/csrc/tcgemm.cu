@@ -15,8 +15,8 @@
 // (B: 64 columns x 64 k, 8 KB each, written once per CTA) live in shared
 // memory; MMA (i, i') = A_i B_i'^T is 128 x 64 x 64 (four K steps of 16).
 // Two TMEM rounds of four regions (128 lanes x 64 columns each):
-//   round 1, columns   0..255: orders 0..3 (10 MMAs)
-//   round 2, columns 256..511: orders 4..7 (26 MMAs)
+//   round 1, columns   0..255: orders 0..3 (10 digit pairs, 40 tcgen05.mma)
+//   round 2, columns 256..511: orders 4..7 (26 digit pairs, 104 tcgen05.mma)
 // so the drain of a tile's first round overlaps its second round's products.
 //
 // Roles (512 threads, one CTA per SM, 16 warps of up to 128 registers):
@@ -27,12 +27,13 @@
 //               memory, and the 8 digits of its 32 entries go to the planes
 //               as 16-byte stores.  The next tile's loads are issued before
 //               waiting for the planes to be free.  Lane 0 of warp 0 issues
-//               the 36 MMAs of the tile once all eight warps have written it.
+//               the tile's 144 MMAs once all eight warps have written it.
 //   warps 8-15  drain: TMEM lane 32 (w % 4) + lane = row of the tile, 32
 //               columns (half (w - 8) / 4): round 1 into one int64 word per
-//               entry, then round 2 eight columns at a time, rounding and
-//               storing each entry of Q (a warp writes 32 consecutive rows of
-//               a column: coalesced).
+//               entry, then round 2 sixteen columns at a time, rounding each
+//               entry of Q with the branch-free exact rounding (its entries'
+//               dependency chains overlap) and storing it (a warp writes 32
+//               consecutive rows of a column: coalesced).
 // Every wait gives up after kQWaitNs of wall time (the CTA then writes NaN
 // rows, and the control step reports a breakdown) and TMEM is still freed.
 #include <cuda_bf16.h>
