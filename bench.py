@@ -440,7 +440,14 @@ def factorisation_hbm(m, n, passes, ms, hbm_peak):
             "formula": "(8 m n + 16 m n x passes) / ms_per_step"}
 
 
-def leg_update(cq, torch, m, p=8, count=32, seed=0, cache=True):
+def append_hbm_bytes(m: int, q: int, p: int, iters: int) -> float:
+    """Algorithmic HBM bytes of one append (Alg. 2) with `iters` outer
+    iterations: the first sweep reads [Q_in A_in] (8 m (q + p)), every
+    iteration reads [Q_in Y] and writes the new block (8 m (q + p) + 8 m p)."""
+    return 8.0 * m * (q + p) + iters * (8.0 * m * (q + p) + 8.0 * m * p)
+
+
+def leg_update(cq, torch, m, p=8, count=32, seed=0, cache=True, hbm_peak=0.0):
     """Basis growth (Alg. 2): 32 appends of 8 columns up to n = 256 at m rows.
     block_k = Q_prev G 0.1 + N eta (eta log-uniform in [1e-12, 1]); the first
     block is N.  Inputs are drawn on the device from a seeded generator; the
@@ -469,6 +476,7 @@ def leg_update(cq, torch, m, p=8, count=32, seed=0, cache=True):
         b.enable_digit_cache()
     blk = cq.colmajor(m, p)
     times, worst, iters, shifts, statuses = [], 0.0, [], [], []
+    bytes_alg = 0.0
     torch.cuda.synchronize()
     for k in range(count):
         N = torch.randn((p, m), generator=gen, device="cuda", dtype=torch.float64).t()
@@ -483,6 +491,7 @@ def leg_update(cq, torch, m, p=8, count=32, seed=0, cache=True):
         t0 = time.perf_counter()
         st, info = b.append(blk)
         times.append(time.perf_counter() - t0)
+        bytes_alg += append_hbm_bytes(m, k * p, p, info["iters"])
         statuses.append(st)
         iters.append(info["iters"])
         shifts.append(info["shifts"])
@@ -493,18 +502,21 @@ def leg_update(cq, torch, m, p=8, count=32, seed=0, cache=True):
         worst = max(worst, float(torch.linalg.norm(Gm)))
     q_end = b.cols
     b.close()
-    bytes_alg = 0.0
     tot = sum(times)
+    gbs = bytes_alg / tot / 1e9
     return {"workload": f"basis growth m={m}: {count} appends of p={p} to n={q_end}, blocks Q_prev G 0.1 + N eta"
                         + (", basis digit cache" if cache else ", FP64 projection and cross Gramian"),
             "appends_per_s": count / tot, "ms_per_append_mean": 1e3 * tot / count,
             "ms_per_append_median": 1e3 * statistics.median(times), "ms_first_append": 1e3 * times[0],
             "ms_per_append_last": 1e3 * times[-1], "rows_cols_per_s": m * q_end / tot,
             "max_block_orth_frob": worst, "iters": iters, "shifts": shifts,
-            "status": sorted(set(statuses))}
+            "status": sorted(set(statuses)),
+            "hbm": {"bytes": bytes_alg, "achieved_gbs": gbs, "peak_gbs": hbm_peak,
+                    "frac": gbs / hbm_peak if hbm_peak else 0.0,
+                    "formula": "sum over appends of 8 m (q + p) + iters (8 m (q + p) + 8 m p), over the summed append times"}}
 
 
-def leg_mixed(cq, torch, synth, m, n=128, kappas=(1e6, 1e10, 1e14), steps=3):
+def leg_mixed(cq, torch, synth, m, n=128, kappas=(1e6, 1e10, 1e14), steps=3, hbm_peak=0.0):
     """Mixed precision vs plain FP64 at m x 128 on the same matrices; beside
     each factorisation, its first-pass Gramian alone (cholqr_gram with the
     same options: the exact digit Gramian for FP64, the reduced-digit one for
@@ -533,7 +545,8 @@ def leg_mixed(cq, torch, synth, m, n=128, kappas=(1e6, 1e10, 1e14), steps=3):
             row[name] = {"ms": ms, "rows_cols_per_s": m * n / (ms * 1e-3), "iters": res.info["iters"],
                          "status": res.status, "loo_frob": loo, "rrr_frob": rrr,
                          "sigma_first": res.info["sigma_first"],
-                         "first_gram_ms": g0.elapsed_time(g1) / steps}
+                         "first_gram_ms": g0.elapsed_time(g1) / steps,
+                         "hbm_frac": factorisation_hbm(m, n, res.info["iters"], ms, hbm_peak)["frac"]}
         row["speedup_mixed_vs_fp64"] = row["fp64"]["ms"] / row["mixed"]["ms"]
         out.append(row)
         del dA, dQ, dR
@@ -750,13 +763,13 @@ def run_ours(args):
         line["sweep"] = sweep
 
     if rank == 0 and not args.no_update:
-        line["update"] = leg_update(cq, torch, args.update_m)
-        fp64 = leg_update(cq, torch, args.update_m, cache=False)
+        line["update"] = leg_update(cq, torch, args.update_m, hbm_peak=hbm_peak)
+        fp64 = leg_update(cq, torch, args.update_m, cache=False, hbm_peak=hbm_peak)
         line["update"]["without_cache"] = {k: fp64[k] for k in ("ms_per_append_mean", "ms_per_append_last",
-                                                                 "rows_cols_per_s", "max_block_orth_frob")}
+                                                                 "rows_cols_per_s", "max_block_orth_frob", "hbm")}
 
     if rank == 0 and not args.no_mixed:
-        line["mixed"] = leg_mixed(cq, torch, synth, args.mixed_m)
+        line["mixed"] = leg_mixed(cq, torch, synth, args.mixed_m, hbm_peak=hbm_peak)
 
     if rank == 0 and not args.no_pn:
         line["pn"] = leg_pn(cq, torch, synth, m)

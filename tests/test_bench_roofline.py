@@ -127,3 +127,12 @@ def test_whole_factorisation_bytes():
     h = bench.factorisation_hbm(1_000_000, 64, 3, 6.5, 6686.8)
     assert h["bytes"] == 56.0 * 1_000_000 * 64
     assert h["frac"] == pytest.approx(56.0 * 64e6 / 6.5e-3 / 1e9 / 6686.8, rel=1e-12)
+
+
+def test_append_bytes_follow_alg2_sweeps():
+    # the first sweep reads [Q_in A_in]; each outer iteration reads [Q_in Y]
+    # and writes the new block
+    m, q, p = 1000, 16, 8
+    assert bench.append_hbm_bytes(m, q, p, 0) == 8.0 * m * (q + p)
+    assert bench.append_hbm_bytes(m, q, p, 2) == 8.0 * m * (q + p) + 2 * (8.0 * m * (q + p) + 8.0 * m * p)
+    assert bench.append_hbm_bytes(m, 0, p, 1) == 8.0 * m * p + 16.0 * m * p
