@@ -145,8 +145,11 @@ typedef struct cqr_info {
 
 /* Largest Gramian width handled by the kernels: n of cholqr_factor and p of
  * basis_append must not exceed it.  Basis capacity (q + p) up to
- * CQR_MAX_BASIS. */
-#define CQR_MAX_N 128
+ * CQR_MAX_BASIS.  Widths above 128 run on the FP64 CUDA cores (the row
+ * sweeps, with the Gramian split over several sweeps of its entries) and
+ * their control step keeps its n x n working storage in global memory: a
+ * correct wide path, not a fast one (no tensor-core kernel for them). */
+#define CQR_MAX_N 256
 #define CQR_MAX_BASIS 1024
 
 /* Fills *o with the defaults listed above.  o must not be NULL. */

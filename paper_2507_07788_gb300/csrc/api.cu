@@ -225,6 +225,7 @@ struct Scratch {
   uint16_t *Bd;  // digits of the scaled B~ (cached-digit projection)
   int *fexp;
   int *emax;     // column exponents of the reduced-digit first Gramian
+  double *cwork; // global working storage of the control step (p > kCtrlSmemMaxP)
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -239,8 +240,9 @@ cudaError_t scratch_alloc(Scratch &s, int q, int p, int G, int64_t E, cudaStream
   keep_pool_memory();
   const size_t b_Ts = align256(sizeof(int) * (size_t)p);
   const size_t b_Bd = align256(ozcproj_scratch_bytes());
-  cudaError_t e =
-      cudaMallocAsync((void **)&s.base, b_st + b_C + 2 * b_Rt + b_Rd + b_Bt + 2 * b_Ts + b_Bd + b_P, str);
+  const size_t b_W = (p > kCtrlSmemMaxP) ? align256(ctrl_smem_bytes(p)) : 0;
+  cudaError_t e = cudaMallocAsync((void **)&s.base,
+                                  b_st + b_C + 2 * b_Rt + b_Rd + b_Bt + 2 * b_Ts + b_Bd + b_W + b_P, str);
   if (e != cudaSuccess) return e;
   char *p0 = s.base;
   s.st = (DevState *)p0;
@@ -262,6 +264,8 @@ cudaError_t scratch_alloc(Scratch &s, int q, int p, int G, int64_t E, cudaStream
   s.Bd = (uint16_t *)p0;
   s.fexp = (int *)(p0 + sizeof(uint16_t) * 7 * 16 * (256 + 8));
   p0 += b_Bd;
+  s.cwork = b_W ? (double *)p0 : nullptr;
+  p0 += b_W;
   s.partials = (double *)p0;
   return cudaSuccess;
 }
@@ -716,6 +720,7 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
     c.first_shift_coeff = mixed_coeff;
     c.emax = mixed_oz ? s.emax : nullptr;
     c.emax_coeff = mixed_emax_coeff;
+    c.work = s.cwork;
     c.C = s.C;
     c.Rt = s.Rt;
     c.Rdinv = s.Rdinv;

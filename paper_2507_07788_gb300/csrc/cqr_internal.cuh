@@ -132,7 +132,13 @@ struct Ctrl {
   double *B;        // accumulated B (q x p block), ld ldb (update only)
   int64_t ldb;
   DevState *st;
+  // Working storage of the control step (X, packed R~, two vectors:
+  // ctrl_smem_bytes(p) bytes) in global memory, for widths whose working set
+  // does not fit in shared memory (p > kCtrlSmemMaxP); null otherwise.
+  double *work;
 };
+// Widest p whose control step works in shared memory (197 KB at 128).
+constexpr int kCtrlSmemMaxP = 128;
 
 // Launchers (return cudaGetLastError() of the launch).
 cudaError_t launch_init(double *R, int64_t ldr, int p, double *B, int64_t ldb, int q,

@@ -18,6 +18,7 @@
 namespace cqr {
 
 constexpr int kCqrMaxN = CQR_MAX_N;
+constexpr int kTinvMaxN = 128;  // widths of the tensor-core solve, whose T the tinv kernel forms
 
 __device__ __forceinline__ int pk(int i, int j) { return i + j * (j + 1) / 2; }  // i <= j
 
@@ -174,7 +175,9 @@ __device__ __forceinline__ double shift_alg2_first(int64_t m, int q, int p, doub
 }
 
 // One control step of one problem; shared by the single and batched kernels.
-__device__ void ctrl_body(const Ctrl &c, double *sm) {
+// sm: the working storage (X, packed R~, two vectors), or with gX set, X in
+// gX and the rest in sm.
+__device__ void ctrl_body(const Ctrl &c, double *sm, double *gX = nullptr) {
   DevState *st = c.st;
   if (st->done) return;
   __shared__ double red[32];
@@ -183,8 +186,8 @@ __device__ void ctrl_body(const Ctrl &c, double *sm) {
   __shared__ double s_inv;
   const int p = c.p, q = c.q, t = threadIdx.x, NT = blockDim.x;
   const int ldc = q + p;
-  double *X = sm;          // p x p, full
-  double *Rk = X + p * p;  // packed upper, p (p + 1) / 2
+  double *X = gX ? gX : sm;             // p x p, full
+  double *Rk = gX ? sm : X + p * p;     // packed upper, p (p + 1) / 2
   float *vecs = (float *)(Rk + p * (p + 1) / 2 + 1);
   float *v = vecs, *w = vecs + p;
 
@@ -379,6 +382,17 @@ __global__ void __launch_bounds__(kCtrlThreads) ctrl_kernel(Ctrl c) {
   ctrl_body(c, sm);
 }
 
+// The same control step for widths above kCtrlSmemMaxP, whose n x n Gramian
+// does not fit in shared memory: X in global memory (c.work) and the packed
+// R~ with the vectors in shared memory (the Cholesky works there), or, when
+// even R~ does not fit (ctrl_split_smem_bytes above 200 KB), everything in
+// global memory (through L1 and L2).
+__global__ void __launch_bounds__(kCtrlThreads) ctrl_split_kernel(Ctrl c) {
+  extern __shared__ double sm[];
+  ctrl_body(c, sm, c.work);
+}
+__global__ void __launch_bounds__(kCtrlThreads) ctrl_global_kernel(Ctrl c) { ctrl_body(c, c.work); }
+
 // Batched control: CTA b handles problems b, b + grid, ...
 __global__ void __launch_bounds__(kCtrlThreads) ctrl_batched_kernel(const Ctrl *reqs, const int *nreq) {
   extern __shared__ double sm[];
@@ -399,6 +413,11 @@ cudaError_t launch_ctrl_batched(const Ctrl *reqs, const int *nreq, int grid, siz
 }
 
 // X (p x p), packed R~, two float vectors.
+// bytes of the packed R~ and the two vectors (the split layout's shared part)
+static size_t ctrl_split_smem_bytes(int p) {
+  return (size_t)(p * (p + 1) / 2 + 1) * sizeof(double) + (size_t)2 * p * sizeof(float) + 64;
+}
+
 size_t ctrl_smem_bytes(int p) {
   return (size_t)p * p * sizeof(double) + (size_t)(p * (p + 1) / 2 + 1) * sizeof(double) +
          (size_t)2 * p * sizeof(float) + 64;
@@ -492,9 +511,9 @@ cudaError_t launch_rupdate(const double *Rt, int p, double *R, int64_t ldr, cons
 
 cudaError_t launch_tinv(const double *Rt, const double *Rdinv, const double *C, int ldc, int q, int p,
                         double *Tinv, int *Tscale, const DevState *st, cudaStream_t s) {
-  if (p > kCqrMaxN) return cudaErrorInvalidValue;  // R~ and a row of T in shared memory (133 KB at 128)
+  if (p > kTinvMaxN) return cudaErrorInvalidValue;  // R~ and a row of T in shared memory (133 KB at 128)
   static KernelAttr attr;
-  const size_t smem = sizeof(double) * ((size_t)kCqrMaxN * kCqrMaxN + 2 * kCqrMaxN);
+  const size_t smem = sizeof(double) * ((size_t)kTinvMaxN * kTinvMaxN + 2 * kTinvMaxN);
   set_smem_attr(attr, tinv_kernel, (int)smem, false);
   tinv_kernel<<<p, 128, sizeof(double) * ((size_t)p * p + 2 * p), s>>>(Rt, Rdinv, C, ldc, q, p, Tinv, Tscale,
                                                                       st);
@@ -502,6 +521,18 @@ cudaError_t launch_tinv(const double *Rt, const double *Rdinv, const double *C, 
 }
 
 cudaError_t launch_ctrl(const Ctrl &a, cudaStream_t s) {
+  if (a.p > kCtrlSmemMaxP) {
+    if (a.work == nullptr) return cudaErrorInvalidValue;
+    const size_t sm = ctrl_split_smem_bytes(a.p);
+    if (sm <= 200 * 1024) {
+      static KernelAttr sattr;
+      set_smem_attr(sattr, ctrl_split_kernel, 200 * 1024, false);
+      ctrl_split_kernel<<<1, kCtrlThreads, sm, s>>>(a);
+    } else {
+      ctrl_global_kernel<<<1, kCtrlThreads, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+  }
   static KernelAttr attr;
   set_smem_attr(attr, ctrl_kernel, 200 * 1024, false);
   ctrl_kernel<<<1, kCtrlThreads, ctrl_smem_bytes(a.p), s>>>(a);
