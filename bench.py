@@ -71,6 +71,7 @@ def parse():
     ap.add_argument("--update-m", type=int, default=2_000_000)
     ap.add_argument("--mixed-m", type=int, default=4_000_000)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-wide", action="store_true")
     ap.add_argument("--no-pn", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=512)
     return ap.parse_args()
@@ -554,6 +555,25 @@ def leg_mixed(cq, torch, synth, m, n=128, kappas=(1e6, 1e10, 1e14), steps=3, hbm
     return {"workload": f"mixed vs FP64 sCholQR3, m={m} n={n}, A=U diag(s) V^T", "rows": out}
 
 
+def leg_wide(cq, torch, synth, m=200000, ns=(192, 256), kappa=1e12, steps=2, hbm_peak=0.0):
+    """Widths above 128: the FP64 row sweeps and the global-memory control
+    step (no tensor-core kernel for these widths), beside n = 128."""
+    rows = []
+    for n in (128,) + tuple(ns):
+        A = synth.test_matrix(m, n, kappa, rep=41)
+        dA = cq.to_colmajor(A)
+        del A
+        dQ, dR = cq.colmajor(m, n), cq.colmajor(n, n)
+        ms, res = time_factor(cq, torch, dA, dQ, dR, cq.default_opts(), steps, 1)
+        rows.append({"n": n, "ms": ms, "rows_cols_per_s": m * n / (ms * 1e-3), "iters": res.info["iters"],
+                     "status": res.status, "orth_frob": res.info["orth_frob"],
+                     "hbm_frac": factorisation_hbm(m, n, res.info["iters"], ms, hbm_peak)["frac"],
+                     "path": "tensor-core digit kernels" if n <= 128 else "FP64 CUDA cores"})
+        del dA, dQ, dR
+        torch.cuda.empty_cache()
+    return {"workload": f"sCholQR3 at m={m}, kappa={kappa:g}, n = 128 and above", "rows": rows}
+
+
 def leg_pn(cq, torch, synth, m, n=64, kappa=1e12, rs=(1, 2, 4, 8), steps=2):
     """pnCholQR (Alg. 3) with r panels against sCholQR3 on the same matrix.
     The paper's flop model puts pnCholQR at G(r) = 1/2 + 1/(2r) of the
@@ -773,6 +793,9 @@ def run_ours(args):
 
     if rank == 0 and not args.no_pn:
         line["pn"] = leg_pn(cq, torch, synth, m)
+
+    if rank == 0 and not args.no_wide:
+        line["wide"] = leg_wide(cq, torch, synth, hbm_peak=hbm_peak)
 
     if rank == 0 and not args.no_serve:
         line["serve"] = leg_serve(cq, torch, args.serve_requests)
