@@ -28,6 +28,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import os
 import statistics
@@ -187,13 +188,22 @@ def tc05_kernels(emulation: str, n: int):
     return gram, solve
 
 
+def strip_comments(src: str) -> str:
+    """C/C++ source without its comments and blank lines, each line
+    right-stripped (string literals in the kernels hold no comment
+    markers)."""
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    return "\n".join(line.rstrip() for line in src.splitlines() if line.strip())
+
+
 def kernel_source_hash(name: str) -> str:
-    """Hash of one kernel's source files: the DRAM counters of a kernel stay
-    valid while they do not change."""
+    """Hash of one kernel's source files with their comments removed: the
+    DRAM counters of a kernel stay valid while its code does not change."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2507_07788_gb300", "csrc")
     for f in KERNEL_FILES[name]:
-        h.update(open(os.path.join(csrc, f), "rb").read())
+        h.update(strip_comments(open(os.path.join(csrc, f)).read()).encode())
     return h.hexdigest()[:16]
 
 
@@ -555,20 +565,31 @@ def leg_mixed(cq, torch, synth, m, n=128, kappas=(1e6, 1e10, 1e14), steps=3, hbm
     return {"workload": f"mixed vs FP64 sCholQR3, m={m} n={n}, A=U diag(s) V^T", "rows": out}
 
 
-def leg_wide(cq, torch, synth, m=200000, ns=(192, 256), kappa=1e12, steps=2, hbm_peak=0.0):
-    """Widths above 128: the FP64 row sweeps and the global-memory control
-    step (no tensor-core kernel for these widths), beside n = 128."""
+def leg_wide(cq, torch, synth, m=200000, ns=(192, 256, 384, 512), off_ns=(256, 512), kappa=1e12, steps=2,
+             hbm_peak=0.0):
+    """Widths above 128: the Gramian by column blocks of at most 64 on the
+    tensor-core cross-Gramian kernel, the FP64 row solve and the
+    global-memory control step, beside n = 128 (tensor-core pipeline) and,
+    at the widths in off_ns, the FP64 Gramian (emulation off)."""
     rows = []
-    for n in (128,) + tuple(ns):
+    cases = [(n, "auto") for n in (128,) + tuple(ns)] + [(n, "off") for n in off_ns]
+    cases.sort()
+    for n, emu in cases:
         A = synth.test_matrix(m, n, kappa, rep=41)
         dA = cq.to_colmajor(A)
         del A
         dQ, dR = cq.colmajor(m, n), cq.colmajor(n, n)
-        ms, res = time_factor(cq, torch, dA, dQ, dR, cq.default_opts(), steps, 1)
-        rows.append({"n": n, "ms": ms, "rows_cols_per_s": m * n / (ms * 1e-3), "iters": res.info["iters"],
-                     "status": res.status, "orth_frob": res.info["orth_frob"],
-                     "hbm_frac": factorisation_hbm(m, n, res.info["iters"], ms, hbm_peak)["frac"],
-                     "path": "tensor-core digit kernels" if n <= 128 else "FP64 CUDA cores"})
+        opts = cq.default_opts(emulation=cq.EMU_OFF if emu == "off" else cq.EMU_AUTO)
+        ms, res = time_factor(cq, torch, dA, dQ, dR, opts, steps, 1)
+        if n <= 128:
+            path = "tensor-core digit kernels"
+        elif emu == "off":
+            path = "FP64 CUDA cores (Gramian and solve)"
+        else:
+            path = "digit Gramian by 64-column blocks, FP64 solve"
+        rows.append({"n": n, "emulation": emu, "ms": ms, "rows_cols_per_s": m * n / (ms * 1e-3),
+                     "iters": res.info["iters"], "status": res.status, "orth_frob": res.info["orth_frob"],
+                     "hbm_frac": factorisation_hbm(m, n, res.info["iters"], ms, hbm_peak)["frac"], "path": path})
         del dA, dQ, dR
         torch.cuda.empty_cache()
     return {"workload": f"sCholQR3 at m={m}, kappa={kappa:g}, n = 128 and above", "rows": rows}

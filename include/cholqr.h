@@ -52,8 +52,8 @@ typedef enum cqr_status {
 /* Shift policy of the factorisation (Alg. 1, Sec. 2.1, and Sec. 4.1 item 2):
  *   CQR_SHIFT_SCHOLQR3      first pass always shifted (sCholQR3), later
  *                           passes unshifted; a later breakdown recomputes
- *                           the shift from the current Gramian (Alg. 1
- *                           lines 5-7).  Default.
+ *                           the shift from the current Gramian (Alg. 1).
+ *                           Default.
  *   CQR_SHIFT_ON_BREAKDOWN  Alg. 1 exactly as printed.
  *   CQR_SHIFT_NONE          no shift at all (CholQR / CholQR2); a breakdown
  *                           returns CQR_ERR_BREAKDOWN.
@@ -77,13 +77,13 @@ enum {
 };
 
 /* Stopping rule: ||X - I||_F < tol (Sec. 4.1, default tol = 1e-13), or the
- * literal u*sqrt(n) of Alg. 1 line 4 / Alg. 2 line 6. */
+ * literal u*sqrt(n) of Alg. 1 / Alg. 2. */
 enum { CQR_STOP_FROB_TOL = 0, CQR_STOP_U_SQRT_N = 1 };
 
 /* Arithmetic of the row-sweeping kernels.  CQR_PREC_FP64: every step in FP64.
  * CQR_PREC_MIXED (cholqr_factor only): the Gramian of the first (shifted)
  * pass is formed at reduced precision and the first shift is sized for its
- * error bound, in the form of Alg. 1 line 6; the norm estimate, Cholesky,
+ * error bound, in the form of Alg. 1; the norm estimate, Cholesky,
  * solves and all later passes stay FP64.  With the digit kernels (n <= 128,
  * emulation not CQR_EMU_OFF, no reducer) that Gramian keeps 5 balanced
  * base-256 digits (40 bits relative to each column's largest binary
@@ -145,11 +145,14 @@ typedef struct cqr_info {
 
 /* Largest Gramian width handled by the kernels: n of cholqr_factor and p of
  * basis_append must not exceed it.  Basis capacity (q + p) up to
- * CQR_MAX_BASIS.  Widths above 128 run on the FP64 CUDA cores (the row
- * sweeps, with the Gramian split over several sweeps of its entries) and
- * their control step keeps its n x n working storage in global memory: a
- * correct wide path, not a fast one (no tensor-core kernel for them). */
-#define CQR_MAX_N 256
+ * CQR_MAX_BASIS.  Above 128 columns the Gramian of cholqr_factor,
+ * cholqr_gram and of an append to an empty basis is formed by column blocks
+ * of at most 64 on the tensor cores (exact digit products, unless
+ * opts->emulation is CQR_EMU_OFF: then, and for appends to a non-empty
+ * basis, the FP64 row sweep, split over several sweeps of its entries); the
+ * triangular solve is the FP64 row substitution, and the control step keeps
+ * its n x n working storage in global memory (one CTA). */
+#define CQR_MAX_N 512
 #define CQR_MAX_BASIS 1024
 
 /* Fills *o with the defaults listed above.  o must not be NULL. */
@@ -161,7 +164,7 @@ const char *cqr_status_string(int status);
 /*
  * cholqr_factor -- QR factorisation A = Q R of a tall-skinny m x n block by
  * iterated shifted Cholesky QR: Alg. 1 (rsCholQR, Sec. 2.1) with the shift of
- * Alg. 1 line 6, sigma = max{11 (m n + n (n+1)) u ||X||, 2u}, and the
+ * Alg. 1, sigma = max{11 (m n + n (n+1)) u ||X||, 2u}, and the
  * sCholQR3 first-pass shift named in Sec. 4.1 (opts->shift_policy).
  *
  *   opts      host pointer, may be NULL (defaults).
@@ -180,7 +183,7 @@ cqr_status cholqr_factor(const cqr_opts *opts, int64_t m, int64_t n, const doubl
                          cqr_info *info, void *stream);
 
 /*
- * cholqr_gram -- the Gramian X = A^T A of Alg. 1 line 3, formed by the same
+ * cholqr_gram -- the Gramian X = A^T A of Alg. 1, formed by the same
  * row sweep and fixed-order reduction as the factorisation's first pass
  * (tensor-core digit arithmetic for n <= 128 unless opts->emulation is
  * CQR_EMU_OFF; FP64 CUDA cores otherwise).  With opts->precision =
@@ -286,7 +289,7 @@ typedef struct cqr_reducer {
 /*
  * cholqr_factor_sharded -- cholqr_factor (Alg. 1 with the sCholQR3 first
  * shift, Sec. 2.1 and 4.1) on this rank's row block of a matrix with m_total
- * rows.  The shift uses m_total (Alg. 1 line 6).  Every rank must call it
+ * rows.  The shift uses m_total (Alg. 1).  Every rank must call it
  * with the same opts, n and m_total; the results are this rank's rows of Q
  * and the full R (the same on every rank).
  *   m_local   rows of this rank's block, 1 <= m_local <= m_total, m_total >= n.
@@ -349,7 +352,7 @@ cqr_status basis_create(int64_t m, int64_t n_max, const cqr_opts *opts, void *st
  * given the basis Q_in R_in = A_prev (m x q) and new columns A_in (m x p),
  * extend it to [Q_in Q] and [[R_in, B], [0, R]] with
  * [Q_in Q][[R_in, B], [0, R]] = [A_prev A_in] (Proposition 2.1).  The shift
- * loop is Alg. 2 lines 7-11: sigma starts at 0, then
+ * loop is Alg. 2: sigma starts at 0, then
  * 11 (m q + q (q+1)) u ||X|| (Alg. 1's formula with p when q = 0), then x10,
  * floored at 2u.  At least opts->update_min_iter outer iterations are made.
  *   p         1 <= p <= CQR_MAX_N, q + p <= n_max (else CQR_ERR_CAPACITY).
@@ -365,9 +368,9 @@ cqr_status basis_append(cqr_basis *b, int64_t p, const double *A_in, int64_t lda
  * basis_enable_digit_cache -- keep a digit copy of the basis columns on the
  * device (7 bf16 digits per entry, 14 bytes: 1.75x the size of Q) so that
  * later appends of p <= 16 columns to a basis of more than 262144 rows form
- * their cross Gramian [Q_in A_in]^T A_in (Alg. 2 lines 2-4, 15-16) and, while
+ * their cross Gramian [Q_in A_in]^T A_in (Alg. 2) and, while
  * the basis has at most 256 columns, the projection Q_in B~ of the solve
- * (Alg. 2 line 12) on the tensor cores from the cached digits instead of
+ * (Alg. 2) on the tensor cores from the cached digits instead of
  * FP64 products.  Each column is written as sign * V * 2^(E_k - 1078) with
  * E_k its largest biased exponent and V < 2^56 in 7 balanced base-256
  * digits; the cache fills for the present columns now and for new ones at

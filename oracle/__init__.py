@@ -10,8 +10,8 @@ with gcc and marshals numpy arrays (column-major, float64) through ctypes.
 
 Function to paper map (arXiv 2507.07788):
   gram, chol, trsm, trmm ..... the steps of Alg. 1 (Sec. 2.1)
-  shift ...................... Alg. 1 line 6 (sigma formula, 2u floor)
-  update_shift ............... Alg. 2 line 9 (first shift of the update)
+  shift ...................... Alg. 1 (sigma formula, 2u floor)
+  update_shift ............... Alg. 2 (first shift of the update)
   cholqr ..................... Alg. 1 (+ the sCholQR3 first-pass shift, Sec. 4.1)
   cholqr_update .............. Alg. 2 (Sec. 2.2), Proposition 2.1
   pncholqr ................... Alg. 3 (Sec. 2.3)

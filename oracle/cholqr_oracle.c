@@ -42,7 +42,7 @@ static const double ORC_U = 1.1102230246251565404236316680908203125e-16;
 /* ------------------------------------------------------------------------- */
 
 /* X = A^T A (n x n, both triangles), A m x n.  Definition of the Gramian
- * (Alg. 1 line 3): X_ij = sum_k A_ki A_kj, k ascending. */
+ * (Alg. 1): X_ij = sum_k A_ki A_kj, k ascending. */
 void orc_gram(int64_t m, int64_t n, const double *A, int64_t lda, double *X,
               int64_t ldx) {
   for (int64_t j = 0; j < n; ++j)
@@ -67,7 +67,7 @@ void orc_gemm_tn(int64_t m, int64_t p, int64_t q, const double *A,
 }
 
 /* Cholesky factorisation R^T R = X + sigma I, R upper triangular (the
- * "chol" of Alg. 1 line 5/7 and Alg. 2 line 8).  Row-oriented textbook
+ * "chol" of Alg. 1 and Alg. 2).  Row-oriented textbook
  * algorithm reading only the upper triangle of X.
  * Breakdown: a pivot d_j = X_jj + sigma - sum_{k<j} R_kj^2 that is not
  * strictly positive (or not finite).  Returns 0 on success, else j+1 for the
@@ -92,7 +92,7 @@ int orc_chol(int64_t n, const double *X, int64_t ldx, double sigma, double *R,
 }
 
 /* Q = A R^{-1} for upper triangular R, one row at a time by forward
- * substitution on R^T q^T = a^T (Alg. 1 line 9, Alg. 2 line 12).  Q may
+ * substitution on R^T q^T = a^T (Alg. 1, Alg. 2).  Q may
  * alias A: each row is read before it is overwritten. */
 void orc_trsm_runn(int64_t m, int64_t n, const double *A, int64_t lda,
                    const double *R, int64_t ldr, double *Q, int64_t ldq) {
@@ -105,7 +105,7 @@ void orc_trsm_runn(int64_t m, int64_t n, const double *A, int64_t lda,
 }
 
 /* C = T R for upper triangular T (n x n) and R (n x n): the R <- R~ R of
- * Alg. 1 line 10 / Alg. 2 line 14.  C must not alias T or R. */
+ * Alg. 1 / Alg. 2.  C must not alias T or R. */
 void orc_trmm_upper(int64_t n, const double *T, int64_t ldt, const double *R,
                     int64_t ldr, double *C, int64_t ldc) {
   for (int64_t j = 0; j < n; ++j)
@@ -116,7 +116,7 @@ void orc_trmm_upper(int64_t n, const double *T, int64_t ldt, const double *R,
     }
 }
 
-/* ||X - I||_F (Alg. 1 line 4, Alg. 2 line 6, and the Sec. 4.1 stop rule). */
+/* ||X - I||_F (Alg. 1, Alg. 2, and the Sec. 4.1 stop rule). */
 double orc_frob_minus_identity(int64_t n, const double *X, int64_t ldx) {
   double s = 0.0;
   for (int64_t j = 0; j < n; ++j)
@@ -178,7 +178,7 @@ int orc_sym_eigvals(int64_t n, const double *X, int64_t ldx, double *w) {
 }
 
 /* Spectral norm of a symmetric matrix, max_i |lambda_i|.  This is the
- * ||X|| of Alg. 1 line 6 and Alg. 2 line 9; the paper estimates it with a
+ * ||X|| of Alg. 1 and Alg. 2; the paper estimates it with a
  * Lanczos eigensolver to 1e-2 relative accuracy (App. A, Listing 1), the
  * oracle computes it to full accuracy. */
 double orc_sym_norm2(int64_t n, const double *X, int64_t ldx) {
@@ -191,7 +191,7 @@ double orc_sym_norm2(int64_t n, const double *X, int64_t ldx) {
   return mx;
 }
 
-/* Shift of Alg. 1 line 6: sigma = max{11 (m n + n (n + 1)) u ||X||, 2u}.
+/* Shift of Alg. 1: sigma = max{11 (m n + n (n + 1)) u ||X||, 2u}.
  * The 2u floor is the paper's guard against a vanishing shift (Sec. 2.1). */
 double orc_shift(int64_t m, int64_t n, double normX) {
   double c = 11.0 * ((double)m * (double)n + (double)n * ((double)n + 1.0));
@@ -228,17 +228,17 @@ static double stop_tol(const orc_opts *o, int64_t n) {
  *                          sCholQR3 of Fukaya et al. 2020, Alg. 4.2, named
  *                          in Sec. 4.1); later passes unshifted unless the
  *                          Cholesky breaks down, then the shift is recomputed
- *                          from the current X (Alg. 1 lines 5-7).
+ *                          from the current X (Alg. 1).
  *   ORC_SHIFT_ON_BREAKDOWN Alg. 1 as printed.
  *   ORC_SHIFT_SCHOLQR3_STRICT  pass 1 shifted, later breakdown = failure
  *                          (Fukaya's sCholQR3, a Fig. 1 comparison system).
  *   ORC_SHIFT_ISCHOLQR     shift computed once from the first X and reused
  *                          on every breakdown (isCholQR, Fukaya Alg. 4.1).
  *   ORC_SHIFT_NONE         no shift; breakdown = failure (CholQR, CholQR2).
- * The loop runs while ||X - I||_F >= tol (Alg. 1 line 4; the tolerance of
+ * The loop runs while ||X - I||_F >= tol (Alg. 1; the tolerance of
  * Sec. 4.1) or fewer than min_iter passes were made, for at most max_iter
  * passes.  If a shifted Cholesky still breaks down (Alg. 1 is silent), the
- * shift is multiplied by 10 as in Alg. 2 line 9, at most max_escalations
+ * shift is multiplied by 10 as in Alg. 2, at most max_escalations
  * times.
  * Returns ORC_OK, ORC_NOT_CONVERGED (valid Q, R; tolerance not met) or
  * ORC_ERR_BREAKDOWN.  Q may alias A.
@@ -255,16 +255,16 @@ int orc_cholqr(const orc_opts *o, int64_t m, int64_t n, const double *A,
   const double tol = stop_tol(o, n);
   double sigma_once = -1.0; /* isCholQR's single shift */
 
-  /* line 1: Q <- A */
+  /* Q <- A */
   if (Q != A)
     for (int64_t j = 0; j < n; ++j)
       for (int64_t i = 0; i < m; ++i) AT(Q, i, j, ldq) = AT(A, i, j, lda);
-  /* line 2: R <- I */
+  /* R <- I */
   set_identity(n, R, ldr);
-  /* line 3: X <- Q^T Q */
+  /* X <- Q^T Q */
   orc_gram(m, n, Q, ldq, X, n);
   double orth = orc_frob_minus_identity(n, X, n);
-  /* A non-finite Gramian (NaN or Inf in A) leaves the loop test of line 4
+  /* A non-finite Gramian (NaN or Inf in A) leaves the loop's stop test
    * undefined; it cannot be factored, so it is reported as a breakdown. */
   if (!isfinite(orth)) status = ORC_ERR_BREAKDOWN;
 
@@ -283,7 +283,7 @@ int orc_cholqr(const orc_opts *o, int64_t m, int64_t n, const double *A,
       inf.chol_attempts++;
       rc = orc_chol(n, X, n, sigma, Rt, n);
     } else {
-      /* line 5: try the unshifted Cholesky factorisation */
+      /* try the unshifted Cholesky factorisation */
       inf.chol_attempts++;
       rc = orc_chol(n, X, n, 0.0, Rt, n);
       if (rc != 0) {
@@ -292,7 +292,7 @@ int orc_cholqr(const orc_opts *o, int64_t m, int64_t n, const double *A,
           status = ORC_ERR_BREAKDOWN;
           break;
         }
-        /* line 6: recompute the shift from the current X */
+        /* recompute the shift from the current X */
         if (o->shift_policy == ORC_SHIFT_ISCHOLQR) {
           if (sigma_once < 0.0) sigma_once = orc_shift(m, n, orc_sym_norm2(n, X, n));
           sigma = sigma_once;
@@ -302,7 +302,7 @@ int orc_cholqr(const orc_opts *o, int64_t m, int64_t n, const double *A,
         inf.shifts++;
         if (inf.shifts == 1) inf.sigma_first = sigma;
         inf.sigma_last = sigma;
-        /* line 7: shifted Cholesky */
+        /* shifted Cholesky */
         inf.chol_attempts++;
         rc = orc_chol(n, X, n, sigma, Rt, n);
       }
@@ -321,13 +321,13 @@ int orc_cholqr(const orc_opts *o, int64_t m, int64_t n, const double *A,
       status = ORC_ERR_BREAKDOWN;
       break;
     }
-    /* line 9: Q <- Q R~^{-1} */
+    /* Q <- Q R~^{-1} */
     orc_trsm_runn(m, n, Q, ldq, Rt, n, Q, ldq);
-    /* line 10: R <- R~ R */
+    /* R <- R~ R */
     orc_trmm_upper(n, Rt, n, R, ldr, Rn, n);
     for (int64_t j = 0; j < n; ++j)
       for (int64_t i = 0; i < n; ++i) AT(R, i, j, ldr) = AT(Rn, i, j, n);
-    /* line 11: X <- Q^T Q */
+    /* X <- Q^T Q */
     orc_gram(m, n, Q, ldq, X, n);
     orth = orc_frob_minus_identity(n, X, n);
     ++it;
@@ -347,7 +347,7 @@ int orc_cholqr(const orc_opts *o, int64_t m, int64_t n, const double *A,
 /* Alg. 2 (cholQRUpdate).                                                     */
 /* ------------------------------------------------------------------------- */
 
-/* Shift of Alg. 2 line 9, first attempt: 11 (m q + q (q + 1)) u ||X||, with
+/* Shift of Alg. 2, first attempt: 11 (m q + q (q + 1)) u ||X||, with
  * q the number of existing basis columns.  For q = 0 this is zero; the
  * oracle then uses Alg. 1's formula with the block width p (a reading: with
  * no basis the update is a plain shifted CholQR of the block). */
@@ -357,7 +357,7 @@ double orc_update_shift(int64_t m, int64_t q, int64_t p, double normX) {
   return c * ORC_U * normX;
 }
 
-/* X = Q^T Q - Bt^T Bt (Alg. 2 lines 5 and 16); Q m x p, Bt q x p. */
+/* X = Q^T Q - Bt^T Bt (Alg. 2); Q m x p, Bt q x p. */
 static void update_gram(int64_t m, int64_t q, int64_t p, const double *Q,
                         int64_t ldq, const double *Bt, double *X) {
   orc_gram(m, p, Q, ldq, X, p);
@@ -375,7 +375,7 @@ static void update_gram(int64_t m, int64_t q, int64_t p, const double *Q,
  *   [Q_in Q] [[R_in, B], [0, R]] = [Q_in R_in, A_in]  (Proposition 2.1).
  * The loop runs while ||X - I||_F >= tol or fewer than min_iter outer
  * iterations were made, at most max_iter.  The inner shift loop starts at
- * sigma = 0 and follows Alg. 2 lines 8-11 (first shift from ||X||, then
+ * sigma = 0 and follows Alg. 2 (first shift from ||X||, then
  * times 10, floored at 2u), at most max_escalations shifted attempts.
  * Q_out may not alias A_in or Q_in.
  */
@@ -396,24 +396,24 @@ int orc_cholqr_update(const orc_opts *o, int64_t m, int64_t q,
   double *Bn = (double *)malloc(sizeof(double) * (size_t)(qq * p));
   double *row = (double *)malloc(sizeof(double) * (size_t)p);
 
-  /* line 1: Q <- A_in */
+  /* Q <- A_in */
   for (int64_t j = 0; j < p; ++j)
     for (int64_t i = 0; i < m; ++i) AT(Q, i, j, ldq) = AT(Ain, i, j, lda);
-  /* line 2: B <- 0 */
+  /* B <- 0 */
   for (int64_t j = 0; j < p; ++j)
     for (int64_t i = 0; i < q; ++i) AT(B, i, j, ldb) = 0.0;
-  /* line 3: R <- I_p */
+  /* R <- I_p */
   set_identity(p, R, ldr);
-  /* line 4: Bt <- Q_in^T Q */
+  /* Bt <- Q_in^T Q */
   if (q > 0) orc_gemm_tn(m, q, p, Qin, ldqin, Q, ldq, Bt, q);
-  /* line 5: X <- Q^T Q - Bt^T Bt */
+  /* X <- Q^T Q - Bt^T Bt */
   update_gram(m, q, p, Q, ldq, Bt, X);
   double orth = orc_frob_minus_identity(p, X, p);
   if (!isfinite(orth)) status = ORC_ERR_BREAKDOWN; /* as in orc_cholqr */
 
   int it = 0;
   while (status == ORC_OK && (orth >= tol || it < o->min_iter) && it < o->max_iter) {
-    /* lines 7-11: shift loop */
+    /* shift loop */
     double sigma = 0.0;
     double normX = -1.0;
     inf.chol_attempts++;
@@ -439,7 +439,7 @@ int orc_cholqr_update(const orc_opts *o, int64_t m, int64_t q,
       status = ORC_ERR_BREAKDOWN;
       break;
     }
-    /* line 12: Q <- (Q - Q_in Bt) R~^{-1}, row by row */
+    /* Q <- (Q - Q_in Bt) R~^{-1}, row by row */
     for (int64_t r = 0; r < m; ++r) {
       for (int64_t j = 0; j < p; ++j) {
         double s = AT(Q, r, j, ldq);
@@ -449,7 +449,7 @@ int orc_cholqr_update(const orc_opts *o, int64_t m, int64_t q,
       for (int64_t j = 0; j < p; ++j) AT(Q, r, j, ldq) = row[j];
     }
     orc_trsm_runn(m, p, Q, ldq, Rt, p, Q, ldq);
-    /* line 13: B <- B + Bt R */
+    /* B <- B + Bt R */
     for (int64_t j = 0; j < p; ++j)
       for (int64_t i = 0; i < q; ++i) {
         double s = 0.0;
@@ -458,13 +458,13 @@ int orc_cholqr_update(const orc_opts *o, int64_t m, int64_t q,
       }
     for (int64_t j = 0; j < p; ++j)
       for (int64_t i = 0; i < q; ++i) AT(B, i, j, ldb) = AT(Bn, i, j, q);
-    /* line 14: R <- R~ R */
+    /* R <- R~ R */
     orc_trmm_upper(p, Rt, p, R, ldr, Rn, p);
     for (int64_t j = 0; j < p; ++j)
       for (int64_t i = 0; i < p; ++i) AT(R, i, j, ldr) = AT(Rn, i, j, p);
-    /* line 15: Bt <- Q_in^T Q */
+    /* Bt <- Q_in^T Q */
     if (q > 0) orc_gemm_tn(m, q, p, Qin, ldqin, Q, ldq, Bt, q);
-    /* line 16: X <- Q^T Q - Bt^T Bt */
+    /* X <- Q^T Q - Bt^T Bt */
     update_gram(m, q, p, Q, ldq, Bt, X);
     orth = orc_frob_minus_identity(p, X, p);
     ++it;

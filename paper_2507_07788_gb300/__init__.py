@@ -40,7 +40,7 @@ SHIFT_SCHOLQR3, SHIFT_ON_BREAKDOWN, SHIFT_NONE, SHIFT_SCHOLQR3_STRICT, SHIFT_ISC
 STOP_FROB_TOL, STOP_U_SQRT_N = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 EMU_AUTO, EMU_OFF, EMU_TCGEN05 = 0, 1, 2
-MAX_N, MAX_BASIS = 128, 1024
+MAX_N, MAX_BASIS = 512, 1024
 
 
 class Opts(C.Structure):

@@ -329,7 +329,7 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
   // covers its truncation (m rows of at most e_row Ubar_i Ubar_j each, a
   // rank-one bound of norm e_row sum_j Ubar_j^2), the single rounding of the
   // G partials and their fixed-order sum (at most (G + 9) u ||X|| per entry)
-  // and the FP64 Cholesky (n (n + 1) u ||X||), in the form of Alg. 1 line 6.
+  // and the FP64 Cholesky (n (n + 1) u ||X||), in the form of Alg. 1.
   // Otherwise it is the FP32 sweep.  A sharded factorisation keeps the FP32
   // sweep: its shift does not depend on the rank's rows.
   const bool mixed_oz = mixed && (p <= kOzMaxN) && (P.o.emulation != CQR_EMU_OFF) && (P.red == nullptr);
@@ -370,6 +370,11 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
     x_rows_per_cta = ((tiles + Gx - 1) / Gx) * tr;
   }
   const bool oz = ((P.mode == MODE_FACTOR) || ozu) && (p <= kOzMaxN) && (P.o.emulation != CQR_EMU_OFF);
+  // Blocks wider than the digit Gramian (p > 128) in a factorisation or an
+  // append to an empty basis: the Gramian by column blocks on the
+  // cross-Gramian kernel (wgx), the solve the FP64 row substitution.
+  const bool wgx = ((P.mode == MODE_FACTOR) || (P.mode == MODE_UPDATE && q == 0)) && (p > kOzMaxN) &&
+                   (P.o.emulation != CQR_EMU_OFF);
   // tcgen05 kernels: the Gramian under AUTO for 33 <= n <= 64 and under
   // TCGEN05 for 17 <= n <= 64 (tc05_gram_mode); the solve under TCGEN05
   const bool tc05 = P.o.emulation == CQR_EMU_TCGEN05;
@@ -420,8 +425,10 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
   const int64_t oz_parts =
       oz ? std::max<int64_t>(std::max<int64_t>((int64_t)Goz, (int64_t)Gc), (int64_t)Gmix) * p * p : 0;
   const int64_t x_parts = (xoz || cxg) ? (int64_t)Gx * (q + p) * p : 0;
-  const int64_t part_elems = std::max<int64_t>(E, (std::max(oz_parts, x_parts) + G - 1) / G);
+  const int64_t w_parts = wgx ? wide_gram_partial_elems(P.m, p) : 0;
+  const int64_t part_elems = std::max<int64_t>(E, (std::max(std::max(oz_parts, x_parts), w_parts) + G - 1) / G);
   bool last_x = false;   // the last sweep left dense cross-Gramian partials
+  bool last_w = false;   // the last sweep left the reduced wide Gramian in C
   bool last_oz = false;  // which reduction the last sweep needs
   int last_oz_G = Goz;   // and over how many partials
 
@@ -498,6 +505,7 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
     cudaError_t e = cudaSuccess;
     last_oz = false;
     last_x = false;
+    last_w = false;
     if (xoz || cxg) {
       // projection + solve on the FP64 sweep (transform only), then the
       // cross Gramian of the new block on the tensor cores
@@ -666,6 +674,24 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
       if (mk != nullptr) cudaEventRecord(mk->b, str);
       return e;
     }
+    if (wgx && !(first && !trsm && mixed)) {
+      // the FP64 solve (transform only), then the Gramian of the result by
+      // column blocks, reduced into C
+      if (trsm) {
+        RowSweep t = a;
+        t.E = 0;
+        e = launch_rowsweep(t, G, str);
+        g_launches++;
+      }
+      int nl = 0;
+      const double *Yg = trsm ? P.Y : a.Yin;
+      const int64_t ldg = trsm ? P.ldy : a.ldyin;
+      if (e == cudaSuccess) e = launch_wide_gram(Yg, ldg, P.m, p, s.partials, s.C, p, s.st, str, &nl);
+      g_launches += nl;
+      last_w = true;
+      if (mk != nullptr) cudaEventRecord(mk->b, str);
+      return e;
+    }
     if (trsm && split) {
       // transform only, then a separate Gram sweep over the result
       RowSweep t = a;
@@ -685,6 +711,7 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
   };
   bool red_failed = false;  // a reducer call of a sharded factorisation failed
   auto reduce_local = [&]() -> cudaError_t {
+    if (last_w) return cudaSuccess;  // reduced block by block after each launch
     g_launches++;
     if (last_x) return launch_reduce_dense(s.partials, Gx, (int64_t)(q + p) * p, s.C, s.st, str);
     if (last_oz) return launch_reduce_oz(s.partials, last_oz_G, p, s.C, s.st, str);
@@ -796,7 +823,7 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
   } else {
     result = (cqr_status)hs->status;
     if (hs->iters == 0 && P.Y != P.Y0) {
-      // loop not entered (X = I): Q = A (Alg. 1 line 1 / Alg. 2 line 1)
+      // loop not entered (X = I): Q = A (Alg. 1 / Alg. 2)
       e = cudaMemcpy2DAsync(P.Y, sizeof(double) * P.ldy, P.Y0, sizeof(double) * P.ldy0,
                             sizeof(double) * P.m, p, cudaMemcpyDeviceToDevice, str);
     }
@@ -1012,11 +1039,14 @@ cqr_status cholqr_gram(const cqr_opts *opts, int64_t m, int64_t n, const double 
   // (reduced-digit on the tensor cores, or FP32 with emulation off)
   const bool mixed = o.precision == CQR_PREC_MIXED;
   const bool tc05 = tc05_gram_mode(o.emulation, p) && !mixed;
+  // wider than the digit Gramian: by column blocks, as the factorisation
+  const bool wide = (p > kOzMaxN) && (o.emulation != CQR_EMU_OFF) && !mixed;
   const int G = oz ? ozgram_grid(m, p, tc05) : rowsweep_grid(m, tile_rows);
   const int64_t tr = oz ? ozgram_tile_rows() : tile_rows;
   const int64_t tiles = (m + tr - 1) / tr;
   const int64_t rows_per_cta = ((tiles + G - 1) / G) * tr;
-  const int64_t E = oz ? (int64_t)p * p : (int64_t)p * (p + 1) / 2;
+  const int64_t E0 = oz ? (int64_t)p * p : (int64_t)p * (p + 1) / 2;
+  const int64_t E = wide ? std::max<int64_t>(E0, (wide_gram_partial_elems(m, p) + G - 1) / G) : E0;
   Scratch s;
   CQR_TRY(scratch_alloc(s, 0, p, G, E, str));
   RowSweep a{};
@@ -1041,6 +1071,10 @@ cqr_status cholqr_gram(const cqr_opts *opts, int64_t m, int64_t n, const double 
       e = cudaMemsetAsync(s.emax, 0, sizeof(int) * p, str);
     }
     if (e == cudaSuccess) e = launch_ozgram(a, G, str);
+  } else if (wide) {
+    int nl = 0;
+    e = launch_wide_gram(A, lda, m, p, s.partials, s.C, p, nullptr, str, &nl);
+    g_launches += nl - 1;
   } else if (mixed) {
     size_t smem32;
     gram32_geometry(0, p, &a.tile_rows, &a.lds, &smem32);
@@ -1049,7 +1083,7 @@ cqr_status cholqr_gram(const cqr_opts *opts, int64_t m, int64_t n, const double 
     e = launch_rowsweep(a, G, str);
   }
   g_launches++;
-  if (e == cudaSuccess) {
+  if (e == cudaSuccess && !wide) {
     if (oz) {
       e = launch_reduce_oz(s.partials, G, p, s.C, nullptr, str);
     } else {

@@ -66,8 +66,8 @@ struct DevState {
 
 // One sweep over the m rows.  The block being orthogonalised is Y (m x p);
 // Q_in (m x q, q may be 0) is the fixed basis of an update.  With do_trsm the
-// sweep first replaces each row y by (y - q_in B~) R~^{-1} (Alg. 1 line 9,
-// Alg. 2 line 12) and writes it to Yout; in every case it accumulates the
+// sweep first replaces each row y by (y - q_in B~) R~^{-1} (Alg. 1,
+// Alg. 2) and writes it to Yout; in every case it accumulates the
 // per-CTA partial sums of C = [Q_in Y]^T Y restricted to the B~ part
 // (q x p) and the upper triangle of Y^T Y, in a fixed row order.
 struct RowSweep {
@@ -154,7 +154,7 @@ constexpr int kGram32Depth = 64 + 2;
 cudaError_t launch_reduce(const Reduce &a, cudaStream_t s);
 cudaError_t launch_ctrl(const Ctrl &a, cudaStream_t s);
 size_t ctrl_smem_bytes(int p);
-// R <- R~ R (Alg. 1 line 10) with one CTA per column of R, after the control
+// R <- R~ R (Alg. 1) with one CTA per column of R, after the control
 // kernel of a pass that continues (for controls run with r_external = 1).
 cudaError_t launch_rupdate(const double *Rt, int p, double *R, int64_t ldr, const DevState *st,
                            cudaStream_t s);
@@ -220,6 +220,14 @@ int ozxgram_grid(int64_t m, int q, int p);
 int ozxgram_tile_rows();
 cudaError_t launch_reduce_dense(const double *partials, int G, int64_t E, double *C, const DevState *st,
                                 cudaStream_t s);
+// The Gramian X = Y^T Y (ld ldx, both triangles) of a block wider than the
+// digit Gramian (p > 128) by column blocks of at most 64 on the cross-Gramian
+// kernel, through `partials` (wide_gram_partial_elems doubles); adds its
+// kernel launches to *launches.
+cudaError_t launch_wide_gram(const double *Y, int64_t ldy, int64_t m, int p, double *partials, double *X,
+                             int64_t ldx, const DevState *st, cudaStream_t s, int *launches);
+int64_t wide_gram_partial_elems(int64_t m, int p);
+int wide_gram_blocks(int p);
 // Appends of at least kOzUpdMinP columns to bases of at least kOzUpdMinRows
 // rows take the tensor-core cross Gramian.  Narrower blocks keep the fused
 // FP64 sweep (its projection and Gramian share one read, and their FP64 work

@@ -2,14 +2,14 @@
 //
 // Reads the reduced Gramian C = [Q_in Y]^T Y and performs, for one pass of
 // Alg. 1 (MODE_FACTOR) or one outer iteration of Alg. 2 (MODE_UPDATE):
-//   X = Y^T Y - B~^T B~             (Alg. 2 lines 5/16; B~ empty for Alg. 1)
-//   stop test ||X - I||_F < tol     (Alg. 1 line 4, Alg. 2 line 6, Sec. 4.1)
+//   X = Y^T Y - B~^T B~             (Alg. 2; B~ empty for Alg. 1)
+//   stop test ||X - I||_F < tol     (Alg. 1, Alg. 2, Sec. 4.1)
 //   shift and Cholesky with breakdown detection and retry
-//                                   (Alg. 1 lines 5-7, Alg. 2 lines 7-11)
+//                                   (Alg. 1, Alg. 2)
 //   R~ and 1/diag(R~) for the row sweep, B <- B + B~ R, R <- R~ R
-//                                   (Alg. 1 line 10, Alg. 2 lines 13-14)
+//                                   (Alg. 1, Alg. 2)
 // Every loop is bounded (max_iter passes, max_escalations shift retries,
-// 100 power iterations), so the kernel always terminates; a failure is
+// kPowerMaxIter power iterations), so the kernel always terminates; a failure is
 // recorded in the device state and stops all later kernels of the call.
 #include <math.h>
 
@@ -19,6 +19,7 @@ namespace cqr {
 
 constexpr int kCqrMaxN = CQR_MAX_N;
 constexpr int kTinvMaxN = 128;  // widths of the tensor-core solve, whose T the tinv kernel forms
+constexpr int kPowerMaxIter = 300;  // power iterations of the norm estimate
 
 __device__ __forceinline__ int pk(int i, int j) { return i + j * (j + 1) / 2; }  // i <= j
 
@@ -62,11 +63,13 @@ __device__ __forceinline__ float d2f_trunc(double x) {
   return __int_as_float((int)(sign | ((unsigned)(e + 127) << 23) | mant));
 }
 
-// Estimate of ||X||_2 for symmetric X (the norm of Alg. 1 line 6 / Alg. 2
-// line 9, which the paper computes with a Lanczos solver at tolerance 1e-2
+// Estimate of ||X||_2 for symmetric X (the norm in the shifts of Alg. 1 and
+// Alg. 2, which the paper computes with a Lanczos solver at tolerance 1e-2
 // starting from the all-ones vector).  Power iteration in FP32 from the
-// all-ones vector, stopped when the Rayleigh quotient changes by < 1e-3
-// relative (at most 100 steps); the result is never below max_i |X_ii|.
+// all-ones vector, stopped when the part of the Rayleigh quotient still
+// missing, extrapolated from the ratio of its last two increments, is below
+// 1e-3 relative, or an increment is at FP32 resolution (at most
+// kPowerMaxIter steps); the result is never below max_i |X_ii|.
 // X enters the FP32 iteration scaled by 2^-e, e the exponent of max_i |X_ii|
 // (exact, so the iteration is the same as on X itself wherever X fits FP32),
 // which keeps Gramians of norm beyond the FP32 range (||A|| > 2^64) or
@@ -94,8 +97,8 @@ __device__ double norm_estimate(const double *X, int p, float *Xf, float *v, flo
   const float inv = rsqrtf((float)p);
   for (int i = t; i < p; i += NT) v[i] = inv;
   __syncthreads();
-  float lam = 0.0f, lam_prev = 0.0f;
-  for (int it = 0; it < 100; ++it) {
+  float lam = 0.0f, lam_prev = 0.0f, dprev = 0.0f;
+  for (int it = 0; it < kPowerMaxIter; ++it) {
     float part_l = 0.0f, part_n = 0.0f;
     for (int i = t; i < p; i += NT) {
       float s = 0.0f;
@@ -110,7 +113,16 @@ __device__ double norm_estimate(const double *X, int p, float *Xf, float *v, flo
     const float rn = 1.0f / nrm;
     for (int i = t; i < p; i += NT) v[i] = w[i] * rn;
     __syncthreads();
-    if (it > 0 && fabsf(lam - lam_prev) <= 1e-3f * fabsf(lam)) break;
+    if (it > 0) {
+      // the increments of the Rayleigh quotient shrink geometrically (ratio
+      // rho, the squared ratio of the two largest eigenvalues): the part
+      // still missing is about d rho / (1 - rho), which a close second
+      // eigenvalue makes far larger than the last increment d
+      const float d = fabsf(lam - lam_prev);
+      if (d <= 1e-6f * fabsf(lam)) break;  // at FP32 resolution
+      if (it > 1 && d < dprev && d * (d / dprev) <= 1e-3f * (1.0f - d / dprev) * fabsf(lam)) break;
+      dprev = d;
+    }
     lam_prev = lam;
   }
   double l = (double)lam * up;
@@ -345,7 +357,7 @@ __device__ void ctrl_body(const Ctrl &c, double *sm, double *gX = nullptr) {
   }
   __syncthreads();
   if (c.mode == MODE_UPDATE && q > 0) {
-    // B~ for the row sweep; B <- B + B~ R_old  (Alg. 2 line 13)
+    // B~ for the row sweep; B <- B + B~ R_old  (Alg. 2)
     for (int e = t; e < q * p; e += NT) {
       const int i = e % q, j = e / q;
       c.Bt[e] = c.C[i + (int64_t)j * ldc];
@@ -354,7 +366,7 @@ __device__ void ctrl_body(const Ctrl &c, double *sm, double *gX = nullptr) {
       c.B[i + (int64_t)j * c.ldb] = c.B[i + (int64_t)j * c.ldb] + s;
     }
   }
-  // R <- R~ R_old  (Alg. 1 line 10, Alg. 2 line 14); with r_external the
+  // R <- R~ R_old  (Alg. 1, Alg. 2); with r_external the
   // factorisation leaves it to rupdate_kernel, which spreads the columns of
   // R over SMs
   for (int e = t; e < (c.r_external ? 0 : p * p); e += NT) {

@@ -1,7 +1,7 @@
 // FP32 Gramian sweep for the mixed-precision first pass.
 //
 // The first (shifted) pass of sCholQR3 only needs its Gramian to the accuracy
-// its shift covers (the role of the shift in Alg. 1 line 6): with a shift
+// its shift covers (the role of the shift in Alg. 1): with a shift
 // sized for FP32 roundoff the Gramian can be formed from FP32 data.  On GB300
 // an FP32 FMA is ~67x cheaper than an FP64 one, so this sweep runs at memory
 // speed where the FP64 sweep is bound by the FP64 pipe.  Everything after the

@@ -1,5 +1,5 @@
 // Digit cache of a basis and the cross Gramian of narrow appends that reads
-// it (Alg. 2 lines 2-4 and 15-16: B~ = Q_in^T Y and Y^T Y in one sweep).
+// it (Alg. 2: B~ = Q_in^T Y and Y^T Y in one sweep).
 //
 // Why: an append of p <= 16 columns to a basis of q columns does about 2 q p
 // FP64 FMAs per row and pass; splitting Q_in's rows into digits on every
@@ -328,7 +328,7 @@ __global__ void __launch_bounds__(kCThreads, 2) ozcgram_kernel(RowSweep a, const
 }
 
 // ---- projection P = Q_in B~ from the cached digits, then y <- (y - P) R~^{-1}
-// (Alg. 2 line 12) in FP64, for p <= 16 and q <= 256.
+// (Alg. 2) in FP64, for p <= 16 and q <= 256.
 //
 // B~ is scaled by rows, B'_kj = B~_kj 2^(E_k - Emax) (exact powers of two,
 // Emax = max_k E_k), so that every cached digit of q_rk meets B' in one unit:

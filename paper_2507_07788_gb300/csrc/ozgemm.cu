@@ -1,5 +1,5 @@
 // Q = Y T on the tensor cores, T = R~^{-1}: the triangular solve of Alg. 1
-// line 9 in the form the paper's implementation uses (an explicit triangular
+// in the form the paper's implementation uses (an explicit triangular
 // inverse, then a matrix product; App. A), with the product done exactly on
 // bf16 digits (the Ozaki splitting scheme).
 //

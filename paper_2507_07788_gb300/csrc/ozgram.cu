@@ -2,7 +2,7 @@
 // splitting scheme: Ozaki, Ogita, Oishi, Rump, "Error-free transformations of
 // matrix multiplication by using fast routines of matrix multiplication and
 // its applications", Numer. Algorithms 59, 2012), for the FP64 Gramian
-// X = Y^T Y of Alg. 1 lines 3 and 11.
+// X = Y^T Y of Alg. 1.
 //
 // Why: GB300 retires ~1.6 FP64 FMAs per SM per clock but ~570 dense bf16
 // TFLOP/s through mma.sync, so the Gramian is computed from bf16 "digits"
@@ -96,7 +96,7 @@ __host__ __device__ constexpr OzGeom oz_geom(int NT, int PR) {
 }
 
 // One CTA: rows [g * rows_per_cta, ...) of row group g in tiles of 64;
-// optional FP64 row solve (Alg. 1 line 9, n <= 64) before the Gramian of the
+// optional FP64 row solve (Alg. 1, n <= 64) before the Gramian of the
 // tile.  Writes rows [h PR, (h+1) PR) of the group's partial P (n x n, ld n)
 // to partials[g * n * n], h = the CTA's half.
 //

@@ -1,12 +1,12 @@
 // Row sweeps over the tall dimension m (FP64 CUDA-core version).
 //
 // One kernel covers the three bandwidth-bound steps of the method:
-//   * the Gramian X = A^T A of the first pass (Alg. 1 line 3),
+//   * the Gramian X = A^T A of the first pass (Alg. 1),
 //   * the row-wise triangular solve Q = Q R~^{-1} of a pass fused with the
-//     Gramian of the result for the next pass (Alg. 1 lines 9 and 11),
+//     Gramian of the result for the next pass (Alg. 1),
 //   * for the update, the projection y <- (y - q_in B~) R~^{-1} fused with
-//     the next B~ = Q_in^T Q and Q^T Q (Alg. 2 lines 12, 15, 16; lines 4-5
-//     for the first sweep without the solve).
+//     the next B~ = Q_in^T Q and Q^T Q (Alg. 2; its initial B~ and
+//     Gramian are the first sweep, without the solve).
 // Each CTA owns a contiguous range of rows, walks it in tiles staged in
 // shared memory, and accumulates its share of C = [Q_in Y]^T Y in registers
 // in ascending row order.  The per-CTA partials are summed afterwards in a
@@ -82,7 +82,7 @@ __device__ __forceinline__ void rowsweep_body(const RowSweep &a, int bx, int by,
     if (a.do_trsm) {
       if (t < nr) {
         double *row = tile + t * lds;
-        // y <- y - q_in B~  (Alg. 2 line 12, first factor)
+        // y <- y - q_in B~  (Alg. 2, first factor)
         if (q > 0) {
           for (int j = 0; j < p; ++j) {
             double s = row[q + j];

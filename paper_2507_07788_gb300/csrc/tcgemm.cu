@@ -1,5 +1,5 @@
 // Q = Y T on the Blackwell tensor cores with tcgen05, T = D R~^{-1} (the
-// triangular solve of Alg. 1 line 9 as an explicit inverse and a product,
+// triangular solve of Alg. 1 as an explicit inverse and a product,
 // App. A), for widths 17 <= n <= 64 (padded to 64 with zeros).  The
 // arithmetic is exactly that of ozgemm.cu (the Ozaki splitting scheme with
 // balanced base-256 digits): Y's rows, scaled by D^-1, and T's columns are

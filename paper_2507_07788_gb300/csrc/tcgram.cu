@@ -1,4 +1,4 @@
-// Exact FP64 Gramian X = Y^T Y (Alg. 1 lines 3 and 11) on the Blackwell
+// Exact FP64 Gramian X = Y^T Y (Alg. 1) on the Blackwell
 // tensor cores with tcgen05: the digit scheme of ozgram.cu (Ozaki, Ogita,
 // Oishi, Rump, Numer. Algorithms 59, 2012), moved from warp-level mma.sync to
 // tcgen05.mma with TMEM accumulators, TMA row tiles and warp-specialised

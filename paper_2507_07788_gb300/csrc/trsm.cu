@@ -1,4 +1,4 @@
-// Row-wise triangular solve Q = Y R~^{-1} in FP64 (Alg. 1 line 9), one thread
+// Row-wise triangular solve Q = Y R~^{-1} in FP64 (Alg. 1), one thread
 // per row with the row held in registers.
 //
 // The solve is forward substitution on R~^T q^T = y^T, done right-looking:

@@ -57,7 +57,7 @@ def test_default_opts_and_status_strings(cq):
     (10, 4, 9, 10, 4),       # lda < m
     (10, 4, 10, 9, 4),       # ldq < m
     (10, 4, 10, 10, 3),      # ldr < n
-    (1000, 257, 1000, 1000, 257),  # n > CQR_MAX_N
+    (1000, 513, 1000, 1000, 513),  # n > CQR_MAX_N
 ])
 def test_factor_rejects_bad_sizes_without_gpu(cq, m, n, lda, ldq, ldr):
     fake = C.c_void_p(0x1000)
@@ -104,7 +104,7 @@ def test_factor_host_rejects_overlap_without_gpu(cq):
 @pytest.mark.parametrize("m,n,r,lda,ldq,ldr", [
     (100, 8, 0, 100, 100, 8),       # r = 0
     (100, 8, 9, 100, 100, 8),       # r > n
-    (2000, 600, 2, 2000, 2000, 600),  # panel of 300 columns > CQR_MAX_N
+    (2000, 1000, 1, 2000, 2000, 1000),  # panel of 1000 columns > CQR_MAX_N
     (5, 8, 2, 5, 5, 8),             # m < n
     (100, 8, 2, 99, 100, 8),        # lda < m
     (100, 8, 2, 100, 100, 7),       # ldr < n

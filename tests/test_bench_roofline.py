@@ -136,3 +136,13 @@ def test_append_bytes_follow_alg2_sweeps():
     assert bench.append_hbm_bytes(m, q, p, 0) == 8.0 * m * (q + p)
     assert bench.append_hbm_bytes(m, q, p, 2) == 8.0 * m * (q + p) + 2 * (8.0 * m * (q + p) + 8.0 * m * p)
     assert bench.append_hbm_bytes(m, 0, p, 1) == 8.0 * m * p + 16.0 * m * p
+
+
+def test_kernel_hash_ignores_comments_only():
+    # a comment or blank-line change keeps a capture's counters valid; a
+    # change of code does not
+    a = "int x; // old note\n/* a block\n   comment */\nint y;\n"
+    b = "int x;   // new note\n\nint y;  /* another */\n"
+    assert bench.strip_comments(a) == bench.strip_comments(b)
+    assert bench.strip_comments("int x = 1;") != bench.strip_comments("int x = 2;")
+

@@ -265,7 +265,7 @@ def test_host_entry_point_last_pass_not_foreseen(cq):
 
 
 def test_host_entry_point_orthonormal_input(cq):
-    # X = I on the first Gramian: no pass runs and Q = A, R = I (Alg. 1 line 1)
+    # X = I on the first Gramian: no pass runs and Q = A, R = I (Alg. 1)
     m, n = 160003, 8
     A = np.zeros((m, n))
     A[np.arange(n) * 1000, np.arange(n)] = 1.0

@@ -1,4 +1,4 @@
-"""The Gramian X = A^T A (Alg. 1 line 3) as the library forms it
+"""The Gramian X = A^T A (Alg. 1) as the library forms it
 (cholqr_gram): tensor-core digit arithmetic (Ozaki splitting) for n <= 128
 (emulation AUTO: the tcgen05 kernel for 33 <= n <= 64 and the warp-level
 mma.sync kernels elsewhere; emulation TCGEN05: the tcgen05 kernel for

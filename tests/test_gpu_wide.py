@@ -1,11 +1,15 @@
-"""Widths above 128 (up to CQR_MAX_N = 256): the FP64 row sweeps (the
-Gramian split over several sweeps of its entries, the solve as a row-wise
-substitution) and the control step on a global-memory working buffer.
-Parity with the oracle by the bounds of tests/parity.py for the
-factorisation at n = 129, 200 and 256, the Gramian at n = 256, an append of
+"""Widths above 128 (up to CQR_MAX_N = 512).  The Gramian is formed by
+column blocks of at most 64 on the tensor-core cross-Gramian kernel (exact
+digit products; with CQR_EMU_OFF the FP64 row sweep split over several
+sweeps of its entries), the solve is the row-wise FP64 substitution, and the
+control step works on a global-memory copy of the n x n Gramian.  Parity with
+the oracle by the bounds of tests/parity.py for the factorisation at n = 129,
+200, 256, 300 and 512 (both Gramians), the Gramian at n = 256 and 512
+(against the oracle's, and exactly on integer data whose Gramian FP64 holds
+without rounding, which any misplaced or dropped block fails), an append of
 160 columns to a basis of 64 (the oracle's Alg. 2 on its own basis of the
-first block), and pnCholQR with 150-column panels (the oracle's Alg. 3); the
-first width on the wide path, n = 129, beside the others."""
+first block), an append of 300 columns to an empty basis, and pnCholQR with
+150-column panels (the oracle's Alg. 3)."""
 import numpy as np
 import pytest
 
@@ -26,11 +30,14 @@ def cq():
     return cq
 
 
+@pytest.mark.parametrize("emulation", ["auto", "off"])
 @pytest.mark.parametrize("m,n,kappa", [(20011, 129, 1e6), (30007, 200, 1e10), (40013, 256, 1e12),
-                                       (20011, 256, 1e4)])
-def test_wide_factor_against_oracle(cq, orc, m, n, kappa):
+                                       (20011, 256, 1e4), (25013, 300, 1e8), (30011, 512, 1e12),
+                                       (12007, 512, 1e3)])
+def test_wide_factor_against_oracle(cq, orc, m, n, kappa, emulation):
     A = synth.test_matrix(m, n, kappa, rep=31)
-    res = cq.factor(cq.to_colmajor(A), check=False)
+    emu = cq.EMU_AUTO if emulation == "auto" else cq.EMU_OFF
+    res = cq.factor(cq.to_colmajor(A), opts=cq.default_opts(emulation=emu), check=False)
     torch.cuda.synchronize()
     assert res.status == cq.OK, res.info
     Q, R = res.Q.cpu().numpy(), res.R.cpu().numpy()
@@ -41,20 +48,52 @@ def test_wide_factor_against_oracle(cq, orc, m, n, kappa):
     assert sto == cq.OK
     check_q(float(np.max(np.abs(Q - Qo))), kappa, m, f"wide n={n} kappa={kappa:g}")
     check_r(float(np.max(np.abs(R - Ro))), kappa, Ro, m, f"wide n={n} kappa={kappa:g}")
-    # the first shift from the Gramian's norm (Alg. 1 line 6)
+    # the first shift from the Gramian's norm (Alg. 1)
     lam = orc.sym_norm2(orc.gram(A))
     assert res.info["sigma_first"] == pytest.approx(orc.shift(m, n, lam), rel=1e-2)
 
 
-def test_wide_gramian_against_oracle(cq, orc):
-    m, n = 30011, 256
+def partials_max():
+    return 2 * torch.cuda.get_device_properties(0).multi_processor_count
+
+
+@pytest.mark.parametrize("emulation", ["auto", "off"])
+@pytest.mark.parametrize("m,n", [(30011, 256), (20011, 512), (7001, 449)])
+def test_wide_gramian_against_oracle(cq, orc, m, n, emulation):
     A = synth.test_matrix(m, n, 1e8, rep=32)
-    X = cq.gram(cq.to_colmajor(A)).cpu().numpy()
+    emu = cq.EMU_AUTO if emulation == "auto" else cq.EMU_OFF
+    X = cq.gram(cq.to_colmajor(A), opts=cq.default_opts(emulation=emu)).cpu().numpy()
     Xo = orc.gram(A)
     absA = np.abs(A)
-    bound = 2.0 * (m * U / (1 - m * U)) * (absA.T @ absA) + 1e-300
-    assert np.all(np.abs(X - Xo) <= bound), float(np.max(np.abs(X - Xo) / bound))
+    err = np.abs(X - Xo)
+    # the oracle's own error plus that of X: the FP64 sweep's m u |A|^T|A|
+    # (recursive summation), or for the digit products the single rounding
+    # of each row group's partial and their fixed-order sum
+    oracle_err = (m * U / (1 - m * U)) * (absA.T @ absA)
+    own = oracle_err if emulation == "off" else (partials_max() + 12) * U * (absA.T @ absA)
+    bound = oracle_err + own + 1e-300
+    assert np.all(err <= bound), float(np.max(err / bound))
     assert np.array_equal(X, X.T)
+
+
+@pytest.mark.parametrize("m,n", [(20011, 512), (5003, 300)])
+def test_wide_gramian_exact_on_integers(cq, m, n):
+    """Integer entries in [-1024, 1024]: every product and partial sum is an
+    integer below 2^53, so the Gramian is exact in any summation order and
+    both kernels must return it bit for bit."""
+    rng = np.random.default_rng(n)
+    A = rng.integers(-1024, 1025, size=(m, n)).astype(np.float64)
+    A[:, 7] = 0.0  # a zero column
+    A[:, n - 1] *= 2.0 ** -30  # a column on another scale (still exact)
+    Ai = A.copy()
+    Ai[:, n - 1] *= 2.0 ** 30
+    Xi = Ai.astype(np.int64).T @ Ai.astype(np.int64)  # exact integer Gramian
+    Xe = Xi.astype(np.float64)
+    Xe[:, n - 1] *= 2.0 ** -30
+    Xe[n - 1, :] *= 2.0 ** -30
+    for emu in (cq.EMU_AUTO, cq.EMU_OFF):
+        X = cq.gram(cq.to_colmajor(A), opts=cq.default_opts(emulation=emu)).cpu().numpy()
+        assert np.array_equal(X, Xe), (emu, float(np.max(np.abs(X - Xe))))
 
 
 def test_wide_append_against_oracle(cq, orc):
@@ -97,3 +136,19 @@ def test_wide_pn_panels(cq, orc):
     assert sto >= 0
     check_q(float(np.max(np.abs(Q - Qo))), kappa, m, "wide pn")
     check_r(float(np.max(np.abs(R - Ro))), kappa, Ro, m, "wide pn")
+
+
+def test_wide_append_to_empty_basis(cq, orc):
+    m, p = 20011, 300
+    A = synth.test_matrix(m, p, 1e6, rep=35)
+    b = cq.Basis(m, p)
+    st, info = b.append(cq.to_colmajor(A))
+    assert st == cq.OK, info
+    Q, R = b.Q().cpu().numpy(), b.R().cpu().numpy()
+    b.close()
+    check_orth(Q, "wide append to an empty basis")
+    assert orc.rrr(A, Q, np.triu(R)) <= 1e-13
+    Qn, Bn, Rn, sto, _ = orc.cholqr_update(np.zeros((m, 0)), A, min_iter=2)
+    assert sto >= 0
+    check_q(float(np.max(np.abs(Q - Qn))), 1e6, m, "wide append to an empty basis")
+    check_r(float(np.max(np.abs(R - Rn))), 1e6, Rn, m, "wide append to an empty basis")

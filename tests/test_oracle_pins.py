@@ -118,7 +118,7 @@ def test_shift_floor(orc):
 
 
 def test_update_shift_uses_basis_width(orc):
-    # Alg. 2 line 9 uses q, the width of the existing basis
+    # Alg. 2 uses q, the width of the existing basis
     assert orc.update_shift(1000, 5, 8, 2.0) == pytest.approx(11 * (1000 * 5 + 5 * 6) * U * 2.0, rel=1e-15)
     # q = 0: falls back to Alg. 1 with the block width
     assert orc.update_shift(1000, 0, 8, 2.0) == pytest.approx(orc.shift(1000, 8, 2.0), rel=0)
@@ -127,7 +127,7 @@ def test_update_shift_uses_basis_width(orc):
 def test_alg1_shift_on_breakdown_uses_spectral_norm(orc):
     # columns a, a, b with a, b orthonormal: X = [[1,1,0],[1,1,0],[0,0,1]],
     # ||X||_2 = 2, ||X||_F = sqrt(5), max diag = 1.  The unshifted Cholesky
-    # breaks down at pivot 2, so Alg. 1 lines 5-7 apply.
+    # breaks down at pivot 2, so Alg. 1 apply.
     m = 64
     A = np.zeros((m, 3))
     A[0, 0] = A[0, 1] = 1.0
