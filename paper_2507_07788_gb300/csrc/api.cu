@@ -226,11 +226,12 @@ struct Scratch {
   int *fexp;
   int *emax;     // column exponents of the reduced-digit first Gramian
   double *cwork; // global working storage of the control step (p > kCtrlSmemMaxP)
+  void *xwork;   // working storage of the wide solve (or null)
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-cudaError_t scratch_alloc(Scratch &s, int q, int p, int G, int64_t E, cudaStream_t str) {
+cudaError_t scratch_alloc(Scratch &s, int q, int p, int G, int64_t E, cudaStream_t str, size_t xbytes = 0) {
   const size_t b_st = align256(sizeof(DevState));
   const size_t b_C = align256(sizeof(double) * (size_t)(q + p) * p);
   const size_t b_Rt = align256(sizeof(double) * (size_t)p * p);
@@ -241,8 +242,9 @@ cudaError_t scratch_alloc(Scratch &s, int q, int p, int G, int64_t E, cudaStream
   const size_t b_Ts = align256(sizeof(int) * (size_t)p);
   const size_t b_Bd = align256(ozcproj_scratch_bytes());
   const size_t b_W = (p > kCtrlSmemMaxP) ? align256(ctrl_smem_bytes(p)) : 0;
+  const size_t b_X = align256(xbytes);
   cudaError_t e = cudaMallocAsync((void **)&s.base,
-                                  b_st + b_C + 2 * b_Rt + b_Rd + b_Bt + 2 * b_Ts + b_Bd + b_W + b_P, str);
+                                  b_st + b_C + 2 * b_Rt + b_Rd + b_Bt + 2 * b_Ts + b_Bd + b_W + b_X + b_P, str);
   if (e != cudaSuccess) return e;
   char *p0 = s.base;
   s.st = (DevState *)p0;
@@ -266,6 +268,8 @@ cudaError_t scratch_alloc(Scratch &s, int q, int p, int G, int64_t E, cudaStream
   p0 += b_Bd;
   s.cwork = b_W ? (double *)p0 : nullptr;
   p0 += b_W;
+  s.xwork = b_X ? (void *)p0 : nullptr;
+  p0 += b_X;
   s.partials = (double *)p0;
   return cudaSuccess;
 }
@@ -375,6 +379,9 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
   // cross-Gramian kernel (wgx), the solve the FP64 row substitution.
   const bool wgx = ((P.mode == MODE_FACTOR) || (P.mode == MODE_UPDATE && q == 0)) && (p > kOzMaxN) &&
                    (P.o.emulation != CQR_EMU_OFF);
+  // and their solve Q = Y T on the tensor cores, T = D R~^{-1} formed after
+  // each control step (the contraction in blocks of 64)
+  const bool wsolve = wgx;
   // tcgen05 kernels: the Gramian under AUTO for 33 <= n <= 64 and under
   // TCGEN05 for 17 <= n <= 64 (tc05_gram_mode); the solve under TCGEN05
   const bool tc05 = P.o.emulation == CQR_EMU_TCGEN05;
@@ -433,7 +440,7 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
   int last_oz_G = Goz;   // and over how many partials
 
   Scratch s;
-  CQR_TRY(scratch_alloc(s, q, p, G, part_elems, str));
+  CQR_TRY(scratch_alloc(s, q, p, G, part_elems, str, wsolve ? wide_solve_scratch_bytes(P.m, p) : 0));
   DevState *hs = host_state();
   cqr_status result = CQR_OK;
   const bool timing = g_timing_on.load() != 0;
@@ -677,7 +684,13 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
     if (wgx && !(first && !trsm && mixed)) {
       // the FP64 solve (transform only), then the Gramian of the result by
       // column blocks, reduced into C
-      if (trsm) {
+      if (trsm && wsolve) {
+        RowSweep t = a;
+        t.Tinv = s.Tinv;
+        t.Tscale = s.Tscale;
+        e = launch_wide_solve(t, s.xwork, str);
+        g_launches += 3;
+      } else if (trsm) {
         RowSweep t = a;
         t.E = 0;
         e = launch_rowsweep(t, G, str);
@@ -765,7 +778,7 @@ cqr_status run(const Problem &P, cqr_info *info, cudaStream_t str) {
       e = launch_rupdate(s.Rt, p, P.R, P.ldr, s.st, str);
     }
     // T = D R~^{-1} for the next pass's tensor-core solve
-    if (e == cudaSuccess && gemm) {
+    if (e == cudaSuccess && (gemm || wsolve)) {
       g_launches++;
       e = launch_tinv(s.Rt, s.Rdinv, s.C, q + p, q, p, s.Tinv, s.Tscale, s.st, str);
     }

@@ -212,6 +212,12 @@ constexpr int kOzCacheMaxP = 16;
 // bf16 FLOPs the tensor-core solve issues per row at width n (digit pairs x
 // the k-blocks its upper-triangular T does not skip).
 double ozgemm_tc_flops_per_row(int n, bool tc05 = true);
+// Q = Y T (T = D R~^{-1}, a.Tinv and a.Tscale from launch_tinv) on the
+// tensor cores for 128 < n <= CQR_MAX_N: the contraction in blocks of 64,
+// one 64-column block of Q per CTA; three launches (T's digits, the row
+// exponents, the product) through `scratch` (wide_solve_scratch_bytes).
+cudaError_t launch_wide_solve(const RowSweep &a, void *scratch, cudaStream_t s);
+size_t wide_solve_scratch_bytes(int64_t m, int n);
 constexpr int kOzGemmMaxN = 128;
 // Cross Gramian of the update, C = [Q_in Y]^T Y, on the tensor cores (exact
 // digit products, p <= 64): partials of `groups` row groups, each (q + p) x p.

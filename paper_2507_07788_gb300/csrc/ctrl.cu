@@ -443,18 +443,22 @@ size_t ctrl_smem_bytes(int p) {
 // by 2^c_i, c_i = floor(log2 sqrt(X_ii)): the product Q = Y T is formed as
 // (Y D^-1)(D T), D = diag(2^c), which balances the columns of Y and the rows
 // of T (exact: powers of two).  Rows are independent, so they run on
-// separate SMs.
+// separate SMs.  Up to kTinvMaxN columns R~ is copied to shared memory;
+// above (GLOBAL_R) the sums read its columns from global memory (L2), 32
+// consecutive entries per step.
+template <bool GLOBAL_R>
 __global__ void __launch_bounds__(128) tinv_kernel(const double *Rt, const double *Rdinv, const double *C,
                                                    int ldc, int q, int p, double *Tinv, int *Tscale,
                                                    const DevState *st) {
   if (st != nullptr && st->done) return;
-  extern __shared__ double sh[];  // R~ (p x p, ld p), 1 / diag, then row i of T
-  double *Rs = sh, *rd = sh + (size_t)p * p, *tr = rd + p;
+  extern __shared__ double sh[];  // [R~ (p x p, ld p)], 1 / diag, then row i of T
+  const double *Rs = GLOBAL_R ? Rt : sh;
+  double *rd = GLOBAL_R ? sh : sh + (size_t)p * p, *tr = rd + p;
   const int i = blockIdx.x, t = threadIdx.x, lane = t & 31;
   if (i >= p) return;
   // the dependent steps below read only shared memory; the copy issues 8
   // loads before it stores (the loads are then in flight together)
-  for (int e0 = 0; e0 < p * p; e0 += 8 * 128) {
+  for (int e0 = 0; !GLOBAL_R && e0 < p * p; e0 += 8 * 128) {
     double v[8];
 #pragma unroll
     for (int h = 0; h < 8; ++h) {
@@ -464,7 +468,7 @@ __global__ void __launch_bounds__(128) tinv_kernel(const double *Rt, const doubl
 #pragma unroll
     for (int h = 0; h < 8; ++h) {
       const int e = e0 + h * 128 + t;
-      if (e < p * p) Rs[e] = v[h];
+      if (e < p * p) sh[e] = v[h];
     }
   }
   for (int j = t; j < p; j += blockDim.x) {
@@ -477,7 +481,7 @@ __global__ void __launch_bounds__(128) tinv_kernel(const double *Rt, const doubl
   __syncwarp();
   for (int j = i + 1; j < p; ++j) {
     double s = 0.0;
-    for (int k = i + lane; k < j; k += 32) s = fma(tr[k], Rs[k + j * p], s);
+    for (int k = i + lane; k < j; k += 32) s = fma(tr[k], Rs[k + (int64_t)j * p], s);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) tr[j] = -s * rd[j];
@@ -523,12 +527,16 @@ cudaError_t launch_rupdate(const double *Rt, int p, double *R, int64_t ldr, cons
 
 cudaError_t launch_tinv(const double *Rt, const double *Rdinv, const double *C, int ldc, int q, int p,
                         double *Tinv, int *Tscale, const DevState *st, cudaStream_t s) {
-  if (p > kTinvMaxN) return cudaErrorInvalidValue;  // R~ and a row of T in shared memory (133 KB at 128)
-  static KernelAttr attr;
+  if (p > kCqrMaxN) return cudaErrorInvalidValue;
+  if (p > kTinvMaxN) {  // R~ read from global memory; 1 / diag and a row of T in shared memory
+    tinv_kernel<true><<<p, 128, sizeof(double) * 2 * (size_t)p, s>>>(Rt, Rdinv, C, ldc, q, p, Tinv, Tscale, st);
+    return cudaGetLastError();
+  }
+  static KernelAttr attr;  // R~ and a row of T in shared memory (133 KB at 128)
   const size_t smem = sizeof(double) * ((size_t)kTinvMaxN * kTinvMaxN + 2 * kTinvMaxN);
-  set_smem_attr(attr, tinv_kernel, (int)smem, false);
-  tinv_kernel<<<p, 128, sizeof(double) * ((size_t)p * p + 2 * p), s>>>(Rt, Rdinv, C, ldc, q, p, Tinv, Tscale,
-                                                                      st);
+  set_smem_attr(attr, tinv_kernel<false>, (int)smem, false);
+  tinv_kernel<false><<<p, 128, sizeof(double) * ((size_t)p * p + 2 * p), s>>>(Rt, Rdinv, C, ldc, q, p, Tinv,
+                                                                             Tscale, st);
   return cudaGetLastError();
 }
 

@@ -541,4 +541,285 @@ cudaError_t launch_ozgemm(const RowSweep &a, int grid, cudaStream_t s) {
   return launch_gm_tiled<128>(a, grid, s);
 }
 
+// ---- The same product for blocks wider than 128 columns (wide solve).
+//
+// D T no longer fits in shared memory, so the contraction runs in blocks of
+// 64 k and the CTA's output is one 64-column block J of Q (k < 64 (J + 1):
+// T is upper triangular).  Per pass, two small kernels prepare the operands:
+//   * wide_tdigits_kernel: the column exponents f_j of D T and its eight
+//     digit planes in global memory, Td[d][j][k] (k < npad = 64 nb, zero for
+//     k > j and k >= n), read by every CTA of block J (L2-resident, 4 MB at
+//     n = 512);
+//   * wide_rowexp_kernel: each row's largest scaled exponent e_r over all n
+//     columns (or kBadRow for a row with a NaN or Inf), so that a row has one
+//     representation in every K block.
+// The digits, orders, drains and the rounding are those of ozgemm_kernel;
+// the two int64 words of an entry add up the K blocks exactly (each block
+// adds less than 2^47 to either word).  A CTA owns whole rows (tiles of 32)
+// and forms their 64-column output blocks one after another, so the product
+// may run in place; 8 warps of 16 rows x 16 columns, T's digit block and the
+// tile's digit planes in shared memory (110 KB: two CTAs per SM); the next K
+// block's Y values are loaded into registers while the current one is
+// multiplied.
+namespace {
+
+constexpr int kWsTR = 32;        // tile rows
+constexpr int kWsJB = 64;        // output columns per CTA
+constexpr int kWsKB = 64;        // contraction block
+constexpr int kWsLd = kWsKB + 8; // bf16 stride of a digit-plane row (k contiguous)
+constexpr int kBadRow = 1 << 29; // row exponent of a row with a NaN or Inf
+constexpr size_t kWsSmem = sizeof(uint16_t) * (size_t)kGmDigits * kWsJB * kWsLd     // T digit block
+                           + sizeof(uint16_t) * (size_t)kGmDigits * kWsTR * kWsLd   // Y tile digits
+                           + sizeof(int) * (size_t)(kWsJB + kWsTR + CQR_MAX_N);
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+
+}  // namespace
+
+struct WideSolve {
+  int64_t m;
+  int32_t n, npad;
+  const double *Y;
+  int64_t ldy;
+  double *Q;
+  int64_t ldq;
+  const int *Tscale;    // n: c_k
+  const uint16_t *Td;   // [8][n][npad] bf16 digits of D T
+  const int *fcol;      // n: column exponents of D T
+  const int *erow;      // m: row exponents (kBadRow: NaN row)
+  int64_t rows_per_cta;
+  const DevState *st;
+};
+
+// f_j and the digit planes of column j of D T (one CTA per column).
+__global__ void __launch_bounds__(128) wide_tdigits_kernel(const double *Tinv, int n, int npad, uint16_t *Td,
+                                                           int *fcol, const DevState *st) {
+  if (st != nullptr && st->done) return;
+  __shared__ int red[4];
+  const int j = blockIdx.x, t = threadIdx.x;
+  const double *col = Tinv + (int64_t)j * n;
+  int mx = 1;
+  for (int k = t; k <= j; k += 128) mx = max(mx, align_exp((unsigned long long)__double_as_longlong(col[k])));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((t & 31) == 0) red[t >> 5] = mx;
+  __syncthreads();
+  const int f = max(max(red[0], red[1]), max(red[2], red[3]));
+  if (t == 0) fcol[j] = f;
+  for (int k = 2 * t; k < npad; k += 256) {
+    unsigned long long b[2] = {0ull, 0ull};
+    for (int h = 0; h < 2; ++h)
+      if (k + h <= j) b[h] = (unsigned long long)__double_as_longlong(col[k + h]);
+    const unsigned long long V0 = digits63(b[0], f, 0) + kBalance, V1 = digits63(b[1], f, 0) + kBalance;
+    const float sg0 = (b[0] >> 63) ? -1.0f : 1.0f, sg1 = (b[1] >> 63) ? -1.0f : 1.0f;
+#pragma unroll
+    for (int d = 0; d < kGmDigits; ++d)
+      *(uint32_t *)(Td + ((size_t)d * n + j) * npad + k) = digit_pair_bf16(V0, V1, d, sg0, sg1);
+  }
+}
+
+// e_r = max_k (exponent of y_rk - c_k) over the row (zeros ignored), or
+// kBadRow when the row holds a NaN or Inf (one thread per row).
+__global__ void __launch_bounds__(256) wide_rowexp_kernel(const double *Y, int64_t ldy, int64_t m, int n,
+                                                          const int *Tscale, int *erow, const DevState *st) {
+  if (st != nullptr && st->done) return;
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= m) return;
+  int mx = kNoExp;
+  bool bad = false;
+#pragma unroll 8
+  for (int k = 0; k < n; ++k) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(Y[r + (int64_t)k * ldy]);
+    bad |= ((b >> 52) & 0x7FF) == 0x7FF;
+    mx = max(mx, scaled_exp(b, __ldg(Tscale + k)));
+  }
+  erow[r] = bad ? kBadRow : mx;
+}
+
+// CTA x: rows [x rows_per_cta, ...) in tiles of 32; for each tile the
+// output blocks J = nb - 1, ..., 0 in turn.  Block J reads columns
+// k < 64 (J + 1) and writes columns 64 J .. 64 J + 63, so with Q == Y (in
+// place) no later block of the tile reads what an earlier one wrote.
+__global__ void __launch_bounds__(kGmThreads, 2) ozwsolve_kernel(WideSolve a) {
+  if (a.st != nullptr && a.st->done) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint16_t *planesT = (uint16_t *)smem;                                   // [8][64 j][kWsLd]
+  uint16_t *planesY = planesT + (size_t)kGmDigits * kWsJB * kWsLd;        // [8][32 rows][kWsLd]
+  int *fc = (int *)(planesY + (size_t)kGmDigits * kWsTR * kWsLd);         // [64]
+  int *er = fc + kWsJB;                                                   // [32]
+  int *cs = er + kWsTR;                                                   // [n]
+
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int n = a.n, nb = a.npad / kWsKB;
+  const int64_t row0 = (int64_t)blockIdx.x * a.rows_per_cta;
+  const int64_t row1 = min(a.m, row0 + a.rows_per_cta);
+  if (row0 >= row1) return;
+  for (int k = t; k < n; k += kGmThreads) cs[k] = a.Tscale[k];
+
+  // warp -> rows 16 ib .. + 15, columns 16 cg .. + 15 (two 8-column tiles)
+  const int ib = warp & 1, cg = warp >> 1, i0 = 16 * ib;
+  const int mi = lane >> 3, rr = lane & 7;
+  const uint32_t aY = smem_u32(planesY + (size_t)(i0 + (mi & 1) * 8 + rr) * kWsLd + (mi >> 1) * 8);
+  const uint32_t bT = smem_u32(planesT + (size_t)(16 * cg + (mi >> 1) * 8 + rr) * kWsLd + (mi & 1) * 8);
+  constexpr uint32_t kStrY = 2u * kWsTR * kWsLd, kStrT = 2u * kWsJB * kWsLd;
+  // loader: thread (lr, kc) holds k = 8 kc .. 8 kc + 7 of row lr of a K block
+  const int lr = t & (kWsTR - 1), kc = t >> 5;
+
+  for (int64_t r0 = row0; r0 < row1; r0 += kWsTR) {
+    const int nr = (int)min((int64_t)kWsTR, row1 - r0);
+    const int e_r = (lr < nr) ? a.erow[r0 + lr] : kNoExp;
+    auto load_y = [&](int kb, unsigned long long (&bv)[8]) {
+#pragma unroll
+      for (int h = 0; h < 8; ++h) {
+        const int k = kWsKB * kb + 8 * kc + h;
+        bv[h] = (lr < nr && k < n) ? (unsigned long long)__double_as_longlong(a.Y[(r0 + lr) + (int64_t)k * a.ldy])
+                                   : 0ull;
+      }
+    };
+    for (int J = nb - 1; J >= 0; --J) {
+      const int j0 = kWsJB * J;
+      unsigned long long bv[8];
+      load_y(0, bv);
+      long long hi[8], lo[8];
+#pragma unroll
+      for (int o = 0; o < 8; ++o) hi[o] = lo[o] = 0;
+      for (int kb = 0; kb <= J; ++kb) {
+        __syncthreads();  // every warp is done with the previous planes (and fc, er)
+        if (kb == 0) {
+          if (t < kWsJB) fc[t] = (j0 + t < n) ? a.fcol[j0 + t] : 0;
+          if (kc == 0 && J == nb - 1) er[lr] = e_r;
+        }
+        // T's digit block (kb, J): 8 planes x 64 columns x 64 k, zero past n
+        for (int e = t; e < kGmDigits * kWsJB * (kWsKB / 8); e += kGmThreads) {
+          const int c8 = e & 7, jj = (e >> 3) & (kWsJB - 1), d = e >> 9;
+          const bool live = j0 + jj < n;
+          const uint16_t *src = live ? a.Td + ((size_t)d * n + j0 + jj) * a.npad + kWsKB * kb + 8 * c8 : a.Td;
+          cp_async16(planesT + ((size_t)d * kWsJB + jj) * kWsLd + 8 * c8, src, live ? 16 : 0);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        // the tile's digits of this block
+        {
+          unsigned long long V[8];
+          float sg[8];
+#pragma unroll
+          for (int h = 0; h < 8; ++h) {
+            const int k = kWsKB * kb + 8 * kc + h;
+            V[h] = digits63(bv[h], e_r, k < n ? cs[k] : 0) + kBalance;
+            sg[h] = (bv[h] >> 63) ? -1.0f : 1.0f;
+          }
+#pragma unroll
+          for (int d = 0; d < kGmDigits; ++d) {
+            uint4 w;
+            w.x = digit_pair_bf16(V[0], V[1], d, sg[0], sg[1]);
+            w.y = digit_pair_bf16(V[2], V[3], d, sg[2], sg[3]);
+            w.z = digit_pair_bf16(V[4], V[5], d, sg[4], sg[5]);
+            w.w = digit_pair_bf16(V[6], V[7], d, sg[6], sg[7]);
+            *(uint4 *)(planesY + ((size_t)d * kWsTR + lr) * kWsLd + 8 * kc) = w;
+          }
+        }
+        if (kb < J) load_y(kb + 1, bv);  // in flight during the products
+        cp_async_wait_all();
+        __syncthreads();
+        // orders 0..3 into hi, orders 4..7 into lo (exact: below 2^24 per block)
+        {
+          float c[4][2][4];
+#pragma unroll
+          for (int d = 0; d < 4; ++d)
+#pragma unroll
+            for (int tl = 0; tl < 2; ++tl) c[d][tl][0] = c[d][tl][1] = c[d][tl][2] = c[d][tl][3] = 0.0f;
+          gm_steps<2, 5, 4, 0>(c, aY, kStrY, bT, kStrT, 0, kWsKB / 16);
+#pragma unroll
+          for (int o = 0; o < 8; ++o) {
+            const int tl = o >> 2, r = o & 3;
+            const int t0 = f2i(c[0][tl][r]), t1 = f2i(c[1][tl][r]), t2 = f2i(c[2][tl][r]);
+            const int t3 = f2i(c[3][tl][r]);
+            hi[o] += ((long long)(t0 * 256 + t1) << 16) + (long long)(t2 * 256 + t3);
+          }
+        }
+        {
+          float c[4][2][4];
+#pragma unroll
+          for (int d = 0; d < 4; ++d)
+#pragma unroll
+            for (int tl = 0; tl < 2; ++tl) c[d][tl][0] = c[d][tl][1] = c[d][tl][2] = c[d][tl][3] = 0.0f;
+          gm_steps<6, 9, 8, 0>(c, aY, kStrY, bT, kStrT, 0, kWsKB / 16);
+#pragma unroll
+          for (int o = 0; o < 8; ++o) {
+            const int tl = o >> 2, r = o & 3;
+            const int t4 = f2i(c[0][tl][r]), t5 = f2i(c[1][tl][r]), t6 = f2i(c[2][tl][r]);
+            const int t7 = f2i(c[3][tl][r]);
+            lo[o] += ((long long)(t4 * 256 + t5) << 16) + (long long)(t6 * 256 + t7);
+          }
+        }
+      }
+      // ---- Q_rj = (hi 2^32 + lo) 2^(e_r + f_j - 2114), rounded once
+#pragma unroll
+      for (int o = 0; o < 8; ++o) {
+        const int tl = o >> 2, r = o & 3;
+        const int row = i0 + (lane >> 2) + ((r >> 1) << 3);
+        const int jj = 16 * cg + 8 * tl + 2 * (lane & 3) + (r & 1);
+        if (row >= nr || j0 + jj >= n) continue;
+        const int e = er[row];
+        const double v = (e == kBadRow) ? __longlong_as_double(0x7FF8000000000000ll)
+                                        : fixed_to_double(hi[o], lo[o], 32, e + fc[jj] - 2114);
+        a.Q[(r0 + row) + (int64_t)(j0 + jj) * a.ldq] = v;
+      }
+    }
+  }
+}
+
+int wide_solve_npad(int n) { return ((n + kWsKB - 1) / kWsKB) * kWsKB; }
+
+size_t wide_solve_scratch_bytes(int64_t m, int n) {
+  return sizeof(uint16_t) * (size_t)kGmDigits * n * wide_solve_npad(n) + sizeof(int) * (size_t)n +
+         sizeof(int) * (size_t)m + 1024;
+}
+
+// Q = Y T for 128 < n <= CQR_MAX_N (a.Yin, a.Yout, a.Tinv, a.Tscale, a.m,
+// a.p, a.st); `scratch` holds wide_solve_scratch_bytes(m, n) bytes.
+cudaError_t launch_wide_solve(const RowSweep &a, void *scratch, cudaStream_t s) {
+  const int n = a.p;
+  if (a.Tinv == nullptr || a.Tscale == nullptr || scratch == nullptr) return cudaErrorInvalidValue;
+  if (n <= kOzGemmMaxN || n > CQR_MAX_N) return cudaErrorInvalidValue;
+  const int npad = wide_solve_npad(n);
+  char *p0 = (char *)scratch;
+  uint16_t *Td = (uint16_t *)p0;
+  p0 += ((sizeof(uint16_t) * (size_t)kGmDigits * n * npad + 255) & ~(size_t)255);
+  int *fcol = (int *)p0;
+  p0 += ((sizeof(int) * (size_t)n + 255) & ~(size_t)255);
+  int *erow = (int *)p0;
+  wide_tdigits_kernel<<<n, 128, 0, s>>>(a.Tinv, n, npad, Td, fcol, a.st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  wide_rowexp_kernel<<<(unsigned)((a.m + 255) / 256), 256, 0, s>>>(a.Yin, a.ldyin, a.m, n, a.Tscale, erow, a.st);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  WideSolve w;
+  w.m = a.m;
+  w.n = n;
+  w.npad = npad;
+  w.Y = a.Yin;
+  w.ldy = a.ldyin;
+  w.Q = a.Yout;
+  w.ldq = a.ldyout;
+  w.Tscale = a.Tscale;
+  w.Td = Td;
+  w.fcol = fcol;
+  w.erow = erow;
+  // two CTAs per SM, each with the same number of tiles (every tile does
+  // the same work)
+  const int64_t tiles = (a.m + kWsTR - 1) / kWsTR;
+  const int64_t G = std::max<int64_t>(1, std::min<int64_t>(tiles, 2 * (int64_t)num_sms()));
+  w.rows_per_cta = ((tiles + G - 1) / G) * kWsTR;
+  w.st = a.st;
+  static KernelAttr attr;
+  set_smem_attr(attr, ozwsolve_kernel, (int)kWsSmem, true);
+  const int64_t gx = (a.m + w.rows_per_cta - 1) / w.rows_per_cta;
+  ozwsolve_kernel<<<(unsigned)gx, kGmThreads, kWsSmem, s>>>(w);
+  return cudaGetLastError();
+}
+
 }  // namespace cqr

@@ -1,15 +1,18 @@
 """Widths above 128 (up to CQR_MAX_N = 512).  The Gramian is formed by
-column blocks of at most 64 on the tensor-core cross-Gramian kernel (exact
-digit products; with CQR_EMU_OFF the FP64 row sweep split over several
-sweeps of its entries), the solve is the row-wise FP64 substitution, and the
-control step works on a global-memory copy of the n x n Gramian.  Parity with
+column blocks of at most 64 on the tensor-core cross-Gramian kernel and the
+solve Q = Y T (T = D R~^{-1}) on the tensor cores with the contraction in
+blocks of 64 (exact digit products; with CQR_EMU_OFF the FP64 row sweeps:
+the Gramian split over several sweeps of its entries, the row-wise
+substitution), and the control step works on a global-memory copy of the
+n x n Gramian.  Parity with
 the oracle by the bounds of tests/parity.py for the factorisation at n = 129,
 200, 256, 300 and 512 (both Gramians), the Gramian at n = 256 and 512
 (against the oracle's, and exactly on integer data whose Gramian FP64 holds
 without rounding, which any misplaced or dropped block fails), an append of
 160 columns to a basis of 64 (the oracle's Alg. 2 on its own basis of the
 first block), an append of 300 columns to an empty basis, and pnCholQR with
-150-column panels (the oracle's Alg. 3)."""
+150-column panels (the oracle's Alg. 3); the in-place factorisation equals
+the out-of-place one bit for bit."""
 import numpy as np
 import pytest
 
@@ -152,3 +155,19 @@ def test_wide_append_to_empty_basis(cq, orc):
     assert sto >= 0
     check_q(float(np.max(np.abs(Q - Qn))), 1e6, m, "wide append to an empty basis")
     check_r(float(np.max(np.abs(R - Rn))), 1e6, Rn, m, "wide append to an empty basis")
+
+
+@pytest.mark.parametrize("n", [300, 512])
+def test_wide_factor_in_place(cq, n):
+    """Q == A: the tensor-core solve of a row tile forms its 64-column output
+    blocks from the last to the first, so no block reads a column an earlier
+    one overwrote; the result equals the out-of-place one bit for bit."""
+    m = 9011
+    A = synth.test_matrix(m, n, 1e10, rep=36)
+    dA = cq.to_colmajor(A)
+    ref = cq.factor(dA, check=False)
+    res = cq.factor(dA, Q=dA, check=False)
+    torch.cuda.synchronize()
+    assert ref.status == cq.OK and res.status == cq.OK
+    assert torch.equal(res.Q, ref.Q) and torch.equal(res.R, ref.R)
+    assert res.Q.data_ptr() == dA.data_ptr()
