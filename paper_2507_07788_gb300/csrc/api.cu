@@ -241,7 +241,7 @@ cudaError_t scratch_alloc(Scratch &s, int q, int p, int G, int64_t E, cudaStream
   keep_pool_memory();
   const size_t b_Ts = align256(sizeof(int) * (size_t)p);
   const size_t b_Bd = align256(ozcproj_scratch_bytes());
-  const size_t b_W = (p > kCtrlSmemMaxP) ? align256(ctrl_smem_bytes(p)) : 0;
+  const size_t b_W = (p > kCtrlSmemMaxP) ? align256(ctrl_work_bytes(p)) : 0;
   const size_t b_X = align256(xbytes);
   cudaError_t e = cudaMallocAsync((void **)&s.base,
                                   b_st + b_C + 2 * b_Rt + b_Rd + b_Bt + 2 * b_Ts + b_Bd + b_W + b_X + b_P, str);

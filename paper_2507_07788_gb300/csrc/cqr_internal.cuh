@@ -132,9 +132,10 @@ struct Ctrl {
   double *B;        // accumulated B (q x p block), ld ldb (update only)
   int64_t ldb;
   DevState *st;
-  // Working storage of the control step (X, packed R~, two vectors:
-  // ctrl_smem_bytes(p) bytes) in global memory, for widths whose working set
-  // does not fit in shared memory (p > kCtrlSmemMaxP); null otherwise.
+  // Working storage of the control step (X, packed R~, two vectors and the
+  // cooperative launch's control words: ctrl_work_bytes(p) bytes) in global
+  // memory, for widths whose working set does not fit in shared memory
+  // (p > kCtrlSmemMaxP); null otherwise.
   double *work;
 };
 // Widest p whose control step works in shared memory (197 KB at 128).
@@ -154,6 +155,7 @@ constexpr int kGram32Depth = 64 + 2;
 cudaError_t launch_reduce(const Reduce &a, cudaStream_t s);
 cudaError_t launch_ctrl(const Ctrl &a, cudaStream_t s);
 size_t ctrl_smem_bytes(int p);
+size_t ctrl_work_bytes(int p);  // Ctrl::work bytes for p > kCtrlSmemMaxP
 // R <- R~ R (Alg. 1) with one CTA per column of R, after the control
 // kernel of a pass that continues (for controls run with r_external = 1).
 cudaError_t launch_rupdate(const double *Rt, int p, double *R, int64_t ldr, const DevState *st,

@@ -13,6 +13,8 @@
 // recorded in the device state and stops all later kernels of the call.
 #include <math.h>
 
+#include <atomic>
+
 #include "cqr_internal.cuh"
 
 namespace cqr {
@@ -186,10 +188,20 @@ __device__ __forceinline__ double shift_alg2_first(int64_t m, int q, int p, doub
   return c * kU64 * normX;
 }
 
-// One control step of one problem; shared by the single and batched kernels.
-// sm: the working storage (X, packed R~, two vectors), or with gX set, X in
-// gX and the rest in sm.
-__device__ void ctrl_body(const Ctrl &c, double *sm, double *gX = nullptr) {
+// The Cholesky of the control step on the calling CTA alone.
+struct LocalChol {
+  __device__ int operator()(const double *X, int p, double sigma, double *Rk, double *s_inv, int *s_fail) const {
+    return cholesky(X, p, sigma, Rk, s_inv, s_fail);
+  }
+};
+
+// One control step of one problem; shared by the single, batched and
+// cooperative kernels.  sm: the working storage (X, packed R~, two
+// vectors), or with gX set, X in gX and the rest in sm.  chol(X, p, sigma,
+// Rk, s_inv, s_fail) factors X + sigma I into the packed Rk (0, or j + 1 of
+// the failing pivot).
+template <class Chol>
+__device__ void ctrl_body_t(const Ctrl &c, double *sm, double *gX, const Chol &chol) {
   DevState *st = c.st;
   if (st->done) return;
   __shared__ double red[32];
@@ -281,7 +293,7 @@ __device__ void ctrl_body(const Ctrl &c, double *sm, double *gX = nullptr) {
       ++shifts;
       s_first = sigma;
     }
-    rc = cholesky(X, p, sigma, Rk, &s_inv, &s_fail);
+    rc = chol(X, p, sigma, Rk, &s_inv, &s_fail);
     ++attempts;
     if (rc != 0 && !shifted_first) {
       if (c.shift_policy == CQR_SHIFT_NONE || c.shift_policy == CQR_SHIFT_SCHOLQR3_STRICT) {
@@ -296,7 +308,7 @@ __device__ void ctrl_body(const Ctrl &c, double *sm, double *gX = nullptr) {
         }
         ++shifts;
         s_first = sigma;
-        rc = cholesky(X, p, sigma, Rk, &s_inv, &s_fail);
+        rc = chol(X, p, sigma, Rk, &s_inv, &s_fail);
         ++attempts;
       }
     }
@@ -305,11 +317,11 @@ __device__ void ctrl_body(const Ctrl &c, double *sm, double *gX = nullptr) {
       sigma *= 10.0;
       ++escal;
       ++esc;
-      rc = cholesky(X, p, sigma, Rk, &s_inv, &s_fail);
+      rc = chol(X, p, sigma, Rk, &s_inv, &s_fail);
       ++attempts;
     }
   } else {
-    rc = cholesky(X, p, 0.0, Rk, &s_inv, &s_fail);
+    rc = chol(X, p, 0.0, Rk, &s_inv, &s_fail);
     ++attempts;
     int esc = 0;
     while (rc != 0 && esc < c.max_escalations) {
@@ -324,7 +336,7 @@ __device__ void ctrl_body(const Ctrl &c, double *sm, double *gX = nullptr) {
       }
       sigma = fmax(sigma, 2.0 * kU64);
       ++esc;
-      rc = cholesky(X, p, sigma, Rk, &s_inv, &s_fail);
+      rc = chol(X, p, sigma, Rk, &s_inv, &s_fail);
       ++attempts;
     }
   }
@@ -389,6 +401,10 @@ __device__ void ctrl_body(const Ctrl &c, double *sm, double *gX = nullptr) {
   }
 }
 
+__device__ __forceinline__ void ctrl_body(const Ctrl &c, double *sm, double *gX = nullptr) {
+  ctrl_body_t(c, sm, gX, LocalChol{});
+}
+
 __global__ void __launch_bounds__(kCtrlThreads) ctrl_kernel(Ctrl c) {
   extern __shared__ double sm[];
   ctrl_body(c, sm);
@@ -404,6 +420,296 @@ __global__ void __launch_bounds__(kCtrlThreads) ctrl_split_kernel(Ctrl c) {
   ctrl_body(c, sm, c.work);
 }
 __global__ void __launch_bounds__(kCtrlThreads) ctrl_global_kernel(Ctrl c) { ctrl_body(c, c.work); }
+
+// ---- Cooperative control step for wide blocks (p > kCtrlSmemMaxP)
+//
+// The Cholesky is the one O(n^3) part of the step, and on one SM it runs at
+// ~2 FP64 FMAs per clock.  Here CTA 0 runs the control step above (stop
+// test, norm estimate and shifts, retries, outputs) with its working storage
+// in global memory, and every Cholesky it starts is shared by all CTAs of
+// the cooperative launch, which wait for it in between.  The factorisation
+// is right-looking by panels of 64 columns [j0, j1):
+//   (a) every CTA copies the panel's diagonal block to shared memory and
+//       factors it (the same arithmetic in each; CTA 0 writes it back);
+//   (b) the row panel R_12 = R_11^{-T} A_12, one column per warp across the
+//       grid, by the same scale-then-update steps as the unblocked routine;
+//   (c) the trailing update A_22 -= R_12^T R_12 in 32 x 32 tiles across the
+//       grid, each entry subtracting the panel's products in increasing row
+//       order,
+// so every entry of R~ takes the operations of `cholesky` in the same order.
+// Grid barriers separate (b) and (c) and the panels; a Cholesky starts
+// with a barrier (the previous one may have ended early at a failing pivot
+// in some CTAs) and ends with one.  Every wait is bounded in wall time: one
+// that runs out sets `timeout`, after which no CTA waits again and the step
+// ends with CQR_ERR_TIMEOUT.
+struct CoopCtl {
+  unsigned job;        // number of Choleskys CTA 0 has posted
+  unsigned quit;       // CTA 0 has finished the control step
+  unsigned bar_count;  // grid barrier: arrivals of the current phase
+  unsigned bar_gen;    // grid barrier: completed phases
+  int timeout;         // a wait gave up
+  int pad;
+  double sigma;        // shift of the posted Cholesky
+};
+
+namespace {
+
+constexpr int kCoopPanel = 64;
+constexpr int kCoopTile = 32;
+constexpr uint64_t kCoopWaitNs = 5000000000ull;  // 5 s
+// shared memory of a cooperative CTA: the diagonal block (64 x 64), its
+// inverse pivots, two 64 x 32 slices of the row panel
+constexpr size_t kCoopSmem = sizeof(double) * ((size_t)kCoopPanel * kCoopPanel + kCoopPanel +
+                                               2 * (size_t)kCoopPanel * kCoopTile);
+
+__device__ __forceinline__ uint64_t gtimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// All CTAs of the grid reach this point (sense by generation count); false
+// when the wait ran out (then `timeout` is set for everyone).
+__device__ bool coop_sync(CoopCtl *cc) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *gen = &cc->bar_gen;
+    volatile int *to = &cc->timeout;
+    int ok = (*to == 0);
+    if (ok) {
+      const unsigned g = *gen;
+      __threadfence();
+      if (atomicAdd(&cc->bar_count, 1u) == gridDim.x - 1) {
+        cc->bar_count = 0;
+        __threadfence();
+        atomicAdd(&cc->bar_gen, 1u);
+      } else {
+        const uint64_t t0 = gtimer_ns();
+        while (*gen == g) {
+          if (*to != 0 || gtimer_ns() - t0 > kCoopWaitNs) {
+            atomicExch(&cc->timeout, 1);
+            ok = 0;
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+      __threadfence();
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Unblocked right-looking factorisation of the diagonal block in shared
+// memory (D, ld kCoopPanel, upper triangle), the steps of `cholesky`;
+// inv[j] = 1 / R_jj.  Returns 0 or j0 + j + 1 of the failing pivot.
+__device__ int coop_diag(double *D, double *inv, int nb, int j0) {
+  __shared__ int s_fail;
+  const int t = threadIdx.x, NT = blockDim.x;
+  if (t == 0) s_fail = 0;
+  __syncthreads();
+  const int cl = t >> 3, rl = t & 7, cstep = NT >> 3;
+  for (int j = 0; j < nb; ++j) {
+    if (t == 0) {
+      const double d = D[j + j * kCoopPanel];
+      if (!(d > 0.0) || !isfinite(d)) {
+        s_fail = j0 + j + 1;
+      } else {
+        const double r = sqrt(d);
+        D[j + j * kCoopPanel] = r;
+        inv[j] = 1.0 / r;
+      }
+    }
+    __syncthreads();
+    if (s_fail) return s_fail;
+    const double iv = inv[j];
+    for (int k = j + 1 + t; k < nb; k += NT) D[j + k * kCoopPanel] *= iv;
+    __syncthreads();
+    for (int k = j + 1 + cl; k < nb; k += cstep) {
+      const double rjk = D[j + k * kCoopPanel];
+      for (int i = j + 1 + rl; i <= k; i += 8) D[i + k * kCoopPanel] -= D[j + i * kCoopPanel] * rjk;
+    }
+    __syncthreads();
+  }
+  return 0;
+}
+
+// R~^T R~ = X + sigma I into the packed Rk (global), by all CTAs of the
+// grid.  Returns 0, j + 1 of the failing pivot, or -1 after a timeout.
+__device__ int coop_cholesky(const double *X, int p, double sigma, double *Rk, CoopCtl *cc, double *csm) {
+  double *D = csm, *inv = D + kCoopPanel * kCoopPanel, *Pi = inv + kCoopPanel, *Pk = Pi + kCoopPanel * kCoopTile;
+  const int t = threadIdx.x, NT = blockDim.x, lane = t & 31, warp = t >> 5;
+  const int G = gridDim.x, b = blockIdx.x;
+  if (!coop_sync(cc)) return -1;  // every CTA has left the previous Cholesky
+  for (int64_t e = (int64_t)b * NT + t; e < (int64_t)p * p; e += (int64_t)G * NT) {
+    const int i = (int)(e % p), j = (int)(e / p);
+    if (i <= j) Rk[pk(i, j)] = X[e] + (i == j ? sigma : 0.0);
+  }
+  if (!coop_sync(cc)) return -1;
+  for (int j0 = 0; j0 < p; j0 += kCoopPanel) {
+    const int nb = min(kCoopPanel, p - j0), j1 = j0 + nb;
+    // (a) the diagonal block
+    for (int e = t; e < nb * nb; e += NT) {
+      const int i = e % nb, j = e / nb;
+      D[i + j * kCoopPanel] = (i <= j) ? Rk[pk(j0 + i, j0 + j)] : 0.0;
+    }
+    __syncthreads();
+    const int rc = coop_diag(D, inv, nb, j0);
+    if (rc != 0) return rc;  // the same pivot fails in every CTA
+    if (b == 0)
+      for (int e = t; e < nb * nb; e += NT) {
+        const int i = e % nb, j = e / nb;
+        if (i <= j) Rk[pk(j0 + i, j0 + j)] = D[i + j * kCoopPanel];
+      }
+    // (b) row panel: column k of A_12 by one warp; lane l holds rows l, l + 32
+    const int nw = NT >> 5;
+    for (int k = j1 + b * nw + warp; k < p; k += G * nw) {
+      double a0 = (lane < nb) ? Rk[pk(j0 + lane, k)] : 0.0;
+      double a1 = (lane + 32 < nb) ? Rk[pk(j0 + lane + 32, k)] : 0.0;
+      for (int j = 0; j < nb; ++j) {
+        // scale row j, then subtract its product from the rows below
+        const bool mine0 = (j < 32) && (lane == j), mine1 = (j >= 32) && (lane == j - 32);
+        if (mine0) a0 *= inv[j];
+        if (mine1) a1 *= inv[j];
+        const double x = __shfl_sync(0xffffffffu, j < 32 ? a0 : a1, j & 31);
+        if (lane > j && lane < nb) a0 -= D[j + lane * kCoopPanel] * x;
+        if (lane + 32 > j && lane + 32 < nb) a1 -= D[j + (lane + 32) * kCoopPanel] * x;
+      }
+      if (lane < nb) Rk[pk(j0 + lane, k)] = a0;
+      if (lane + 32 < nb) Rk[pk(j0 + lane + 32, k)] = a1;
+    }
+    if (!coop_sync(cc)) return -1;
+    // (c) trailing update of the upper triangle of [j1, p)^2 in tiles
+    const int nt = (p - j1 + kCoopTile - 1) / kCoopTile;
+    const int ntiles = nt * (nt + 1) / 2;
+    for (int w = b; w < ntiles; w += G) {
+      int K = 0;
+      while ((K + 1) * (K + 2) / 2 <= w) ++K;
+      const int I = w - K * (K + 1) / 2;  // tile (I, K), I <= K
+      const int i0 = j1 + kCoopTile * I, k0 = j1 + kCoopTile * K;
+      __syncthreads();  // the previous tile's readers are done
+      for (int e = t; e < nb * kCoopTile; e += NT) {
+        const int j = e % nb, c = e / nb;
+        Pi[j + c * kCoopPanel] = (i0 + c < p) ? Rk[pk(j0 + j, i0 + c)] : 0.0;
+        Pk[j + c * kCoopPanel] = (k0 + c < p) ? Rk[pk(j0 + j, k0 + c)] : 0.0;
+      }
+      __syncthreads();
+      for (int e = t; e < kCoopTile * kCoopTile; e += NT) {
+        const int il = e % kCoopTile, kl = e / kCoopTile, i = i0 + il, k = k0 + kl;
+        if (i > k || k >= p) continue;
+        double a = Rk[pk(i, k)];
+        for (int j = 0; j < nb; ++j) a -= Pi[j + il * kCoopPanel] * Pk[j + kl * kCoopPanel];
+        Rk[pk(i, k)] = a;
+      }
+    }
+    if (!coop_sync(cc)) return -1;
+  }
+  return 0;
+}
+
+// CTA 0's Cholesky: post the shift, then take part like the others.
+struct CoopChol {
+  CoopCtl *cc;
+  double *csm;
+  __device__ int operator()(const double *X, int p, double sigma, double *Rk, double *, int *) const {
+    __shared__ int s_to;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_to = *(volatile int *)&cc->timeout;
+      if (!s_to) {
+        *(volatile double *)&cc->sigma = sigma;
+        __threadfence();
+        atomicAdd(&cc->job, 1u);
+      }
+    }
+    __syncthreads();
+    if (s_to) return -1;
+    return coop_cholesky(X, p, sigma, Rk, cc, csm);
+  }
+};
+
+}  // namespace
+
+__global__ void __launch_bounds__(kCtrlThreads, 1) ctrl_coop_kernel(Ctrl c, CoopCtl *cc) {
+  extern __shared__ double csm[];
+  const int p = c.p;
+  double *X = c.work, *Rk = X + (size_t)p * p;
+  if (blockIdx.x == 0) {
+    ctrl_body_t(c, c.work, nullptr, CoopChol{cc, csm});
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (*(volatile int *)&cc->timeout) {
+        c.st->done = 1;
+        c.st->status = CQR_ERR_TIMEOUT;
+        c.st->active = 0;
+      }
+      __threadfence();
+      atomicExch(&cc->quit, 1u);
+    }
+    return;
+  }
+  __shared__ int s_go;
+  __shared__ double s_sigma;
+  unsigned seen = 0;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      volatile unsigned *job = &cc->job, *quit = &cc->quit;
+      const uint64_t t0 = gtimer_ns();
+      int go = 0;
+      for (;;) {
+        const unsigned jb = *job;
+        if (jb != seen) {
+          seen = jb;
+          go = 1;
+          break;
+        }
+        if (*quit || *(volatile int *)&cc->timeout) break;
+        if (gtimer_ns() - t0 > kCoopWaitNs) {
+          atomicExch(&cc->timeout, 1);
+          break;
+        }
+        __nanosleep(128);
+      }
+      __threadfence();
+      s_go = go;
+      s_sigma = *(volatile double *)&cc->sigma;
+    }
+    __syncthreads();
+    if (!s_go) return;
+    (void)coop_cholesky(X, p, s_sigma, Rk, cc, csm);
+    __syncthreads();
+  }
+}
+
+// Cooperative grid of the wide control step (0: not available).
+static int ctrl_coop_grid() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const bool cached = dev >= 0 && dev < 64;
+  int g = cached ? cache[dev].load(std::memory_order_relaxed) : 0;
+  if (g != 0) return g > 0 ? g : 0;
+  int coop = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (coop && cudaFuncSetAttribute(ctrl_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)kCoopSmem) == cudaSuccess &&
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ctrl_coop_kernel, kCtrlThreads, kCoopSmem) ==
+          cudaSuccess &&
+      per_sm > 0)
+    g = num_sms();  // one CTA per SM
+  else
+    g = -1;
+  (void)cudaGetLastError();
+  if (cached) cache[dev].store(g, std::memory_order_relaxed);
+  return g > 0 ? g : 0;
+}
+
+// Bytes of the global working storage of a wide control step: X, packed R~,
+// two vectors (ctrl_smem_bytes) and the cooperative launch's control words.
+size_t ctrl_work_bytes(int p) { return ((ctrl_smem_bytes(p) + 255) & ~(size_t)255) + sizeof(CoopCtl); }
 
 // Batched control: CTA b handles problems b, b + grid, ...
 __global__ void __launch_bounds__(kCtrlThreads) ctrl_batched_kernel(const Ctrl *reqs, const int *nreq) {
@@ -543,6 +849,16 @@ cudaError_t launch_tinv(const double *Rt, const double *Rdinv, const double *C, 
 cudaError_t launch_ctrl(const Ctrl &a, cudaStream_t s) {
   if (a.p > kCtrlSmemMaxP) {
     if (a.work == nullptr) return cudaErrorInvalidValue;
+    const int G = ctrl_coop_grid();
+    if (G > 0) {
+      CoopCtl *cc = (CoopCtl *)((char *)a.work + ((ctrl_smem_bytes(a.p) + 255) & ~(size_t)255));
+      cudaError_t e = cudaMemsetAsync(cc, 0, sizeof(CoopCtl), s);
+      if (e != cudaSuccess) return e;
+      Ctrl c = a;
+      void *args[] = {(void *)&c, (void *)&cc};
+      return cudaLaunchCooperativeKernel((const void *)ctrl_coop_kernel, dim3(G), dim3(kCtrlThreads), args,
+                                         kCoopSmem, s);
+    }
     const size_t sm = ctrl_split_smem_bytes(a.p);
     if (sm <= 200 * 1024) {
       static KernelAttr sattr;

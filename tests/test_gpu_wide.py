@@ -4,7 +4,8 @@ solve Q = Y T (T = D R~^{-1}) on the tensor cores with the contraction in
 blocks of 64 (exact digit products; with CQR_EMU_OFF the FP64 row sweeps:
 the Gramian split over several sweeps of its entries, the row-wise
 substitution), and the control step works on a global-memory copy of the
-n x n Gramian.  Parity with
+n x n Gramian whose Cholesky is shared by the CTAs of a cooperative launch
+(panels of 64 columns, grid barriers in between).  Parity with
 the oracle by the bounds of tests/parity.py for the factorisation at n = 129,
 200, 256, 300 and 512 (both Gramians), the Gramian at n = 256 and 512
 (against the oracle's, and exactly on integer data whose Gramian FP64 holds
@@ -12,7 +13,8 @@ without rounding, which any misplaced or dropped block fails), an append of
 160 columns to a basis of 64 (the oracle's Alg. 2 on its own basis of the
 first block), an append of 300 columns to an empty basis, and pnCholQR with
 150-column panels (the oracle's Alg. 3); the in-place factorisation equals
-the out-of-place one bit for bit."""
+the out-of-place one bit for bit; a failing pivot, the recomputed shift and
+the retry match the oracle's counters."""
 import numpy as np
 import pytest
 
@@ -171,3 +173,28 @@ def test_wide_factor_in_place(cq, n):
     assert ref.status == cq.OK and res.status == cq.OK
     assert torch.equal(res.Q, ref.Q) and torch.equal(res.R, ref.R)
     assert res.Q.data_ptr() == dA.data_ptr()
+
+
+@pytest.mark.parametrize("n", [160, 320])
+def test_wide_breakdown_and_retry(cq, orc, n):
+    """The wide control step's Cholesky is shared by the CTAs of a
+    cooperative launch: a zero column makes the unshifted first attempt
+    fail at its pivot in every CTA, the shift is recomputed and the retry
+    succeeds (SHIFT_ON_BREAKDOWN); without shifts the same matrix breaks
+    down.  Counters and the result against the oracle."""
+    m = 8009
+    A = synth.test_matrix(m, n, 1e2, rep=37)
+    A[:, n - 70] = 0.0  # the failing pivot lies in the second 64-column panel or later
+    dA = cq.to_colmajor(A)
+    res = cq.factor(dA, opts=cq.default_opts(shift_policy=cq.SHIFT_ON_BREAKDOWN), check=False)
+    torch.cuda.synchronize()
+    Qo, Ro, sto, info_o = orc.cholqr(A, shift_policy=orc.SHIFT_ON_BREAKDOWN)
+    assert res.status == sto and res.status >= 0, (res.status, sto)
+    assert res.info["shifts"] == info_o.shifts >= 1
+    assert res.info["chol_attempts"] == info_o.chol_attempts
+    Q, R = res.Q.cpu().numpy(), res.R.cpu().numpy()
+    assert orc.rrr(A, Q, R) <= 1e-13
+    res0 = cq.factor(dA, opts=cq.default_opts(shift_policy=cq.SHIFT_NONE), check=False)
+    torch.cuda.synchronize()
+    _, _, sto0, _ = orc.cholqr(A, shift_policy=orc.SHIFT_NONE)
+    assert res0.status == sto0 == cq.ERR_BREAKDOWN
