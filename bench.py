@@ -568,9 +568,10 @@ def leg_mixed(cq, torch, synth, m, n=128, kappas=(1e6, 1e10, 1e14), steps=3, hbm
 def leg_wide(cq, torch, synth, m=200000, ns=(192, 256, 384, 512), off_ns=(256, 512), kappa=1e12, steps=2,
              hbm_peak=0.0):
     """Widths above 128: the Gramian by column blocks of at most 64 on the
-    tensor-core cross-Gramian kernel, the FP64 row solve and the
-    global-memory control step, beside n = 128 (tensor-core pipeline) and,
-    at the widths in off_ns, the FP64 Gramian (emulation off)."""
+    tensor-core cross-Gramian kernel, the tensor-core solve with its
+    contraction in blocks of 64 and the cooperative control step, beside
+    n = 128 (tensor-core pipeline) and, at the widths in off_ns, the FP64
+    row sweeps (emulation off)."""
     rows = []
     cases = [(n, "auto") for n in (128,) + tuple(ns)] + [(n, "off") for n in off_ns]
     cases.sort()
@@ -584,9 +585,9 @@ def leg_wide(cq, torch, synth, m=200000, ns=(192, 256, 384, 512), off_ns=(256, 5
         if n <= 128:
             path = "tensor-core digit kernels"
         elif emu == "off":
-            path = "FP64 CUDA cores (Gramian and solve)"
+            path = "FP64 CUDA cores (Gramian and solve), cooperative control step"
         else:
-            path = "digit Gramian by 64-column blocks, FP64 solve"
+            path = "tensor-core Gramian and solve by 64-column blocks, cooperative control step"
         rows.append({"n": n, "emulation": emu, "ms": ms, "rows_cols_per_s": m * n / (ms * 1e-3),
                      "iters": res.info["iters"], "status": res.status, "orth_frob": res.info["orth_frob"],
                      "hbm_frac": factorisation_hbm(m, n, res.info["iters"], ms, hbm_peak)["frac"], "path": path})
