@@ -150,8 +150,12 @@ typedef struct cqr_info {
  * of at most 64 on the tensor cores (exact digit products, unless
  * opts->emulation is CQR_EMU_OFF: then, and for appends to a non-empty
  * basis, the FP64 row sweep, split over several sweeps of its entries); the
- * triangular solve is the FP64 row substitution, and the control step keeps
- * its n x n working storage in global memory (one CTA). */
+ * triangular solve Q = Y R~^{-1} is an exact digit product with the
+ * contraction in blocks of 64 (the FP64 row substitution under the same
+ * exceptions); the control step keeps its n x n working storage in global
+ * memory and shares each Cholesky among one CTA per SM (a cooperative
+ * launch, whose grid barriers wait at most 5 s each: a wait that runs out
+ * ends the call with CQR_ERR_TIMEOUT). */
 #define CQR_MAX_N 512
 #define CQR_MAX_BASIS 1024
 
