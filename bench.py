@@ -567,8 +567,8 @@ def leg_mixed(cq, torch, synth, m, n=128, kappas=(1e6, 1e10, 1e14), steps=3, hbm
 
 def leg_wide(cq, torch, synth, m=200000, ns=(192, 256, 384, 512), off_ns=(256, 512), kappa=1e12, steps=2,
              hbm_peak=0.0):
-    """Widths above 128: the Gramian by column blocks of at most 64 on the
-    tensor-core cross-Gramian kernel, the tensor-core solve with its
+    """Widths above 128: the Gramian by 64 x 64 block pairs on the tensor
+    cores, the tensor-core solve with its
     contraction in blocks of 64 and the cooperative control step, beside
     n = 128 (tensor-core pipeline) and, at the widths in off_ns, the FP64
     row sweeps (emulation off)."""
@@ -587,7 +587,7 @@ def leg_wide(cq, torch, synth, m=200000, ns=(192, 256, 384, 512), off_ns=(256, 5
         elif emu == "off":
             path = "FP64 CUDA cores (Gramian and solve), cooperative control step"
         else:
-            path = "tensor-core Gramian and solve by 64-column blocks, cooperative control step"
+            path = "tensor-core Gramian (64 x 64 block pairs) and solve (blocks of 64), cooperative control step"
         rows.append({"n": n, "emulation": emu, "ms": ms, "rows_cols_per_s": m * n / (ms * 1e-3),
                      "iters": res.info["iters"], "status": res.status, "orth_frob": res.info["orth_frob"],
                      "hbm_frac": factorisation_hbm(m, n, res.info["iters"], ms, hbm_peak)["frac"], "path": path})

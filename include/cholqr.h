@@ -146,8 +146,8 @@ typedef struct cqr_info {
 /* Largest Gramian width handled by the kernels: n of cholqr_factor and p of
  * basis_append must not exceed it.  Basis capacity (q + p) up to
  * CQR_MAX_BASIS.  Above 128 columns the Gramian of cholqr_factor,
- * cholqr_gram and of an append to an empty basis is formed by column blocks
- * of at most 64 on the tensor cores (exact digit products, unless
+ * cholqr_gram and of an append to an empty basis is formed by 64 x 64 block
+ * pairs on the tensor cores (exact digit products, unless
  * opts->emulation is CQR_EMU_OFF: then, and for appends to a non-empty
  * basis, the FP64 row sweep, split over several sweeps of its entries); the
  * triangular solve Q = Y R~^{-1} is an exact digit product with the

@@ -229,13 +229,12 @@ int ozxgram_tile_rows();
 cudaError_t launch_reduce_dense(const double *partials, int G, int64_t E, double *C, const DevState *st,
                                 cudaStream_t s);
 // The Gramian X = Y^T Y (ld ldx, both triangles) of a block wider than the
-// digit Gramian (p > 128) by column blocks of at most 64 on the cross-Gramian
-// kernel, through `partials` (wide_gram_partial_elems doubles); adds its
-// kernel launches to *launches.
+// digit Gramian (128 < p <= CQR_MAX_N) by 64 x 64 block pairs on the tensor
+// cores (csrc/ozgemm.cu), through `partials` (wide_gram_partial_elems
+// doubles); adds its kernel launches to *launches.
 cudaError_t launch_wide_gram(const double *Y, int64_t ldy, int64_t m, int p, double *partials, double *X,
                              int64_t ldx, const DevState *st, cudaStream_t s, int *launches);
 int64_t wide_gram_partial_elems(int64_t m, int p);
-int wide_gram_blocks(int p);
 // Appends of at least kOzUpdMinP columns to bases of at least kOzUpdMinRows
 // rows take the tensor-core cross Gramian.  Narrower blocks keep the fused
 // FP64 sweep (its projection and Gramian share one read, and their FP64 work

@@ -822,4 +822,267 @@ cudaError_t launch_wide_solve(const RowSweep &a, void *scratch, cudaStream_t s) 
   return cudaGetLastError();
 }
 
+// ---- Gramian of a block wider than 128 columns (wide Gramian).
+//
+// X = Y^T Y by 64 x 64 block pairs (I, J), I <= J, on the tensor cores with
+// the digits of the solve above.  Every column is written against its
+// largest biased exponent over all m rows, E_c (wide_colexp_kernel; a NaN
+// or Inf makes it 2047), as y_rc = sign V 2^(E_c - 1085) with V < 2^63 in 8
+// balanced base-256 digits, so no CTA rescales as it goes.  CTA (g, w) takes
+// the rows of row group g in tiles of 64 and block pair w: the tile's 64
+// columns of block I and of block J become digit planes with the rows
+// contiguous (block I alone when I = J), the products of each digit order
+// <= 7 (36 pairs) are summed exactly in FP32 over the tile (below 2^23) and
+// added into two int64 words per entry (each tile adds less than 2^47; a
+// group has at most 2^20 rows, so the words stay below 2^61), and the
+// group's partial is rounded to FP64 once:
+//   X_ij = (hi 2^32 + lo) 2^(E_i + E_j - 2114).
+// The dropped orders change an entry by at most about m 2^-60 max|y_i|
+// max|y_j|.  The groups' partials are summed in a fixed order into the upper
+// triangle and mirrored, so X is symmetric bit for bit.  16 warps of 16 x 16
+// outputs, both blocks' digit planes in shared memory (144 KB, one CTA per
+// SM); the next tile's values are loaded while the current one is
+// multiplied.
+namespace {
+
+constexpr int kWgTR = 64;                   // tile rows (the contraction block)
+constexpr int kWgB = 64;                    // columns of a block
+constexpr int kWgLd = kWgTR + 8;            // bf16 stride of a digit-plane column (rows contiguous)
+constexpr int kWgThreads = 512;             // 16 warps: 4 x 4 output tiles of 16 x 16
+constexpr int64_t kWgMaxRows = 1 << 20;     // rows of one group
+constexpr int kWgEcolPad = 256;             // doubles reserved ahead of the partials (E_c, 2 KB)
+constexpr int kBadExp = 0x7FF;              // E_c of a column holding a NaN or Inf
+constexpr size_t kWgSmem = 2 * sizeof(uint16_t) * (size_t)kGmDigits * kWgB * kWgLd + sizeof(int) * 2 * kWgB;
+
+}  // namespace
+
+struct WideGram {
+  int64_t m;
+  int32_t n, npairs;
+  const double *Y;
+  int64_t ldy;
+  const int *Ecol;      // npad: largest biased exponent of each column (>= 1)
+  double *partials;     // [G][npairs][64 x 64]
+  int64_t rows_per_cta;
+  const DevState *st;
+};
+
+// E_c = max over the rows of column c of its biased exponent (zeros and
+// subnormals count as 1, NaN and Inf as 2047): CTA (s, c) takes a slice of
+// rows, combined by atomicMax into a zeroed E.
+__global__ void __launch_bounds__(256) wide_colexp_kernel(const double *Y, int64_t ldy, int64_t m,
+                                                          int64_t rows_per_cta, int *Ecol, const DevState *st) {
+  if (st != nullptr && st->done) return;
+  __shared__ int red[8];
+  const int c = blockIdx.y, t = threadIdx.x;
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta, r1 = min(m, r0 + rows_per_cta);
+  const unsigned long long *col = (const unsigned long long *)(Y + (int64_t)c * ldy);
+  int mx = 1;
+  int64_t r = r0 + t;
+  for (; r + 3 * 256 < r1; r += 4 * 256) {
+    unsigned long long v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = __ldg(col + r + u * 256);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) mx = max(mx, align_exp(v[u]));
+  }
+  for (; r < r1; r += 256) mx = max(mx, align_exp(__ldg(col + r)));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((t & 31) == 0) red[t >> 5] = mx;
+  __syncthreads();
+  if (t == 0) {
+    int b = red[0];
+    for (int w = 1; w < 8; ++w) b = max(b, red[w]);
+    atomicMax(Ecol + c, b);
+  }
+}
+
+__global__ void __launch_bounds__(kWgThreads, 1) ozwgram_kernel(WideGram a) {
+  if (a.st != nullptr && a.st->done) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint16_t *planesA = (uint16_t *)smem;                                // [8][64 columns of I][kWgLd]
+  uint16_t *planesB = planesA + (size_t)kGmDigits * kWgB * kWgLd;      // [8][64 columns of J][kWgLd]
+  int *eI = (int *)(planesB + (size_t)kGmDigits * kWgB * kWgLd);      // [64]
+  int *eJ = eI + kWgB;                                                // [64]
+
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int w = blockIdx.y;
+  int J = 0;
+  while ((J + 1) * (J + 2) / 2 <= w) ++J;
+  const int I = w - J * (J + 1) / 2;  // block pair (I, J), I <= J
+  const bool diag = I == J;
+  const int ci = kWgB * I, cj = kWgB * J, n = a.n;
+  const int64_t row0 = (int64_t)blockIdx.x * a.rows_per_cta;
+  const int64_t row1 = min(a.m, row0 + a.rows_per_cta);
+  if (t < kWgB) {
+    eI[t] = a.Ecol[ci + t];
+    eJ[t] = a.Ecol[cj + t];
+  }
+  // warp -> outputs (columns of I) 16 wi .. + 15 x (columns of J) 16 wj .. + 15
+  const int wi = warp & 3, wj = warp >> 2;
+  const int mi = lane >> 3, rr = lane & 7;
+  const uint32_t aA = smem_u32(planesA + (size_t)(16 * wi + (mi & 1) * 8 + rr) * kWgLd + (mi >> 1) * 8);
+  const uint16_t *pB = diag ? planesA : planesB;
+  const uint32_t bB = smem_u32(pB + (size_t)(16 * wj + (mi >> 1) * 8 + rr) * kWgLd + (mi & 1) * 8);
+  constexpr uint32_t kStr = 2u * kWgB * kWgLd;
+  // loader: thread t holds rows 8 (t & 7) .. + 7 of column t >> 3 of each block
+  const int lc = t >> 3, lr = 8 * (t & 7);
+  const bool liveI = ci + lc < n, liveJ = !diag && cj + lc < n;
+  __syncthreads();
+  const int eIc = eI[lc], eJc = eJ[lc];
+
+  auto load = [&](int64_t r0, unsigned long long (&va)[8], unsigned long long (&vb)[8]) {
+    const int nr = (int)min((int64_t)kWgTR, row1 - r0);
+    const double *yi = a.Y + r0 + (int64_t)(ci + lc) * a.ldy, *yj = a.Y + r0 + (int64_t)(cj + lc) * a.ldy;
+#pragma unroll
+    for (int h = 0; h < 8; ++h) {
+      const bool in = lr + h < nr;
+      va[h] = (in && liveI) ? (unsigned long long)__double_as_longlong(yi[lr + h]) : 0ull;
+      vb[h] = (in && liveJ) ? (unsigned long long)__double_as_longlong(yj[lr + h]) : 0ull;
+    }
+  };
+  auto split = [&](const unsigned long long (&v)[8], int e, uint16_t *planes) {
+    unsigned long long V[8];
+    float sg[8];
+#pragma unroll
+    for (int h = 0; h < 8; ++h) {
+      V[h] = digits63(v[h], e, 0) + kBalance;
+      sg[h] = (v[h] >> 63) ? -1.0f : 1.0f;
+    }
+#pragma unroll
+    for (int d = 0; d < kGmDigits; ++d) {
+      uint4 q;
+      q.x = digit_pair_bf16(V[0], V[1], d, sg[0], sg[1]);
+      q.y = digit_pair_bf16(V[2], V[3], d, sg[2], sg[3]);
+      q.z = digit_pair_bf16(V[4], V[5], d, sg[4], sg[5]);
+      q.w = digit_pair_bf16(V[6], V[7], d, sg[6], sg[7]);
+      *(uint4 *)(planes + ((size_t)d * kWgB + lc) * kWgLd + lr) = q;
+    }
+  };
+
+  long long hi[8], lo[8];
+#pragma unroll
+  for (int o = 0; o < 8; ++o) hi[o] = lo[o] = 0;
+  unsigned long long va[8], vb[8];
+  if (row0 < row1) load(row0, va, vb);
+  for (int64_t r0 = row0; r0 < row1; r0 += kWgTR) {
+    __syncthreads();  // every warp is done with the previous tile's planes
+    split(va, eIc, planesA);
+    if (!diag) split(vb, eJc, planesB);
+    if (r0 + kWgTR < row1) load(r0 + kWgTR, va, vb);  // in flight during the products
+    __syncthreads();
+    {
+      float c[4][2][4];
+#pragma unroll
+      for (int d = 0; d < 4; ++d)
+#pragma unroll
+        for (int tl = 0; tl < 2; ++tl) c[d][tl][0] = c[d][tl][1] = c[d][tl][2] = c[d][tl][3] = 0.0f;
+      gm_steps<2, 5, 4, 0>(c, aA, kStr, bB, kStr, 0, kWgTR / 16);
+#pragma unroll
+      for (int o = 0; o < 8; ++o) {
+        const int tl = o >> 2, r = o & 3;
+        const int t0 = f2i(c[0][tl][r]), t1 = f2i(c[1][tl][r]), t2 = f2i(c[2][tl][r]);
+        const int t3 = f2i(c[3][tl][r]);
+        hi[o] += ((long long)(t0 * 256 + t1) << 16) + (long long)(t2 * 256 + t3);
+      }
+    }
+    {
+      float c[4][2][4];
+#pragma unroll
+      for (int d = 0; d < 4; ++d)
+#pragma unroll
+        for (int tl = 0; tl < 2; ++tl) c[d][tl][0] = c[d][tl][1] = c[d][tl][2] = c[d][tl][3] = 0.0f;
+      gm_steps<6, 9, 8, 0>(c, aA, kStr, bB, kStr, 0, kWgTR / 16);
+#pragma unroll
+      for (int o = 0; o < 8; ++o) {
+        const int tl = o >> 2, r = o & 3;
+        const int t4 = f2i(c[0][tl][r]), t5 = f2i(c[1][tl][r]), t6 = f2i(c[2][tl][r]);
+        const int t7 = f2i(c[3][tl][r]);
+        lo[o] += ((long long)(t4 * 256 + t5) << 16) + (long long)(t6 * 256 + t7);
+      }
+    }
+  }
+  // this group's partial of X_IJ, rounded once
+  double *P = a.partials + ((int64_t)blockIdx.x * a.npairs + w) * (kWgB * kWgB);
+#pragma unroll
+  for (int o = 0; o < 8; ++o) {
+    const int tl = o >> 2, r = o & 3;
+    const int il = 16 * wi + (lane >> 2) + ((r >> 1) << 3);
+    const int jl = 16 * wj + 8 * tl + 2 * (lane & 3) + (r & 1);
+    const bool bad = eI[il] == kBadExp || eJ[jl] == kBadExp;
+    P[il + kWgB * jl] = bad ? __longlong_as_double(0x7FF8000000000000ll)
+                            : fixed_to_double(hi[o], lo[o], 32, eI[il] + eJ[jl] - 2114);
+  }
+}
+
+// X_ij = X_ji = sum over the groups of their partials, in group order, for
+// i <= j < n (one thread per entry of a block pair).
+__global__ void __launch_bounds__(256) reduce_wide_pairs_kernel(const double *partials, int G, int npairs, int n,
+                                                                double *X, int64_t ldx, const DevState *st) {
+  if (st != nullptr && st->done) return;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)npairs * kWgB * kWgB) return;
+  const int w = (int)(e / (kWgB * kWgB)), l = (int)(e % (kWgB * kWgB));
+  int J = 0;
+  while ((J + 1) * (J + 2) / 2 <= w) ++J;
+  const int I = w - J * (J + 1) / 2;
+  const int i = kWgB * I + l % kWgB, j = kWgB * J + l / kWgB;
+  if (i > j || j >= n) return;
+  double s = 0.0;
+  for (int g = 0; g < G; ++g) s += partials[((int64_t)g * npairs + w) * (kWgB * kWgB) + l];
+  X[i + (int64_t)j * ldx] = s;
+  X[j + (int64_t)i * ldx] = s;
+}
+
+static int wide_gram_groups(int64_t m, int npairs) {
+  const int64_t tiles = std::max<int64_t>(1, (m + kWgTR - 1) / kWgTR);
+  int64_t G = std::max<int64_t>(1, num_sms() / npairs);  // about one CTA per SM
+  G = std::max<int64_t>(G, (m + kWgMaxRows - 1) / kWgMaxRows);
+  return (int)std::min<int64_t>(G, tiles);
+}
+
+int64_t wide_gram_partial_elems(int64_t m, int p) {
+  const int nb = (p + kWgB - 1) / kWgB, npairs = nb * (nb + 1) / 2;
+  return kWgEcolPad + (int64_t)wide_gram_groups(m, npairs) * npairs * (kWgB * kWgB);
+}
+
+cudaError_t launch_wide_gram(const double *Y, int64_t ldy, int64_t m, int p, double *partials, double *X,
+                             int64_t ldx, const DevState *st, cudaStream_t s, int *launches) {
+  if (p <= kOzGemmMaxN || p > CQR_MAX_N || m < 1) return cudaErrorInvalidValue;
+  const int nb = (p + kWgB - 1) / kWgB, npairs = nb * (nb + 1) / 2;
+  int *Ecol = (int *)partials;  // nb 64 <= 512 ints in the reserved 2 KB
+  double *P = partials + kWgEcolPad;
+  cudaError_t e = cudaMemsetAsync(Ecol, 0, sizeof(int) * (size_t)nb * kWgB, s);
+  if (e != cudaSuccess) return e;
+  const int64_t slices = std::max<int64_t>(1, std::min<int64_t>((m + 4095) / 4096, 64));
+  const int64_t rpc = (m + slices - 1) / slices;
+  wide_colexp_kernel<<<dim3((unsigned)slices, (unsigned)p), 256, 0, s>>>(Y, ldy, m, rpc, Ecol, st);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  WideGram w;
+  w.m = m;
+  w.n = p;
+  w.npairs = npairs;
+  w.Y = Y;
+  w.ldy = ldy;
+  w.Ecol = Ecol;
+  w.partials = P;
+  const int G = wide_gram_groups(m, npairs);
+  const int64_t tiles = (m + kWgTR - 1) / kWgTR;
+  w.rows_per_cta = ((tiles + G - 1) / G) * kWgTR;
+  w.st = st;
+  static KernelAttr attr;
+  set_smem_attr(attr, ozwgram_kernel, (int)kWgSmem, true);
+  const int gx = (int)((m + w.rows_per_cta - 1) / w.rows_per_cta);
+  ozwgram_kernel<<<dim3((unsigned)gx, (unsigned)npairs), kWgThreads, kWgSmem, s>>>(w);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int64_t E = (int64_t)npairs * kWgB * kWgB;
+  reduce_wide_pairs_kernel<<<(unsigned)((E + 255) / 256), 256, 0, s>>>(P, gx, npairs, p, X, ldx, st);
+  e = cudaGetLastError();
+  if (launches != nullptr) *launches += 3;
+  return e;
+}
+
 }  // namespace cqr

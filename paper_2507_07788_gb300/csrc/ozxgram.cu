@@ -326,82 +326,4 @@ cudaError_t launch_reduce_dense(const double *partials, int G, int64_t E, double
 }
 
 
-// ---- Gramian of a wide block (p > 128 columns) by block columns
-//
-// The columns are cut into nb = ceil(p / 64) blocks of near-equal width
-// (block J holds columns [J p / nb, (J + 1) p / nb), between 42 and 64
-// columns once p > 128).  Block column J of the upper triangle of X = Y^T Y
-// is the cross Gramian [Y_{:, <c0} Y_J]^T Y_J with the preceding columns as
-// Q_in, formed by the kernel above; its row groups' partials are summed in a
-// fixed order into X_ij (i <= j) and mirrored to X_ji, so X is symmetric
-// bit for bit.  The launches run in order on one stream, reusing one
-// partial buffer.
-
-int wide_gram_blocks(int p) { return (p + kXZ - 1) / kXZ; }
-
-static void wide_block(int p, int J, int *c0, int *w) {
-  const int nb = wide_gram_blocks(p);
-  const int a = (int)((int64_t)J * p / nb), b = (int)((int64_t)(J + 1) * p / nb);
-  *c0 = a;
-  *w = b - a;
-}
-
-int64_t wide_gram_partial_elems(int64_t m, int p) {
-  int64_t mx = 0;
-  for (int J = 0; J < wide_gram_blocks(p); ++J) {
-    int c0, w;
-    wide_block(p, J, &c0, &w);
-    mx = std::max<int64_t>(mx, (int64_t)ozxgram_grid(m, c0, w) * (c0 + w) * w);
-  }
-  return mx;
-}
-
-// X_ij = X_ji = sum_g P_g[i, j - c0] for i <= j, c0 <= j < c0 + w
-// (P_g is (c0 + w) x w, ld c0 + w).
-__global__ void reduce_wide_block_kernel(const double *partials, int G, int c0, int w, double *X, int64_t ldx,
-                                         const DevState *st) {
-  if (st != nullptr && st->done) return;
-  const int rows = c0 + w;
-  const int64_t E = (int64_t)rows * w;
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= E) return;
-  const int i = (int)(e % rows), j = c0 + (int)(e / rows);
-  if (i > j) return;
-  double s = 0.0;
-  for (int g = 0; g < G; ++g) s += partials[(int64_t)g * E + e];
-  X[i + (int64_t)j * ldx] = s;
-  X[j + (int64_t)i * ldx] = s;
-}
-
-cudaError_t launch_wide_gram(const double *Y, int64_t ldy, int64_t m, int p, double *partials, double *X,
-                             int64_t ldx, const DevState *st, cudaStream_t s, int *launches) {
-  if (p <= 2 * kXZ || p < kOzUpdMinP) return cudaErrorInvalidValue;
-  cudaError_t e = cudaSuccess;
-  for (int J = 0; J < wide_gram_blocks(p) && e == cudaSuccess; ++J) {
-    int c0, w;
-    wide_block(p, J, &c0, &w);
-    RowSweep x{};
-    x.m = m;
-    x.q = c0;
-    x.p = w;
-    x.Qin = Y;
-    x.ldqin = ldy;
-    x.Yin = Y + (int64_t)c0 * ldy;
-    x.ldyin = ldy;
-    x.partials = partials;
-    x.st = st;
-    const int G = ozxgram_grid(m, c0, w);
-    const int64_t tiles = (m + kXTR - 1) / kXTR;
-    x.rows_per_cta = ((tiles + G - 1) / G) * kXTR;
-    e = launch_ozxgram(x, G, s);
-    if (e == cudaSuccess) {
-      const int64_t E = (int64_t)(c0 + w) * w;
-      reduce_wide_block_kernel<<<(unsigned)((E + 127) / 128), 128, 0, s>>>(partials, G, c0, w, X, ldx, st);
-      e = cudaGetLastError();
-    }
-    if (launches != nullptr) *launches += 2;
-  }
-  return e;
-}
-
 }  // namespace cqr

@@ -1,5 +1,5 @@
 """Widths above 128 (up to CQR_MAX_N = 512).  The Gramian is formed by
-column blocks of at most 64 on the tensor-core cross-Gramian kernel and the
+64 x 64 block pairs on the tensor cores and the
 solve Q = Y T (T = D R~^{-1}) on the tensor cores with the contraction in
 blocks of 64 (exact digit products; with CQR_EMU_OFF the FP64 row sweeps:
 the Gramian split over several sweeps of its entries, the row-wise
