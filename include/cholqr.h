@@ -155,7 +155,9 @@ typedef struct cqr_info {
  * exceptions); the control step keeps its n x n working storage in global
  * memory and shares each Cholesky among one CTA per SM (a cooperative
  * launch, whose grid barriers wait at most 5 s each: a wait that runs out
- * ends the call with CQR_ERR_TIMEOUT). */
+ * ends the call with CQR_ERR_TIMEOUT).  The cooperative steps of all calls
+ * on a device run on one internal stream, ordered after the caller's
+ * stream by events, so concurrent wide calls take turns there. */
 #define CQR_MAX_N 512
 #define CQR_MAX_BASIS 1024
 

@@ -14,6 +14,7 @@
 #include <math.h>
 
 #include <atomic>
+#include <mutex>
 
 #include "cqr_internal.cuh"
 
@@ -707,6 +708,33 @@ static int ctrl_coop_grid() {
   return g > 0 ? g : 0;
 }
 
+// The stream on which every cooperative control step of the current device
+// runs (created once per device, with the two events that join it to the
+// caller's stream), or null when it cannot be created: the single-CTA
+// kernels then take the step.  Two cooperative grids running at once could
+// each hold SMs that the other's barriers wait for.
+struct CoopLane {
+  std::mutex mu;
+  cudaStream_t st = nullptr;
+  cudaEvent_t in = nullptr, out = nullptr;
+  int state = 0;  // 0 not tried, 1 ready, -1 failed
+};
+static CoopLane *coop_lane() {
+  static CoopLane lanes[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  CoopLane &L = lanes[dev];
+  std::lock_guard<std::mutex> lock(L.mu);
+  if (L.state == 0) {
+    const bool ok = cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking) == cudaSuccess &&
+                    cudaEventCreateWithFlags(&L.in, cudaEventDisableTiming) == cudaSuccess &&
+                    cudaEventCreateWithFlags(&L.out, cudaEventDisableTiming) == cudaSuccess;
+    (void)cudaGetLastError();
+    L.state = ok ? 1 : -1;
+  }
+  return L.state == 1 ? &L : nullptr;
+}
+
 // Bytes of the global working storage of a wide control step: X, packed R~,
 // two vectors (ctrl_smem_bytes) and the cooperative launch's control words.
 size_t ctrl_work_bytes(int p) { return ((ctrl_smem_bytes(p) + 255) & ~(size_t)255) + sizeof(CoopCtl); }
@@ -850,14 +878,24 @@ cudaError_t launch_ctrl(const Ctrl &a, cudaStream_t s) {
   if (a.p > kCtrlSmemMaxP) {
     if (a.work == nullptr) return cudaErrorInvalidValue;
     const int G = ctrl_coop_grid();
-    if (G > 0) {
+    CoopLane *L = G > 0 ? coop_lane() : nullptr;
+    if (L != nullptr) {
+      // on the device's cooperative stream, between two events on the
+      // caller's stream: cooperative steps of concurrent calls run one
+      // after another, so none holds SMs that another's barriers wait for
+      std::lock_guard<std::mutex> lock(L->mu);
       CoopCtl *cc = (CoopCtl *)((char *)a.work + ((ctrl_smem_bytes(a.p) + 255) & ~(size_t)255));
       cudaError_t e = cudaMemsetAsync(cc, 0, sizeof(CoopCtl), s);
+      if (e == cudaSuccess) e = cudaEventRecord(L->in, s);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(L->st, L->in, 0);
       if (e != cudaSuccess) return e;
       Ctrl c = a;
       void *args[] = {(void *)&c, (void *)&cc};
-      return cudaLaunchCooperativeKernel((const void *)ctrl_coop_kernel, dim3(G), dim3(kCtrlThreads), args,
-                                         kCoopSmem, s);
+      e = cudaLaunchCooperativeKernel((const void *)ctrl_coop_kernel, dim3(G), dim3(kCtrlThreads), args,
+                                      kCoopSmem, L->st);
+      if (e == cudaSuccess) e = cudaEventRecord(L->out, L->st);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, L->out, 0);
+      return e;
     }
     const size_t sm = ctrl_split_smem_bytes(a.p);
     if (sm <= 200 * 1024) {

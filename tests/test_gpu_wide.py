@@ -14,7 +14,9 @@ without rounding, which any misplaced or dropped block fails), an append of
 first block), an append of 300 columns to an empty basis, and pnCholQR with
 150-column panels (the oracle's Alg. 3); the in-place factorisation equals
 the out-of-place one bit for bit; a failing pivot, the recomputed shift and
-the retry match the oracle's counters."""
+the retry match the oracle's counters; the mixed variant, two row-sharded
+ranks, and two concurrent factorisations on two streams (whose cooperative
+steps take turns on the device's cooperative stream)."""
 import numpy as np
 import pytest
 
@@ -198,3 +200,88 @@ def test_wide_breakdown_and_retry(cq, orc, n):
     torch.cuda.synchronize()
     _, _, sto0, _ = orc.cholqr(A, shift_policy=orc.SHIFT_NONE)
     assert res0.status == sto0 == cq.ERR_BREAKDOWN
+
+
+def test_wide_mixed_against_oracle(cq, orc):
+    """CQR_PREC_MIXED above 128 columns: the FP32 first Gramian with its
+    shift, then the FP64 passes of the wide path."""
+    m, n, kappa = 20011, 300, 1e10
+    A = synth.test_matrix(m, n, kappa, rep=38)
+    res = cq.factor(cq.to_colmajor(A), opts=cq.default_opts(precision=cq.PREC_MIXED), check=False)
+    torch.cuda.synchronize()
+    assert res.status == cq.OK, res.info
+    Q, R = res.Q.cpu().numpy(), res.R.cpu().numpy()
+    check_orth(Q, "wide mixed")
+    assert orc.rrr(A, Q, R) <= 1e-13
+    Qo, Ro, sto, _ = orc.cholqr(A)
+    assert sto == cq.OK
+    check_q(float(np.max(np.abs(Q - Qo))), kappa, m, "wide mixed")
+    check_r(float(np.max(np.abs(R - Ro))), kappa, Ro, m, "wide mixed")
+
+
+def test_wide_sharded_two_ranks(cq, orc):
+    """Two row shards as host threads with their own streams on one GPU: each
+    forms its wide Gramian, the reducer sums them in rank order, and both
+    ranks' cooperative control steps run (one after another on the device's
+    cooperative stream) to the same R."""
+    import threading
+    from paper_2507_07788_gb300.sharded import LocalReducerGroup, factor_sharded, split_rows
+    m, n, kappa, world = 20011, 200, 1e8, 2
+    A = synth.test_matrix(m, n, kappa, rep=39)
+    grp = LocalReducerGroup(world, n * n, timeout_s=60.0)
+    shards = [cq.to_colmajor(A[r0:r1]) for r0, r1 in split_rows(m, world)]
+    torch.cuda.synchronize()
+    out = [None] * world
+
+    def rank_main(r):
+        torch.cuda.set_device(0)
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            out[r] = factor_sharded(shards[r], m, grp.reducer(r), stream=s, check=False)
+        s.synchronize()
+
+    th = [threading.Thread(target=rank_main, args=(r,)) for r in range(world)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    for r in range(world):
+        assert out[r].status == cq.OK, (r, out[r].status, grp.reducer(r).error)
+    assert torch.equal(out[0].R, out[1].R)
+    Q = np.vstack([o.Q.cpu().numpy() for o in out])
+    R = np.triu(out[0].R.cpu().numpy())
+    check_orth(Q, "wide sharded")
+    assert orc.rrr(A, Q, R) <= 1e-13
+    Qo, Ro, sto, _ = orc.cholqr(A)
+    assert sto == cq.OK
+    check_q(float(np.max(np.abs(Q - Qo))), kappa, m, "wide sharded")
+    check_r(float(np.max(np.abs(R - Ro))), kappa, Ro, m, "wide sharded")
+
+
+def test_wide_concurrent_streams(cq):
+    """Two wide factorisations issued at once from two host threads on two
+    streams: their cooperative control steps take turns on the device's
+    cooperative stream, and each result equals the same call made alone,
+    bit for bit."""
+    import threading
+    m = 15013
+    mats = [cq.to_colmajor(synth.test_matrix(m, n, 1e10, rep=40 + n)) for n in (300, 512)]
+    alone = [cq.factor(dA, check=False) for dA in mats]
+    torch.cuda.synchronize()
+    out = [None, None]
+
+    def run(i):
+        torch.cuda.set_device(0)
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            out[i] = cq.factor(mats[i], stream=s, check=False)
+        s.synchronize()
+
+    th = [threading.Thread(target=run, args=(i,)) for i in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    for i in range(2):
+        assert alone[i].status == cq.OK and out[i].status == cq.OK, (alone[i].status, out[i].status)
+        assert torch.equal(out[i].Q, alone[i].Q) and torch.equal(out[i].R, alone[i].R)
