@@ -191,6 +191,27 @@ def test_cholqr_matches_householder_tiny(orc, policy, m, n, kappa):
     assert np.all(np.diag(R) > 0) and np.all(np.tril(R, -1) == 0)
 
 
+@pytest.mark.parametrize("m,n,kappa", [(700, 300, 1e6), (1000, 512, 1e4)])
+def test_cholqr_wide_matches_lapack_qr(orc, m, n, kappa):
+    """The widths of the GPU's wide path (above 128 columns): the oracle's
+    sCholQR3 against LAPACK's Householder QR, normalised to a positive
+    diagonal of R (the factors are then unique), and its Gramian and
+    spectral norm (cyclic Jacobi) against LAPACK's at the same width."""
+    A = synth.test_matrix(m, n, kappa, rep=2)
+    Q, R, st, info = orc.cholqr(A)
+    assert st == orc.OK
+    Ql, Rl = np.linalg.qr(A)
+    sg = np.sign(np.diag(Rl))
+    Ql, Rl = Ql * sg, (Rl.T * sg).T
+    assert np.max(np.abs(R - Rl)) <= 50 * kappa * U * np.max(np.abs(Rl))
+    assert np.max(np.abs(Q - Ql)) <= 50 * kappa * U
+    assert np.all(np.diag(R) > 0) and np.all(np.tril(R, -1) == 0)
+    X = orc.gram(A)
+    assert np.allclose(X, A.T @ A, rtol=0, atol=4 * m * U * np.max(np.abs(A)) ** 2)
+    lam = orc.sym_norm2(X)
+    assert lam == pytest.approx(np.max(np.abs(np.linalg.eigvalsh(A.T @ A))), rel=1e-12)
+
+
 def test_cholqr_n1_closed_form(orc):
     a = rng(11).standard_normal((37, 1))
     Q, R, st, info = orc.cholqr(a, shift_policy=orc.SHIFT_ON_BREAKDOWN)
